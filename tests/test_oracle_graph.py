@@ -1,0 +1,102 @@
+"""Pins of the oracle's patch operators, graph weights and Laplacian (Eq. 6-10)."""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+from oracle import graph, patches
+
+
+def test_three_node_laplacian_layout():
+    w12, w13, w23 = 0.3, 0.7, 0.2
+    W = np.array([[0, w12, w13], [w12, 0, w23], [w13, w23, 0]])
+    expect = np.array([[w12 + w13, -w12, -w13],
+                       [-w12, w12 + w23, -w23],
+                       [-w13, -w23, w13 + w23]])
+    np.testing.assert_allclose(graph.laplacian(W), expect, rtol=0, atol=0)
+
+
+def test_patch_origins_and_coverage():
+    np.testing.assert_array_equal(patches.origins(128, 11, 5)[-2:], [115, 117])
+    pg = patches.PatchGrid(256, 256, 8, 4)
+    assert pg.count == 63 * 63
+    cnt = pg.coverage()
+    assert cnt[0, 0] == 1 and cnt[5, 5] == 4 and cnt[0, 5] == 2 and cnt.min() >= 1
+
+
+def test_patch_adjoint():
+    rng = np.random.default_rng(0)
+    pg = patches.PatchGrid(20, 17, 6, 3)
+    x = rng.standard_normal((20, 17, 3)) + 1j * rng.standard_normal((20, 17, 3))
+    y = rng.standard_normal((pg.count, 36, 3)) + 1j * rng.standard_normal((pg.count, 36, 3))
+    assert np.vdot(pg.extract(x), y) == pytest.approx(np.vdot(x, pg.adjoint(y)), rel=1e-12)
+
+
+def test_knn_matches_kdtree():
+    rng = np.random.default_rng(1)
+    F = rng.standard_normal((200, 7))
+    nbr, d2 = graph.knn(F, 5)
+    dist, _ = cKDTree(F).query(F, k=6)
+    np.testing.assert_allclose(np.sqrt(d2), dist[:, 1:], rtol=1e-12)
+    assert not np.any(nbr == np.arange(200)[:, None])
+
+
+def test_knn_ties_take_lower_index():
+    F = np.zeros((6, 2))
+    F[5] = 1.0
+    nbr, d2 = graph.knn(F, 3)
+    np.testing.assert_array_equal(nbr[0], [1, 2, 3])
+    np.testing.assert_array_equal(nbr[4], [0, 1, 2])
+    assert graph.sigma2(d2) == pytest.approx(2.0)         # only the non-zero distances
+    assert graph.sigma2(np.zeros((3, 2))) == 1.0
+
+
+def test_laplacian_properties():
+    rng = np.random.default_rng(2)
+    F = rng.standard_normal((40, 4))
+    nbr, d2 = graph.knn(F, 6)
+    W = graph.adjacency(nbr, d2, graph.sigma2(d2))
+    L = graph.laplacian(W)
+    np.testing.assert_allclose(L, L.T, atol=0)
+    np.testing.assert_allclose(L.sum(axis=1), 0, atol=1e-12)
+    assert np.linalg.eigvalsh(L).min() > -1e-12
+    assert L.max() == pytest.approx(np.diag(L).max())
+
+
+def test_trace_form_equals_pairwise_form():
+    # Eq. 8 <-> Eq. 9: Tr(Q L Q^H) = 1/2 sum_ij W_ij ||Q_i - Q_j||^2
+    rng = np.random.default_rng(3)
+    pg = patches.PatchGrid(12, 12, 4, 4)
+    X = rng.standard_normal((12, 12, 3)) + 1j * rng.standard_normal((12, 12, 3))
+    W = rng.uniform(0, 1, (pg.count, pg.count))
+    W = 0.5 * (W + W.T)
+    np.fill_diagonal(W, 0)
+    L = graph.laplacian(W)
+    Q = pg.extract(X)
+    pair = sum(W[i, j] * np.sum(np.abs(Q[i] - Q[j]) ** 2)
+               for i in range(pg.count) for j in range(pg.count))
+    assert graph.trace_term(X, L, pg) == pytest.approx(0.5 * pair, rel=1e-12)
+
+
+def test_graph_term_is_gradient_of_trace():
+    # d/de Tr(Q(X+eE) L Q(X+eE)^H) at e=0 equals 2 Re <E, Q^*(Q(X) L)>
+    rng = np.random.default_rng(4)
+    pg = patches.PatchGrid(10, 10, 4, 2)
+    X = rng.standard_normal((10, 10, 2)) + 1j * rng.standard_normal((10, 10, 2))
+    E = rng.standard_normal((10, 10, 2)) + 1j * rng.standard_normal((10, 10, 2))
+    W = rng.uniform(0, 1, (pg.count, pg.count))
+    W = 0.5 * (W + W.T)
+    np.fill_diagonal(W, 0)
+    L = graph.laplacian(W)
+    h = 1e-6
+    fd = (graph.trace_term(X + h * E, L, pg) - graph.trace_term(X - h * E, L, pg)) / (2 * h)
+    an = 2 * np.real(np.vdot(E, graph.graph_term(X, L, pg)))
+    assert fd == pytest.approx(an, rel=1e-6)
+
+
+def test_features_scale():
+    pg = patches.PatchGrid(8, 8, 4, 4)
+    t1 = np.full((8, 8), 1000.0)
+    t2 = np.full((8, 8), 50.0)
+    F = graph.features(t1, t2, pg, 2000.0, 100.0)
+    assert F.shape == (4, 32)
+    np.testing.assert_allclose(F, 0.5)
