@@ -1,0 +1,208 @@
+/*
+ * mrf.h -- C ABI of the GB300 (sm_103a) MS-LLR MR-fingerprinting hot path.
+ *
+ * Method: Li, Ji, Hu, "Exploiting Manifold Structured Data Priors for
+ * Improved MR Fingerprinting Reconstruction" (MS-LLR).  The calls below
+ * follow its problem statement b = A X + n (Eq. 1), the matching operator
+ * Phi_D (Eq. 5) and Algorithm 1.
+ *
+ * Conventions shared by every call
+ *  - Complex numbers are interleaved float pairs (mrf_c64 = {re, im}); all
+ *    arrays are dense and row-major with the shapes given per argument.
+ *  - "dev" pointers are CUDA device (or managed) memory of the current
+ *    device; "host" pointers are ordinary host memory.  The caller owns every
+ *    pointer argument; the library never frees them.  Plans and recon
+ *    objects own their internal workspace and release it in *_destroy.
+ *  - Every call is asynchronous and stream-ordered on `stream` (a
+ *    cudaStream_t passed as void*, NULL = legacy default stream) unless its
+ *    comment says it synchronises.  Inputs must stay valid until the work
+ *    completes.
+ *  - Sizes and pointers are validated on the host before any launch; a
+ *    rejected call returns MRF_EINVAL and launches nothing.  Errors are
+ *    reported as an mrf_status plus a thread-local message from
+ *    mrf_last_error(); nothing is thrown across the ABI.
+ *  - Image index: x[t][iy][ix] with centred coordinates
+ *    n = (ix - nx/2, iy - ny/2).  k-space positions are (kx, ky) in radians
+ *    per voxel in [-pi, pi).
+ */
+#ifndef MRF_H
+#define MRF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MRF_OK = 0,
+    MRF_EINVAL = 1,        /* bad argument (size, null pointer, unsupported combination) */
+    MRF_ENOMEM = 2,        /* device allocation failed */
+    MRF_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    MRF_ETIMEOUT = 4,      /* a bounded device wait gave up */
+    MRF_EUNSUPPORTED = 5   /* valid request this build does not implement */
+} mrf_status;
+
+typedef struct { float re, im; } mrf_c64;
+typedef void* mrf_stream;                 /* cudaStream_t */
+typedef struct mrf_plan_s* mrf_plan;       /* NUFFT plan (opaque) */
+typedef struct mrf_recon_s* mrf_recon;     /* Algorithm 1 state (opaque) */
+
+/* Last error message of the calling thread ("" if none). */
+const char* mrf_last_error(void);
+/* ABI version, incremented on any signature change. */
+int mrf_abi_version(void);
+
+/* ------------------------------------------------------------------------
+ * Acquisition operator A = F_u (Eq. 1 with one coil, C = I).
+ * Kaiser-Bessel gridding NUFFT (the GPU NUFFT of Sec. III-D, Implementation
+ * Details): A x = interp_KB(FFT_G(zero-pad(x / psi_hat))) on an os-times
+ * oversampled grid G = os * n, and the exact adjoint A^H y =
+ * psi_hat^-1 . crop(IFFT_G(spread_KB(y))) (unnormalised transforms, no
+ * density compensation; X^0 = A^H b of Algorithm 1).
+ * ---------------------------------------------------------------------- */
+
+/* Build a plan for `nframes` frames of an ny x nx image, `ns` samples per
+ * frame.  traj: dev float [nframes][ns][2] = (kx, ky) rad/voxel; read once
+ * (the plan keeps its own sorted copy).  os must be 2; kb_width in {4, 6};
+ * square images (nx == ny, even) with os*nx in {64, 128, 256, 512}.  Synchronises
+ * `stream` (the trajectory is binned on the host).  MRF_ENOMEM if the
+ * workspace (about nframes*ny*os*nx*8 bytes plus 32 bytes per sample) does
+ * not fit. */
+mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int nframes, int ns,
+                          const float* traj, int os, int kb_width, mrf_stream stream);
+mrf_status mrf_nufft_destroy(mrf_plan plan);
+
+/* y = A x over all frames.  x: dev [nframes][ny][nx] mrf_c64;
+ * y: dev [nframes][ns] mrf_c64 (overwritten). */
+mrf_status mrf_nufft_forward(mrf_plan plan, const mrf_c64* x, mrf_c64* y, mrf_stream stream);
+
+/* x = A^H y over all frames.  y: dev [nframes][ns]; x: dev [nframes][ny][nx]
+ * (overwritten).  Spreading uses shared-memory atomics, so the float
+ * summation order (and the last bits) can vary between runs. */
+mrf_status mrf_nufft_adjoint(mrf_plan plan, const mrf_c64* y, mrf_c64* x, mrf_stream stream);
+
+/* Subspace forms used by the reconstruction loop.  With X = alpha Phi^H
+ * (Eq. 14, P_S(X) = X Phi Phi^H), frame t of X is x_t = sum_k alpha_k
+ * conj(Phi[t][k]).
+ *   forward:  y = A(alpha Phi^H) - b          (b may be NULL: no subtraction)
+ *   adjoint:  alpha_out = (A^H y) Phi          i.e. alpha_out[n][k] =
+ *             sum_t (A^H y)_t[n] Phi[t][k]
+ * alpha: dev [ny][nx][K]; phi: dev [nframes][K]; y, b: dev [nframes][ns].
+ * 1 <= K <= 16.  `scale` multiplies the operator (A/a of Algorithm 1's
+ * scaled problem: pass 1/a).  mode 0 = per-frame transforms (T NUFFTs per
+ * call, the literal multi-frame operator); mode 1 = grouped (the same
+ * operator evaluated with K oversampled FFTs: the FFT is linear and the same
+ * for every frame, so A(alpha Phi^H)_t = interp_t(sum over the K transformed
+ * coefficient images weighted by conj(Phi[t][k]))).  Both modes give the
+ * same values up to float rounding. */
+mrf_status mrf_nufft_forward_subspace(mrf_plan plan, const mrf_c64* alpha, const mrf_c64* phi,
+                                      int K, float scale, const mrf_c64* b, mrf_c64* y,
+                                      int mode, mrf_stream stream);
+mrf_status mrf_nufft_adjoint_subspace(mrf_plan plan, const mrf_c64* y, const mrf_c64* phi,
+                                      int K, float scale, mrf_c64* alpha_out,
+                                      int mode, mrf_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Dictionary simulation and matching.
+ * ---------------------------------------------------------------------- */
+
+/* Dictionary atoms d_m = B(eta_m; theta) with PD = 1 (Eq. 2-3) by the
+ * extended-phase-graph FISP recursion: per repetition an RF rotation of
+ * flip fa_deg[t] about x, relaxation over TE, the signal F+_0, relaxation
+ * over tr_ms[t] - TE and one full dephasing.  The magnetisation starts at
+ * equilibrium, is inverted and relaxes ti_ms before the train when
+ * `inversion` != 0.  All T+1 states are kept (no truncation).
+ * t1t2: dev float [m][2] (ms); fa_deg, tr_ms: dev float [T]; out: dev
+ * [m][T] mrf_c64.  1 <= T <= 4094. */
+mrf_status mrf_epg_fisp(const float* t1t2, int m, const float* fa_deg, const float* tr_ms,
+                        int T, float te_ms, float ti_ms, int inversion,
+                        mrf_c64* out, mrf_stream stream);
+
+/* Temporal subspace of a dictionary (Eq. 14: the orthonormal basis d of
+ * P_S, approximated from D).  phi (dev [T][K]) receives the top-K right
+ * singular vectors of D (dev [m][T]), computed by randomised block subspace
+ * iteration on the Gram matrix D^H D (Yang et al., cited in Sec. I);
+ * compressed (dev [m][K], nullable) receives d_m Phi and norm2 (dev [m],
+ * nullable) receives ||d_m||^2 of the full atoms.  Needs 1 <= K <= 16,
+ * K + 8 <= T <= 4096.  Allocates and frees its own workspace; synchronises
+ * `stream`. */
+mrf_status mrf_dict_subspace(const mrf_c64* dict, int m, int T, int K, mrf_c64* phi,
+                             mrf_c64* compressed, float* norm2, mrf_stream stream);
+
+enum {
+    MRF_MATCH_FP32 = 0,        /* exhaustive FP32 inner products (plain form) */
+    MRF_MATCH_BF16 = 1,        /* BF16 tensor-core scores, FP32 top-8 re-rank */
+    MRF_MATCH_LITERAL_NORM2 = 0x100 /* flag: argmax of |<d,x>|/||d||^2 as printed in Eq. 5 */
+};
+
+/* Phi_D of Eq. 5 for n fingerprints of length len:
+ *   k_i   = argmax_m |<d_m, x_i>| / ||d_m||     (||d_m||^2 with the LITERAL flag)
+ *   eta_i = LUT[k_i],  rho_i = max(Re<d_k, x_i> / ||d_k||^2, 0)
+ * <a, b> = sum conj(a) b; ties go to the lowest index (an all-zero x gives
+ * index 0, PD 0).  x: dev [n][len]; dict: dev [m][len]; atom_norm2: dev [m]
+ * ||d_m||^2 or NULL to use the rows of dict (pass the full-length norms when
+ * dict holds subspace-compressed atoms d_m Phi); lut: dev float [m][2]
+ * (T1, T2).  Outputs (each nullable): idx dev int [n], pd dev float [n],
+ * t1t2 dev float [n][2].  1 <= len <= 2048, 1 <= m <= 2^24. */
+mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64* dict,
+                     const float* atom_norm2, const float* lut, int m, int precision,
+                     int* idx, float* pd, float* t1t2, mrf_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Algorithm 1 (MS-LLR).  The iterate is held in the temporal subspace,
+ * X = alpha Phi^H with alpha dev [ny][nx][K]; the problem is posed over
+ * X in S (Eq. 11, 13), so X^0 = P_S(A^H b).  Per iteration:
+ *   Z     = P_S(X - mu [A^H(A X - b) + lambda1 Q^*(Q(X) L)])        (Eq. 12)
+ *   P_i   = SVT_{1/beta}(Q_i(X))                                    (Eq. 18)
+ *   X     = (Z + mu lambda2 beta Q^*(P)) / (1 + mu lambda2 beta cnt)  (Eq. 19)
+ *   cost  = 1/2||A X - b||^2 + lambda1 Tr(Q L Q^H) + lambda2 sum||Q_i X||_*
+ *   M     = Phi_D(X);  L = D - W of the k-nearest-patch graph of M  (Eq. 7-10)
+ *   lambda1 = lambda1^0 / max(L)
+ * A is scaled by 1/a, a = ||A P_S|| (power iteration), and b by gamma so
+ * that the largest PD matched from X^0 equals pd_target.
+ * ---------------------------------------------------------------------- */
+enum {
+    MRF_RECON_LITERAL_XUPDATE = 1,  /* Eq. 19 as printed: divide by 1 + mu lambda2 beta */
+    MRF_RECON_LITERAL_LAMBDA1 = 2,  /* lambda1 = lambda1^0 * max(L) as printed */
+    MRF_RECON_NO_COST = 4,          /* skip the cost evaluation */
+    MRF_RECON_GROUPED = 8           /* data term through the grouped subspace operator */
+};
+
+typedef struct {
+    float mu, lam1_0, lam2, beta;   /* step and weights; paper: 1, 0.1, 0.1, 1/5 */
+    int patch, stride, knn;         /* patch side p, stride s, graph neighbours */
+    int power_iters;                /* iterations of the ||A P_S|| power method */
+    float pd_target;                /* PD scale of the matched initial maps (100) */
+    float a_norm, x_scale;          /* > 0: use these instead of deriving a, gamma */
+    int flags;                      /* MRF_RECON_* */
+    int match_precision;            /* MRF_MATCH_FP32 or MRF_MATCH_BF16 */
+} mrf_recon_params;
+
+/* Create the loop state and run Algorithm 1's initialisation (X^0, M^0,
+ * L^0, lambda1).  plan: a NUFFT plan whose trajectory produced b;
+ * phi: dev [T][K]; dict_c: dev [m][K] compressed atoms d_m Phi;
+ * atom_norm2: dev [m] ||d_m||^2 of the full atoms; lut: dev [m][2];
+ * b: dev [T][ns] k-space.  The pointers must stay valid for the object's
+ * lifetime (they are not copied).  Requires K <= 16, patch <= 16, knn <= 32,
+ * at least knn + 1 patches.  Synchronises `stream`. */
+mrf_status mrf_recon_create(mrf_recon* out, mrf_plan plan, const mrf_recon_params* params,
+                            const mrf_c64* phi, int K, const mrf_c64* dict_c,
+                            const float* atom_norm2, const float* lut, int m,
+                            const mrf_c64* b, mrf_stream stream);
+/* Run n_iters iterations.  cost_out: host double [n_iters] (nullable); when
+ * given (and costs are enabled) the call synchronises to return them. */
+mrf_status mrf_recon_iter(mrf_recon r, int n_iters, double* cost_out, mrf_stream stream);
+/* Current maps: t1, t2, pd (PD divided back by gamma): dev float [ny][nx];
+ * idx: dev int [ny][nx].  Each nullable. */
+mrf_status mrf_recon_maps(mrf_recon r, float* t1, float* t2, float* pd, int* idx,
+                          mrf_stream stream);
+/* Copy of the coefficient images alpha (dev [ny][nx][K]). */
+mrf_status mrf_recon_alpha(mrf_recon r, mrf_c64* alpha, mrf_stream stream);
+/* Scalars of the current state (host outputs, each nullable; synchronises). */
+mrf_status mrf_recon_info(mrf_recon r, double* a_norm, double* x_scale, double* lam1,
+                          double* sigma2, mrf_stream stream);
+mrf_status mrf_recon_destroy(mrf_recon r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRF_H */

@@ -1,0 +1,15 @@
+"""GB300 (sm_103a) hot path of the MS-LLR MR-fingerprinting reconstruction.
+
+Thin PyTorch-facing binding over the C ABI of ``include/mrf.h``: tensors are
+passed as device pointers plus the current CUDA stream; every computation runs
+in this package's CUDA kernels (``csrc/``).  Importing the package does not
+touch the GPU; the first call loads ``libmrf.so`` and fails loudly if it has
+not been built.
+"""
+from .api import (MRFError, NufftPlan, Recon, ReconParams, dict_subspace, epg_fisp, match,
+                  nufft_adjoint, nufft_adjoint_subspace, nufft_forward, nufft_forward_subspace,
+                  nufft_plan)
+
+__all__ = ["MRFError", "NufftPlan", "Recon", "ReconParams", "dict_subspace", "epg_fisp", "match",
+           "nufft_adjoint", "nufft_adjoint_subspace", "nufft_forward", "nufft_forward_subspace",
+           "nufft_plan"]

@@ -1,0 +1,235 @@
+"""PyTorch-facing wrappers with the same names as the C ABI (marshalling only).
+
+Every function takes CUDA tensors, checks dtype/shape/contiguity, allocates
+outputs with torch (device memory plumbing) and calls the matching ``mrf_*``
+entry point on the current CUDA stream.  No arithmetic of the method happens
+here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, fields
+
+import torch
+
+from . import _lib
+from ._lib import MRFError
+
+__all__ = ["MRFError", "NufftPlan", "Recon", "ReconParams", "dict_subspace", "epg_fisp", "match",
+           "nufft_adjoint", "nufft_adjoint_subspace", "nufft_forward", "nufft_forward_subspace",
+           "nufft_plan"]
+
+MATCH_FP32, MATCH_BF16, MATCH_LITERAL_NORM2 = 0, 1, 0x100
+RECON_LITERAL_XUPDATE, RECON_LITERAL_LAMBDA1, RECON_NO_COST, RECON_GROUPED = 1, 2, 4, 8
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _check(t, name, dtype, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+# ---------------------------------------------------------------------------
+# NUFFT
+# ---------------------------------------------------------------------------
+class NufftPlan:
+    """Owner of an mrf_plan (KB gridding NUFFT for T frames of ny x nx)."""
+
+    def __init__(self, nx, ny, traj, os=2, kb_width=4):
+        traj = _check(traj, "traj", torch.float32)
+        if traj.dim() != 3 or traj.shape[2] != 2:
+            raise ValueError("traj must be [T, ns, 2]")
+        self.nx, self.ny, self.T, self.ns = nx, ny, traj.shape[0], traj.shape[1]
+        self.device = traj.device
+        h = C.c_void_p()
+        _lib.call("mrf_nufft_plan", C.byref(h), nx, ny, self.T, self.ns, _ptr(traj), os, kb_width, _stream())
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.call("mrf_nufft_destroy", h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def nufft_plan(nx, ny, traj, os=2, kb_width=4):
+    return NufftPlan(nx, ny, traj, os, kb_width)
+
+
+def nufft_forward(plan: NufftPlan, x, out=None):
+    _check(x, "x", torch.complex64, (plan.T, plan.ny, plan.nx))
+    y = out if out is not None else torch.empty((plan.T, plan.ns), dtype=torch.complex64, device=x.device)
+    _check(y, "y", torch.complex64, (plan.T, plan.ns))
+    _lib.call("mrf_nufft_forward", plan.handle, _ptr(x), _ptr(y), _stream())
+    return y
+
+
+def nufft_adjoint(plan: NufftPlan, y, out=None):
+    _check(y, "y", torch.complex64, (plan.T, plan.ns))
+    x = out if out is not None else torch.empty((plan.T, plan.ny, plan.nx), dtype=torch.complex64, device=y.device)
+    _check(x, "x", torch.complex64, (plan.T, plan.ny, plan.nx))
+    _lib.call("mrf_nufft_adjoint", plan.handle, _ptr(y), _ptr(x), _stream())
+    return x
+
+
+def nufft_forward_subspace(plan: NufftPlan, alpha, phi, scale=1.0, b=None, mode=0, out=None):
+    K = phi.shape[1]
+    _check(alpha, "alpha", torch.complex64, (plan.ny, plan.nx, K))
+    _check(phi, "phi", torch.complex64, (plan.T, K))
+    if b is not None:
+        _check(b, "b", torch.complex64, (plan.T, plan.ns))
+    y = out if out is not None else torch.empty((plan.T, plan.ns), dtype=torch.complex64, device=alpha.device)
+    _lib.call("mrf_nufft_forward_subspace", plan.handle, _ptr(alpha), _ptr(phi), K, float(scale), _ptr(b),
+              _ptr(y), mode, _stream())
+    return y
+
+
+def nufft_adjoint_subspace(plan: NufftPlan, y, phi, scale=1.0, mode=0, out=None):
+    K = phi.shape[1]
+    _check(y, "y", torch.complex64, (plan.T, plan.ns))
+    _check(phi, "phi", torch.complex64, (plan.T, K))
+    a = out if out is not None else torch.empty((plan.ny, plan.nx, K), dtype=torch.complex64, device=y.device)
+    _lib.call("mrf_nufft_adjoint_subspace", plan.handle, _ptr(y), _ptr(phi), K, float(scale), _ptr(a), mode,
+              _stream())
+    return a
+
+
+# ---------------------------------------------------------------------------
+# Dictionary
+# ---------------------------------------------------------------------------
+def epg_fisp(t1t2, fa_deg, tr_ms, te_ms=2.94, ti_ms=20.0, inversion=True):
+    _check(t1t2, "t1t2", torch.float32)
+    _check(fa_deg, "fa_deg", torch.float32)
+    _check(tr_ms, "tr_ms", torch.float32, fa_deg.shape)
+    m, T = t1t2.shape[0], fa_deg.shape[0]
+    out = torch.empty((m, T), dtype=torch.complex64, device=t1t2.device)
+    _lib.call("mrf_epg_fisp", _ptr(t1t2), m, _ptr(fa_deg), _ptr(tr_ms), T, float(te_ms), float(ti_ms),
+              1 if inversion else 0, _ptr(out), _stream())
+    return out
+
+
+def dict_subspace(D, K):
+    """(phi [T, K], compressed atoms [m, K], ||d||^2 [m]) of dictionary D [m, T]."""
+    _check(D, "D", torch.complex64)
+    m, T = D.shape
+    phi = torch.empty((T, K), dtype=torch.complex64, device=D.device)
+    comp = torch.empty((m, K), dtype=torch.complex64, device=D.device)
+    n2 = torch.empty((m,), dtype=torch.float32, device=D.device)
+    _lib.call("mrf_dict_subspace", _ptr(D), m, T, K, _ptr(phi), _ptr(comp), _ptr(n2), _stream())
+    return phi, comp, n2
+
+
+def match(x, D, lut, atom_norm2=None, precision=MATCH_FP32):
+    """(idx [n] int32, pd [n], t1t2 [n, 2]) of fingerprints x [n, L] against D [m, L]."""
+    _check(x, "x", torch.complex64)
+    _check(D, "D", torch.complex64)
+    n, L = x.shape
+    m = D.shape[0]
+    if D.shape[1] != L:
+        raise ValueError("x and D lengths differ")
+    _check(lut, "lut", torch.float32, (m, 2))
+    if atom_norm2 is not None:
+        _check(atom_norm2, "atom_norm2", torch.float32, (m,))
+    idx = torch.empty((n,), dtype=torch.int32, device=x.device)
+    pd = torch.empty((n,), dtype=torch.float32, device=x.device)
+    t1t2 = torch.empty((n, 2), dtype=torch.float32, device=x.device)
+    _lib.call("mrf_match", _ptr(x), n, L, _ptr(D), _ptr(atom_norm2), _ptr(lut), m, int(precision), _ptr(idx),
+              _ptr(pd), _ptr(t1t2), _stream())
+    return idx, pd, t1t2
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1
+# ---------------------------------------------------------------------------
+@dataclass
+class ReconParams:
+    mu: float = 1.0
+    lam1_0: float = 0.1
+    lam2: float = 0.1
+    beta: float = 0.2
+    patch: int = 8
+    stride: int = 4
+    knn: int = 10
+    power_iters: int = 20
+    pd_target: float = 100.0
+    a_norm: float = 0.0
+    x_scale: float = 0.0
+    flags: int = 0
+    match_precision: int = MATCH_FP32
+
+    def as_c(self):
+        return _lib.ReconParams(*[getattr(self, f.name) for f in fields(self)])
+
+
+class Recon:
+    """Owner of an mrf_recon: Algorithm 1 state on the GPU."""
+
+    def __init__(self, plan: NufftPlan, params: ReconParams, phi, dict_c, atom_norm2, lut, b):
+        K = phi.shape[1]
+        m = dict_c.shape[0]
+        _check(phi, "phi", torch.complex64, (plan.T, K))
+        _check(dict_c, "dict_c", torch.complex64, (m, K))
+        _check(atom_norm2, "atom_norm2", torch.float32, (m,))
+        _check(lut, "lut", torch.float32, (m, 2))
+        _check(b, "b", torch.complex64, (plan.T, plan.ns))
+        self.plan, self.K = plan, K
+        self._keep = (phi, dict_c, atom_norm2, lut, b)      # the C object borrows these
+        self._params = params.as_c()
+        h = C.c_void_p()
+        _lib.call("mrf_recon_create", C.byref(h), plan.handle, C.byref(self._params), _ptr(phi), K, _ptr(dict_c),
+                  _ptr(atom_norm2), _ptr(lut), m, _ptr(b), _stream())
+        self.handle = h
+
+    def iterate(self, n=1, costs=False):
+        buf = (C.c_double * n)() if costs else None
+        _lib.call("mrf_recon_iter", self.handle, n, buf if costs else None, _stream())
+        return list(buf) if costs else None
+
+    def maps(self):
+        p = self.plan
+        dev = self._keep[0].device
+        t1 = torch.empty((p.ny, p.nx), dtype=torch.float32, device=dev)
+        t2 = torch.empty_like(t1)
+        pd = torch.empty_like(t1)
+        idx = torch.empty((p.ny, p.nx), dtype=torch.int32, device=dev)
+        _lib.call("mrf_recon_maps", self.handle, _ptr(t1), _ptr(t2), _ptr(pd), _ptr(idx), _stream())
+        return t1, t2, pd, idx
+
+    def alpha(self):
+        p = self.plan
+        a = torch.empty((p.ny, p.nx, self.K), dtype=torch.complex64, device=self._keep[0].device)
+        _lib.call("mrf_recon_alpha", self.handle, _ptr(a), _stream())
+        return a
+
+    def info(self):
+        vals = [C.c_double() for _ in range(4)]
+        _lib.call("mrf_recon_info", self.handle, *[C.byref(v) for v in vals], _stream())
+        return dict(zip(["a_norm", "x_scale", "lam1", "sigma2"], [v.value for v in vals]))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.call("mrf_recon_destroy", h)
+            except Exception:
+                pass
+            self.handle = None

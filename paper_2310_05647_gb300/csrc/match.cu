@@ -1,0 +1,237 @@
+// Dictionary matching Phi_D (Eq. 5): for every fingerprint x_i
+//   k_i = argmax_m |<d_m, x_i>| / ||d_m||   (||d_m||^2 with the literal flag)
+//   rho_i = max(Re<d_k, x_i> / ||d_k||^2, 0),  eta_i = LUT[k_i]
+// with <a, b> = sum conj(a) b and ties resolved to the lowest index.
+//
+// The plain form (MRF_MATCH_FP32) is a SIMT FP32 GEMM tile (64 fingerprints x
+// 64 atoms, 4 x 4 complex micro-tiles per thread) whose epilogue keeps, per
+// fingerprint, the running best (score, index, inner product) over all atom
+// tiles; no fingerprint x atom score is ever written to memory.  The BF16
+// tensor-core form lives in match_tc.cu.
+#include "common.h"
+#include "match.h"
+
+namespace mrf {
+
+constexpr int BM = 64, BN = 64, BK = 8;
+
+__device__ __forceinline__ bool better(float s, int i, float bs, int bi) {
+    return s > bs || (s == bs && i < bi);
+}
+
+__global__ void __launch_bounds__(256) k_match_fp32(const float2* __restrict__ x, int n, int len,
+                                                    const float2* __restrict__ dict,
+                                                    const float* __restrict__ wscore, int m,
+                                                    int* __restrict__ best_idx, float2* __restrict__ best_ip) {
+    __shared__ float2 xs[BK][BM + 1];
+    __shared__ float2 ds[BK][BN + 1];
+    __shared__ float ws[BN];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int v0 = blockIdx.x * BM;
+    float bsc[4];
+    int bid[4];
+    float2 bip[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { bsc[i] = -1.f; bid[i] = 0x7fffffff; bip[i] = make_float2(0.f, 0.f); }
+    for (int a0 = 0; a0 < m; a0 += BN) {
+        float2 acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+        if (threadIdx.x < BN) ws[threadIdx.x] = (a0 + threadIdx.x < m) ? wscore[a0 + threadIdx.x] : 0.f;
+        for (int k0 = 0; k0 < len; k0 += BK) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int e = threadIdx.x + q * 256;
+                const int r = e >> 3, kk = e & 7;
+                const int k = k0 + kk;
+                const int v = v0 + r, a = a0 + r;
+                xs[kk][r] = (v < n && k < len) ? x[(size_t)v * len + k] : make_float2(0.f, 0.f);
+                ds[kk][r] = (a < m && k < len) ? dict[(size_t)a * len + k] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                float2 xv[4], dv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xv[i] = xs[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dv[j] = ds[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        // conj(d) * x
+                        acc[i][j].x = fmaf(dv[j].x, xv[i].x, fmaf(dv[j].y, xv[i].y, acc[i][j].x));
+                        acc[i][j].y = fmaf(dv[j].x, xv[i].y, fmaf(-dv[j].y, xv[i].x, acc[i][j].y));
+                    }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int a = a0 + tx + 16 * j;
+            if (a < m) {
+                const float w = ws[tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float sc = cabs2(acc[i][j]) * w;
+                    if (better(sc, a, bsc[i], bid[i])) { bsc[i] = sc; bid[i] = a; bip[i] = acc[i][j]; }
+                }
+            }
+        }
+    }
+    // reduce over the 16 threads (tx) that share the same fingerprints
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int o = 8; o >= 1; o >>= 1) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, bsc[i], o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bid[i], o);
+            const float px = __shfl_xor_sync(0xffffffffu, bip[i].x, o);
+            const float py = __shfl_xor_sync(0xffffffffu, bip[i].y, o);
+            if (better(s2, i2, bsc[i], bid[i])) { bsc[i] = s2; bid[i] = i2; bip[i] = make_float2(px, py); }
+        }
+        const int v = v0 + ty + 16 * i;
+        if (tx == 0 && v < n) { best_idx[v] = bid[i]; best_ip[v] = bip[i]; }
+    }
+}
+
+// per-atom weights of the score: 1/||d||^2 (argmax of |s|^2/||d||^2 is the
+// argmax of |s|/||d||) or 1/||d||^4 for the literal |s|/||d||^2.
+__global__ void k_match_weights(const float2* __restrict__ dict, const float* __restrict__ norm2_in, int m, int len,
+                                int literal, float* __restrict__ norm2, float* __restrict__ wscore) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= m) return;
+    float n2;
+    if (norm2_in) {
+        n2 = norm2_in[a];
+    } else {
+        double s = 0.0;
+        for (int k = 0; k < len; ++k) s += (double)cabs2(dict[(size_t)a * len + k]);
+        n2 = (float)s;
+    }
+    norm2[a] = n2;
+    const float inv = n2 > 0.f ? 1.0f / n2 : 0.f;
+    wscore[a] = literal ? inv * inv : inv;
+}
+
+__global__ void k_match_finish(const int* __restrict__ best_idx, const float2* __restrict__ best_ip, int n,
+                               const float* __restrict__ norm2, const float* __restrict__ lut,
+                               int* __restrict__ idx, float* __restrict__ pd, float* __restrict__ t1t2,
+                               float pd_scale) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int k = best_idx[v];
+    const float n2 = norm2[k];
+    if (idx) idx[v] = k;
+    if (pd) pd[v] = n2 > 0.f ? fmaxf(best_ip[v].x / n2, 0.f) * pd_scale : 0.f;
+    if (t1t2) {
+        t1t2[2 * v] = lut[2 * k];
+        t1t2[2 * v + 1] = lut[2 * k + 1];
+    }
+}
+
+MatchWorkspace::~MatchWorkspace() { release(); }
+
+void MatchWorkspace::carve(char* base, int n, int m) {
+    auto take = [&](size_t b) { char* p = base; base += (b + 255) / 256 * 256; return p; };
+    best_idx = reinterpret_cast<int*>(take(sizeof(int) * (size_t)n));
+    best_ip = reinterpret_cast<float2*>(take(sizeof(float2) * (size_t)n));
+    cand = reinterpret_cast<int*>(take(sizeof(int) * (size_t)n * kTopK));
+    norm2 = reinterpret_cast<float*>(take(sizeof(float) * (size_t)m));
+    wscore = reinterpret_cast<float*>(take(sizeof(float) * (size_t)m));
+    cap_n = n;
+    cap_m = m;
+    borrowed = true;
+}
+
+void MatchWorkspace::detach() {
+    best_idx = nullptr; best_ip = nullptr; norm2 = nullptr; wscore = nullptr; cand = nullptr;
+    cap_n = cap_m = 0;
+    borrowed = false;
+}
+
+void MatchWorkspace::release() {
+    if (borrowed) { detach(); return; }
+    cudaFree(best_idx); cudaFree(best_ip); cudaFree(norm2); cudaFree(wscore);
+    cudaFree(cand);
+    best_idx = nullptr; best_ip = nullptr; norm2 = nullptr; wscore = nullptr; cand = nullptr;
+    cap_n = cap_m = 0;
+}
+
+mrf_status MatchWorkspace::reserve(int n, int m) {
+    if (n > cap_n) {
+        cudaFree(best_idx); cudaFree(best_ip); cudaFree(cand);
+        best_idx = nullptr; best_ip = nullptr; cand = nullptr;
+        MRF_CUDA(cudaMalloc(&best_idx, sizeof(int) * (size_t)n));
+        MRF_CUDA(cudaMalloc(&best_ip, sizeof(float2) * (size_t)n));
+        MRF_CUDA(cudaMalloc(&cand, sizeof(int) * (size_t)n * kTopK));
+        cap_n = n;
+    }
+    if (m > cap_m) {
+        cudaFree(norm2); cudaFree(wscore);
+        norm2 = nullptr; wscore = nullptr;
+        MRF_CUDA(cudaMalloc(&norm2, sizeof(float) * (size_t)m));
+        MRF_CUDA(cudaMalloc(&wscore, sizeof(float) * (size_t)m));
+        cap_m = m;
+    }
+    return MRF_OK;
+}
+
+mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* norm2_in, int m, int len,
+                         int literal, cudaStream_t s) {
+    k_match_weights<<<(m + 255) / 256, 256, 0, s>>>(dict, norm2_in, m, len, literal, ws.norm2, ws.wscore);
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
+                     int precision, const float* lut, int* idx, float* pd, float* t1t2, float pd_scale,
+                     cudaStream_t s) {
+    if (precision == MRF_MATCH_BF16) {
+        MRF_PROPAGATE(match_bf16_candidates(ws, x, n, len, dict, m, s));
+        MRF_PROPAGATE(match_rerank(ws, x, n, len, dict, s));
+    } else {
+        k_match_fp32<<<(n + BM - 1) / BM, 256, 0, s>>>(x, n, len, dict, ws.wscore, m, ws.best_idx, ws.best_ip);
+        MRF_LAUNCHED();
+    }
+    k_match_finish<<<(n + 255) / 256, 256, 0, s>>>(ws.best_idx, ws.best_ip, n, ws.norm2, lut, idx, pd, t1t2,
+                                                   pd_scale);
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+}  // namespace mrf
+
+using namespace mrf;
+
+extern "C" mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64* dict, const float* atom_norm2,
+                                const float* lut, int m, int precision, int* idx, float* pd, float* t1t2,
+                                mrf_stream stream) {
+    MRF_REQUIRE(x && dict && lut, "mrf_match: NULL x, dict or lut");
+    MRF_REQUIRE(n >= 0 && len >= 1 && len <= 2048, "mrf_match: bad n or len (%d, %d)", n, len);
+    MRF_REQUIRE(m >= 1 && m <= (1 << 24), "mrf_match: bad m (%d)", m);
+    const int prec = precision & 0xff;
+    const int literal = (precision & MRF_MATCH_LITERAL_NORM2) ? 1 : 0;
+    MRF_REQUIRE(prec == MRF_MATCH_FP32 || prec == MRF_MATCH_BF16, "mrf_match: unknown precision %d", prec);
+    MRF_REQUIRE(!(literal && prec != MRF_MATCH_FP32), "mrf_match: the literal norm flag needs FP32");
+    if (n == 0) return MRF_OK;
+    cudaStream_t s = as_stream(stream);
+    // stream-ordered scratch: released on the stream after the kernels
+    MatchWorkspace ws;
+    const size_t bytes = sizeof(int) * (size_t)n + sizeof(float2) * (size_t)n + sizeof(int) * (size_t)n * kTopK +
+                         2 * sizeof(float) * (size_t)m + 5 * 256;
+    char* base = nullptr;
+    MRF_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, s));
+    ws.carve(base, n, m);
+    mrf_status st = match_prepare(ws, reinterpret_cast<const float2*>(dict), atom_norm2, m, len, literal, s);
+    if (st == MRF_OK)
+        st = match_run(ws, reinterpret_cast<const float2*>(x), n, len, reinterpret_cast<const float2*>(dict), m,
+                       prec, lut, idx, pd, t1t2, 1.0f, s);
+    ws.detach();
+    MRF_CUDA(cudaFreeAsync(base, s));
+    return st;
+    return MRF_OK;
+}

@@ -1,0 +1,38 @@
+// Matching workspace and entry points shared by match.cu, match_tc.cu and the
+// reconstruction loop.
+#pragma once
+#include "common.h"
+
+namespace mrf {
+
+constexpr int kTopK = 8;   // candidates kept by the BF16 scorer for the FP32 re-rank
+
+struct MatchWorkspace {
+    int* best_idx = nullptr;   // [n] winning atom
+    float2* best_ip = nullptr; // [n] <d_k, x> of the winner
+    int* cand = nullptr;       // [n][kTopK] BF16 candidates
+    float* norm2 = nullptr;    // [m] ||d_m||^2
+    float* wscore = nullptr;   // [m] score weight
+    int cap_n = 0, cap_m = 0;
+    bool borrowed = false;     // pointers carved from a caller-owned block
+    ~MatchWorkspace();
+    mrf_status reserve(int n, int m);
+    void carve(char* base, int n, int m);
+    void detach();
+    void release();
+};
+
+// norm2/score weights of the atoms (norm2_in nullable: computed from dict)
+mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* norm2_in, int m, int len,
+                         int literal, cudaStream_t s);
+// winners for n fingerprints; outputs nullable; pd multiplied by pd_scale
+mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
+                     int precision, const float* lut, int* idx, float* pd, float* t1t2, float pd_scale,
+                     cudaStream_t s);
+// BF16 tensor-core candidate search and FP32 re-rank (match_tc.cu)
+mrf_status match_bf16_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
+                                 cudaStream_t s);
+mrf_status match_rerank(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict,
+                        cudaStream_t s);
+
+}  // namespace mrf

@@ -1,0 +1,870 @@
+// Multi-frame Kaiser-Bessel NUFFT: the acquisition operator A = F_u of Eq. 1
+// (one coil) and its adjoint, for all T frames of an MRF series.
+//
+// Forward, per frame:  deapodise + zero-pad + FFT along x   (k_rows_fwd)
+//                      FFT along y + KB interpolation       (k_cols_interp)
+// Adjoint, per frame:  KB spread + inverse FFT along y      (k_spread_cols)
+//                      inverse FFT along x + crop + deapod  (k_rows_adj)
+//
+// The oversampled grid G x G of a frame is never written to HBM: the column
+// kernels own a 32-column strip of the frame in shared memory, transform it
+// there and interpolate (or spread) the samples binned to that strip.  Only
+// the half-oversampled intermediate H1 [T][ny][G] (rows transformed along x)
+// goes through memory.  Samples are binned per strip on the host when the plan
+// is built; frames with identical sample positions share one binned copy.
+//
+// Kernel: psi(u) = I0(beta sqrt(1 - (2u/W)^2)), |u| <= W/2, with Beatty's
+// beta = pi sqrt((W/os)^2 (os - 1/2)^2 - 0.8); deapodisation divides by its
+// continuous Fourier transform W sinh(z)/z, z = sqrt(beta^2 - (pi W f)^2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "common.h"
+#include "fft.cuh"
+#include "nufft_plan.h"
+
+namespace mrf {
+
+constexpr int kStrip = 32;      // grid columns per strip
+constexpr int kThreads = 512;   // threads of every FFT kernel
+
+template <int W>
+__device__ __forceinline__ void kb_weights(float f, float beta, float* w) {
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        const float z = 2.0f * (f - (float)a) / (float)W;
+        w[a] = cyl_bessel_i0f(beta * sqrtf(fmaxf(0.0f, 1.0f - z * z)));
+    }
+}
+
+__device__ __forceinline__ void unpack(const int4 r, int& j, int& mx0, int& my0, float& fx, float& fy) {
+    j = r.x;
+    mx0 = r.y & 0xffff;
+    my0 = (r.y >> 16) & 0xffff;
+    fx = __int_as_float(r.z);
+    fy = __int_as_float(r.w);
+}
+
+// centred coordinate held at grid index g
+template <int G>
+__device__ __forceinline__ int centred(int g) { return g < G / 2 ? g : g - G; }
+
+// ---------------------------------------------------------------------------
+// Forward stage 1: rows.  SRC 0: frames x[t][iy][ix]; SRC 1: coefficient image
+// k of alpha[iy][ix][K] (blockIdx.y = k).
+// ---------------------------------------------------------------------------
+template <int G, int SRC>
+__global__ void __launch_bounds__(kThreads) k_rows_fwd(const float2* __restrict__ x, int K,
+                                                       float2* __restrict__ h1,
+                                                       const float* __restrict__ inv_dx,
+                                                       const float* __restrict__ inv_dy, int nx, int ny) {
+    constexpr int TPF = G / 8;
+    constexpr int RPC = kThreads / TPF;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
+    float2* row = sm + G + grp * G;
+    const int t = blockIdx.y;
+    const int iy = blockIdx.x * RPC + grp;
+    const bool active = iy < ny;
+    fft_twiddles<G>(tw);
+    if (active) {
+        const float sy = inv_dy[iy];
+        for (int g = tid; g < G; g += TPF) {
+            const int ix = centred<G>(g) + nx / 2;
+            float2 v = make_float2(0.f, 0.f);
+            if (ix >= 0 && ix < nx) {
+                if (SRC == 0) v = x[((size_t)t * ny + iy) * nx + ix];
+                else v = x[((size_t)iy * nx + ix) * K + t];
+                v = cscale(v, inv_dx[ix] * sy);
+            }
+            row[g] = v;
+        }
+    }
+    __syncthreads();
+    fft_smem<G, false>(row, 1, tid, active, tw);
+    if (active) {
+        float2* dst = h1 + ((size_t)t * ny + iy) * G;
+        for (int g = tid; g < G; g += TPF) dst[g] = row[g];
+    }
+}
+
+// Forward stage 1 in subspace form: frame t row iy is sum_k alpha[iy][ix][k]
+// conj(phi[t][k]).  Block = one image row x (kThreads / (G/8)) frames.
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_rows_fwd_expand(const float2* __restrict__ alpha,
+                                                              const float2* __restrict__ phi, int K, int T,
+                                                              float2* __restrict__ h1,
+                                                              const float* __restrict__ inv_dx,
+                                                              const float* __restrict__ inv_dy, int nx,
+                                                              int ny) {
+    constexpr int TPF = G / 8;
+    constexpr int FPC = kThreads / TPF;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* rows = sm + G;                 // [FPC][G]
+    float2* arow = rows + FPC * G;         // [nx][K]
+    float2* ph = arow + nx * K;            // [FPC][K]
+    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
+    const int iy = blockIdx.x;
+    const int t0 = blockIdx.y * FPC;
+    const int t = t0 + grp;
+    const bool active = t < T;
+    fft_twiddles<G>(tw);
+    for (int i = threadIdx.x; i < nx * K; i += blockDim.x) arow[i] = alpha[(size_t)iy * nx * K + i];
+    for (int i = threadIdx.x; i < FPC * K; i += blockDim.x) {
+        const int tt = t0 + i / K;
+        ph[i] = tt < T ? phi[(size_t)tt * K + (i % K)] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* row = rows + grp * G;
+    if (active) {
+        const float sy = inv_dy[iy];
+        for (int g = tid; g < G; g += TPF) {
+            const int ix = centred<G>(g) + nx / 2;
+            float2 v = make_float2(0.f, 0.f);
+            if (ix >= 0 && ix < nx) {
+                for (int k = 0; k < K; ++k) v = cadd(v, cmulc(arow[ix * K + k], ph[grp * K + k]));
+                v = cscale(v, inv_dx[ix] * sy);
+            }
+            row[g] = v;
+        }
+    }
+    __syncthreads();
+    fft_smem<G, false>(row, 1, tid, active, tw);
+    if (active) {
+        float2* dst = h1 + ((size_t)t * ny + iy) * G;
+        for (int g = tid; g < G; g += TPF) dst[g] = row[g];
+    }
+}
+
+// Load a strip (C columns starting at c0, wrapping) of frame f's H1 into the
+// shared tile [G][C]; rows outside the image's support are zero.
+template <int G, int C>
+__device__ __forceinline__ void load_strip(float2* tile, const float2* __restrict__ h1f, int c0, int ny) {
+    for (int idx = threadIdx.x; idx < G * C; idx += blockDim.x) {
+        const int gy = idx / C, c = idx - gy * C;
+        const int iy = centred<G>(gy) + ny / 2;
+        float2 v = make_float2(0.f, 0.f);
+        if (iy >= 0 && iy < ny) v = h1f[(size_t)iy * G + ((c0 + c) & (G - 1))];
+        tile[idx] = v;
+    }
+    __syncthreads();
+}
+
+template <int G, bool INV>
+__device__ __forceinline__ void strip_column_ffts(float2* tile, int C, const float2* tw) {
+    constexpr int TPF = G / 8;
+    const int cpr = blockDim.x / TPF;
+    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
+    for (int cb = 0; cb < C; cb += cpr) {
+        const int c = cb + grp;
+        const bool active = c < C;
+        fft_smem<G, INV>(tile + (active ? c : 0), C, tid, active, tw);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward stage 2: FFT of a strip's columns in shared memory, then KB
+// interpolation of the samples whose first x-node falls in the strip.
+// y = scale * interp - b  (b nullable).
+// ---------------------------------------------------------------------------
+template <int G, int W>
+__global__ void __launch_bounds__(kThreads) k_cols_interp(const float2* __restrict__ h1, float2* __restrict__ y,
+                                                          const float2* __restrict__ bsub, float scale,
+                                                          const int4* __restrict__ rec,
+                                                          const int* __restrict__ off,
+                                                          const int* __restrict__ group_of, int ny, int ns,
+                                                          int nstrips, float beta) {
+    constexpr int C = kStrip + W - 1;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* tile = sm + G;
+    const int strip = blockIdx.x, t = blockIdx.y;
+    const int c0 = strip * kStrip;
+    fft_twiddles<G>(tw);
+    load_strip<G, C>(tile, h1 + (size_t)t * ny * G, c0, ny);
+    strip_column_ffts<G, false>(tile, C, tw);
+    const int g = group_of[t];
+    const int beg = off[g * nstrips + strip], end = off[g * nstrips + strip + 1];
+    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        int j, mx0, my0;
+        float fx, fy;
+        unpack(rec[i], j, mx0, my0, fx, fy);
+        float wx[W], wy[W];
+        kb_weights<W>(fx, beta, wx);
+        kb_weights<W>(fy, beta, wy);
+        const int lc = mx0 - c0;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2* tr = tile + ((my0 + b) & (G - 1)) * C + lc;
+            float2 rs = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < W; ++a) rs = cadd(rs, cscale(tr[a], wx[a]));
+            acc = cadd(acc, cscale(rs, wy[b]));
+        }
+        acc = cscale(acc, scale);
+        const size_t o = (size_t)t * ns + j;
+        if (bsub) acc = csub(acc, bsub[o]);
+        y[o] = acc;
+    }
+}
+
+// Column FFTs of whole images, spectrum written out (grouped subspace form).
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_cols_store(const float2* __restrict__ h1, float2* __restrict__ spec,
+                                                         int ny) {
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* tile = sm + G;
+    const int strip = blockIdx.x, f = blockIdx.y;
+    const int c0 = strip * kStrip;
+    fft_twiddles<G>(tw);
+    load_strip<G, kStrip>(tile, h1 + (size_t)f * ny * G, c0, ny);
+    strip_column_ffts<G, false>(tile, kStrip, tw);
+    float2* dst = spec + (size_t)f * G * G;
+    for (int idx = threadIdx.x; idx < G * kStrip; idx += blockDim.x) {
+        const int gy = idx / kStrip, c = idx % kStrip;
+        dst[(size_t)gy * G + c0 + c] = tile[idx];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint stage 1: spread the samples touching a strip into a shared tile
+// (shared-memory atomics), inverse FFT of the strip's columns, keep the image
+// rows.  SRC 0: y[t][j] per frame (blockIdx.y = t);  SRC 1: grouped values
+// R[g][j][k] of every group (blockIdx.y = k).
+// ---------------------------------------------------------------------------
+template <int G, int W, int SRC>
+__global__ void __launch_bounds__(kThreads) k_spread_cols(const float2* __restrict__ y, int K,
+                                                          float2* __restrict__ h1, const int4* __restrict__ rec,
+                                                          const int* __restrict__ off,
+                                                          const int* __restrict__ group_of, int ngroups,
+                                                          int ny, int ns, int nstrips, float beta) {
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* tile = sm + G;                 // [G][kStrip]
+    const int strip = blockIdx.x, f = blockIdx.y;
+    const int c0 = strip * kStrip;
+    fft_twiddles<G>(tw);
+    for (int i = threadIdx.x; i < G * kStrip; i += blockDim.x) tile[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int g_lo = SRC == 0 ? group_of[f] : 0;
+    const int g_hi = SRC == 0 ? g_lo + 1 : ngroups;
+    for (int g = g_lo; g < g_hi; ++g) {
+        const int beg = off[g * nstrips + strip], end = off[g * nstrips + strip + 1];
+        for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+            int j, mx0, my0;
+            float fx, fy;
+            unpack(rec[i], j, mx0, my0, fx, fy);
+            const float2 v = SRC == 0 ? y[(size_t)f * ns + j] : y[((size_t)g * ns + j) * K + f];
+            float wx[W], wy[W];
+            kb_weights<W>(fx, beta, wx);
+            kb_weights<W>(fy, beta, wy);
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                const int lc = ((mx0 + a) & (G - 1)) - c0;
+                if (lc < 0 || lc >= kStrip) continue;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    float2* p = tile + ((my0 + b) & (G - 1)) * kStrip + lc;
+                    const float w = wx[a] * wy[b];
+                    atomicAdd(&p->x, w * v.x);
+                    atomicAdd(&p->y, w * v.y);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    strip_column_ffts<G, true>(tile, kStrip, tw);
+    float2* dst = h1 + (size_t)f * ny * G;
+    for (int idx = threadIdx.x; idx < ny * kStrip; idx += blockDim.x) {
+        const int iy = idx / kStrip, c = idx % kStrip;
+        const int gy = (iy - ny / 2) & (G - 1);
+        dst[(size_t)iy * G + c0 + c] = tile[gy * kStrip + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint stage 2: inverse FFT along x, crop, deapodise.  DST 0: frames
+// x[t][iy][ix]; DST 1: coefficient image k, alpha[iy][ix][K] (times scale).
+// ---------------------------------------------------------------------------
+template <int G, int DST>
+__global__ void __launch_bounds__(kThreads) k_rows_adj(const float2* __restrict__ h1, float2* __restrict__ x,
+                                                       int K, float scale, const float* __restrict__ inv_dx,
+                                                       const float* __restrict__ inv_dy, int nx, int ny) {
+    constexpr int TPF = G / 8;
+    constexpr int RPC = kThreads / TPF;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
+    float2* row = sm + G + grp * G;
+    const int t = blockIdx.y;
+    const int iy = blockIdx.x * RPC + grp;
+    const bool active = iy < ny;
+    fft_twiddles<G>(tw);
+    if (active) {
+        const float2* src = h1 + ((size_t)t * ny + iy) * G;
+        for (int g = tid; g < G; g += TPF) row[g] = src[g];
+    }
+    __syncthreads();
+    fft_smem<G, true>(row, 1, tid, active, tw);
+    if (active) {
+        const float sy = inv_dy[iy] * scale;
+        for (int ix = tid; ix < nx; ix += TPF) {
+            const float2 v = cscale(row[(ix - nx / 2) & (G - 1)], inv_dx[ix] * sy);
+            if (DST == 0) x[((size_t)t * ny + iy) * nx + ix] = v;
+            else x[((size_t)iy * nx + ix) * K + t] = v;
+        }
+    }
+}
+
+// Adjoint stage 2 in subspace form: partial[p][iy][ix][k] = sum over the
+// frames t of part p of (A^H y)_t[iy][ix] phi[t][k].
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_rows_adj_reduce(const float2* __restrict__ h1,
+                                                              const float2* __restrict__ phi, int K, int T,
+                                                              int frames_per_part, float2* __restrict__ partial,
+                                                              const float* __restrict__ inv_dx,
+                                                              const float* __restrict__ inv_dy, int nx, int ny) {
+    constexpr int TPF = G / 8;
+    constexpr int FPC = kThreads / TPF;
+    constexpr int MAXQ = 8;                 // (nx * K) / kThreads <= 8 (nx <= 256, K <= 16)
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* rows = sm + G;                  // [FPC][G]
+    float2* ph = rows + FPC * G;            // [FPC][K]
+    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
+    const int iy = blockIdx.x, part = blockIdx.y;
+    const int tb = part * frames_per_part;
+    const int te = min(T, tb + frames_per_part);
+    fft_twiddles<G>(tw);
+    float2 acc[MAXQ];
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) acc[q] = make_float2(0.f, 0.f);
+    const float sy = inv_dy[iy];
+    for (int t0 = tb; t0 < te; t0 += FPC) {
+        const int t = t0 + grp;
+        const bool active = t < te;
+        if (active) {
+            const float2* src = h1 + ((size_t)t * ny + iy) * G;
+            float2* row = rows + grp * G;
+            for (int g = tid; g < G; g += TPF) row[g] = src[g];
+        }
+        for (int i = threadIdx.x; i < FPC * K; i += blockDim.x) {
+            const int tt = t0 + i / K;
+            ph[i] = tt < te ? phi[(size_t)tt * K + (i % K)] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        fft_smem<G, true>(rows + grp * G, 1, tid, active, tw);
+        const int nf = min(FPC, te - t0);
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q) {
+            const int pidx = threadIdx.x + q * kThreads;
+            if (pidx < nx * K) {
+                const int ix = pidx / K, k = pidx - ix * K;
+                const int gx = (ix - nx / 2) & (G - 1);
+                float2 s = make_float2(0.f, 0.f);
+                for (int f = 0; f < nf; ++f) s = cadd(s, cmul(rows[f * G + gx], ph[f * K + k]));
+                acc[q] = cadd(acc[q], cscale(s, inv_dx[ix] * sy));
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+        const int pidx = threadIdx.x + q * kThreads;
+        if (pidx < nx * K) partial[((size_t)part * ny + iy) * nx * K + pidx] = acc[q];
+    }
+}
+
+__global__ void k_sum_parts(const float2* __restrict__ partial, int parts, size_t n, float scale,
+                            float2* __restrict__ out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int p = 0; p < parts; ++p) s = cadd(s, partial[p * n + i]);
+        out[i] = cscale(s, scale);
+    }
+}
+
+// Grouped subspace form ------------------------------------------------------
+// Y[g][j][k] = interp of spectrum k at group g's sample j.
+template <int G, int W>
+__global__ void k_interp_groups(const float2* __restrict__ spec, int K, const int4* __restrict__ grec,
+                                int total, float2* __restrict__ Y, float beta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    int j, mx0, my0;
+    float fx, fy;
+    unpack(grec[i], j, mx0, my0, fx, fy);
+    float wx[W], wy[W];
+    kb_weights<W>(fx, beta, wx);
+    kb_weights<W>(fy, beta, wy);
+    int col[W];
+#pragma unroll
+    for (int a = 0; a < W; ++a) col[a] = (mx0 + a) & (G - 1);
+    for (int k = 0; k < K; ++k) {
+        const float2* s = spec + (size_t)k * G * G;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const float2* r = s + (size_t)((my0 + b) & (G - 1)) * G;
+            float2 rs = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < W; ++a) rs = cadd(rs, cscale(r[col[a]], wx[a]));
+            acc = cadd(acc, cscale(rs, wy[b]));
+        }
+        Y[(size_t)i * K + k] = acc;
+    }
+}
+
+// y[t][j] = scale * sum_k conj(phi[t][k]) Y[g(t)][j][k] - b[t][j]
+__global__ void k_combine_fwd(const float2* __restrict__ Y, const float2* __restrict__ phi, int K,
+                              const int* __restrict__ group_of, int T, int ns, float scale,
+                              const float2* __restrict__ bsub, float2* __restrict__ y) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)T * ns) return;
+    const int t = (int)(i / ns), j = (int)(i - (size_t)t * ns);
+    const float2* yv = Y + ((size_t)group_of[t] * ns + j) * K;
+    const float2* p = phi + (size_t)t * K;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) acc = cadd(acc, cmulc(yv[k], p[k]));
+    acc = cscale(acc, scale);
+    if (bsub) acc = csub(acc, bsub[i]);
+    y[i] = acc;
+}
+
+// R[g][j][k] = sum_{t in g} phi[t][k] r[t][j]
+__global__ void k_combine_adj(const float2* __restrict__ r, const float2* __restrict__ phi, int K,
+                              const int* __restrict__ gf_off, const int* __restrict__ gf, int ngroups, int ns,
+                              float2* __restrict__ R) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)ngroups * ns) return;
+    const int g = (int)(i / ns), j = (int)(i - (size_t)g * ns);
+    float2 acc[16];
+    for (int k = 0; k < K; ++k) acc[k] = make_float2(0.f, 0.f);
+    for (int q = gf_off[g]; q < gf_off[g + 1]; ++q) {
+        const int t = gf[q];
+        const float2 v = r[(size_t)t * ns + j];
+        const float2* p = phi + (size_t)t * K;
+        for (int k = 0; k < K; ++k) acc[k] = cadd(acc[k], cmul(v, p[k]));
+    }
+    for (int k = 0; k < K; ++k) R[i * K + k] = acc[k];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static double psi_hat(double f, int W, double beta) {
+    const double z2 = beta * beta - (M_PI * W * f) * (M_PI * W * f);
+    if (z2 > 0) {
+        const double z = std::sqrt(z2);
+        return W * std::sinh(z) / z;
+    }
+    if (z2 < 0) {
+        const double z = std::sqrt(-z2);
+        return W * std::sin(z) / z;
+    }
+    return W;
+}
+
+template <typename K>
+static mrf_status set_smem(K kernel, size_t bytes) {
+    MRF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return MRF_OK;
+}
+
+static bool supported_grid(int g) { return g == 64 || g == 128 || g == 256 || g == 512; }
+
+// dispatch helpers ------------------------------------------------------------
+#define MRF_DISPATCH_G(G_, ...)                                                          \
+    switch (G_) {                                                                        \
+        case 64: { constexpr int GG = 64; __VA_ARGS__; break; }                          \
+        case 128: { constexpr int GG = 128; __VA_ARGS__; break; }                        \
+        case 256: { constexpr int GG = 256; __VA_ARGS__; break; }                        \
+        case 512: { constexpr int GG = 512; __VA_ARGS__; break; }                        \
+        default: MRF_REQUIRE(false, "unsupported grid size %d", G_);                     \
+    }
+
+#define MRF_DISPATCH_W(W_, ...)                                                          \
+    switch (W_) {                                                                        \
+        case 4: { constexpr int WW = 4; __VA_ARGS__; break; }                            \
+        case 6: { constexpr int WW = 6; __VA_ARGS__; break; }                            \
+        default: MRF_REQUIRE(false, "unsupported kernel width %d", W_);                  \
+    }
+
+static size_t rows_smem(int G) { return (size_t)(G + kThreads / (G / 8) * G) * sizeof(float2); }
+
+mrf_status launch_rows_fwd(const mrf_plan_s* p, const float2* src, int src_mode, int K, int nf, float2* h1,
+                           cudaStream_t s) {
+    const int G = p->gx;
+    const int rpc = kThreads / (G / 8);
+    dim3 grid((p->ny + rpc - 1) / rpc, nf);
+    const size_t sm = rows_smem(G);
+    MRF_DISPATCH_G(G, {
+        if (src_mode == 0) {
+            MRF_PROPAGATE(set_smem(k_rows_fwd<GG, 0>, sm));
+            k_rows_fwd<GG, 0><<<grid, kThreads, sm, s>>>(src, K, h1, p->inv_dx, p->inv_dy, p->nx, p->ny);
+        } else {
+            MRF_PROPAGATE(set_smem(k_rows_fwd<GG, 1>, sm));
+            k_rows_fwd<GG, 1><<<grid, kThreads, sm, s>>>(src, K, h1, p->inv_dx, p->inv_dy, p->nx, p->ny);
+        }
+    });
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+mrf_status launch_cols_interp(const mrf_plan_s* p, const float2* h1, float2* y, const float2* b, float scale,
+                              cudaStream_t s) {
+    const int G = p->gy;
+    dim3 grid(p->nstrips, p->T);
+    const size_t sm = (size_t)(G + G * (kStrip + p->W - 1)) * sizeof(float2);
+    MRF_DISPATCH_G(G, MRF_DISPATCH_W(p->W, {
+        MRF_PROPAGATE(set_smem(k_cols_interp<GG, WW>, sm));
+        k_cols_interp<GG, WW><<<grid, kThreads, sm, s>>>(h1, y, b, scale, p->fwd_rec, p->fwd_off, p->group_of,
+                                                         p->ny, p->ns, p->nstrips, p->beta);
+    }));
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+mrf_status launch_spread_cols(const mrf_plan_s* p, const float2* y, int src_mode, int K, int nf, float2* h1,
+                              cudaStream_t s) {
+    const int G = p->gy;
+    dim3 grid(p->nstrips, nf);
+    const size_t sm = (size_t)(G + G * kStrip) * sizeof(float2);
+    MRF_DISPATCH_G(G, MRF_DISPATCH_W(p->W, {
+        if (src_mode == 0) {
+            MRF_PROPAGATE(set_smem(k_spread_cols<GG, WW, 0>, sm));
+            k_spread_cols<GG, WW, 0><<<grid, kThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_off, p->group_of,
+                                                                p->ngroups, p->ny, p->ns, p->nstrips, p->beta);
+        } else {
+            MRF_PROPAGATE(set_smem(k_spread_cols<GG, WW, 1>, sm));
+            k_spread_cols<GG, WW, 1><<<grid, kThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_off, p->group_of,
+                                                                p->ngroups, p->ny, p->ns, p->nstrips, p->beta);
+        }
+    }));
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+mrf_status launch_rows_adj(const mrf_plan_s* p, const float2* h1, float2* dst, int dst_mode, int K, int nf,
+                           float scale, cudaStream_t s) {
+    const int G = p->gx;
+    const int rpc = kThreads / (G / 8);
+    dim3 grid((p->ny + rpc - 1) / rpc, nf);
+    const size_t sm = rows_smem(G);
+    MRF_DISPATCH_G(G, {
+        if (dst_mode == 0) {
+            MRF_PROPAGATE(set_smem(k_rows_adj<GG, 0>, sm));
+            k_rows_adj<GG, 0><<<grid, kThreads, sm, s>>>(h1, dst, K, scale, p->inv_dx, p->inv_dy, p->nx, p->ny);
+        } else {
+            MRF_PROPAGATE(set_smem(k_rows_adj<GG, 1>, sm));
+            k_rows_adj<GG, 1><<<grid, kThreads, sm, s>>>(h1, dst, K, scale, p->inv_dx, p->inv_dy, p->nx, p->ny);
+        }
+    });
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+static void free_plan(mrf_plan_s* p) {
+    if (!p) return;
+    void* ptrs[] = {p->inv_dx, p->inv_dy, p->fwd_rec, p->fwd_off, p->adj_rec, p->adj_off, p->grec,
+                    p->group_of, p->gf_off, p->gf, p->h1, p->sub_h1, p->sub_spec, p->sub_Y, p->sub_R,
+                    p->sub_partial};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+mrf_status ensure_subspace_workspace(mrf_plan_s* p, int K) {
+    if (p->sub_K >= K) return MRF_OK;
+    const int Kc = 16;
+    if (p->sub_h1) { cudaFree(p->sub_h1); cudaFree(p->sub_spec); cudaFree(p->sub_Y); cudaFree(p->sub_R); cudaFree(p->sub_partial); }
+    p->sub_h1 = p->sub_spec = p->sub_Y = p->sub_R = p->sub_partial = nullptr;
+    MRF_CUDA(cudaMalloc(&p->sub_h1, sizeof(float2) * (size_t)Kc * p->ny * p->gx));
+    MRF_CUDA(cudaMalloc(&p->sub_spec, sizeof(float2) * (size_t)Kc * p->gy * p->gx));
+    MRF_CUDA(cudaMalloc(&p->sub_Y, sizeof(float2) * (size_t)Kc * p->ngroups * p->ns));
+    MRF_CUDA(cudaMalloc(&p->sub_R, sizeof(float2) * (size_t)Kc * p->ngroups * p->ns));
+    MRF_CUDA(cudaMalloc(&p->sub_partial, sizeof(float2) * (size_t)Kc * p->parts * p->ny * p->nx));
+    p->sub_K = Kc;
+    return MRF_OK;
+}
+
+}  // namespace mrf
+
+using namespace mrf;
+
+extern "C" mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int T, int ns, const float* traj, int os,
+                                     int W, mrf_stream stream) {
+    MRF_REQUIRE(out != nullptr, "mrf_nufft_plan: out is NULL");
+    *out = nullptr;
+    MRF_REQUIRE(traj != nullptr, "mrf_nufft_plan: traj is NULL");
+    MRF_REQUIRE(os == 2, "mrf_nufft_plan: os must be 2 (got %d)", os);
+    MRF_REQUIRE(W == 4 || W == 6, "mrf_nufft_plan: kb_width must be 4 or 6 (got %d)", W);
+    MRF_REQUIRE(nx > 0 && ny > 0 && nx % 2 == 0 && ny % 2 == 0, "mrf_nufft_plan: nx, ny must be even and > 0");
+    MRF_REQUIRE(nx == ny, "mrf_nufft_plan: square images only (nx %d, ny %d)", nx, ny);
+    MRF_REQUIRE(supported_grid(os * nx) && supported_grid(os * ny),
+                "mrf_nufft_plan: os*nx and os*ny must be in {64,128,256,512} (got %d, %d)", os * nx, os * ny);
+    MRF_REQUIRE(T >= 1 && ns >= 1 && ns < (1 << 24), "mrf_nufft_plan: bad nframes/ns (%d, %d)", T, ns);
+    cudaStream_t s = as_stream(stream);
+    auto* p = new mrf_plan_s();
+    p->nx = nx; p->ny = ny; p->T = T; p->ns = ns; p->os = os; p->W = W;
+    p->gx = os * nx; p->gy = os * ny;
+    p->beta = (float)(M_PI * std::sqrt((W / (double)os) * (W / (double)os) * (os - 0.5) * (os - 0.5) - 0.8));
+    const double beta = M_PI * std::sqrt((W / (double)os) * (W / (double)os) * (os - 0.5) * (os - 0.5) - 0.8);
+    p->nstrips = p->gx / kStrip;
+
+    std::vector<float> h((size_t)T * ns * 2);
+    cudaError_t e = cudaMemcpyAsync(h.data(), traj, h.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        set_error("mrf_nufft_plan: reading traj failed: %s", cudaGetErrorString(e));
+        return MRF_ECUDA;
+    }
+    for (size_t i = 0; i < h.size(); ++i) {
+        if (!(std::fabs(h[i]) <= 3.2f)) {
+            free_plan(p);
+            set_error("mrf_nufft_plan: trajectory value %g at %zu outside [-pi, pi]", (double)h[i], i);
+            return MRF_EINVAL;
+        }
+    }
+    // group frames with identical sample positions
+    std::vector<int> group_of(T), rep;
+    std::unordered_map<uint64_t, std::vector<int>> by_hash;
+    const size_t fbytes = (size_t)ns * 2 * sizeof(float);
+    for (int t = 0; t < T; ++t) {
+        const unsigned char* d = reinterpret_cast<const unsigned char*>(h.data() + (size_t)t * ns * 2);
+        uint64_t hv = 1469598103934665603ull;
+        for (size_t i = 0; i < fbytes; ++i) hv = (hv ^ d[i]) * 1099511628211ull;
+        int found = -1;
+        for (int g : by_hash[hv])
+            if (std::memcmp(h.data() + (size_t)rep[g] * ns * 2, d, fbytes) == 0) { found = g; break; }
+        if (found < 0) {
+            found = (int)rep.size();
+            rep.push_back(t);
+            by_hash[hv].push_back(found);
+        }
+        group_of[t] = found;
+    }
+    const int NG = (int)rep.size();
+    p->ngroups = NG;
+    // per-sample records (host double precision decides the nodes)
+    const int S = p->nstrips;
+    std::vector<int4> grec((size_t)NG * ns);
+    std::vector<int> fcount((size_t)NG * S, 0), acount((size_t)NG * S, 0);
+    auto strip_of = [&](int col) { return col / kStrip; };
+    for (int g = 0; g < NG; ++g) {
+        const float* kt = h.data() + (size_t)rep[g] * ns * 2;
+        for (int j = 0; j < ns; ++j) {
+            double ux = kt[2 * j] * p->gx / (2 * M_PI), uy = kt[2 * j + 1] * p->gy / (2 * M_PI);
+            if (ux < 0) ux += p->gx;
+            if (uy < 0) uy += p->gy;
+            const long mx = (long)std::floor(ux - W / 2.0) + 1, my = (long)std::floor(uy - W / 2.0) + 1;
+            const float fx = (float)(ux - mx), fy = (float)(uy - my);
+            const int mxw = (int)(((mx % p->gx) + p->gx) % p->gx), myw = (int)(((my % p->gy) + p->gy) % p->gy);
+            int4 r;
+            r.x = j;
+            r.y = mxw | (myw << 16);
+            std::memcpy(&r.z, &fx, 4);
+            std::memcpy(&r.w, &fy, 4);
+            grec[(size_t)g * ns + j] = r;
+            const int s1 = strip_of(mxw), s2 = strip_of((mxw + W - 1) % p->gx);
+            fcount[(size_t)g * S + s1]++;
+            acount[(size_t)g * S + s1]++;
+            if (s2 != s1) acount[(size_t)g * S + s2]++;
+        }
+    }
+    std::vector<int> foff((size_t)NG * S + 1, 0), aoff((size_t)NG * S + 1, 0);
+    for (size_t i = 0; i < (size_t)NG * S; ++i) {
+        foff[i + 1] = foff[i] + fcount[i];
+        aoff[i + 1] = aoff[i] + acount[i];
+    }
+    std::vector<int4> frec(foff.back()), arec(aoff.back());
+    std::vector<int> fpos(foff.begin(), foff.end() - 1), apos(aoff.begin(), aoff.end() - 1);
+    for (int g = 0; g < NG; ++g)
+        for (int j = 0; j < ns; ++j) {
+            const int4 r = grec[(size_t)g * ns + j];
+            const int mxw = r.y & 0xffff;
+            const int s1 = strip_of(mxw), s2 = strip_of((mxw + W - 1) % p->gx);
+            frec[fpos[(size_t)g * S + s1]++] = r;
+            arec[apos[(size_t)g * S + s1]++] = r;
+            if (s2 != s1) arec[apos[(size_t)g * S + s2]++] = r;
+        }
+    // frames of each group (CSR)
+    std::vector<int> gfoff(NG + 1, 0), gf(T);
+    for (int t = 0; t < T; ++t) gfoff[group_of[t] + 1]++;
+    for (int g = 0; g < NG; ++g) gfoff[g + 1] += gfoff[g];
+    {
+        std::vector<int> pos(gfoff.begin(), gfoff.end() - 1);
+        for (int t = 0; t < T; ++t) gf[pos[group_of[t]]++] = t;
+    }
+    std::vector<float> idx_(nx), idy_(ny);
+    for (int i = 0; i < nx; ++i) idx_[i] = (float)(1.0 / psi_hat((i - nx / 2) / (double)p->gx, W, beta));
+    for (int i = 0; i < ny; ++i) idy_[i] = (float)(1.0 / psi_hat((i - ny / 2) / (double)p->gy, W, beta));
+    // frame parts of the subspace adjoint reduction
+    {
+        const int fpc = kThreads / (p->gx / 8);
+        int parts = std::max(1, (4 * 152 + ny - 1) / ny);
+        parts = std::min(parts, (T + fpc - 1) / fpc);
+        int per = (T + parts - 1) / parts;
+        per = (per + fpc - 1) / fpc * fpc;
+        p->frames_per_part = per;
+        p->parts = (T + per - 1) / per;
+    }
+
+#define ALLOC_COPY(dst, vec)                                                                         \
+    do {                                                                                             \
+        e = cudaMalloc(&dst, sizeof(vec[0]) * std::max<size_t>(vec.size(), 1));                      \
+        if (e == cudaSuccess && !vec.empty())                                                        \
+            e = cudaMemcpy(dst, vec.data(), sizeof(vec[0]) * vec.size(), cudaMemcpyHostToDevice);    \
+        if (e != cudaSuccess) goto fail;                                                             \
+    } while (0)
+    ALLOC_COPY(p->inv_dx, idx_);
+    ALLOC_COPY(p->inv_dy, idy_);
+    ALLOC_COPY(p->fwd_rec, frec);
+    ALLOC_COPY(p->fwd_off, foff);
+    ALLOC_COPY(p->adj_rec, arec);
+    ALLOC_COPY(p->adj_off, aoff);
+    ALLOC_COPY(p->grec, grec);
+    ALLOC_COPY(p->group_of, group_of);
+    ALLOC_COPY(p->gf_off, gfoff);
+    ALLOC_COPY(p->gf, gf);
+#undef ALLOC_COPY
+    e = cudaMalloc(&p->h1, sizeof(float2) * (size_t)T * ny * p->gx);
+    if (e != cudaSuccess) goto fail;
+    *out = p;
+    return MRF_OK;
+fail:
+    free_plan(p);
+    cudaGetLastError();
+    set_error("mrf_nufft_plan: device allocation/copy failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MRF_ENOMEM : MRF_ECUDA;
+}
+
+extern "C" mrf_status mrf_nufft_destroy(mrf_plan p) {
+    free_plan(p);
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_nufft_forward(mrf_plan p, const mrf_c64* x, mrf_c64* y, mrf_stream stream) {
+    MRF_REQUIRE(p && x && y, "mrf_nufft_forward: NULL argument");
+    cudaStream_t s = as_stream(stream);
+    MRF_PROPAGATE(launch_rows_fwd(p, reinterpret_cast<const float2*>(x), 0, 0, p->T, p->h1, s));
+    MRF_PROPAGATE(launch_cols_interp(p, p->h1, reinterpret_cast<float2*>(y), nullptr, 1.0f, s));
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_nufft_adjoint(mrf_plan p, const mrf_c64* y, mrf_c64* x, mrf_stream stream) {
+    MRF_REQUIRE(p && x && y, "mrf_nufft_adjoint: NULL argument");
+    cudaStream_t s = as_stream(stream);
+    MRF_PROPAGATE(launch_spread_cols(p, reinterpret_cast<const float2*>(y), 0, 0, p->T, p->h1, s));
+    MRF_PROPAGATE(launch_rows_adj(p, p->h1, reinterpret_cast<float2*>(x), 0, 0, p->T, 1.0f, s));
+    return MRF_OK;
+}
+
+namespace mrf {
+mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* phi, int K, float scale,
+                            const float2* b, float2* y, int mode, cudaStream_t s) {
+    MRF_REQUIRE(K >= 1 && K <= 16, "subspace rank K must be in [1, 16] (got %d)", K);
+    MRF_REQUIRE(mode == 0 || mode == 1, "subspace mode must be 0 or 1 (got %d)", mode);
+    MRF_REQUIRE(p->nx <= 256, "subspace forms need nx <= 256");
+    if (mode == 0) {
+        const int G = p->gx;
+        const int fpc = kThreads / (G / 8);
+        dim3 grid(p->ny, (p->T + fpc - 1) / fpc);
+        const size_t sm = (size_t)(G + fpc * G + p->nx * K + fpc * K) * sizeof(float2);
+        MRF_DISPATCH_G(G, {
+            MRF_PROPAGATE(set_smem(k_rows_fwd_expand<GG>, sm));
+            k_rows_fwd_expand<GG><<<grid, kThreads, sm, s>>>(alpha, phi, K, p->T, p->h1, p->inv_dx, p->inv_dy,
+                                                             p->nx, p->ny);
+        });
+        MRF_LAUNCHED();
+        return launch_cols_interp(p, p->h1, y, b, scale, s);
+    }
+    MRF_PROPAGATE(ensure_subspace_workspace(p, K));
+    MRF_PROPAGATE(launch_rows_fwd(p, alpha, 1, K, K, p->sub_h1, s));
+    {
+        const int G = p->gy;
+        dim3 grid(p->nstrips, K);
+        const size_t sm = (size_t)(G + G * kStrip) * sizeof(float2);
+        MRF_DISPATCH_G(G, {
+            MRF_PROPAGATE(set_smem(k_cols_store<GG>, sm));
+            k_cols_store<GG><<<grid, kThreads, sm, s>>>(p->sub_h1, p->sub_spec, p->ny);
+        });
+        MRF_LAUNCHED();
+    }
+    {
+        const int total = p->ngroups * p->ns;
+        MRF_DISPATCH_G(p->gx, MRF_DISPATCH_W(p->W, {
+            k_interp_groups<GG, WW><<<(total + 255) / 256, 256, 0, s>>>(p->sub_spec, K, p->grec, total, p->sub_Y,
+                                                                        p->beta);
+        }));
+        MRF_LAUNCHED();
+    }
+    const size_t n = (size_t)p->T * p->ns;
+    k_combine_fwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->sub_Y, phi, K, p->group_of, p->T, p->ns, scale,
+                                                               b, y);
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, int K, float scale,
+                            float2* alpha_out, int mode, cudaStream_t s) {
+    MRF_REQUIRE(K >= 1 && K <= 16, "subspace rank K must be in [1, 16] (got %d)", K);
+    MRF_REQUIRE(mode == 0 || mode == 1, "subspace mode must be 0 or 1 (got %d)", mode);
+    MRF_REQUIRE(p->nx <= 256, "subspace forms need nx <= 256");
+    MRF_PROPAGATE(ensure_subspace_workspace(p, K));
+    if (mode == 0) {
+        MRF_PROPAGATE(launch_spread_cols(p, y, 0, 0, p->T, p->h1, s));
+        const int G = p->gx;
+        const int fpc = kThreads / (G / 8);
+        dim3 grid(p->ny, p->parts);
+        const size_t sm = (size_t)(G + fpc * G + fpc * K) * sizeof(float2);
+        MRF_DISPATCH_G(G, {
+            MRF_PROPAGATE(set_smem(k_rows_adj_reduce<GG>, sm));
+            k_rows_adj_reduce<GG><<<grid, kThreads, sm, s>>>(p->h1, phi, K, p->T, p->frames_per_part,
+                                                             p->sub_partial, p->inv_dx, p->inv_dy, p->nx, p->ny);
+        });
+        MRF_LAUNCHED();
+        const size_t n = (size_t)p->ny * p->nx * K;
+        k_sum_parts<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(p->sub_partial, p->parts, n,
+                                                                                        scale, alpha_out);
+        MRF_LAUNCHED();
+        return MRF_OK;
+    }
+    {
+        const size_t n = (size_t)p->ngroups * p->ns;
+        k_combine_adj<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(y, phi, K, p->gf_off, p->gf, p->ngroups, p->ns,
+                                                                   p->sub_R);
+        MRF_LAUNCHED();
+    }
+    MRF_PROPAGATE(launch_spread_cols(p, p->sub_R, 1, K, K, p->sub_h1, s));
+    MRF_PROPAGATE(launch_rows_adj(p, p->sub_h1, alpha_out, 1, K, K, scale, s));
+    return MRF_OK;
+}
+}  // namespace mrf
+
+extern "C" mrf_status mrf_nufft_forward_subspace(mrf_plan p, const mrf_c64* alpha, const mrf_c64* phi, int K,
+                                                 float scale, const mrf_c64* b, mrf_c64* y, int mode,
+                                                 mrf_stream stream) {
+    MRF_REQUIRE(p && alpha && phi && y, "mrf_nufft_forward_subspace: NULL argument");
+    return subspace_forward(p, reinterpret_cast<const float2*>(alpha), reinterpret_cast<const float2*>(phi), K,
+                            scale, reinterpret_cast<const float2*>(b), reinterpret_cast<float2*>(y), mode,
+                            as_stream(stream));
+}
+
+extern "C" mrf_status mrf_nufft_adjoint_subspace(mrf_plan p, const mrf_c64* y, const mrf_c64* phi, int K,
+                                                 float scale, mrf_c64* alpha_out, int mode, mrf_stream stream) {
+    MRF_REQUIRE(p && y && phi && alpha_out, "mrf_nufft_adjoint_subspace: NULL argument");
+    return subspace_adjoint(p, reinterpret_cast<const float2*>(y), reinterpret_cast<const float2*>(phi), K, scale,
+                            reinterpret_cast<float2*>(alpha_out), mode, as_stream(stream));
+}

@@ -1,0 +1,37 @@
+// NUFFT plan layout shared by the NUFFT and reconstruction translation units.
+#pragma once
+#include "common.h"
+
+struct mrf_plan_s {
+    int nx = 0, ny = 0, T = 0, ns = 0, os = 2, W = 4;
+    int gx = 0, gy = 0;           // oversampled grid
+    int nstrips = 0;              // gx / 32 column strips
+    int ngroups = 0;              // distinct per-frame trajectories
+    float beta = 0.f;             // Kaiser-Bessel shape
+    int parts = 1, frames_per_part = 1;  // frame split of the subspace adjoint reduction
+    float* inv_dx = nullptr;      // [nx] 1 / psi_hat(x)
+    float* inv_dy = nullptr;      // [ny]
+    int4* fwd_rec = nullptr;      // samples by (group, strip of first x node)
+    int* fwd_off = nullptr;       // [ngroups * nstrips + 1]
+    int4* adj_rec = nullptr;      // samples by (group, every strip they touch)
+    int* adj_off = nullptr;       // [ngroups * nstrips + 1]
+    int4* grec = nullptr;         // samples in (group, index) order
+    int* group_of = nullptr;      // [T]
+    int* gf_off = nullptr;        // [ngroups + 1] frames of each group (CSR)
+    int* gf = nullptr;            // [T]
+    float2* h1 = nullptr;         // [T][ny][gx] rows transformed along x
+    // subspace workspace (allocated on first use, for K <= 16)
+    int sub_K = 0;
+    float2* sub_h1 = nullptr;     // [16][ny][gx]
+    float2* sub_spec = nullptr;   // [16][gy][gx]
+    float2* sub_Y = nullptr;      // [ngroups][ns][16]
+    float2* sub_R = nullptr;      // [ngroups][ns][16]
+    float2* sub_partial = nullptr;  // [parts][ny][nx][16]
+};
+
+namespace mrf {
+mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* phi, int K, float scale,
+                            const float2* b, float2* y, int mode, cudaStream_t s);
+mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, int K, float scale,
+                            float2* alpha_out, int mode, cudaStream_t s);
+}  // namespace mrf
