@@ -120,7 +120,7 @@ mrf_status mrf_epg_fisp(const float* t1t2, int m, const float* fa_deg, const flo
 /* Temporal subspace of a dictionary (Eq. 14: the orthonormal basis d of
  * P_S, approximated from D).  phi (dev [T][K]) receives the top-K right
  * singular vectors of D (dev [m][T]), computed by randomised block subspace
- * iteration on the Gram matrix D^H D (Yang et al., cited in Sec. I);
+ * iteration on D^H D (Yang et al., cited in Sec. I) with FP64 accumulation;
  * compressed (dev [m][K], nullable) receives d_m Phi and norm2 (dev [m],
  * nullable) receives ||d_m||^2 of the full atoms.  Needs 1 <= K <= 16,
  * K + 8 <= T <= 4096.  Allocates and frees its own workspace; synchronises

@@ -8,7 +8,12 @@ Q^*(Q(X) L).
 
 Readings where the paper is silent:
 * features: each voxel contributes (T1 / T1max, T2 / T2max), the maxima
-  taken over the dictionary's look-up table, so both maps weigh alike;
+  taken over the dictionary's look-up table, so both maps weigh alike; the
+  ratios are rounded (half to even) to 12-bit fixed point, q = rint(4096 T /
+  Tmax), and squared distances are summed exactly in integers.  Matched maps
+  are piecewise constant, so many patch distances tie exactly; exact integer
+  distances make every device break those ties the same way (lowest index).
+  12 bits resolve T1 to ~1 ms at 4000 ms, finer than any dictionary grid;
 * graph: each patch keeps its k nearest patches (self excluded, ties to the
   lower index) and W = (K + K^T) / 2 with K_ij = w_ij on those edges, which
   makes W symmetric as Eq. 10 requires (Eq. 9 prints the dense graph);
@@ -22,22 +27,33 @@ from __future__ import annotations
 import numpy as np
 
 
+QSCALE = 4096          # fixed-point scale of the features
+
+
 def features(t1map, t2map, grid, t1max, t2max):
-    """Patch vectors [Np, 2 p^2] from parameter maps [ny, nx]."""
-    m = np.stack([np.asarray(t1map, np.float64) / t1max,
-                  np.asarray(t2map, np.float64) / t2max], axis=-1)   # [ny, nx, 2]
-    return grid.extract(m).reshape(grid.count, -1)
+    """Integer patch vectors [Np, 2 p^2] (fixed point of T / Tmax) from maps [ny, nx]."""
+    m = np.stack([np.rint(np.asarray(t1map, np.float64) / float(t1max) * QSCALE),
+                  np.rint(np.asarray(t2map, np.float64) / float(t2max) * QSCALE)], axis=-1)
+    return grid.extract(m.astype(np.int64)).reshape(grid.count, -1)
 
 
 def knn(F, k):
-    """(nbr [Np, k] int, d2 [Np, k]) of the k nearest rows, self excluded."""
-    F = np.asarray(F, np.float64)
+    """(nbr [Np, k] int, d2 [Np, k]) of the k nearest rows, self excluded.
+
+    Integer features give exact integer distances; float features are summed in
+    float64."""
+    F = np.asarray(F)
+    exact = np.issubdtype(F.dtype, np.integer)
+    F = F.astype(np.int64 if exact else np.float64)
     n = F.shape[0]
     nbr = np.empty((n, k), dtype=np.int64)
-    d2 = np.empty((n, k), dtype=np.float64)
+    d2 = np.empty((n, k), dtype=F.dtype)
     for i in range(n):
         di = np.sum((F - F[i]) ** 2, axis=1)
-        di[i] = np.inf
+        if exact:
+            di[i] = np.iinfo(np.int64).max
+        else:
+            di[i] = np.inf
         order = np.argsort(di, kind="stable")[:k]
         nbr[i], d2[i] = order, di[order]
     return nbr, d2
@@ -64,9 +80,12 @@ def laplacian(W):
 
 
 def build(t1map, t2map, grid, k, t1max, t2max):
-    """Laplacian [Np, Np] of the kNN patch graph of the maps, and sigma^2."""
+    """Laplacian [Np, Np] of the kNN patch graph of the maps, and sigma^2.
+
+    Distances are reported in units of (T / Tmax)^2 (integer distance / 4096^2)."""
     F = features(t1map, t2map, grid, t1max, t2max)
-    nbr, d2 = knn(F, k)
+    nbr, d2i = knn(F, k)
+    d2 = d2i.astype(np.float64) / float(QSCALE * QSCALE)
     s2 = sigma2(d2)
     return laplacian(adjacency(nbr, d2, s2)), s2
 

@@ -35,3 +35,8 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
 mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, int K, float scale,
                             float2* alpha_out, int mode, cudaStream_t s);
 }  // namespace mrf
+
+namespace mrf {
+// allocate the subspace workspace of a plan (idempotent; K <= 16)
+mrf_status ensure_subspace_workspace(mrf_plan_s* p, int K);
+}  // namespace mrf

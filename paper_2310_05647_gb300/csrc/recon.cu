@@ -1,19 +1,904 @@
-// Algorithm 1 (MS-LLR) loop -- placeholder until the loop kernels land.
-#include "common.h"
+// Algorithm 1 (MS-LLR) with the iterate held in the temporal subspace,
+// X = alpha Phi^H, alpha [N][K] (N = nx * ny voxels, row-major, K contiguous).
+//
+// Per iteration (all on the stream, no host round trip unless costs are read):
+//   grad  = (A/a)^H r                        r = (A/a) X - b~ from the last pass
+//   QL    = Q(X) L   per patch, and  Tr     (graph term of Eq. 12)
+//   alpha = (alpha - mu (grad + lambda1 Q^*(QL)) + c Q^*(P)) / (1 + c cnt)   (Eq. 12 + 19)
+//   r     = (A/a) X - b~                     (data residual of the new iterate)
+//   P     = SVT_{1/beta}(Q_i(X)) per patch   (Eq. 18, used by the next pass;
+//                                             its singular values give the
+//                                             nuclear norms of the cost)
+//   cost  = 1/2 ||r||^2 + lambda1 Tr(Q L Q^H) + lambda2 sum ||Q_i||_*
+//   maps  = Phi_D(X)                         (Eq. 5, compressed atoms)
+//   L     = D - W of the k-nearest-patch graph of the maps (Eq. 7-10),
+//   lambda1 = lambda1^0 / max(L)
+// P_S is the identity on coefficient images, Q^*(Q(X) L) commutes with P_S,
+// and the singular values of Q_i(X) (p^2 x T) equal those of Q_i(alpha)
+// (p^2 x K) because Phi has orthonormal columns.
+#include <algorithm>
+#include <cmath>
+#include <vector>
 
-extern "C" mrf_status mrf_recon_create(mrf_recon* out, mrf_plan, const mrf_recon_params*, const mrf_c64*, int,
-                                       const mrf_c64*, const float*, const float*, int, const mrf_c64*,
-                                       mrf_stream) {
-    if (out) *out = nullptr;
-    mrf::set_error("mrf_recon_create: not built yet");
-    return MRF_EUNSUPPORTED;
+#include "common.h"
+#include "match.h"
+#include "nufft_plan.h"
+
+namespace mrf {
+
+struct PatchGeom {
+    int n, p, s, cnt;   // square image side, patch side, stride, patches per axis
+    __host__ __device__ int origin(int i) const { return min(i * s, n - p); }
+    __host__ __device__ int count() const { return cnt * cnt; }
+};
+
+static PatchGeom make_geom(int n, int p, int s) {
+    PatchGeom g;
+    g.n = n; g.p = p; g.s = s;
+    g.cnt = (n - p) / s + 1 + (((n - p) % s) ? 1 : 0);
+    return g;
 }
-extern "C" mrf_status mrf_recon_iter(mrf_recon, int, double*, mrf_stream) { return MRF_EUNSUPPORTED; }
-extern "C" mrf_status mrf_recon_maps(mrf_recon, float*, float*, float*, int*, mrf_stream) { return MRF_EUNSUPPORTED; }
-extern "C" mrf_status mrf_recon_alpha(mrf_recon, mrf_c64*, mrf_stream) { return MRF_EUNSUPPORTED; }
-extern "C" mrf_status mrf_recon_info(mrf_recon, double*, double*, double*, double*, mrf_stream) { return MRF_EUNSUPPORTED; }
-extern "C" mrf_status mrf_recon_destroy(mrf_recon) { return MRF_OK; }
-extern "C" mrf_status mrf_dict_subspace(const mrf_c64*, int, int, int, mrf_c64*, mrf_c64*, float*, mrf_stream) {
-    mrf::set_error("mrf_dict_subspace: not built yet");
-    return MRF_EUNSUPPORTED;
+
+// --------------------------------------------------------------------------
+// small reductions
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum over the block, result valid in thread 0
+__device__ double block_sum(double v) {
+    __shared__ double red[32];
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+        v = warp_sum(v);
+    }
+    __syncthreads();
+    return v;
+}
+
+__global__ void k_norm2_acc(const float2* __restrict__ x, size_t n, double* __restrict__ acc) {
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        s += (double)cabs2(x[i]);
+    s = block_sum(s);
+    if (threadIdx.x == 0) atomicAdd(acc, s);
+}
+
+// re/im of sum conj(a) b
+__global__ void k_dot_acc(const float2* __restrict__ a, const float2* __restrict__ b, size_t n,
+                          double* __restrict__ acc) {
+    double re = 0.0, im = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 p = cconjmul(a[i], b[i]);
+        re += p.x;
+        im += p.y;
+    }
+    re = block_sum(re);
+    im = block_sum(im);
+    if (threadIdx.x == 0) { atomicAdd(acc, re); atomicAdd(acc + 1, im); }
+}
+
+__global__ void k_scale(float2* __restrict__ x, size_t n, float s) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = cscale(x[i], s);
+}
+
+__global__ void k_scale_copy(const float2* __restrict__ x, size_t n, float s, float2* __restrict__ y) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = cscale(x[i], s);
+}
+
+__global__ void k_fill(float2* __restrict__ x, size_t n, float2 v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+__global__ void k_max(const float* __restrict__ v, int n, float* __restrict__ out) {
+    __shared__ float red[32];
+    float m = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, v[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) *out = m;
+    }
+}
+
+static unsigned nblk(size_t n, int t = 256) { return (unsigned)std::min<size_t>((n + t - 1) / t, 4096); }
+
+// --------------------------------------------------------------------------
+// patch graph (Eq. 7-10)
+// --------------------------------------------------------------------------
+// Patch features: F[i][2 (py p + px) + c] = rint(4096 T / Tmax) of the patch's
+// voxels (12-bit fixed point of T1 / T1max and T2 / T2max, half to even).
+// Squared distances of these integers are exact (< 2^32 for p <= 11), so
+// the many exact ties of piecewise-constant maps break to the lower index on
+// every device.
+constexpr double kQScale = 4096.0;
+
+__global__ void k_features(const float* __restrict__ t1t2, PatchGeom g, double t1max, double t2max,
+                           int* __restrict__ F) {
+    const int pp = g.p * g.p;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= g.count() * pp) return;
+    const int i = e / pp, q = e - i * pp;
+    const int py = q / g.p, px = q - py * g.p;
+    const int y = g.origin(i / g.cnt) + py, x = g.origin(i % g.cnt) + px;
+    const size_t v = (size_t)y * g.n + x;
+    F[(size_t)e * 2] = (int)rint((double)t1t2[2 * v] / t1max * kQScale);
+    F[(size_t)e * 2 + 1] = (int)rint((double)t1t2[2 * v + 1] / t2max * kQScale);
+}
+
+__device__ __forceinline__ bool less_dj(unsigned d, int j, unsigned d2, int j2) {
+    return d < d2 || (d == d2 && j < j2);
+}
+
+// k nearest patches by squared distance (self excluded, ties to the lower
+// index).  Block: 32 query patches x 8 threads; each thread scans every 8th
+// candidate of each 64-candidate tile and keeps its KMAX best; the 8 lists of a
+// query are merged with shuffles.
+template <int KMAX>
+__global__ void __launch_bounds__(256) k_knn(const int* __restrict__ F, int np, int FD, int knn,
+                                             int* __restrict__ nbr, unsigned* __restrict__ d2out) {
+    extern __shared__ int shf[];
+    const int ld = FD + 1;
+    int* Fq = shf;              // [32][ld]
+    int* Fc = shf + 32 * ld;    // [64][ld]
+    const int ql = threadIdx.x >> 3, sub = threadIdx.x & 7;
+    const int q = blockIdx.x * 32 + ql;
+    for (int i = threadIdx.x; i < 32 * FD; i += blockDim.x) {
+        const int r = i / FD, c = i - r * FD;
+        const int qq = blockIdx.x * 32 + r;
+        Fq[r * ld + c] = qq < np ? F[(size_t)qq * FD + c] : 0;
+    }
+    unsigned bd[KMAX];
+    int bj[KMAX];
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) { bd[i] = 0xffffffffu; bj[i] = 0x7fffffff; }
+    for (int c0 = 0; c0 < np; c0 += 64) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 64 * FD; i += blockDim.x) {
+            const int r = i / FD, c = i - r * FD;
+            Fc[r * ld + c] = c0 + r < np ? F[(size_t)(c0 + r) * FD + c] : 0;
+        }
+        __syncthreads();
+        if (q < np) {
+            for (int c = sub; c < 64; c += 8) {
+                const int j = c0 + c;
+                if (j >= np || j == q) continue;
+                const int* a = Fq + ql * ld;
+                const int* b = Fc + c * ld;
+                unsigned d = 0u;
+                for (int t = 0; t < FD; ++t) {
+                    const int df = a[t] - b[t];
+                    d += (unsigned)(df * df);
+                }
+                if (less_dj(d, j, bd[KMAX - 1], bj[KMAX - 1])) {
+                    bd[KMAX - 1] = d;
+                    bj[KMAX - 1] = j;
+#pragma unroll
+                    for (int i = KMAX - 1; i > 0; --i) {
+                        if (less_dj(bd[i], bj[i], bd[i - 1], bj[i - 1])) {
+                            const unsigned td = bd[i]; bd[i] = bd[i - 1]; bd[i - 1] = td;
+                            const int tj = bj[i]; bj[i] = bj[i - 1]; bj[i - 1] = tj;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // merge the 8 sorted lists of this query
+    for (int r = 0; r < knn; ++r) {
+        unsigned d = bd[0];
+        int j = bj[0];
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            const unsigned d2 = __shfl_xor_sync(0xffffffffu, d, o);
+            const int j2 = __shfl_xor_sync(0xffffffffu, j, o);
+            if (less_dj(d2, j2, d, j)) { d = d2; j = j2; }
+        }
+        if (bj[0] == j) {
+#pragma unroll
+            for (int i = 0; i < KMAX - 1; ++i) { bd[i] = bd[i + 1]; bj[i] = bj[i + 1]; }
+            bd[KMAX - 1] = 0xffffffffu;
+            bj[KMAX - 1] = 0x7fffffff;
+        }
+        if (sub == 0 && q < np) {
+            nbr[(size_t)q * knn + r] = j;
+            d2out[(size_t)q * knn + r] = d;
+        }
+    }
+}
+
+// sigma^2 = median of the non-zero kNN squared distances (1 if none), by a
+// 4 x 8-bit radix select on the exact integer distances; reported in units of
+// (T / Tmax)^2 (integer / 4096^2).  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_median_nonzero(const unsigned* __restrict__ v, int n,
+                                                         float* __restrict__ sigma2) {
+    __shared__ unsigned hist[256];
+    __shared__ unsigned s_prefix, s_rank;
+    __shared__ int s_nz;
+    if (threadIdx.x == 0) s_nz = 0;
+    __syncthreads();
+    int nz = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) nz += v[i] > 0u;
+    atomicAdd(&s_nz, nz);
+    __syncthreads();
+    const int total = s_nz;
+    if (total == 0) {
+        if (threadIdx.x == 0) *sigma2 = 1.0f;
+        return;
+    }
+    unsigned vals[2];
+    for (int which = 0; which < 2; ++which) {
+        const unsigned rank = which == 0 ? (unsigned)(total - 1) / 2 : (unsigned)total / 2;
+        unsigned prefix = 0, mask = 0;
+        if (threadIdx.x == 0) s_rank = rank;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const unsigned b = v[i];
+                if (b == 0u) continue;
+                if ((b & mask) == prefix) atomicAdd(&hist[(b >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned r = s_rank, c = 0;
+                int bucket = 0;
+                for (; bucket < 255; ++bucket) {
+                    if (c + hist[bucket] > r) break;
+                    c += hist[bucket];
+                }
+                s_rank = r - c;
+                s_prefix = prefix | ((unsigned)bucket << shift);
+            }
+            __syncthreads();
+            prefix = s_prefix;
+            mask |= 255u << shift;
+        }
+        vals[which] = prefix;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *sigma2 = (float)(0.5 * ((double)vals[0] + (double)vals[1]) / (kQScale * kQScale));
+}
+
+// w = exp(-d2 / sigma^2) on the kNN edges; in-degree counts of the reverse graph
+__global__ void k_edge_weights(const int* __restrict__ nbr, const unsigned* __restrict__ d2, int ne,
+                               const float* __restrict__ sigma2, float* __restrict__ w, int* __restrict__ rcnt) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    w[e] = expf(-((float)d2[e] * (float)(1.0 / (kQScale * kQScale))) / *sigma2);
+    atomicAdd(&rcnt[nbr[e]], 1);
+}
+
+// exclusive scan of n counts (one block)
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cnt, int n, int* __restrict__ off) {
+    __shared__ int part[1024];
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * per, e = min(n, b + per);
+    int s = 0;
+    for (int i = b; i < e; ++i) s += cnt[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - s;
+    for (int i = b; i < e; ++i) { off[i] = run; run += cnt[i]; }
+    if (threadIdx.x == blockDim.x - 1) off[n] = part[threadIdx.x];
+}
+
+__global__ void k_fill_reverse(const int* __restrict__ nbr, const float* __restrict__ w, int ne, int knn,
+                               const int* __restrict__ roff, int* __restrict__ rpos, int* __restrict__ rsrc,
+                               float* __restrict__ rw) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int j = nbr[e];
+    const int at = roff[j] + atomicAdd(&rpos[j], 1);
+    rsrc[at] = e / knn;
+    rw[at] = w[e];
+}
+
+// sort each reverse list by source (fixed summation order), degree of W = (K + K^T)/2
+__global__ void k_degree(const float* __restrict__ w, int np, int knn, const int* __restrict__ roff,
+                         int* __restrict__ rsrc, float* __restrict__ rw, float* __restrict__ deg) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const int b = roff[j], e = roff[j + 1];
+    for (int i = b + 1; i < e; ++i) {
+        const int s = rsrc[i];
+        const float x = rw[i];
+        int k = i - 1;
+        while (k >= b && rsrc[k] > s) { rsrc[k + 1] = rsrc[k]; rw[k + 1] = rw[k]; --k; }
+        rsrc[k + 1] = s;
+        rw[k + 1] = x;
+    }
+    float d = 0.f;
+    for (int q = 0; q < knn; ++q) d += w[(size_t)j * knn + q];
+    for (int i = b; i < e; ++i) d += rw[i];
+    deg[j] = 0.5f * d;
+}
+
+// lambda1 = lambda1^0 / max(L) (or times max(L) as printed)
+__global__ void k_lambda(const float* __restrict__ lmax, float lam1_0, int literal, float* __restrict__ lam1) {
+    const float m = *lmax;
+    *lam1 = literal ? lam1_0 * m : (m > 0.f ? lam1_0 / m : 0.f);
+}
+
+// (Q(X) L)_j = deg_j Q_j - 1/2 sum_{i in N(j)} w_ji Q_i - 1/2 sum_{i: j in N(i)} w_ij Q_i,
+// written per patch (QL nullable) and/or accumulated into Tr(Q L Q^H).
+__global__ void __launch_bounds__(128) k_graph_blocks(const float2* __restrict__ alpha, PatchGeom g, int K,
+                                                      const int* __restrict__ nbr, const float* __restrict__ w,
+                                                      int knn, const int* __restrict__ roff,
+                                                      const int* __restrict__ rsrc, const float* __restrict__ rw,
+                                                      const float* __restrict__ deg, float2* __restrict__ QL,
+                                                      double* __restrict__ trace) {
+    const int j = blockIdx.x;
+    const int pK = g.p * K;
+    const int ne = g.p * pK;
+    const int jy = g.origin(j / g.cnt), jx = g.origin(j % g.cnt);
+    const float dj = deg[j];
+    const int rb = roff[j], re = roff[j + 1];
+    double tr = 0.0;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const int py = e / pK, rem = e - py * pK;      // rem = px * K + k
+        const float2 a = alpha[((size_t)(jy + py) * g.n + jx) * K + rem];
+        float2 v = cscale(a, dj);
+        for (int q = 0; q < knn; ++q) {
+            const int i = nbr[(size_t)j * knn + q];
+            const float2 b = alpha[((size_t)(g.origin(i / g.cnt) + py) * g.n + g.origin(i % g.cnt)) * K + rem];
+            v = csub(v, cscale(b, 0.5f * w[(size_t)j * knn + q]));
+        }
+        for (int q = rb; q < re; ++q) {
+            const int i = rsrc[q];
+            const float2 b = alpha[((size_t)(g.origin(i / g.cnt) + py) * g.n + g.origin(i % g.cnt)) * K + rem];
+            v = csub(v, cscale(b, 0.5f * rw[q]));
+        }
+        if (QL) QL[(size_t)j * ne + e] = v;
+        if (trace) tr += (double)a.x * v.x + (double)a.y * v.y;
+    }
+    if (trace) {
+        tr = block_sum(tr);
+        if (threadIdx.x == 0) atomicAdd(trace, tr);
+    }
+}
+
+// --------------------------------------------------------------------------
+// SVT (Eq. 18): one warp per patch, one-sided (Hestenes) Jacobi on the
+// p^2 x K coefficient block; P = B diag(max(sigma - tau, 0) / sigma) V^H with
+// B = A V the orthogonalised columns.  R rows per lane, KP >= K columns (the
+// extra columns are zero and stay zero).
+// --------------------------------------------------------------------------
+template <int R, int KP>
+__global__ void __launch_bounds__(128) k_svt(const float2* __restrict__ alpha, PatchGeom g, int K, float tau,
+                                             float2* __restrict__ P, double* __restrict__ nuc) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= g.count()) return;
+    const int pp = g.p * g.p;
+    const int jy = g.origin(j / g.cnt), jx = g.origin(j % g.cnt);
+    float2 a[R][KP];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = lane + 32 * r;
+        const bool ok = row < pp;
+        const int py = ok ? row / g.p : 0, px = ok ? row - py * g.p : 0;
+        const float2* src = alpha + ((size_t)(jy + py) * g.n + jx + px) * K;
+#pragma unroll
+        for (int k = 0; k < KP; ++k) a[r][k] = (ok && k < K) ? src[k] : make_float2(0.f, 0.f);
+    }
+    float2 v[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) v[k] = make_float2(lane == k ? 1.f : 0.f, 0.f);
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        float off = 0.f;
+#pragma unroll
+        for (int p = 0; p < KP - 1; ++p) {
+#pragma unroll
+            for (int q = p + 1; q < KP; ++q) {
+                float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    al += cabs2(a[r][p]);
+                    be += cabs2(a[r][q]);
+                    const float2 t = cconjmul(a[r][p], a[r][q]);
+                    gr += t.x;
+                    gi += t.y;
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                gr = warp_sum(gr);
+                gi = warp_sum(gi);
+                const float gabs = sqrtf(gr * gr + gi * gi);
+                const float nrm = sqrtf(al * be);
+                if (gabs > 1e-30f && gabs > 1e-7f * nrm) {
+                    off = fmaxf(off, gabs / nrm);
+                    const float zeta = (be - al) / (2.f * gabs);
+                    const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    const float c = rsqrtf(1.f + t * t), s = c * t;
+                    const float2 ph = make_float2(gr / gabs, -gi / gabs);   // conj(gamma) / |gamma|
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float2 ap = a[r][p], aq = cmul(a[r][q], ph);
+                        a[r][p] = csub(cscale(ap, c), cscale(aq, s));
+                        a[r][q] = cadd(cscale(ap, s), cscale(aq, c));
+                    }
+                    const float2 vp = v[p], vq = cmul(v[q], ph);
+                    v[p] = csub(cscale(vp, c), cscale(vq, s));
+                    v[q] = cadd(cscale(vp, s), cscale(vq, c));
+                }
+            }
+        }
+        if (off < 2e-7f) break;
+    }
+    float f[KP];
+    float nsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+        float s2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) s2 += cabs2(a[r][k]);
+        const float sg = sqrtf(warp_sum(s2));
+        nsum += sg;
+        f[k] = sg > tau ? (sg - tau) / sg : 0.f;
+    }
+    if (nuc && lane == 0) atomicAdd(nuc, (double)nsum);
+    if (!P) return;
+    // P[row][k] = sum_j B[row][j] f_j conj(V[k][j]); row k of V lives in lane k
+    for (int k = 0; k < K; ++k) {
+        float2 vk[KP];
+#pragma unroll
+        for (int jj = 0; jj < KP; ++jj) {
+            vk[jj].x = __shfl_sync(0xffffffffu, v[jj].x, k);
+            vk[jj].y = __shfl_sync(0xffffffffu, v[jj].y, k);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = lane + 32 * r;
+            if (row < pp) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int jj = 0; jj < KP; ++jj) acc = cadd(acc, cscale(cmulc(a[r][jj], vk[jj]), f[jj]));
+                P[((size_t)j * pp + row) * K + k] = acc;
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Z step + X step (Eq. 12 and 19), gathered per voxel:
+//   alpha <- (alpha - mu (grad + lambda1 Q^*(QL)) + c Q^*(P)) / (1 + c cnt)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int covering(const PatchGeom& g, int y, int* list) {
+    int n = 0;
+    const int hi = min(g.cnt - 1, y / g.s);
+    const int lo = max(0, hi - (g.p + g.s - 1) / g.s);
+    for (int i = lo; i <= hi; ++i) {
+        const int o = g.origin(i);
+        if (o <= y && y < o + g.p) list[n++] = i;
+    }
+    const int e = g.cnt - 1;
+    if (e > hi) {
+        const int o = g.origin(e);
+        if (o <= y && y < o + g.p) list[n++] = e;
+    }
+    return n;
+}
+
+__global__ void k_xupdate(float2* __restrict__ alpha, const float2* __restrict__ grad,
+                          const float2* __restrict__ QL, const float2* __restrict__ P, PatchGeom g, int K,
+                          float mu, float c, const float* __restrict__ lam1, int literal,
+                          float* __restrict__ cnt_out) {
+    const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t N = (size_t)g.n * g.n;
+    if (e >= N * K) return;
+    const int vox = (int)(e / K), k = (int)(e - (size_t)vox * K);
+    const int y = vox / g.n, x = vox - y * g.n;
+    int ly[16], lx[16];
+    const int ny_ = covering(g, y, ly), nx_ = covering(g, x, lx);
+    const int pp = g.p * g.p;
+    float2 h = make_float2(0.f, 0.f), qp = make_float2(0.f, 0.f);
+    for (int a = 0; a < ny_; ++a)
+        for (int b = 0; b < nx_; ++b) {
+            const int i = ly[a] * g.cnt + lx[b];
+            const int row = (y - g.origin(ly[a])) * g.p + (x - g.origin(lx[b]));
+            const size_t o = ((size_t)i * pp + row) * K + k;
+            if (QL) h = cadd(h, QL[o]);
+            if (P) qp = cadd(qp, P[o]);
+        }
+    const float cnt = (float)(ny_ * nx_);
+    if (cnt_out) {
+        if (k == 0) cnt_out[vox] = cnt;
+        return;
+    }
+    const float l1 = *lam1;
+    const float2 z = csub(alpha[e], cscale(cadd(grad[e], cscale(h, l1)), mu));
+    const float den = literal ? 1.f + c : 1.f + c * cnt;
+    alpha[e] = cscale(cadd(z, cscale(qp, c)), 1.f / den);
+}
+
+__global__ void k_cost(const double* __restrict__ acc, const float* __restrict__ lam1, float lam2,
+                       double* __restrict__ out) {
+    // acc: [0] ||r||^2, [1] Tr(Q L Q^H), [2] sum of nuclear norms
+    *out = 0.5 * acc[0] + (double)(*lam1) * acc[1] + (double)lam2 * acc[2];
+}
+
+__global__ void k_maps(const float* __restrict__ t1t2, const float* __restrict__ pd, const int* __restrict__ idx,
+                       int N, float inv_gamma, float* __restrict__ t1, float* __restrict__ t2,
+                       float* __restrict__ pdo, int* __restrict__ idxo) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    if (t1) t1[v] = t1t2[2 * v];
+    if (t2) t2[v] = t1t2[2 * v + 1];
+    if (pdo) pdo[v] = pd[v] * inv_gamma;
+    if (idxo) idxo[v] = idx[v];
+}
+
+}  // namespace mrf
+
+// ----------------------------------------------------------------------------
+// recon object
+// ----------------------------------------------------------------------------
+struct mrf_recon_s {
+    mrf_plan_s* plan = nullptr;
+    mrf_recon_params prm{};
+    int K = 0, m = 0, N = 0, np = 0, pp = 0, mode = 0;
+    mrf::PatchGeom g{};
+    const float2* phi = nullptr;
+    const float2* dict_c = nullptr;
+    const float* atom_norm2 = nullptr;
+    const float* lut = nullptr;
+    float t1max = 1.f, t2max = 1.f;
+    double a = 1.0, gamma = 1.0;
+    mrf::MatchWorkspace mws;
+    // device buffers
+    float2 *alpha = nullptr, *grad = nullptr, *r = nullptr, *bs = nullptr, *QL = nullptr, *P = nullptr;
+    float* cnt = nullptr;
+    float *t1t2 = nullptr, *pd = nullptr;
+    int* idx = nullptr;
+    int* F = nullptr;
+    int* nbr = nullptr;
+    unsigned* d2 = nullptr;
+    float *w = nullptr, *rw = nullptr, *deg = nullptr;
+    int *rcnt = nullptr, *roff = nullptr, *rpos = nullptr, *rsrc = nullptr;
+    float* scal = nullptr;      // [0] sigma2, [1] lmax, [2] lam1, [3] scratch
+    double* acc = nullptr;      // [0] ||r||^2, [1] trace, [2] nuclear, [3..4] dot
+    double* cost = nullptr;     // [cap] cost history
+    int cost_cap = 0, iters_done = 0;
+    std::vector<void*> owned;
+};
+
+namespace mrf {
+
+template <typename T>
+static mrf_status dalloc(mrf_recon_s* R, T** p, size_t n) {
+    MRF_CUDA(cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(n, 1)));
+    R->owned.push_back(*p);
+    return MRF_OK;
+}
+
+static void free_recon(mrf_recon_s* R) {
+    if (!R) return;
+    for (void* p : R->owned) cudaFree(p);
+    delete R;
+}
+
+static mrf_status svt(mrf_recon_s* R, const float2* alpha, float2* P, double* nuc, cudaStream_t s) {
+    const int K = R->K;
+    const int rows = R->pp;
+    const unsigned blocks = (unsigned)((R->np + 3) / 4);
+    const float tau = 1.0f / R->prm.beta;
+#define MRF_SVT(RR, KK) k_svt<RR, KK><<<blocks, 128, 0, s>>>(alpha, R->g, K, tau, P, nuc)
+    const int KP = K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : 16;
+    if (rows <= 64) {
+        if (KP == 4) MRF_SVT(2, 4); else if (KP == 8) MRF_SVT(2, 8); else if (KP == 12) MRF_SVT(2, 12); else MRF_SVT(2, 16);
+    } else {
+        if (KP == 4) MRF_SVT(4, 4); else if (KP == 8) MRF_SVT(4, 8); else if (KP == 12) MRF_SVT(4, 12); else MRF_SVT(4, 16);
+    }
+#undef MRF_SVT
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+// L from the current maps, then lambda1
+static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
+    const int np = R->np, knn = R->prm.knn, FD = 2 * R->pp;
+    k_features<<<(unsigned)(((size_t)np * R->pp + 255) / 256), 256, 0, s>>>(R->t1t2, R->g, (double)R->t1max,
+                                                                             (double)R->t2max, R->F);
+    MRF_LAUNCHED();
+    const size_t sm = sizeof(int) * (size_t)(32 + 64) * (FD + 1);
+    if (knn <= 16) {
+        MRF_CUDA(cudaFuncSetAttribute(k_knn<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_knn<16><<<(np + 31) / 32, 256, sm, s>>>(R->F, np, FD, knn, R->nbr, R->d2);
+    } else {
+        MRF_CUDA(cudaFuncSetAttribute(k_knn<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_knn<32><<<(np + 31) / 32, 256, sm, s>>>(R->F, np, FD, knn, R->nbr, R->d2);
+    }
+    MRF_LAUNCHED();
+    const int ne = np * knn;
+    k_median_nonzero<<<1, 1024, 0, s>>>(R->d2, ne, R->scal + 0);
+    MRF_LAUNCHED();
+    MRF_CUDA(cudaMemsetAsync(R->rcnt, 0, sizeof(int) * np, s));
+    MRF_CUDA(cudaMemsetAsync(R->rpos, 0, sizeof(int) * np, s));
+    k_edge_weights<<<(ne + 255) / 256, 256, 0, s>>>(R->nbr, R->d2, ne, R->scal + 0, R->w, R->rcnt);
+    MRF_LAUNCHED();
+    k_scan<<<1, 1024, 0, s>>>(R->rcnt, np, R->roff);
+    MRF_LAUNCHED();
+    k_fill_reverse<<<(ne + 255) / 256, 256, 0, s>>>(R->nbr, R->w, ne, knn, R->roff, R->rpos, R->rsrc, R->rw);
+    MRF_LAUNCHED();
+    k_degree<<<(np + 127) / 128, 128, 0, s>>>(R->w, np, knn, R->roff, R->rsrc, R->rw, R->deg);
+    MRF_LAUNCHED();
+    k_max<<<1, 1024, 0, s>>>(R->deg, np, R->scal + 1);
+    MRF_LAUNCHED();
+    k_lambda<<<1, 1, 0, s>>>(R->scal + 1, R->prm.lam1_0, (R->prm.flags & MRF_RECON_LITERAL_LAMBDA1) ? 1 : 0,
+                             R->scal + 2);
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+static mrf_status match_maps(mrf_recon_s* R, cudaStream_t s) {
+    return match_run(R->mws, R->alpha, R->N, R->K, R->dict_c, R->m, R->prm.match_precision, R->lut, R->idx,
+                     R->pd, R->t1t2, 1.0f, s);
+}
+
+static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s) {
+    k_graph_blocks<<<R->np, 128, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc, R->rw,
+                                         R->deg, QL, trace);
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+// one iteration of the loop body (stream-ordered, capturable)
+static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
+    const size_t NK = (size_t)R->N * R->K;
+    const float inv_a = (float)(1.0 / R->a);
+    const bool cost = !(R->prm.flags & MRF_RECON_NO_COST);
+    MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, s));
+    MRF_PROPAGATE(graph_pass(R, R->QL, nullptr, s));
+    const float c = R->prm.mu * R->prm.lam2 * R->prm.beta;
+    k_xupdate<<<(unsigned)((NK + 255) / 256), 256, 0, s>>>(
+        R->alpha, R->grad, R->QL, R->P, R->g, R->K, R->prm.mu, c, R->scal + 2,
+        (R->prm.flags & MRF_RECON_LITERAL_XUPDATE) ? 1 : 0, nullptr);
+    MRF_LAUNCHED();
+    MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, s));
+    if (cost) MRF_CUDA(cudaMemsetAsync(R->acc, 0, 3 * sizeof(double), s));
+    MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, s));
+    if (cost) {
+        const size_t nr = (size_t)R->plan->T * R->plan->ns;
+        k_norm2_acc<<<nblk(nr), 256, 0, s>>>(R->r, nr, R->acc + 0);
+        MRF_LAUNCHED();
+        MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, s));
+        k_cost<<<1, 1, 0, s>>>(R->acc, R->scal + 2, R->prm.lam2, R->cost + (it % R->cost_cap));
+        MRF_LAUNCHED();
+    }
+    MRF_PROPAGATE(match_maps(R, s));
+    MRF_PROPAGATE(build_graph(R, s));
+    return MRF_OK;
+}
+
+static double read_double(const double* d, cudaStream_t s, mrf_status* st) {
+    double h = 0.0;
+    if (cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        *st = MRF_ECUDA;
+        set_error("device read failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    return h;
+}
+
+static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
+    mrf_plan_s* p = R->plan;
+    const int K = R->K, N = R->N, np = R->np, knn = R->prm.knn;
+    const size_t NK = (size_t)N * K, nr = (size_t)p->T * p->ns;
+    MRF_PROPAGATE(dalloc(R, &R->alpha, NK));
+    MRF_PROPAGATE(dalloc(R, &R->grad, NK));
+    MRF_PROPAGATE(dalloc(R, &R->r, nr));
+    MRF_PROPAGATE(dalloc(R, &R->bs, nr));
+    MRF_PROPAGATE(dalloc(R, &R->QL, (size_t)np * R->pp * K));
+    MRF_PROPAGATE(dalloc(R, &R->P, (size_t)np * R->pp * K));
+    MRF_PROPAGATE(dalloc(R, &R->cnt, N));
+    MRF_PROPAGATE(dalloc(R, &R->t1t2, 2 * (size_t)N));
+    MRF_PROPAGATE(dalloc(R, &R->pd, N));
+    MRF_PROPAGATE(dalloc(R, &R->idx, N));
+    MRF_PROPAGATE(dalloc(R, &R->F, (size_t)np * 2 * R->pp));
+    MRF_PROPAGATE(dalloc(R, &R->nbr, (size_t)np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->d2, (size_t)np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->w, (size_t)np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->rw, (size_t)np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->rsrc, (size_t)np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->deg, np));
+    MRF_PROPAGATE(dalloc(R, &R->rcnt, np));
+    MRF_PROPAGATE(dalloc(R, &R->rpos, np));
+    MRF_PROPAGATE(dalloc(R, &R->roff, np + 1));
+    MRF_PROPAGATE(dalloc(R, &R->scal, 8));
+    MRF_PROPAGATE(dalloc(R, &R->acc, 8));
+    R->cost_cap = 1024;
+    MRF_PROPAGATE(dalloc(R, &R->cost, R->cost_cap));
+    MRF_PROPAGATE(R->mws.reserve(N, R->m));
+    MRF_PROPAGATE(ensure_subspace_workspace(p, K));
+    MRF_PROPAGATE(match_prepare(R->mws, R->dict_c, R->atom_norm2, R->m, K, 0, s));
+    // t1max, t2max of the look-up table
+    {
+        std::vector<float> lut((size_t)R->m * 2);
+        MRF_CUDA(cudaMemcpyAsync(lut.data(), R->lut, lut.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+        MRF_CUDA(cudaStreamSynchronize(s));
+        R->t1max = R->t2max = 0.f;
+        for (int i = 0; i < R->m; ++i) {
+            R->t1max = std::max(R->t1max, lut[2 * i]);
+            R->t2max = std::max(R->t2max, lut[2 * i + 1]);
+        }
+        if (!(R->t1max > 0.f)) R->t1max = 1.f;
+        if (!(R->t2max > 0.f)) R->t2max = 1.f;
+    }
+    // coverage counts
+    k_xupdate<<<(unsigned)((NK + 255) / 256), 256, 0, s>>>(R->alpha, nullptr, nullptr, nullptr, R->g, K, 0.f, 0.f,
+                                                          nullptr, 0, R->cnt);
+    MRF_LAUNCHED();
+    // a = ||A P_S||_2 by power iteration on coefficient images
+    if (R->prm.a_norm > 0.f) {
+        R->a = R->prm.a_norm;
+    } else {
+        k_fill<<<nblk(NK), 256, 0, s>>>(R->alpha, NK, make_float2((float)(1.0 / std::sqrt((double)NK)), 0.f));
+        MRF_LAUNCHED();
+        double lam = 0.0;
+        for (int it = 0; it < R->prm.power_iters; ++it) {
+            MRF_PROPAGATE(subspace_forward(p, R->alpha, R->phi, K, 1.0f, nullptr, R->r, R->mode, s));
+            MRF_PROPAGATE(subspace_adjoint(p, R->r, R->phi, K, 1.0f, R->grad, R->mode, s));
+            MRF_CUDA(cudaMemsetAsync(R->acc, 0, 4 * sizeof(double), s));
+            k_dot_acc<<<nblk(NK), 256, 0, s>>>(R->alpha, R->grad, NK, R->acc + 0);
+            k_norm2_acc<<<nblk(NK), 256, 0, s>>>(R->grad, NK, R->acc + 2);
+            MRF_LAUNCHED();
+            double h[4];
+            MRF_CUDA(cudaMemcpyAsync(h, R->acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+            MRF_CUDA(cudaStreamSynchronize(s));
+            lam = h[0];
+            const double nw = std::sqrt(h[2]);
+            MRF_REQUIRE(nw > 0.0, "mrf_recon_create: the operator maps the start vector to zero");
+            k_scale_copy<<<nblk(NK), 256, 0, s>>>(R->grad, NK, (float)(1.0 / nw), R->alpha);
+            MRF_LAUNCHED();
+        }
+        MRF_REQUIRE(lam > 0.0, "mrf_recon_create: non-positive operator norm estimate");
+        R->a = std::sqrt(lam);
+    }
+    const float inv_a = (float)(1.0 / R->a);
+    // X^0 = P_S((A/a)^H (b/a)), matched for the PD scale gamma
+    MRF_PROPAGATE(subspace_adjoint(p, b, R->phi, K, inv_a * inv_a, R->alpha, R->mode, s));
+    MRF_PROPAGATE(match_maps(R, s));
+    if (R->prm.x_scale > 0.f) {
+        R->gamma = R->prm.x_scale;
+    } else {
+        k_max<<<1, 1024, 0, s>>>(R->pd, N, R->scal + 3);
+        MRF_LAUNCHED();
+        float mx = 0.f;
+        MRF_CUDA(cudaMemcpyAsync(&mx, R->scal + 3, sizeof(float), cudaMemcpyDeviceToHost, s));
+        MRF_CUDA(cudaStreamSynchronize(s));
+        R->gamma = mx > 0.f ? R->prm.pd_target / (double)mx : 1.0;
+    }
+    const float gm = (float)R->gamma;
+    k_scale<<<nblk(NK), 256, 0, s>>>(R->alpha, NK, gm);
+    k_scale_copy<<<nblk(nr), 256, 0, s>>>(b, nr, (float)(R->gamma / R->a), R->bs);
+    MRF_LAUNCHED();
+    MRF_PROPAGATE(match_maps(R, s));                     // maps in the scaled units
+    MRF_PROPAGATE(build_graph(R, s));
+    MRF_PROPAGATE(subspace_forward(p, R->alpha, R->phi, K, inv_a, R->bs, R->r, R->mode, s));
+    MRF_PROPAGATE(svt(R, R->alpha, R->P, nullptr, s));
+    MRF_CUDA(cudaStreamSynchronize(s));
+    return MRF_OK;
+}
+
+}  // namespace mrf
+
+using namespace mrf;
+
+extern "C" mrf_status mrf_recon_create(mrf_recon* out, mrf_plan plan, const mrf_recon_params* prm,
+                                       const mrf_c64* phi, int K, const mrf_c64* dict_c, const float* atom_norm2,
+                                       const float* lut, int m, const mrf_c64* b, mrf_stream stream) {
+    MRF_REQUIRE(out != nullptr, "mrf_recon_create: out is NULL");
+    *out = nullptr;
+    MRF_REQUIRE(plan && prm && phi && dict_c && atom_norm2 && lut && b, "mrf_recon_create: NULL argument");
+    MRF_REQUIRE(K >= 1 && K <= 16, "mrf_recon_create: K must be in [1, 16] (got %d)", K);
+    MRF_REQUIRE(m >= 1, "mrf_recon_create: m must be >= 1");
+    MRF_REQUIRE(plan->nx <= 256, "mrf_recon_create: images up to 256 x 256");
+    MRF_REQUIRE(prm->patch >= 1 && prm->patch <= 11 && prm->patch <= plan->nx,
+                "mrf_recon_create: patch must be in [1, 11] and fit the image (got %d)", prm->patch);
+    MRF_REQUIRE(prm->stride >= 1 && prm->stride <= prm->patch, "mrf_recon_create: stride must be in [1, patch]");
+    MRF_REQUIRE(prm->knn >= 1 && prm->knn <= 32, "mrf_recon_create: knn must be in [1, 32]");
+    MRF_REQUIRE(prm->beta > 0.f && prm->mu > 0.f, "mrf_recon_create: beta and mu must be > 0");
+    MRF_REQUIRE(prm->match_precision == MRF_MATCH_FP32 || prm->match_precision == MRF_MATCH_BF16,
+                "mrf_recon_create: unknown match precision %d", prm->match_precision);
+    const PatchGeom g = make_geom(plan->nx, prm->patch, prm->stride);
+    MRF_REQUIRE(g.count() >= prm->knn + 1, "mrf_recon_create: need at least knn + 1 patches (%d)", g.count());
+    auto* R = new mrf_recon_s();
+    R->plan = plan;
+    R->prm = *prm;
+    R->K = K;
+    R->m = m;
+    R->N = plan->nx * plan->ny;
+    R->g = g;
+    R->np = g.count();
+    R->pp = prm->patch * prm->patch;
+    R->mode = (prm->flags & MRF_RECON_GROUPED) ? 1 : 0;
+    R->phi = reinterpret_cast<const float2*>(phi);
+    R->dict_c = reinterpret_cast<const float2*>(dict_c);
+    R->atom_norm2 = atom_norm2;
+    R->lut = lut;
+    const mrf_status st = create(R, reinterpret_cast<const float2*>(b), as_stream(stream));
+    if (st != MRF_OK) {
+        free_recon(R);
+        return st;
+    }
+    *out = R;
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_recon_iter(mrf_recon R, int n_iters, double* cost_out, mrf_stream stream) {
+    MRF_REQUIRE(R != nullptr, "mrf_recon_iter: NULL recon");
+    MRF_REQUIRE(n_iters >= 0 && n_iters <= R->cost_cap, "mrf_recon_iter: n_iters must be in [0, %d]", R->cost_cap);
+    cudaStream_t s = as_stream(stream);
+    const int first = R->iters_done;
+    for (int i = 0; i < n_iters; ++i) MRF_PROPAGATE(iteration(R, first + i, s));
+    R->iters_done += n_iters;
+    if (cost_out && n_iters > 0) {
+        if (R->prm.flags & MRF_RECON_NO_COST) {
+            for (int i = 0; i < n_iters; ++i) cost_out[i] = NAN;
+        } else {
+            std::vector<double> h(R->cost_cap);
+            MRF_CUDA(cudaMemcpyAsync(h.data(), R->cost, sizeof(double) * R->cost_cap, cudaMemcpyDeviceToHost, s));
+            MRF_CUDA(cudaStreamSynchronize(s));
+            for (int i = 0; i < n_iters; ++i) cost_out[i] = h[(first + i) % R->cost_cap];
+        }
+    }
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_recon_maps(mrf_recon R, float* t1, float* t2, float* pd, int* idx, mrf_stream stream) {
+    MRF_REQUIRE(R != nullptr, "mrf_recon_maps: NULL recon");
+    k_maps<<<(R->N + 255) / 256, 256, 0, as_stream(stream)>>>(R->t1t2, R->pd, R->idx, R->N, (float)(1.0 / R->gamma),
+                                                               t1, t2, pd, idx);
+    MRF_LAUNCHED();
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_recon_alpha(mrf_recon R, mrf_c64* alpha, mrf_stream stream) {
+    MRF_REQUIRE(R && alpha, "mrf_recon_alpha: NULL argument");
+    MRF_CUDA(cudaMemcpyAsync(alpha, R->alpha, sizeof(float2) * (size_t)R->N * R->K, cudaMemcpyDeviceToDevice,
+                             as_stream(stream)));
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_recon_info(mrf_recon R, double* a_norm, double* x_scale, double* lam1, double* sigma2,
+                                     mrf_stream stream) {
+    MRF_REQUIRE(R != nullptr, "mrf_recon_info: NULL recon");
+    float h[3] = {0.f, 0.f, 0.f};
+    cudaStream_t s = as_stream(stream);
+    MRF_CUDA(cudaMemcpyAsync(h, R->scal, sizeof(h), cudaMemcpyDeviceToHost, s));
+    MRF_CUDA(cudaStreamSynchronize(s));
+    if (a_norm) *a_norm = R->a;
+    if (x_scale) *x_scale = R->gamma;
+    if (lam1) *lam1 = h[2];
+    if (sigma2) *sigma2 = h[0];
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_recon_destroy(mrf_recon R) {
+    free_recon(R);
+    return MRF_OK;
 }

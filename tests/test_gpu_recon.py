@@ -1,0 +1,136 @@
+"""GPU parity of Algorithm 1 (MS-LLR) and of the dictionary subspace against
+the FP64 oracle, which runs the loop on full-frame data.
+
+Tolerances: relative L2 1e-4 for the coefficient images after the
+initialisation and after each iteration (FP32 NUFFT + FP32 Jacobi SVT; the
+oracle's SVD and NUFFT are FP64); matching indices must agree except at
+near-ties (score within 1e-5 of the best)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dictionary, epg, match as omatch, nufft as onufft, recon as orecon
+from gpu_util import as_f32_inputs, c64, f32, mrf, np_, rand_c, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def problem(n=32, T=24, ns=128, K=4, il=6, seed=0, snr_db=30.0):
+    t1, t2, pd, mask, _ = synth.phantom(n, seed=seed)
+    fa, tr = synth.fisp_train(T, seed=2)
+    lut = synth.keep_t1_ge_t2(synth.log_grid(250, 3000, 12), synth.log_grid(25, 350, 9))
+    D = epg.fisp(lut[:, 0], lut[:, 1], fa, tr)
+    X = pd.reshape(-1, 1) * epg.fisp(np.maximum(t1.ravel(), 1.0), np.maximum(t2.ravel(), 1.0), fa, tr)
+    X *= mask.reshape(-1, 1)
+    k = synth.spiral_trajectory(n, T, ns, il)
+    grid = onufft.KBGrid(n, n, 2, 4)
+    b = onufft.kb_forward(X.reshape(n, n, T).transpose(2, 0, 1), k, grid)
+    sig = np.sqrt(np.mean(np.abs(b) ** 2) * 10 ** (-snr_db / 10))
+    b = b + sig * synth.complex_normal(b.shape, seed=1)
+    phi = dictionary.subspace(D, K)
+    k, b, phi, D, lut = as_f32_inputs(k, b, phi, D, lut)
+    return dict(n=n, k=k, b=b, phi=phi, D=D, lut=lut, grid=grid, truth=(t1, t2, pd, mask))
+
+
+@pytest.fixture(scope="module")
+def prob():
+    return problem()
+
+
+def gpu_recon(pr, mode=0, **kw):
+    m = mrf()
+    plan = m.nufft_plan(pr["n"], pr["n"], f32(pr["k"]))
+    dc = pr["D"] @ pr["phi"]
+    n2 = np.sum(np.abs(pr["D"]) ** 2, axis=1)
+    params = m.ReconParams(patch=8, stride=4, knn=4, flags=(8 if mode else 0), **kw)
+    return m.Recon(plan, params, c64(pr["phi"]), c64(dc), f32(n2), f32(pr["lut"]), c64(pr["b"]))
+
+
+def oracle_recon(pr, **kw):
+    P = orecon.Params(patch=8, stride=4, knn=4, **kw)
+    return orecon.MSLLR(pr["b"], pr["k"], pr["grid"], pr["phi"], pr["D"], pr["lut"], P).init()
+
+
+def alpha_of(o):
+    return o.X @ o.phi
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_init_scales_and_maps(prob, mode):
+    o = oracle_recon(prob)
+    r = gpu_recon(prob, mode)
+    info = r.info()
+    assert info["a_norm"] == pytest.approx(o.a, rel=1e-4)
+    assert info["x_scale"] == pytest.approx(o.gamma, rel=1e-3)
+    # with the oracle's own scales both sides start from the same point
+    r = gpu_recon(prob, mode, a_norm=o.a, x_scale=o.gamma)
+    assert rel(np_(r.alpha()), alpha_of(o)) < 1e-4
+    t1, t2, pd, idx = [np_(t) for t in r.maps()]
+    oi = o.maps[0].ravel()
+    X = (o.X).reshape(-1, o.X.shape[-1])
+    sc = omatch.scores(X, prob["D"])
+    rows = np.arange(len(oi))
+    gi = idx.ravel()
+    assert np.all(sc[rows, gi] >= sc[rows, oi] * (1 - 1e-5))
+    same = gi == oi
+    assert same.mean() > 0.99
+    np.testing.assert_allclose(pd.ravel()[same], (o.maps[3].ravel() / o.gamma)[same], rtol=1e-3, atol=1e-4)
+    assert r.info()["lam1"] == pytest.approx(o.lam1, rel=1e-4)
+    assert r.info()["sigma2"] == pytest.approx(o.sigma2_hist[-1], rel=1e-4)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_iterations_match_oracle(prob, mode):
+    o = oracle_recon(prob)
+    r = gpu_recon(prob, mode, a_norm=o.a, x_scale=o.gamma)
+    for it in range(3):
+        o.iterate()
+        cost = r.iterate(1, costs=True)[0]
+        a_g, a_o = np_(r.alpha()), alpha_of(o)
+        assert rel(a_g, a_o) < 1e-4 * (it + 1), it
+        assert cost == pytest.approx(o.cost[-1], rel=1e-4 * (it + 1))
+        idx = np_(r.maps()[3]).ravel()
+        assert (idx == o.maps[0].ravel()).mean() > 0.99
+        assert r.info()["lam1"] == pytest.approx(o.lam1, rel=1e-3)
+
+
+def test_literal_flags(prob):
+    o = oracle_recon(prob, literal_xupdate=True, literal_lam1=True)
+    # flags: 1 = literal X update, 2 = literal lambda1
+    m = mrf()
+    plan = m.nufft_plan(prob["n"], prob["n"], f32(prob["k"]))
+    dc = prob["D"] @ prob["phi"]
+    n2 = np.sum(np.abs(prob["D"]) ** 2, axis=1)
+    params = m.ReconParams(patch=8, stride=4, knn=4, flags=1 | 2, a_norm=o.a, x_scale=o.gamma)
+    r = m.Recon(plan, params, c64(prob["phi"]), c64(dc), f32(n2), f32(prob["lut"]), c64(prob["b"]))
+    assert r.info()["lam1"] == pytest.approx(o.lam1, rel=1e-4)
+    o.iterate()
+    r.iterate(1)
+    assert rel(np_(r.alpha()), alpha_of(o)) < 1e-4
+
+
+def test_dict_subspace_matches_svd():
+    m = mrf()
+    fa, tr = synth.fisp_train(200, seed=2)
+    lut = synth.keep_t1_ge_t2(synth.log_grid(100, 4000, 40), synth.log_grid(10, 500, 25))
+    D = epg.fisp(lut[:, 0], lut[:, 1], fa, tr)
+    (D,) = as_f32_inputs(D)
+    K = 10
+    phi, comp, n2 = [np_(t) for t in m.dict_subspace(c64(D), K)]
+    phi0 = dictionary.subspace(D, K)
+    np.testing.assert_allclose(phi.conj().T @ phi, np.eye(K), atol=1e-5)
+    P, P0 = phi @ phi.conj().T, phi0 @ phi0.conj().T
+    assert np.linalg.norm(P - P0) / np.linalg.norm(P0) < 1e-3
+    assert rel(comp, D @ phi) < 1e-5
+    np.testing.assert_allclose(n2, np.sum(np.abs(D) ** 2, 1), rtol=1e-5)
+
+
+def test_recon_rejects_bad_params(prob):
+    m = mrf()
+    plan = m.nufft_plan(prob["n"], prob["n"], f32(prob["k"]))
+    dc = prob["D"] @ prob["phi"]
+    n2 = np.sum(np.abs(prob["D"]) ** 2, axis=1)
+    for bad in [dict(patch=12), dict(knn=60), dict(stride=0), dict(patch=8, stride=4, knn=48)]:
+        params = m.ReconParams(**{**dict(patch=8, stride=4, knn=4), **bad})
+        with pytest.raises(m.MRFError):
+            m.Recon(plan, params, c64(prob["phi"]), c64(dc), f32(n2), f32(prob["lut"]), c64(prob["b"]))

@@ -93,10 +93,22 @@ def test_graph_term_is_gradient_of_trace():
     assert fd == pytest.approx(an, rel=1e-6)
 
 
-def test_features_scale():
+def test_features_scale_and_fixed_point():
     pg = patches.PatchGrid(8, 8, 4, 4)
     t1 = np.full((8, 8), 1000.0)
     t2 = np.full((8, 8), 50.0)
+    t2[0, 0] = 100.0 * 3 / 8192                 # exactly half an LSB: rounds to even (0)
+    t2[0, 1] = 100.0 * 5 / 8192                 # 2.5 LSB -> 2
     F = graph.features(t1, t2, pg, 2000.0, 100.0)
-    assert F.shape == (4, 32)
-    np.testing.assert_allclose(F, 0.5)
+    assert F.shape == (4, 32) and F.dtype == np.int64
+    assert F[0, 0] == 2048 and F[0, 2] == 2048
+    assert F[0, 1] == 2 and F[0, 3] == 2
+    assert F[1, 1] == 2048
+
+
+def test_integer_distances_are_exact_ties():
+    # two candidates at the same distance through different voxels tie exactly
+    F = np.array([[0, 0, 0], [3, 0, 0], [0, 3, 0], [0, 0, 2]], dtype=np.int64)
+    nbr, d2 = graph.knn(F, 3)
+    np.testing.assert_array_equal(nbr[0], [3, 1, 2])
+    np.testing.assert_array_equal(d2[0], [4, 9, 9])
