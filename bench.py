@@ -1,0 +1,487 @@
+#!/usr/bin/env python
+"""Benchmark: MS-LLR reconstruction iterations per second at 256^2 x 1000 frames.
+
+One step = one iteration of Algorithm 1 on the GPU (data-term adjoint and
+forward NUFFT over the 1000 frames, graph term, SVT, X update, cost,
+matching and the k-nearest-patch Laplacian), through the C ABI, with every
+input resident in device memory.  Two variants are timed:
+  plain  - per-frame NUFFT (1000 forward + 1000 adjoint transforms per
+           iteration) and FP32 exhaustive matching;
+  chosen - the same operator evaluated in grouped form (K oversampled FFTs
+           and interleaf-grouped interpolation) and FP32 matching.
+`value` is the chosen variant's whole-job iterations/s.  Under torchrun each
+rank reconstructs its own slice (weak scaling, no data-path collective).
+
+Inputs are synthetic and seeded (synth/): a 256^2 phantom of 8 regions, a
+FISP train of 1000 repetitions, 1 of 48 variable-density spiral interleaves of
+2048 samples per frame, complex Gaussian noise at 30 dB, and a dictionary of
+100 x 60 log-spaced (T1, T2) pairs simulated by the library's EPG kernel.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MRF recon iters/s at 256^2x1000 frames, chosen vs plain; T1/T2 NRMSE vs oracle"
+WORKLOAD = "mrf256_t1000"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variants", default="plain,chosen")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (barrier and max over ranks only)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        import torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.file:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_inputs(seed):
+    """Device inputs of the 256^2 x 1000-frame workload, built with the library's kernels."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2310_05647_gb300 as mrf
+
+    w = synth.WORKLOADS[WORKLOAD]
+    dev = torch.device("cuda")
+    t1, t2, pd, mask, label = synth.phantom(w.n, seed=seed)
+    fa, tr = synth.fisp_train(w.frames, seed=w.tr_seed)
+    lut = synth.workload_grid(w)
+    traj = synth.spiral_trajectory(w.n, w.frames, w.ns, w.interleaves)
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    fa_d, tr_d = f32(fa), f32(tr)
+    lut_d = f32(lut)
+    D = mrf.epg_fisp(lut_d, fa_d, tr_d)                              # [M, T]
+    phi, comp, n2 = mrf.dict_subspace(D, w.rank)
+    # ground-truth series: one EPG signal per region, times PD (input synthesis)
+    regions = np.unique(label[label >= 0])
+    pairs = np.stack([[t1[label == r][0], t2[label == r][0]] for r in regions])
+    S = mrf.epg_fisp(f32(pairs), fa_d, tr_d)                          # [R, T]
+    lab = torch.tensor(np.where(label >= 0, np.searchsorted(regions, np.maximum(label, 0)), 0).ravel(),
+                       device=dev, dtype=torch.long)
+    pdm = f32(pd.ravel()).to(torch.complex64)
+    X = (S[lab] * pdm[:, None]).T.contiguous().view(w.frames, w.n, w.n)   # [T, ny, nx]
+    plan = mrf.nufft_plan(w.n, w.n, f32(traj), os=w.os, kb_width=w.kb_width)
+    b = mrf.nufft_forward(plan, X)
+    del X
+    sig = math.sqrt(float((b.abs() ** 2).mean()) * 10 ** (-w.snr_db / 10))
+    g = torch.Generator(device=dev)
+    g.manual_seed(1000 + w.noise_seed + seed)
+    noise = torch.complex(torch.randn(b.shape, generator=g, device=dev),
+                          torch.randn(b.shape, generator=g, device=dev)) * (sig / math.sqrt(2.0))
+    b = (b + noise).contiguous()
+    torch.cuda.synchronize()
+    return dict(w=w, plan=plan, phi=phi, comp=comp, n2=n2, lut=lut_d, b=b, truth=(t1, t2, pd, mask),
+                atoms=int(lut.shape[0]))
+
+
+def params_for(variant, w):
+    import paper_2310_05647_gb300 as mrf
+    from paper_2310_05647_gb300.api import RECON_GROUPED
+    flags = RECON_GROUPED if variant == "chosen" else 0
+    return mrf.ReconParams(patch=w.patch, stride=w.stride, knn=w.knn, flags=flags)
+
+
+def nrmse(truth, maps):
+    import numpy as np
+    t1, t2, pd, mask = truth
+    out = {}
+    for name, ref, est in (("t1", t1, maps[0]), ("t2", t2, maps[1]), ("pd", pd, maps[2])):
+        e = est[mask]
+        r = ref[mask]
+        out[name] = float(np.sqrt(np.sum((e - r) ** 2) / np.sum(r ** 2)))
+    return out
+
+
+# algorithmic bytes (HBM-bound kernels) or flops (ALU-bound) per launch
+def algorithmic_work(kernel, inp):
+    w = inp["w"]
+    T, n, ns, K, G = w.frames, w.n, w.ns, w.rank, w.os * w.n
+    M = inp["atoms"]
+    frame_h1 = n * G * 8                          # one frame's half-oversampled intermediate
+    ngroups = w.interleaves or T
+    table = {
+        # per-frame subspace expansion: coefficients (L2-resident, read once) + H1 write
+        "k_rows_fwd_expand": ("hbm", T * frame_h1 + n * n * K * 8),
+        # column FFT + interpolation: H1 read + samples (trajectory record + value) written
+        "k_cols_interp": ("hbm", T * (frame_h1 + ns * 8 + ns * 8 + ns * 8)),
+        # spread + column IFFT: samples read + H1 written
+        "k_spread_cols": ("hbm", T * (ns * 8 + ns * 8 + frame_h1)),
+        # row IFFT + subspace reduction: H1 read + partial coefficient images
+        "k_rows_adj_reduce": ("hbm", T * frame_h1),
+        "k_rows_fwd": ("hbm", T * (n * n * 8 + frame_h1)),
+        "k_rows_adj": ("hbm", T * (frame_h1 + n * n * 8)),
+        # exhaustive matching: complex MAC = 8 flops
+        "k_match_fp32": ("alu", 8.0 * n * n * M * K),
+    }
+    return table.get(kernel)
+
+
+def time_variant(variant, inp, steps, warmup, dist):
+    import numpy as np
+    import torch
+
+    import paper_2310_05647_gb300 as mrf
+
+    w = inp["w"]
+    rec = mrf.Recon(inp["plan"], params_for(variant, w), inp["phi"], inp["comp"], inp["n2"], inp["lut"], inp["b"])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")    # 256 MiB > L2
+    for _ in range(warmup):
+        flush.zero_()
+        rec.iterate(1)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    mrf.profile_enable(True)
+    launches0 = mrf.launch_count()
+    dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device()) as clk:
+        for i in range(steps):
+            flush.zero_()
+            mrf.profile_mark()
+            starts[i].record()
+            rec.iterate(1)
+            ends[i].record()
+        torch.cuda.synchronize()
+    dist.barrier()
+    launches = mrf.launch_count() - launches0
+    prof = mrf.profile_read()
+    mrf.profile_enable(False)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t1, t2, pd, _ = rec.maps()
+    maps = [t.cpu().numpy() for t in (t1, t2, pd)]
+    info = rec.info()
+    del rec
+    return dict(ms=ms, launches=launches, profile=prof, clocks=clk.summary(),
+                nrmse=nrmse(inp["truth"], maps), info=info, maps=maps)
+
+
+def e2e_chosen(inp, iters, reps=2):
+    """End to end through the public API: pinned host k-space in, host maps out."""
+    import torch
+
+    import paper_2310_05647_gb300 as mrf
+
+    w = inp["w"]
+    b_host = inp["b"].cpu().pin_memory()
+    times = []
+    for r in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = b_host.to("cuda", non_blocking=True)
+        rec = mrf.Recon(inp["plan"], params_for("chosen", w), inp["phi"], inp["comp"], inp["n2"], inp["lut"], b)
+        rec.iterate(iters)
+        maps = [t.to("cpu") for t in rec.maps()]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        del rec
+        if r > 0:
+            times.append(dt)
+    h2d = b_host.numel() * 8
+    d2h = 4 * w.n * w.n * 4
+    return statistics.mean(times), h2d, d2h
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of one iteration, extrapolated)
+# ---------------------------------------------------------------------------
+def oracle_iteration_seconds(scale=1.0):
+    """Seconds the FP64 oracle needs for one Algorithm 1 iteration at 256^2 x 1000,
+    extrapolated from timed samples of each step (frames, voxels, patches and
+    graph rows), with `scale` shrinking every sample."""
+    import numpy as np
+
+    import synth
+    from oracle import graph, llr, match as omatch, nufft as onufft, patches
+
+    w = synth.WORKLOADS[WORKLOAD]
+    n, T, ns = w.n, w.frames, w.ns
+    rng = np.random.default_rng(0)
+    parts = {}
+    # data term: forward + adjoint NUFFT on F frames
+    F = max(1, int(4 * scale))
+    k = synth.spiral_trajectory(n, F, ns, w.interleaves)
+    grid = onufft.KBGrid(n, n, w.os, w.kb_width)
+    x = rng.standard_normal((F, n, n)) + 1j * rng.standard_normal((F, n, n))
+    t0 = time.perf_counter()
+    y = onufft.kb_forward(x, k, grid)
+    onufft.kb_adjoint(y, k, grid)
+    parts["nufft_pair"] = (time.perf_counter() - t0) * T / F * 2      # residual forward + adjoint per pass
+    # matching at full length against the workload's dictionary size
+    M = len(synth.workload_grid(w))
+    nv = max(16, int(256 * scale))
+    X = rng.standard_normal((nv, T)) + 1j * rng.standard_normal((nv, T))
+    D = rng.standard_normal((M, T)) + 1j * rng.standard_normal((M, T))
+    lut = np.ones((M, 2))
+    t0 = time.perf_counter()
+    omatch.match(X, D, lut)
+    parts["match"] = (time.perf_counter() - t0) * (n * n) / nv
+    # SVT of p^2 x T patches (twice: P step and the cost's nuclear norms)
+    pg = patches.PatchGrid(n, n, w.patch, w.stride)
+    npt = max(4, int(32 * scale))
+    Pt = rng.standard_normal((npt, w.patch ** 2, T)) + 1j * rng.standard_normal((npt, w.patch ** 2, T))
+    t0 = time.perf_counter()
+    llr.svt_patches(Pt, 5.0)
+    parts["svt"] = (time.perf_counter() - t0) * pg.count / npt * 2
+    # graph: kNN over all patches on a sample of query rows
+    t1m = rng.uniform(100, 4000, (n, n))
+    t2m = rng.uniform(10, 500, (n, n))
+    Fe = graph.features(t1m, t2m, pg, 4000.0, 500.0)
+    rows = max(8, int(200 * scale))
+    t0 = time.perf_counter()
+    for i in range(rows):
+        di = np.sum((Fe - Fe[i]) ** 2, axis=1)
+        np.argsort(di, kind="stable")[:w.knn]
+    parts["knn"] = (time.perf_counter() - t0) * pg.count / rows
+    # graph term and trace with the dense Laplacian on Tg of the T frames
+    Tg = max(1, int(2 * scale))
+    img = rng.standard_normal((n, n, Tg)) + 1j * rng.standard_normal((n, n, Tg))
+    L = np.zeros((pg.count, pg.count))
+    t0 = time.perf_counter()
+    graph.graph_term(img, L, pg)
+    graph.trace_term(img, L, pg)
+    parts["graph_term"] = (time.perf_counter() - t0) * T / Tg
+    # projection and X update on full data
+    Xf = rng.standard_normal((n * n, T // 10)) + 1j * rng.standard_normal((n * n, T // 10))
+    phi = np.linalg.qr(rng.standard_normal((T // 10, w.rank)))[0]
+    t0 = time.perf_counter()
+    (Xf @ phi) @ phi.conj().T
+    parts["projection"] = (time.perf_counter() - t0) * 10 * 2
+    total = sum(parts.values())
+    sample = (f"per-step samples extrapolated to one iteration: NUFFT pair on {F} of {T} frames, "
+              f"matching {nv} of {n * n} voxels x {M} atoms x {T} frames, SVT of {npt} of {pg.count} "
+              f"{w.patch}x{w.patch}x{T} patches, kNN rows {rows} of {pg.count}, graph term on {Tg} of {T} "
+              f"frames, projection on {T // 10} frames")
+    return total, parts, sample
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    times = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        s, _, sample = oracle_iteration_seconds(scale=0.25)
+        if i >= args.warmup:
+            times.append(s)
+    sec = statistics.mean(times)
+    val = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "implementation": "FP64 CPU oracle (NumPy), literal full-frame form"},
+            "cpu_baseline": {"kind": "oracle", "value": val, "unit": "iters/s", "cores": cores(), "sample": sample},
+            "e2e": {"value": val, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, dist):
+    import torch
+
+    import paper_2310_05647_gb300 as mrf
+    from paper_2310_05647_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(dist.local)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    inp = make_inputs(seed=dist.rank)
+    w = inp["w"]
+    variants = [v for v in args.variants.split(",") if v]
+    res = {}
+    for v in variants:
+        res[v] = time_variant(v, inp, args.steps, args.warmup, dist)
+    main = "chosen" if "chosen" in res else variants[0]
+    r = res[main]
+    ms_step = dist.max(r["ms"]) / args.steps
+    value = dist.world * 1000.0 / ms_step
+    # dominant kernel of the main variant
+    prof = r["profile"]
+    kname = max(prof, key=lambda k: prof[k][0]) if prof else None
+    roof = None
+    if kname:
+        kms = prof[kname][0] / max(prof[kname][1], 1)
+        work = algorithmic_work(kname, inp)
+        if work and work[0] == "hbm":
+            ach = work[1] / (kms * 1e-3) / 1e9
+            roof = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach / hbm_peak, "peak_source": peak_src, "traffic": None,
+                    "algorithmic_bytes_per_launch": work[1], "ms_per_launch": kms}
+        elif work and work[0] == "alu":
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            ach = work[1] / (kms * 1e-3) / 1e12
+            roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock",
+                    "traffic": None, "algorithmic_flops_per_launch": work[1], "ms_per_launch": kms}
+        else:
+            roof = {"kernel": kname, "bound": None, "ms_per_launch": kms,
+                    "note": "no algorithmic-work model for this kernel"}
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in
+               sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": w.n, "frames": w.frames, "samples_per_frame": w.ns,
+                       "interleaves": w.interleaves, "grid": w.os * w.n, "kb_width": w.kb_width,
+                       "atoms": inp["atoms"], "rank": w.rank, "patch": w.patch, "stride": w.stride,
+                       "knn": w.knn, "variant": main, "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": f"{dist.world} independent slices (weak)"},
+            "variants": {v: {"iters_per_s": 1000.0 * args.steps / res[v]["ms"],
+                             "ms_per_step": res[v]["ms"] / args.steps, "nrmse_vs_truth": res[v]["nrmse"],
+                             "lam1": res[v]["info"]["lam1"]} for v in res},
+            "roofline": roof, "kernels": kernels, "clocks": r["clocks"], "gpu_launches": r["launches"]}
+    if "plain" in res and "chosen" in res:
+        import numpy as np
+        a, b = res["plain"]["maps"], res["chosen"]["maps"]
+        mask = inp["truth"][3]
+        line["chosen_vs_plain_nrmse"] = {nm: float(np.sqrt(np.sum((b[i][mask] - a[i][mask]) ** 2) /
+                                                           np.sum(a[i][mask] ** 2)))
+                                         for i, nm in enumerate(("t1", "t2", "pd"))}
+    if not args.no_e2e:
+        sec, h2d, d2h = e2e_chosen(inp, w.iters)
+        sec = dist.max(sec)
+        line["e2e"] = {"value": dist.world * w.iters / sec, "unit": "iters/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h,
+                       "what": f"host k-space -> device, init (A^H b, matching, graph), {w.iters} iterations, "
+                               f"maps -> host"}
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        sec, parts, sample = oracle_iteration_seconds(scale=1.0)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "iters/s", "cores": cores(), "kind": "oracle",
+                                "sample": sample, "seconds_by_step": parts}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

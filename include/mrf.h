@@ -202,6 +202,27 @@ mrf_status mrf_recon_info(mrf_recon r, double* a_norm, double* x_scale, double* 
                           double* sigma2, mrf_stream stream);
 mrf_status mrf_recon_destroy(mrf_recon r);
 
+/* ------------------------------------------------------------------------
+ * Tracing.  Not part of the method: launch accounting and per-kernel timing
+ * with CUDA events on the launching stream.
+ * ---------------------------------------------------------------------- */
+/* Kernels launched by this library since it was loaded (all threads). */
+long long mrf_launch_count(void);
+/* Turn the per-kernel event profiler on (1) or off (0); either way the
+ * recorded marks and totals are cleared.  While on, every launch records one
+ * event after the kernel and the interval since the previous mark on the same
+ * stream is charged to that kernel. */
+mrf_status mrf_profile_enable(int on);
+/* Boundary mark on `stream`: the next kernel's interval starts here (use it
+ * before a timed region so host work or foreign kernels are not charged). */
+mrf_status mrf_profile_mark(mrf_stream stream);
+/* Wait for the recorded events and fold them into per-kernel totals;
+ * returns the number of distinct kernel names (or -1 on a CUDA error). */
+int mrf_profile_collect(void);
+/* Entry i of the totals: kernel name (NUL-terminated, truncated to
+ * name_len), accumulated milliseconds and number of timed launches. */
+mrf_status mrf_profile_entry(int i, char* name, int name_len, double* ms, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

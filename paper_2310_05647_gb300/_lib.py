@@ -44,6 +44,11 @@ SIGNATURES = {
     "mrf_recon_alpha": (i32, [vp, vp, vp]),
     "mrf_recon_info": (i32, [vp, f64p, f64p, f64p, f64p, vp]),
     "mrf_recon_destroy": (i32, [vp]),
+    "mrf_launch_count": (C.c_longlong, []),
+    "mrf_profile_enable": (i32, [i32]),
+    "mrf_profile_mark": (i32, [vp]),
+    "mrf_profile_collect": (i32, []),
+    "mrf_profile_entry": (i32, [i32, C.c_char_p, i32, f64p, C.POINTER(C.c_longlong)]),
 }
 
 STATUS = {0: "MRF_OK", 1: "MRF_EINVAL", 2: "MRF_ENOMEM", 3: "MRF_ECUDA", 4: "MRF_ETIMEOUT",

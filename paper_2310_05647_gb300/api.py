@@ -233,3 +233,36 @@ class Recon:
             except Exception:
                 pass
             self.handle = None
+
+
+# ---------------------------------------------------------------------------
+# Tracing
+# ---------------------------------------------------------------------------
+def launch_count():
+    """Kernels launched by libmrf.so since it was loaded."""
+    return int(_lib.load().mrf_launch_count())
+
+
+def profile_enable(on=True):
+    _lib.call("mrf_profile_enable", 1 if on else 0)
+
+
+def profile_mark():
+    """Boundary on the current stream: the next kernel's interval starts here."""
+    _lib.call("mrf_profile_mark", _stream())
+
+
+def profile_read():
+    """{kernel name: (total ms, timed launches)} of the marks recorded so far."""
+    lib = _lib.load()
+    n = lib.mrf_profile_collect()
+    if n < 0:
+        raise MRFError("mrf_profile_collect", 3, lib.mrf_last_error().decode())
+    out = {}
+    buf = C.create_string_buffer(128)
+    ms = C.c_double()
+    cnt = C.c_longlong()
+    for i in range(n):
+        _lib.call("mrf_profile_entry", i, buf, 128, C.byref(ms), C.byref(cnt))
+        out[buf.value.decode()] = (ms.value, cnt.value)
+    return out

@@ -13,6 +13,12 @@ namespace mrf {
 // Thread-local error message, read back through mrf_last_error().
 void set_error(const char* fmt, ...);
 
+// Launch accounting and the optional per-kernel CUDA-event profiler: every
+// launch site reports itself after the launch; with profiling on, an event is
+// recorded on the launching stream and the interval since the previous event
+// on that stream is charged to the kernel.
+void note_launch(const char* name, cudaStream_t s);
+
 inline cudaStream_t as_stream(mrf_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -51,7 +57,11 @@ __host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a
         }                                                                                \
     } while (0)
 
-#define MRF_LAUNCHED() MRF_CUDA(cudaGetLastError())
+#define MRF_LAUNCHED_AS(name, stream)                                                    \
+    do {                                                                                 \
+        MRF_CUDA(cudaGetLastError());                                                    \
+        mrf::note_launch(name, stream);                                                  \
+    } while (0)
 
 #define MRF_PROPAGATE(expr)                                                              \
     do {                                                                                 \

@@ -106,6 +106,6 @@ extern "C" mrf_status mrf_epg_fisp(const float* t1t2, int m, const float* fa_deg
     MRF_CUDA(cudaFuncSetAttribute(k_epg_fisp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_epg_fisp<<<m, kEpgThreads, smem, as_stream(stream)>>>(t1t2, m, fa_deg, tr_ms, T, te_ms, ti_ms, inversion,
                                                             reinterpret_cast<float2*>(out));
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_epg_fisp", as_stream(stream));
     return MRF_OK;
 }

@@ -183,7 +183,7 @@ mrf_status MatchWorkspace::reserve(int n, int m) {
 mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* norm2_in, int m, int len,
                          int literal, cudaStream_t s) {
     k_match_weights<<<(m + 255) / 256, 256, 0, s>>>(dict, norm2_in, m, len, literal, ws.norm2, ws.wscore);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_match_weights", s);
     return MRF_OK;
 }
 
@@ -195,11 +195,11 @@ mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const 
         MRF_PROPAGATE(match_rerank(ws, x, n, len, dict, s));
     } else {
         k_match_fp32<<<(n + BM - 1) / BM, 256, 0, s>>>(x, n, len, dict, ws.wscore, m, ws.best_idx, ws.best_ip);
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_match_fp32", s);
     }
     k_match_finish<<<(n + 255) / 256, 256, 0, s>>>(ws.best_idx, ws.best_ip, n, ws.norm2, lut, idx, pd, t1t2,
                                                    pd_scale);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_match_finish", s);
     return MRF_OK;
 }
 

@@ -514,7 +514,7 @@ mrf_status launch_rows_fwd(const mrf_plan_s* p, const float2* src, int src_mode,
             k_rows_fwd<GG, 1><<<grid, kThreads, sm, s>>>(src, K, h1, p->inv_dx, p->inv_dy, p->nx, p->ny);
         }
     });
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_rows_fwd", s);
     return MRF_OK;
 }
 
@@ -528,7 +528,7 @@ mrf_status launch_cols_interp(const mrf_plan_s* p, const float2* h1, float2* y, 
         k_cols_interp<GG, WW><<<grid, kThreads, sm, s>>>(h1, y, b, scale, p->fwd_rec, p->fwd_off, p->group_of,
                                                          p->ny, p->ns, p->nstrips, p->beta);
     }));
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_cols_interp", s);
     return MRF_OK;
 }
 
@@ -548,7 +548,7 @@ mrf_status launch_spread_cols(const mrf_plan_s* p, const float2* y, int src_mode
                                                                 p->ngroups, p->ny, p->ns, p->nstrips, p->beta);
         }
     }));
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_spread_cols", s);
     return MRF_OK;
 }
 
@@ -567,7 +567,7 @@ mrf_status launch_rows_adj(const mrf_plan_s* p, const float2* h1, float2* dst, i
             k_rows_adj<GG, 1><<<grid, kThreads, sm, s>>>(h1, dst, K, scale, p->inv_dx, p->inv_dy, p->nx, p->ny);
         }
     });
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_rows_adj", s);
     return MRF_OK;
 }
 
@@ -787,7 +787,7 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
             k_rows_fwd_expand<GG><<<grid, kThreads, sm, s>>>(alpha, phi, K, p->T, p->h1, p->inv_dx, p->inv_dy,
                                                              p->nx, p->ny);
         });
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_rows_fwd_expand", s);
         return launch_cols_interp(p, p->h1, y, b, scale, s);
     }
     MRF_PROPAGATE(ensure_subspace_workspace(p, K));
@@ -800,7 +800,7 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
             MRF_PROPAGATE(set_smem(k_cols_store<GG>, sm));
             k_cols_store<GG><<<grid, kThreads, sm, s>>>(p->sub_h1, p->sub_spec, p->ny);
         });
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_cols_store", s);
     }
     {
         const int total = p->ngroups * p->ns;
@@ -808,12 +808,12 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
             k_interp_groups<GG, WW><<<(total + 255) / 256, 256, 0, s>>>(p->sub_spec, K, p->grec, total, p->sub_Y,
                                                                         p->beta);
         }));
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_interp_groups", s);
     }
     const size_t n = (size_t)p->T * p->ns;
     k_combine_fwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->sub_Y, phi, K, p->group_of, p->T, p->ns, scale,
                                                                b, y);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_combine_fwd", s);
     return MRF_OK;
 }
 
@@ -834,18 +834,18 @@ mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, i
             k_rows_adj_reduce<GG><<<grid, kThreads, sm, s>>>(p->h1, phi, K, p->T, p->frames_per_part,
                                                              p->sub_partial, p->inv_dx, p->inv_dy, p->nx, p->ny);
         });
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_rows_adj_reduce", s);
         const size_t n = (size_t)p->ny * p->nx * K;
         k_sum_parts<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(p->sub_partial, p->parts, n,
                                                                                         scale, alpha_out);
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_sum_parts", s);
         return MRF_OK;
     }
     {
         const size_t n = (size_t)p->ngroups * p->ns;
         k_combine_adj<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(y, phi, K, p->gf_off, p->gf, p->ngroups, p->ns,
                                                                    p->sub_R);
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_combine_adj", s);
     }
     MRF_PROPAGATE(launch_spread_cols(p, p->sub_R, 1, K, K, p->sub_h1, s));
     MRF_PROPAGATE(launch_rows_adj(p, p->sub_h1, alpha_out, 1, K, K, scale, s));

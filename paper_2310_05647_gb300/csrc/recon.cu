@@ -614,7 +614,7 @@ static mrf_status svt(mrf_recon_s* R, const float2* alpha, float2* P, double* nu
         if (KP == 4) MRF_SVT(4, 4); else if (KP == 8) MRF_SVT(4, 8); else if (KP == 12) MRF_SVT(4, 12); else MRF_SVT(4, 16);
     }
 #undef MRF_SVT
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_svt", s);
     return MRF_OK;
 }
 
@@ -623,7 +623,7 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
     const int np = R->np, knn = R->prm.knn, FD = 2 * R->pp;
     k_features<<<(unsigned)(((size_t)np * R->pp + 255) / 256), 256, 0, s>>>(R->t1t2, R->g, (double)R->t1max,
                                                                              (double)R->t2max, R->F);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_features", s);
     const size_t sm = sizeof(int) * (size_t)(32 + 64) * (FD + 1);
     if (knn <= 16) {
         MRF_CUDA(cudaFuncSetAttribute(k_knn<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -632,25 +632,25 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
         MRF_CUDA(cudaFuncSetAttribute(k_knn<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_knn<32><<<(np + 31) / 32, 256, sm, s>>>(R->F, np, FD, knn, R->nbr, R->d2);
     }
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_knn", s);
     const int ne = np * knn;
     k_median_nonzero<<<1, 1024, 0, s>>>(R->d2, ne, R->scal + 0);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_median_nonzero", s);
     MRF_CUDA(cudaMemsetAsync(R->rcnt, 0, sizeof(int) * np, s));
     MRF_CUDA(cudaMemsetAsync(R->rpos, 0, sizeof(int) * np, s));
     k_edge_weights<<<(ne + 255) / 256, 256, 0, s>>>(R->nbr, R->d2, ne, R->scal + 0, R->w, R->rcnt);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_edge_weights", s);
     k_scan<<<1, 1024, 0, s>>>(R->rcnt, np, R->roff);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_scan", s);
     k_fill_reverse<<<(ne + 255) / 256, 256, 0, s>>>(R->nbr, R->w, ne, knn, R->roff, R->rpos, R->rsrc, R->rw);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_fill_reverse", s);
     k_degree<<<(np + 127) / 128, 128, 0, s>>>(R->w, np, knn, R->roff, R->rsrc, R->rw, R->deg);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_degree", s);
     k_max<<<1, 1024, 0, s>>>(R->deg, np, R->scal + 1);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_max", s);
     k_lambda<<<1, 1, 0, s>>>(R->scal + 1, R->prm.lam1_0, (R->prm.flags & MRF_RECON_LITERAL_LAMBDA1) ? 1 : 0,
                              R->scal + 2);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_lambda", s);
     return MRF_OK;
 }
 
@@ -662,7 +662,7 @@ static mrf_status match_maps(mrf_recon_s* R, cudaStream_t s) {
 static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s) {
     k_graph_blocks<<<R->np, 128, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc, R->rw,
                                          R->deg, QL, trace);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_graph_blocks", s);
     return MRF_OK;
 }
 
@@ -677,17 +677,17 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     k_xupdate<<<(unsigned)((NK + 255) / 256), 256, 0, s>>>(
         R->alpha, R->grad, R->QL, R->P, R->g, R->K, R->prm.mu, c, R->scal + 2,
         (R->prm.flags & MRF_RECON_LITERAL_XUPDATE) ? 1 : 0, nullptr);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_xupdate", s);
     MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, s));
     if (cost) MRF_CUDA(cudaMemsetAsync(R->acc, 0, 3 * sizeof(double), s));
     MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, s));
     if (cost) {
         const size_t nr = (size_t)R->plan->T * R->plan->ns;
         k_norm2_acc<<<nblk(nr), 256, 0, s>>>(R->r, nr, R->acc + 0);
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_norm2_acc", s);
         MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, s));
         k_cost<<<1, 1, 0, s>>>(R->acc, R->scal + 2, R->prm.lam2, R->cost + (it % R->cost_cap));
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_cost", s);
     }
     MRF_PROPAGATE(match_maps(R, s));
     MRF_PROPAGATE(build_graph(R, s));
@@ -751,21 +751,22 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     // coverage counts
     k_xupdate<<<(unsigned)((NK + 255) / 256), 256, 0, s>>>(R->alpha, nullptr, nullptr, nullptr, R->g, K, 0.f, 0.f,
                                                           nullptr, 0, R->cnt);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_xupdate", s);
     // a = ||A P_S||_2 by power iteration on coefficient images
     if (R->prm.a_norm > 0.f) {
         R->a = R->prm.a_norm;
     } else {
         k_fill<<<nblk(NK), 256, 0, s>>>(R->alpha, NK, make_float2((float)(1.0 / std::sqrt((double)NK)), 0.f));
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_fill", s);
         double lam = 0.0;
         for (int it = 0; it < R->prm.power_iters; ++it) {
             MRF_PROPAGATE(subspace_forward(p, R->alpha, R->phi, K, 1.0f, nullptr, R->r, R->mode, s));
             MRF_PROPAGATE(subspace_adjoint(p, R->r, R->phi, K, 1.0f, R->grad, R->mode, s));
             MRF_CUDA(cudaMemsetAsync(R->acc, 0, 4 * sizeof(double), s));
             k_dot_acc<<<nblk(NK), 256, 0, s>>>(R->alpha, R->grad, NK, R->acc + 0);
+            MRF_LAUNCHED_AS("k_dot_acc", s);
             k_norm2_acc<<<nblk(NK), 256, 0, s>>>(R->grad, NK, R->acc + 2);
-            MRF_LAUNCHED();
+            MRF_LAUNCHED_AS("k_norm2_acc", s);
             double h[4];
             MRF_CUDA(cudaMemcpyAsync(h, R->acc, sizeof(h), cudaMemcpyDeviceToHost, s));
             MRF_CUDA(cudaStreamSynchronize(s));
@@ -773,7 +774,7 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
             const double nw = std::sqrt(h[2]);
             MRF_REQUIRE(nw > 0.0, "mrf_recon_create: the operator maps the start vector to zero");
             k_scale_copy<<<nblk(NK), 256, 0, s>>>(R->grad, NK, (float)(1.0 / nw), R->alpha);
-            MRF_LAUNCHED();
+            MRF_LAUNCHED_AS("k_scale_copy", s);
         }
         MRF_REQUIRE(lam > 0.0, "mrf_recon_create: non-positive operator norm estimate");
         R->a = std::sqrt(lam);
@@ -786,7 +787,7 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
         R->gamma = R->prm.x_scale;
     } else {
         k_max<<<1, 1024, 0, s>>>(R->pd, N, R->scal + 3);
-        MRF_LAUNCHED();
+        MRF_LAUNCHED_AS("k_max", s);
         float mx = 0.f;
         MRF_CUDA(cudaMemcpyAsync(&mx, R->scal + 3, sizeof(float), cudaMemcpyDeviceToHost, s));
         MRF_CUDA(cudaStreamSynchronize(s));
@@ -794,8 +795,9 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     }
     const float gm = (float)R->gamma;
     k_scale<<<nblk(NK), 256, 0, s>>>(R->alpha, NK, gm);
+    MRF_LAUNCHED_AS("k_scale", s);
     k_scale_copy<<<nblk(nr), 256, 0, s>>>(b, nr, (float)(R->gamma / R->a), R->bs);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_scale_copy", s);
     MRF_PROPAGATE(match_maps(R, s));                     // maps in the scaled units
     MRF_PROPAGATE(build_graph(R, s));
     MRF_PROPAGATE(subspace_forward(p, R->alpha, R->phi, K, inv_a, R->bs, R->r, R->mode, s));
@@ -873,7 +875,7 @@ extern "C" mrf_status mrf_recon_maps(mrf_recon R, float* t1, float* t2, float* p
     MRF_REQUIRE(R != nullptr, "mrf_recon_maps: NULL recon");
     k_maps<<<(R->N + 255) / 256, 256, 0, as_stream(stream)>>>(R->t1t2, R->pd, R->idx, R->N, (float)(1.0 / R->gamma),
                                                                t1, t2, pd, idx);
-    MRF_LAUNCHED();
+    MRF_LAUNCHED_AS("k_maps", as_stream(stream));
     return MRF_OK;
 }
 
