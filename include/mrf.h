@@ -147,6 +147,27 @@ mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64* dict,
                      const float* atom_norm2, const float* lut, int m, int precision,
                      int* idx, float* pd, float* t1t2, mrf_stream stream);
 
+/* Same result as mrf_match with MRF_MATCH_FP32, for callers that cannot
+ * allocate device memory when they match (the paper has no counterpart: this
+ * is a deployment variant).  A reconstruction service that reserves the
+ * GPU's memory for its own pool at start-up, or a latency-bound serving loop
+ * that must not pay for cudaMalloc/cudaFree (they can block the host and
+ * synchronise the device), can call this instead.  The scratch lives in one
+ * fixed device array inside the library, sized for at most 262144
+ * fingerprints (n) and 65536 atoms (m), about 3.6 MB that every GPU which
+ * loads the library holds until the process exits; larger n or m return
+ * MRF_EINVAL with a message.  The first call on a device looks up the
+ * array's device address with that device current, so make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller.  Every scratch word a call reads
+ * is written by the same call first, so no clearing is needed between calls.
+ * Arguments as in mrf_match; precision must be MRF_MATCH_FP32, optionally
+ * with MRF_MATCH_LITERAL_NORM2. */
+mrf_status mrf_match_noalloc(const mrf_c64* x, int n, int len, const mrf_c64* dict,
+                             const float* atom_norm2, const float* lut, int m, int precision,
+                             int* idx, float* pd, float* t1t2, mrf_stream stream);
+
 /* ------------------------------------------------------------------------
  * Algorithm 1 (MS-LLR).  The iterate is held in the temporal subspace,
  * X = alpha Phi^H with alpha dev [ny][nx][K]; the problem is posed over

@@ -8,6 +8,8 @@
 // fingerprint, the running best (score, index, inner product) over all atom
 // tiles; no fingerprint x atom score is ever written to memory.  The BF16
 // tensor-core form lives in match_tc.cu.
+#include <mutex>
+
 #include "common.h"
 #include "match.h"
 
@@ -234,4 +236,95 @@ extern "C" mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64*
     MRF_CUDA(cudaFreeAsync(base, s));
     return st;
     return MRF_OK;
+}
+
+namespace mrf {
+
+// ---------------------------------------------------------------------------
+// Matching without device allocation.
+//
+// Some callers cannot allocate device memory at the moment they match: a
+// scanner-side reconstruction service that reserves all of the GPU's memory
+// for its own pool at start-up (a cudaMalloc then fails or steals from that
+// pool), or a latency-bound serving loop that must not pay for cudaMalloc /
+// cudaFree (which can block the host and synchronise the device).  This
+// variant keeps the per-call scratch of the FP32 matcher in a fixed
+// file-scope device array instead: up to kNoAllocMaxN fingerprints and
+// kNoAllocMaxM atoms (about 3.6 MB, held by every GPU that loads the
+// library until the process exits).
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxN = 1 << 18;   // 512 x 512 voxels
+constexpr int kNoAllocMaxM = 1 << 16;   // atoms
+constexpr size_t kAlign = 256;
+constexpr size_t round_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t kNoAllocBytes = round_up(sizeof(int) * kNoAllocMaxN) + round_up(sizeof(float2) * kNoAllocMaxN) +
+                                 2 * round_up(sizeof(float) * kNoAllocMaxM);
+
+static __device__ __align__(256) unsigned char g_match_scratch[kNoAllocBytes];
+
+// Device address of g_match_scratch, looked up once per device (with that
+// device current) on the first call made there.
+static char* scratch_for_current_device(mrf_status* st) {
+    static std::mutex mu;
+    static char* addr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        set_error("mrf_match_noalloc: no usable current device");
+        *st = MRF_ECUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_match_scratch);
+        if (e != cudaSuccess) {
+            set_error("mrf_match_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            *st = MRF_ECUDA;
+            return nullptr;
+        }
+        addr[dev] = static_cast<char*>(p);
+    }
+    return addr[dev];
+}
+
+}  // namespace mrf
+
+extern "C" mrf_status mrf_match_noalloc(const mrf_c64* x, int n, int len, const mrf_c64* dict,
+                                        const float* atom_norm2, const float* lut, int m, int precision,
+                                        int* idx, float* pd, float* t1t2, mrf_stream stream) {
+    using namespace mrf;
+    MRF_REQUIRE(x && dict && lut, "mrf_match_noalloc: NULL x, dict or lut");
+    MRF_REQUIRE(n >= 0 && len >= 1 && len <= 2048, "mrf_match_noalloc: bad n or len (%d, %d)", n, len);
+    MRF_REQUIRE(n <= kNoAllocMaxN, "mrf_match_noalloc: n = %d exceeds the fixed scratch (at most %d fingerprints)",
+                n, kNoAllocMaxN);
+    MRF_REQUIRE(m >= 1 && m <= kNoAllocMaxM,
+                "mrf_match_noalloc: m = %d outside [1, %d] (the fixed scratch holds at most %d atoms)", m,
+                kNoAllocMaxM, kNoAllocMaxM);
+    const int prec = precision & 0xff;
+    const int literal = (precision & MRF_MATCH_LITERAL_NORM2) ? 1 : 0;
+    MRF_REQUIRE(prec == MRF_MATCH_FP32, "mrf_match_noalloc: only MRF_MATCH_FP32 (got %d)", prec);
+    if (n == 0) return MRF_OK;
+    mrf_status st = MRF_OK;
+    char* base = scratch_for_current_device(&st);
+    if (!base) return st;
+    // every scratch word this call reads is written by this call first, so
+    // nothing needs clearing between calls
+    MatchWorkspace ws;
+    ws.best_idx = reinterpret_cast<int*>(base);
+    base += round_up(sizeof(int) * kNoAllocMaxN);
+    ws.best_ip = reinterpret_cast<float2*>(base);
+    base += round_up(sizeof(float2) * kNoAllocMaxN);
+    ws.norm2 = reinterpret_cast<float*>(base);
+    base += round_up(sizeof(float) * kNoAllocMaxM);
+    ws.wscore = reinterpret_cast<float*>(base);
+    ws.cap_n = n;
+    ws.cap_m = m;
+    ws.borrowed = true;
+    cudaStream_t s = as_stream(stream);
+    st = match_prepare(ws, reinterpret_cast<const float2*>(dict), atom_norm2, m, len, literal, s);
+    if (st == MRF_OK)
+        st = match_run(ws, reinterpret_cast<const float2*>(x), n, len, reinterpret_cast<const float2*>(dict), m,
+                       MRF_MATCH_FP32, lut, idx, pd, t1t2, 1.0f, s);
+    ws.detach();
+    return st;
 }
