@@ -447,7 +447,11 @@ def run_ours(args, dist):
                        "parallelism": f"{dist.world} independent slices (weak)"},
             "variants": {v: {"iters_per_s": 1000.0 * args.steps / res[v]["ms"],
                              "ms_per_step": res[v]["ms"] / args.steps, "nrmse_vs_truth": res[v]["nrmse"],
-                             "lam1": res[v]["info"]["lam1"]} for v in res},
+                             "lam1": res[v]["info"]["lam1"],
+                             "top_kernels_ms_per_step": {k: round(t[0] / args.steps, 4) for k, t in
+                                                         sorted(res[v]["profile"].items(),
+                                                                key=lambda kv: -kv[1][0])[:8]}}
+                         for v in res},
             "roofline": roof, "kernels": kernels, "clocks": r["clocks"], "gpu_launches": r["launches"]}
     if "plain" in res and "chosen" in res:
         import numpy as np

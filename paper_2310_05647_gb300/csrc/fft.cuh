@@ -143,3 +143,69 @@ __device__ __forceinline__ void fft_smem(float2* s, int stride, int tid, bool ac
 }
 
 }  // namespace mrf
+
+namespace mrf {
+
+// ---------------------------------------------------------------------------
+// Batched form: B independent length-N transforms processed by the whole
+// block of NT threads.  Thread t works on transform t % B and on butterflies
+// t / B, t / B + NT / B, ... of every pass, so consecutive lanes touch the
+// same element of consecutive transforms.  Element i of transform b lives at
+// s[b * bstride + i * estride]; with columns of a [rows][B] tile (estride = B,
+// bstride = 1) or rows padded to an odd stride (estride = 1, bstride = N + 1)
+// every shared-memory access of a warp is bank-conflict free.
+// ---------------------------------------------------------------------------
+template <int N, int R, int NWK, bool INV>
+__device__ __forceinline__ void batch_pass(float2* t, int es, int Ns, int wk, const float2* tw) {
+    constexpr int NB = N / R;
+    constexpr int PER = (NB + NWK - 1) / NWK;
+    float2 v[PER][R];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int j = wk + q * NWK;
+        if (j < NB) {
+            const int jm = j & (Ns - 1);
+            const int step = N / (Ns * R);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 x = t[(j + r * NB) * es];
+                if (r > 0) x = twiddle<INV>(x, tw[r * jm * step]);
+                v[q][r] = x;
+            }
+            dft_r<R, INV>(v[q]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int j = wk + q * NWK;
+        if (j < NB) {
+            const int jm = j & (Ns - 1);
+            const int d = (j - jm) * R + jm;
+#pragma unroll
+            for (int r = 0; r < R; ++r) t[(d + r * Ns) * es] = v[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int N, int B, int NT, bool INV>
+__device__ __forceinline__ void fft_batch(float2* s, int estride, int bstride, const float2* tw) {
+    static_assert(NT % B == 0, "block size must be a multiple of the batch");
+    constexpr int NWK = NT / B;
+    constexpr int L = ilog2(N);
+    constexpr int N8 = L / 3;
+    constexpr int REM = L % 3;
+    float2* t = s + (threadIdx.x % B) * bstride;
+    const int wk = threadIdx.x / B;
+    int Ns = 1;
+#pragma unroll
+    for (int p = 0; p < N8; ++p) {
+        batch_pass<N, 8, NWK, INV>(t, estride, Ns, wk, tw);
+        Ns *= 8;
+    }
+    if constexpr (REM == 2) batch_pass<N, 4, NWK, INV>(t, estride, Ns, wk, tw);
+    if constexpr (REM == 1) batch_pass<N, 2, NWK, INV>(t, estride, Ns, wk, tw);
+}
+
+}  // namespace mrf

@@ -7,11 +7,16 @@
 //                      inverse FFT along x + crop + deapod  (k_rows_adj)
 //
 // The oversampled grid G x G of a frame is never written to HBM: the column
-// kernels own a 32-column strip of the frame in shared memory, transform it
-// there and interpolate (or spread) the samples binned to that strip.  Only
-// the half-oversampled intermediate H1 [T][ny][G] (rows transformed along x)
-// goes through memory.  Samples are binned per strip on the host when the plan
-// is built; frames with identical sample positions share one binned copy.
+// kernels own a 32-column strip of the frame in shared memory ([G][32], one
+// column per lane of a warp), transform it there and interpolate (or spread)
+// the samples binned to that strip.  A forward strip owns 32 - (W - 1)
+// columns and carries W - 1 halo columns so each sample's W x W nodes are in
+// the tile; an adjoint strip owns all 32 columns and a sample that straddles
+// two strips is spread by both.  Only the half-oversampled intermediate
+// H1 [T][ny][G] (rows transformed along x) goes through memory.  Row kernels
+// transform 16 rows per block in a [16][G + 1] tile (odd row stride, one row
+// per lane).  Samples are binned on the host when the plan is built; frames
+// with identical sample positions share one binned copy.
 //
 // Kernel: psi(u) = I0(beta sqrt(1 - (2u/W)^2)), |u| <= W/2, with Beatty's
 // beta = pi sqrt((W/os)^2 (os - 1/2)^2 - 0.8); deapodisation divides by its
@@ -28,8 +33,10 @@
 
 namespace mrf {
 
-constexpr int kStrip = 32;      // grid columns per strip
-constexpr int kThreads = 512;   // threads of every FFT kernel
+constexpr int kTile = 32;        // columns per strip tile (one per lane)
+constexpr int kColThreads = 512; // threads of the strip kernels
+constexpr int kRowB = 16;        // rows (or frames) per row-kernel block
+constexpr int kRowThreads = 256; // threads of the row kernels
 
 template <int W>
 __device__ __forceinline__ void kb_weights(float f, float beta, float* w) {
@@ -54,99 +61,91 @@ __device__ __forceinline__ int centred(int g) { return g < G / 2 ? g : g - G; }
 
 // ---------------------------------------------------------------------------
 // Forward stage 1: rows.  SRC 0: frames x[t][iy][ix]; SRC 1: coefficient image
-// k of alpha[iy][ix][K] (blockIdx.y = k).
+// k of alpha[iy][ix][K] (blockIdx.y = k).  Block: 16 rows of one frame.
 // ---------------------------------------------------------------------------
 template <int G, int SRC>
-__global__ void __launch_bounds__(kThreads) k_rows_fwd(const float2* __restrict__ x, int K,
-                                                       float2* __restrict__ h1,
-                                                       const float* __restrict__ inv_dx,
-                                                       const float* __restrict__ inv_dy, int nx, int ny) {
-    constexpr int TPF = G / 8;
-    constexpr int RPC = kThreads / TPF;
+__global__ void __launch_bounds__(kRowThreads) k_rows_fwd(const float2* __restrict__ x, int K,
+                                                          float2* __restrict__ h1,
+                                                          const float* __restrict__ inv_dx,
+                                                          const float* __restrict__ inv_dy, int nx, int ny) {
     extern __shared__ float2 sm[];
     float2* tw = sm;
-    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
-    float2* row = sm + G + grp * G;
+    float2* rows = sm + G;                        // [kRowB][G + 1]
+    constexpr int LD = G + 1;
     const int t = blockIdx.y;
-    const int iy = blockIdx.x * RPC + grp;
-    const bool active = iy < ny;
+    const int iy0 = blockIdx.x * kRowB;
     fft_twiddles<G>(tw);
-    if (active) {
-        const float sy = inv_dy[iy];
-        for (int g = tid; g < G; g += TPF) {
-            const int ix = centred<G>(g) + nx / 2;
-            float2 v = make_float2(0.f, 0.f);
-            if (ix >= 0 && ix < nx) {
-                if (SRC == 0) v = x[((size_t)t * ny + iy) * nx + ix];
-                else v = x[((size_t)iy * nx + ix) * K + t];
-                v = cscale(v, inv_dx[ix] * sy);
-            }
-            row[g] = v;
+    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
+        const int r = idx / G, g = idx - r * G;
+        const int iy = iy0 + r;
+        const int ix = centred<G>(g) + nx / 2;
+        float2 v = make_float2(0.f, 0.f);
+        if (iy < ny && ix >= 0 && ix < nx) {
+            v = SRC == 0 ? x[((size_t)t * ny + iy) * nx + ix] : x[((size_t)iy * nx + ix) * K + t];
+            v = cscale(v, inv_dx[ix] * inv_dy[iy]);
         }
+        rows[r * LD + g] = v;
     }
     __syncthreads();
-    fft_smem<G, false>(row, 1, tid, active, tw);
-    if (active) {
-        float2* dst = h1 + ((size_t)t * ny + iy) * G;
-        for (int g = tid; g < G; g += TPF) dst[g] = row[g];
+    fft_batch<G, kRowB, kRowThreads, false>(rows, 1, LD, tw);
+    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
+        const int r = idx / G, g = idx - r * G;
+        const int iy = iy0 + r;
+        if (iy < ny) h1[((size_t)t * ny + iy) * G + g] = rows[r * LD + g];
     }
 }
 
 // Forward stage 1 in subspace form: frame t row iy is sum_k alpha[iy][ix][k]
-// conj(phi[t][k]).  Block = one image row x (kThreads / (G/8)) frames.
+// conj(phi[t][k]).  Block = one image row x 16 frames.
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_rows_fwd_expand(const float2* __restrict__ alpha,
-                                                              const float2* __restrict__ phi, int K, int T,
-                                                              float2* __restrict__ h1,
-                                                              const float* __restrict__ inv_dx,
-                                                              const float* __restrict__ inv_dy, int nx,
-                                                              int ny) {
-    constexpr int TPF = G / 8;
-    constexpr int FPC = kThreads / TPF;
+__global__ void __launch_bounds__(kRowThreads) k_rows_fwd_expand(const float2* __restrict__ alpha,
+                                                                 const float2* __restrict__ phi, int K, int T,
+                                                                 float2* __restrict__ h1,
+                                                                 const float* __restrict__ inv_dx,
+                                                                 const float* __restrict__ inv_dy, int nx,
+                                                                 int ny) {
     extern __shared__ float2 sm[];
+    constexpr int LD = G + 1;
     float2* tw = sm;
-    float2* rows = sm + G;                 // [FPC][G]
-    float2* arow = rows + FPC * G;         // [nx][K]
-    float2* ph = arow + nx * K;            // [FPC][K]
-    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
+    float2* rows = sm + G;                 // [kRowB][G + 1]
+    float2* arow = rows + kRowB * LD;      // [nx][K]
+    float2* ph = arow + nx * K;            // [kRowB][K]
     const int iy = blockIdx.x;
-    const int t0 = blockIdx.y * FPC;
-    const int t = t0 + grp;
-    const bool active = t < T;
+    const int t0 = blockIdx.y * kRowB;
     fft_twiddles<G>(tw);
-    for (int i = threadIdx.x; i < nx * K; i += blockDim.x) arow[i] = alpha[(size_t)iy * nx * K + i];
-    for (int i = threadIdx.x; i < FPC * K; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nx * K; i += kRowThreads) arow[i] = alpha[(size_t)iy * nx * K + i];
+    for (int i = threadIdx.x; i < kRowB * K; i += kRowThreads) {
         const int tt = t0 + i / K;
         ph[i] = tt < T ? phi[(size_t)tt * K + (i % K)] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2* row = rows + grp * G;
-    if (active) {
-        const float sy = inv_dy[iy];
-        for (int g = tid; g < G; g += TPF) {
-            const int ix = centred<G>(g) + nx / 2;
-            float2 v = make_float2(0.f, 0.f);
-            if (ix >= 0 && ix < nx) {
-                for (int k = 0; k < K; ++k) v = cadd(v, cmulc(arow[ix * K + k], ph[grp * K + k]));
-                v = cscale(v, inv_dx[ix] * sy);
-            }
-            row[g] = v;
+    const float sy = inv_dy[iy];
+    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
+        const int r = idx / G, g = idx - r * G;
+        const int ix = centred<G>(g) + nx / 2;
+        float2 v = make_float2(0.f, 0.f);
+        if (ix >= 0 && ix < nx && t0 + r < T) {
+            const float2* a = arow + ix * K;
+            const float2* p = ph + r * K;
+            for (int k = 0; k < K; ++k) v = cadd(v, cmulc(a[k], p[k]));
+            v = cscale(v, inv_dx[ix] * sy);
         }
+        rows[r * LD + g] = v;
     }
     __syncthreads();
-    fft_smem<G, false>(row, 1, tid, active, tw);
-    if (active) {
-        float2* dst = h1 + ((size_t)t * ny + iy) * G;
-        for (int g = tid; g < G; g += TPF) dst[g] = row[g];
+    fft_batch<G, kRowB, kRowThreads, false>(rows, 1, LD, tw);
+    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
+        const int r = idx / G, g = idx - r * G;
+        if (t0 + r < T) h1[((size_t)(t0 + r) * ny + iy) * G + g] = rows[r * LD + g];
     }
 }
 
-// Load a strip (C columns starting at c0, wrapping) of frame f's H1 into the
-// shared tile [G][C]; rows outside the image's support are zero.
-template <int G, int C>
+// Load a strip (kTile columns starting at c0, wrapping) of one image's H1 into
+// the shared tile [G][kTile]; rows outside the image's support are zero.
+template <int G>
 __device__ __forceinline__ void load_strip(float2* tile, const float2* __restrict__ h1f, int c0, int ny) {
-    for (int idx = threadIdx.x; idx < G * C; idx += blockDim.x) {
-        const int gy = idx / C, c = idx - gy * C;
+    for (int idx = threadIdx.x; idx < G * kTile; idx += blockDim.x) {
+        const int gy = idx / kTile, c = idx & (kTile - 1);
         const int iy = centred<G>(gy) + ny / 2;
         float2 v = make_float2(0.f, 0.f);
         if (iy >= 0 && iy < ny) v = h1f[(size_t)iy * G + ((c0 + c) & (G - 1))];
@@ -155,42 +154,31 @@ __device__ __forceinline__ void load_strip(float2* tile, const float2* __restric
     __syncthreads();
 }
 
-template <int G, bool INV>
-__device__ __forceinline__ void strip_column_ffts(float2* tile, int C, const float2* tw) {
-    constexpr int TPF = G / 8;
-    const int cpr = blockDim.x / TPF;
-    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
-    for (int cb = 0; cb < C; cb += cpr) {
-        const int c = cb + grp;
-        const bool active = c < C;
-        fft_smem<G, INV>(tile + (active ? c : 0), C, tid, active, tw);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Forward stage 2: FFT of a strip's columns in shared memory, then KB
-// interpolation of the samples whose first x-node falls in the strip.
-// y = scale * interp - b  (b nullable).
+// interpolation of the samples whose first x-node falls in the strip's owned
+// columns.  y = scale * interp - b  (b nullable).
 // ---------------------------------------------------------------------------
 template <int G, int W>
-__global__ void __launch_bounds__(kThreads) k_cols_interp(const float2* __restrict__ h1, float2* __restrict__ y,
-                                                          const float2* __restrict__ bsub, float scale,
-                                                          const int4* __restrict__ rec,
-                                                          const int* __restrict__ off,
-                                                          const int* __restrict__ group_of, int ny, int ns,
-                                                          int nstrips, float beta) {
-    constexpr int C = kStrip + W - 1;
+__global__ void __launch_bounds__(kColThreads) k_cols_interp(const float2* __restrict__ h1,
+                                                             float2* __restrict__ y,
+                                                             const float2* __restrict__ bsub, float scale,
+                                                             const int4* __restrict__ rec,
+                                                             const int* __restrict__ off,
+                                                             const int* __restrict__ group_of, int ny, int ns,
+                                                             int nstrips, float beta) {
+    constexpr int SF = kTile - (W - 1);
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* tile = sm + G;
     const int strip = blockIdx.x, t = blockIdx.y;
-    const int c0 = strip * kStrip;
+    const int c0 = strip * SF;
     fft_twiddles<G>(tw);
-    load_strip<G, C>(tile, h1 + (size_t)t * ny * G, c0, ny);
-    strip_column_ffts<G, false>(tile, C, tw);
+    load_strip<G>(tile, h1 + (size_t)t * ny * G, c0, ny);
+    fft_batch<G, kTile, kColThreads, false>(tile, kTile, 1, tw);
     const int g = group_of[t];
     const int beg = off[g * nstrips + strip], end = off[g * nstrips + strip + 1];
-    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    for (int i = beg + threadIdx.x; i < end; i += kColThreads) {
         int j, mx0, my0;
         float fx, fy;
         unpack(rec[i], j, mx0, my0, fx, fy);
@@ -201,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) k_cols_interp(const float2* __restri
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int b = 0; b < W; ++b) {
-            const float2* tr = tile + ((my0 + b) & (G - 1)) * C + lc;
+            const float2* tr = tile + ((my0 + b) & (G - 1)) * kTile + lc;
             float2 rs = make_float2(0.f, 0.f);
 #pragma unroll
             for (int a = 0; a < W; ++a) rs = cadd(rs, cscale(tr[a], wx[a]));
@@ -216,19 +204,19 @@ __global__ void __launch_bounds__(kThreads) k_cols_interp(const float2* __restri
 
 // Column FFTs of whole images, spectrum written out (grouped subspace form).
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_cols_store(const float2* __restrict__ h1, float2* __restrict__ spec,
-                                                         int ny) {
+__global__ void __launch_bounds__(kColThreads) k_cols_store(const float2* __restrict__ h1,
+                                                            float2* __restrict__ spec, int ny) {
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* tile = sm + G;
     const int strip = blockIdx.x, f = blockIdx.y;
-    const int c0 = strip * kStrip;
+    const int c0 = strip * kTile;
     fft_twiddles<G>(tw);
-    load_strip<G, kStrip>(tile, h1 + (size_t)f * ny * G, c0, ny);
-    strip_column_ffts<G, false>(tile, kStrip, tw);
+    load_strip<G>(tile, h1 + (size_t)f * ny * G, c0, ny);
+    fft_batch<G, kTile, kColThreads, false>(tile, kTile, 1, tw);
     float2* dst = spec + (size_t)f * G * G;
-    for (int idx = threadIdx.x; idx < G * kStrip; idx += blockDim.x) {
-        const int gy = idx / kStrip, c = idx % kStrip;
+    for (int idx = threadIdx.x; idx < G * kTile; idx += kColThreads) {
+        const int gy = idx / kTile, c = idx & (kTile - 1);
         dst[(size_t)gy * G + c0 + c] = tile[idx];
     }
 }
@@ -240,24 +228,25 @@ __global__ void __launch_bounds__(kThreads) k_cols_store(const float2* __restric
 // R[g][j][k] of every group (blockIdx.y = k).
 // ---------------------------------------------------------------------------
 template <int G, int W, int SRC>
-__global__ void __launch_bounds__(kThreads) k_spread_cols(const float2* __restrict__ y, int K,
-                                                          float2* __restrict__ h1, const int4* __restrict__ rec,
-                                                          const int* __restrict__ off,
-                                                          const int* __restrict__ group_of, int ngroups,
-                                                          int ny, int ns, int nstrips, float beta) {
+__global__ void __launch_bounds__(kColThreads) k_spread_cols(const float2* __restrict__ y, int K,
+                                                             float2* __restrict__ h1,
+                                                             const int4* __restrict__ rec,
+                                                             const int* __restrict__ off,
+                                                             const int* __restrict__ group_of, int ngroups,
+                                                             int ny, int ns, int nstrips, float beta) {
     extern __shared__ float2 sm[];
     float2* tw = sm;
-    float2* tile = sm + G;                 // [G][kStrip]
+    float2* tile = sm + G;                 // [G][kTile]
     const int strip = blockIdx.x, f = blockIdx.y;
-    const int c0 = strip * kStrip;
+    const int c0 = strip * kTile;
     fft_twiddles<G>(tw);
-    for (int i = threadIdx.x; i < G * kStrip; i += blockDim.x) tile[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < G * kTile; i += kColThreads) tile[i] = make_float2(0.f, 0.f);
     __syncthreads();
     const int g_lo = SRC == 0 ? group_of[f] : 0;
     const int g_hi = SRC == 0 ? g_lo + 1 : ngroups;
     for (int g = g_lo; g < g_hi; ++g) {
         const int beg = off[g * nstrips + strip], end = off[g * nstrips + strip + 1];
-        for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        for (int i = beg + threadIdx.x; i < end; i += kColThreads) {
             int j, mx0, my0;
             float fx, fy;
             unpack(rec[i], j, mx0, my0, fx, fy);
@@ -268,10 +257,10 @@ __global__ void __launch_bounds__(kThreads) k_spread_cols(const float2* __restri
 #pragma unroll
             for (int a = 0; a < W; ++a) {
                 const int lc = ((mx0 + a) & (G - 1)) - c0;
-                if (lc < 0 || lc >= kStrip) continue;
+                if (lc < 0 || lc >= kTile) continue;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
-                    float2* p = tile + ((my0 + b) & (G - 1)) * kStrip + lc;
+                    float2* p = tile + ((my0 + b) & (G - 1)) * kTile + lc;
                     const float w = wx[a] * wy[b];
                     atomicAdd(&p->x, w * v.x);
                     atomicAdd(&p->y, w * v.y);
@@ -280,12 +269,12 @@ __global__ void __launch_bounds__(kThreads) k_spread_cols(const float2* __restri
         }
     }
     __syncthreads();
-    strip_column_ffts<G, true>(tile, kStrip, tw);
+    fft_batch<G, kTile, kColThreads, true>(tile, kTile, 1, tw);
     float2* dst = h1 + (size_t)f * ny * G;
-    for (int idx = threadIdx.x; idx < ny * kStrip; idx += blockDim.x) {
-        const int iy = idx / kStrip, c = idx % kStrip;
+    for (int idx = threadIdx.x; idx < ny * kTile; idx += kColThreads) {
+        const int iy = idx / kTile, c = idx & (kTile - 1);
         const int gy = (iy - ny / 2) & (G - 1);
-        dst[(size_t)iy * G + c0 + c] = tile[gy * kStrip + c];
+        dst[(size_t)iy * G + c0 + c] = tile[gy * kTile + c];
     }
 }
 
@@ -294,51 +283,50 @@ __global__ void __launch_bounds__(kThreads) k_spread_cols(const float2* __restri
 // x[t][iy][ix]; DST 1: coefficient image k, alpha[iy][ix][K] (times scale).
 // ---------------------------------------------------------------------------
 template <int G, int DST>
-__global__ void __launch_bounds__(kThreads) k_rows_adj(const float2* __restrict__ h1, float2* __restrict__ x,
-                                                       int K, float scale, const float* __restrict__ inv_dx,
-                                                       const float* __restrict__ inv_dy, int nx, int ny) {
-    constexpr int TPF = G / 8;
-    constexpr int RPC = kThreads / TPF;
+__global__ void __launch_bounds__(kRowThreads) k_rows_adj(const float2* __restrict__ h1, float2* __restrict__ x,
+                                                          int K, float scale, const float* __restrict__ inv_dx,
+                                                          const float* __restrict__ inv_dy, int nx, int ny) {
     extern __shared__ float2 sm[];
+    constexpr int LD = G + 1;
     float2* tw = sm;
-    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
-    float2* row = sm + G + grp * G;
+    float2* rows = sm + G;
     const int t = blockIdx.y;
-    const int iy = blockIdx.x * RPC + grp;
-    const bool active = iy < ny;
+    const int iy0 = blockIdx.x * kRowB;
     fft_twiddles<G>(tw);
-    if (active) {
-        const float2* src = h1 + ((size_t)t * ny + iy) * G;
-        for (int g = tid; g < G; g += TPF) row[g] = src[g];
+    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
+        const int r = idx / G, g = idx - r * G;
+        const int iy = iy0 + r;
+        rows[r * LD + g] = iy < ny ? h1[((size_t)t * ny + iy) * G + g] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft_smem<G, true>(row, 1, tid, active, tw);
-    if (active) {
-        const float sy = inv_dy[iy] * scale;
-        for (int ix = tid; ix < nx; ix += TPF) {
-            const float2 v = cscale(row[(ix - nx / 2) & (G - 1)], inv_dx[ix] * sy);
-            if (DST == 0) x[((size_t)t * ny + iy) * nx + ix] = v;
-            else x[((size_t)iy * nx + ix) * K + t] = v;
-        }
+    fft_batch<G, kRowB, kRowThreads, true>(rows, 1, LD, tw);
+    for (int idx = threadIdx.x; idx < kRowB * nx; idx += kRowThreads) {
+        const int r = idx / nx, ix = idx - r * nx;
+        const int iy = iy0 + r;
+        if (iy >= ny) continue;
+        const float2 v = cscale(rows[r * LD + ((ix - nx / 2) & (G - 1))], inv_dx[ix] * inv_dy[iy] * scale);
+        if (DST == 0) x[((size_t)t * ny + iy) * nx + ix] = v;
+        else x[((size_t)iy * nx + ix) * K + t] = v;
     }
 }
 
 // Adjoint stage 2 in subspace form: partial[p][iy][ix][k] = sum over the
-// frames t of part p of (A^H y)_t[iy][ix] phi[t][k].
+// frames t of part p of (A^H y)_t[iy][ix] phi[t][k].  Block = one image row,
+// 16 frames per inner step.
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_rows_adj_reduce(const float2* __restrict__ h1,
-                                                              const float2* __restrict__ phi, int K, int T,
-                                                              int frames_per_part, float2* __restrict__ partial,
-                                                              const float* __restrict__ inv_dx,
-                                                              const float* __restrict__ inv_dy, int nx, int ny) {
-    constexpr int TPF = G / 8;
-    constexpr int FPC = kThreads / TPF;
-    constexpr int MAXQ = 8;                 // (nx * K) / kThreads <= 8 (nx <= 256, K <= 16)
+__global__ void __launch_bounds__(kRowThreads) k_rows_adj_reduce(const float2* __restrict__ h1,
+                                                                 const float2* __restrict__ phi, int K, int T,
+                                                                 int frames_per_part,
+                                                                 float2* __restrict__ partial,
+                                                                 const float* __restrict__ inv_dx,
+                                                                 const float* __restrict__ inv_dy, int nx,
+                                                                 int ny) {
+    constexpr int LD = G + 1;
+    constexpr int MAXQ = 16;               // (nx * K) / kRowThreads <= 16 (nx <= 256, K <= 16)
     extern __shared__ float2 sm[];
     float2* tw = sm;
-    float2* rows = sm + G;                  // [FPC][G]
-    float2* ph = rows + FPC * G;            // [FPC][K]
-    const int grp = threadIdx.x / TPF, tid = threadIdx.x % TPF;
+    float2* rows = sm + G;                 // [kRowB][G + 1]
+    float2* ph = rows + kRowB * LD;        // [kRowB][K]
     const int iy = blockIdx.x, part = blockIdx.y;
     const int tb = part * frames_per_part;
     const int te = min(T, tb + frames_per_part);
@@ -347,29 +335,26 @@ __global__ void __launch_bounds__(kThreads) k_rows_adj_reduce(const float2* __re
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) acc[q] = make_float2(0.f, 0.f);
     const float sy = inv_dy[iy];
-    for (int t0 = tb; t0 < te; t0 += FPC) {
-        const int t = t0 + grp;
-        const bool active = t < te;
-        if (active) {
-            const float2* src = h1 + ((size_t)t * ny + iy) * G;
-            float2* row = rows + grp * G;
-            for (int g = tid; g < G; g += TPF) row[g] = src[g];
+    for (int t0 = tb; t0 < te; t0 += kRowB) {
+        for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
+            const int r = idx / G, g = idx - r * G;
+            rows[r * LD + g] = t0 + r < te ? h1[((size_t)(t0 + r) * ny + iy) * G + g] : make_float2(0.f, 0.f);
         }
-        for (int i = threadIdx.x; i < FPC * K; i += blockDim.x) {
+        for (int i = threadIdx.x; i < kRowB * K; i += kRowThreads) {
             const int tt = t0 + i / K;
             ph[i] = tt < te ? phi[(size_t)tt * K + (i % K)] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        fft_smem<G, true>(rows + grp * G, 1, tid, active, tw);
-        const int nf = min(FPC, te - t0);
+        fft_batch<G, kRowB, kRowThreads, true>(rows, 1, LD, tw);
+        const int nf = min(kRowB, te - t0);
 #pragma unroll
         for (int q = 0; q < MAXQ; ++q) {
-            const int pidx = threadIdx.x + q * kThreads;
+            const int pidx = threadIdx.x + q * kRowThreads;
             if (pidx < nx * K) {
                 const int ix = pidx / K, k = pidx - ix * K;
                 const int gx = (ix - nx / 2) & (G - 1);
                 float2 s = make_float2(0.f, 0.f);
-                for (int f = 0; f < nf; ++f) s = cadd(s, cmul(rows[f * G + gx], ph[f * K + k]));
+                for (int f = 0; f < nf; ++f) s = cadd(s, cmul(rows[f * LD + gx], ph[f * K + k]));
                 acc[q] = cadd(acc[q], cscale(s, inv_dx[ix] * sy));
             }
         }
@@ -377,7 +362,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_adj_reduce(const float2* __re
     }
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
-        const int pidx = threadIdx.x + q * kThreads;
+        const int pidx = threadIdx.x + q * kRowThreads;
         if (pidx < nx * K) partial[((size_t)part * ny + iy) * nx * K + pidx] = acc[q];
     }
 }
@@ -446,12 +431,15 @@ __global__ void k_combine_adj(const float2* __restrict__ r, const float2* __rest
     if (i >= (size_t)ngroups * ns) return;
     const int g = (int)(i / ns), j = (int)(i - (size_t)g * ns);
     float2 acc[16];
-    for (int k = 0; k < K; ++k) acc[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
     for (int q = gf_off[g]; q < gf_off[g + 1]; ++q) {
         const int t = gf[q];
         const float2 v = r[(size_t)t * ns + j];
         const float2* p = phi + (size_t)t * K;
-        for (int k = 0; k < K; ++k) acc[k] = cadd(acc[k], cmul(v, p[k]));
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < K) acc[k] = cadd(acc[k], cmul(v, p[k]));
     }
     for (int k = 0; k < K; ++k) R[i * K + k] = acc[k];
 }
@@ -472,15 +460,14 @@ static double psi_hat(double f, int W, double beta) {
     return W;
 }
 
-template <typename K>
-static mrf_status set_smem(K kernel, size_t bytes) {
+template <typename Kern>
+static mrf_status set_smem(Kern kernel, size_t bytes) {
     MRF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     return MRF_OK;
 }
 
 static bool supported_grid(int g) { return g == 64 || g == 128 || g == 256 || g == 512; }
 
-// dispatch helpers ------------------------------------------------------------
 #define MRF_DISPATCH_G(G_, ...)                                                          \
     switch (G_) {                                                                        \
         case 64: { constexpr int GG = 64; __VA_ARGS__; break; }                          \
@@ -497,21 +484,21 @@ static bool supported_grid(int g) { return g == 64 || g == 128 || g == 256 || g 
         default: MRF_REQUIRE(false, "unsupported kernel width %d", W_);                  \
     }
 
-static size_t rows_smem(int G) { return (size_t)(G + kThreads / (G / 8) * G) * sizeof(float2); }
+static size_t rows_smem(int G) { return (size_t)(G + kRowB * (G + 1)) * sizeof(float2); }
+static size_t tile_smem(int G) { return (size_t)(G + G * kTile) * sizeof(float2); }
 
 mrf_status launch_rows_fwd(const mrf_plan_s* p, const float2* src, int src_mode, int K, int nf, float2* h1,
                            cudaStream_t s) {
     const int G = p->gx;
-    const int rpc = kThreads / (G / 8);
-    dim3 grid((p->ny + rpc - 1) / rpc, nf);
+    dim3 grid((p->ny + kRowB - 1) / kRowB, nf);
     const size_t sm = rows_smem(G);
     MRF_DISPATCH_G(G, {
         if (src_mode == 0) {
             MRF_PROPAGATE(set_smem(k_rows_fwd<GG, 0>, sm));
-            k_rows_fwd<GG, 0><<<grid, kThreads, sm, s>>>(src, K, h1, p->inv_dx, p->inv_dy, p->nx, p->ny);
+            k_rows_fwd<GG, 0><<<grid, kRowThreads, sm, s>>>(src, K, h1, p->inv_dx, p->inv_dy, p->nx, p->ny);
         } else {
             MRF_PROPAGATE(set_smem(k_rows_fwd<GG, 1>, sm));
-            k_rows_fwd<GG, 1><<<grid, kThreads, sm, s>>>(src, K, h1, p->inv_dx, p->inv_dy, p->nx, p->ny);
+            k_rows_fwd<GG, 1><<<grid, kRowThreads, sm, s>>>(src, K, h1, p->inv_dx, p->inv_dy, p->nx, p->ny);
         }
     });
     MRF_LAUNCHED_AS("k_rows_fwd", s);
@@ -521,12 +508,12 @@ mrf_status launch_rows_fwd(const mrf_plan_s* p, const float2* src, int src_mode,
 mrf_status launch_cols_interp(const mrf_plan_s* p, const float2* h1, float2* y, const float2* b, float scale,
                               cudaStream_t s) {
     const int G = p->gy;
-    dim3 grid(p->nstrips, p->T);
-    const size_t sm = (size_t)(G + G * (kStrip + p->W - 1)) * sizeof(float2);
+    dim3 grid(p->nstrips_f, p->T);
+    const size_t sm = tile_smem(G);
     MRF_DISPATCH_G(G, MRF_DISPATCH_W(p->W, {
         MRF_PROPAGATE(set_smem(k_cols_interp<GG, WW>, sm));
-        k_cols_interp<GG, WW><<<grid, kThreads, sm, s>>>(h1, y, b, scale, p->fwd_rec, p->fwd_off, p->group_of,
-                                                         p->ny, p->ns, p->nstrips, p->beta);
+        k_cols_interp<GG, WW><<<grid, kColThreads, sm, s>>>(h1, y, b, scale, p->fwd_rec, p->fwd_off,
+                                                            p->group_of, p->ny, p->ns, p->nstrips_f, p->beta);
     }));
     MRF_LAUNCHED_AS("k_cols_interp", s);
     return MRF_OK;
@@ -535,17 +522,19 @@ mrf_status launch_cols_interp(const mrf_plan_s* p, const float2* h1, float2* y, 
 mrf_status launch_spread_cols(const mrf_plan_s* p, const float2* y, int src_mode, int K, int nf, float2* h1,
                               cudaStream_t s) {
     const int G = p->gy;
-    dim3 grid(p->nstrips, nf);
-    const size_t sm = (size_t)(G + G * kStrip) * sizeof(float2);
+    dim3 grid(p->nstrips_a, nf);
+    const size_t sm = tile_smem(G);
     MRF_DISPATCH_G(G, MRF_DISPATCH_W(p->W, {
         if (src_mode == 0) {
             MRF_PROPAGATE(set_smem(k_spread_cols<GG, WW, 0>, sm));
-            k_spread_cols<GG, WW, 0><<<grid, kThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_off, p->group_of,
-                                                                p->ngroups, p->ny, p->ns, p->nstrips, p->beta);
+            k_spread_cols<GG, WW, 0><<<grid, kColThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_off, p->group_of,
+                                                                   p->ngroups, p->ny, p->ns, p->nstrips_a,
+                                                                   p->beta);
         } else {
             MRF_PROPAGATE(set_smem(k_spread_cols<GG, WW, 1>, sm));
-            k_spread_cols<GG, WW, 1><<<grid, kThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_off, p->group_of,
-                                                                p->ngroups, p->ny, p->ns, p->nstrips, p->beta);
+            k_spread_cols<GG, WW, 1><<<grid, kColThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_off, p->group_of,
+                                                                   p->ngroups, p->ny, p->ns, p->nstrips_a,
+                                                                   p->beta);
         }
     }));
     MRF_LAUNCHED_AS("k_spread_cols", s);
@@ -555,16 +544,17 @@ mrf_status launch_spread_cols(const mrf_plan_s* p, const float2* y, int src_mode
 mrf_status launch_rows_adj(const mrf_plan_s* p, const float2* h1, float2* dst, int dst_mode, int K, int nf,
                            float scale, cudaStream_t s) {
     const int G = p->gx;
-    const int rpc = kThreads / (G / 8);
-    dim3 grid((p->ny + rpc - 1) / rpc, nf);
+    dim3 grid((p->ny + kRowB - 1) / kRowB, nf);
     const size_t sm = rows_smem(G);
     MRF_DISPATCH_G(G, {
         if (dst_mode == 0) {
             MRF_PROPAGATE(set_smem(k_rows_adj<GG, 0>, sm));
-            k_rows_adj<GG, 0><<<grid, kThreads, sm, s>>>(h1, dst, K, scale, p->inv_dx, p->inv_dy, p->nx, p->ny);
+            k_rows_adj<GG, 0><<<grid, kRowThreads, sm, s>>>(h1, dst, K, scale, p->inv_dx, p->inv_dy, p->nx,
+                                                            p->ny);
         } else {
             MRF_PROPAGATE(set_smem(k_rows_adj<GG, 1>, sm));
-            k_rows_adj<GG, 1><<<grid, kThreads, sm, s>>>(h1, dst, K, scale, p->inv_dx, p->inv_dy, p->nx, p->ny);
+            k_rows_adj<GG, 1><<<grid, kRowThreads, sm, s>>>(h1, dst, K, scale, p->inv_dx, p->inv_dy, p->nx,
+                                                            p->ny);
         }
     });
     MRF_LAUNCHED_AS("k_rows_adj", s);
@@ -587,7 +577,13 @@ static void free_plan(mrf_plan_s* p) {
 mrf_status ensure_subspace_workspace(mrf_plan_s* p, int K) {
     if (p->sub_K >= K) return MRF_OK;
     const int Kc = 16;
-    if (p->sub_h1) { cudaFree(p->sub_h1); cudaFree(p->sub_spec); cudaFree(p->sub_Y); cudaFree(p->sub_R); cudaFree(p->sub_partial); }
+    if (p->sub_h1) {
+        cudaFree(p->sub_h1);
+        cudaFree(p->sub_spec);
+        cudaFree(p->sub_Y);
+        cudaFree(p->sub_R);
+        cudaFree(p->sub_partial);
+    }
     p->sub_h1 = p->sub_spec = p->sub_Y = p->sub_R = p->sub_partial = nullptr;
     MRF_CUDA(cudaMalloc(&p->sub_h1, sizeof(float2) * (size_t)Kc * p->ny * p->gx));
     MRF_CUDA(cudaMalloc(&p->sub_spec, sizeof(float2) * (size_t)Kc * p->gy * p->gx));
@@ -618,9 +614,11 @@ extern "C" mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int T, int n
     auto* p = new mrf_plan_s();
     p->nx = nx; p->ny = ny; p->T = T; p->ns = ns; p->os = os; p->W = W;
     p->gx = os * nx; p->gy = os * ny;
-    p->beta = (float)(M_PI * std::sqrt((W / (double)os) * (W / (double)os) * (os - 0.5) * (os - 0.5) - 0.8));
     const double beta = M_PI * std::sqrt((W / (double)os) * (W / (double)os) * (os - 0.5) * (os - 0.5) - 0.8);
-    p->nstrips = p->gx / kStrip;
+    p->beta = (float)beta;
+    p->sf = kTile - (W - 1);
+    p->nstrips_f = (p->gx + p->sf - 1) / p->sf;
+    p->nstrips_a = p->gx / kTile;
 
     std::vector<float> h((size_t)T * ns * 2);
     cudaError_t e = cudaMemcpyAsync(h.data(), traj, h.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
@@ -658,10 +656,9 @@ extern "C" mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int T, int n
     const int NG = (int)rep.size();
     p->ngroups = NG;
     // per-sample records (host double precision decides the nodes)
-    const int S = p->nstrips;
+    const int SFN = p->nstrips_f, SAN = p->nstrips_a;
     std::vector<int4> grec((size_t)NG * ns);
-    std::vector<int> fcount((size_t)NG * S, 0), acount((size_t)NG * S, 0);
-    auto strip_of = [&](int col) { return col / kStrip; };
+    std::vector<int> fcount((size_t)NG * SFN, 0), acount((size_t)NG * SAN, 0);
     for (int g = 0; g < NG; ++g) {
         const float* kt = h.data() + (size_t)rep[g] * ns * 2;
         for (int j = 0; j < ns; ++j) {
@@ -677,27 +674,25 @@ extern "C" mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int T, int n
             std::memcpy(&r.z, &fx, 4);
             std::memcpy(&r.w, &fy, 4);
             grec[(size_t)g * ns + j] = r;
-            const int s1 = strip_of(mxw), s2 = strip_of((mxw + W - 1) % p->gx);
-            fcount[(size_t)g * S + s1]++;
-            acount[(size_t)g * S + s1]++;
-            if (s2 != s1) acount[(size_t)g * S + s2]++;
+            fcount[(size_t)g * SFN + mxw / p->sf]++;
+            const int a1 = mxw / kTile, a2 = ((mxw + W - 1) % p->gx) / kTile;
+            acount[(size_t)g * SAN + a1]++;
+            if (a2 != a1) acount[(size_t)g * SAN + a2]++;
         }
     }
-    std::vector<int> foff((size_t)NG * S + 1, 0), aoff((size_t)NG * S + 1, 0);
-    for (size_t i = 0; i < (size_t)NG * S; ++i) {
-        foff[i + 1] = foff[i] + fcount[i];
-        aoff[i + 1] = aoff[i] + acount[i];
-    }
+    std::vector<int> foff((size_t)NG * SFN + 1, 0), aoff((size_t)NG * SAN + 1, 0);
+    for (size_t i = 0; i < (size_t)NG * SFN; ++i) foff[i + 1] = foff[i] + fcount[i];
+    for (size_t i = 0; i < (size_t)NG * SAN; ++i) aoff[i + 1] = aoff[i] + acount[i];
     std::vector<int4> frec(foff.back()), arec(aoff.back());
     std::vector<int> fpos(foff.begin(), foff.end() - 1), apos(aoff.begin(), aoff.end() - 1);
     for (int g = 0; g < NG; ++g)
         for (int j = 0; j < ns; ++j) {
             const int4 r = grec[(size_t)g * ns + j];
             const int mxw = r.y & 0xffff;
-            const int s1 = strip_of(mxw), s2 = strip_of((mxw + W - 1) % p->gx);
-            frec[fpos[(size_t)g * S + s1]++] = r;
-            arec[apos[(size_t)g * S + s1]++] = r;
-            if (s2 != s1) arec[apos[(size_t)g * S + s2]++] = r;
+            frec[fpos[(size_t)g * SFN + mxw / p->sf]++] = r;
+            const int a1 = mxw / kTile, a2 = ((mxw + W - 1) % p->gx) / kTile;
+            arec[apos[(size_t)g * SAN + a1]++] = r;
+            if (a2 != a1) arec[apos[(size_t)g * SAN + a2]++] = r;
         }
     // frames of each group (CSR)
     std::vector<int> gfoff(NG + 1, 0), gf(T);
@@ -710,13 +705,12 @@ extern "C" mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int T, int n
     std::vector<float> idx_(nx), idy_(ny);
     for (int i = 0; i < nx; ++i) idx_[i] = (float)(1.0 / psi_hat((i - nx / 2) / (double)p->gx, W, beta));
     for (int i = 0; i < ny; ++i) idy_[i] = (float)(1.0 / psi_hat((i - ny / 2) / (double)p->gy, W, beta));
-    // frame parts of the subspace adjoint reduction
+    // frame parts of the subspace adjoint reduction (about 4 blocks per SM)
     {
-        const int fpc = kThreads / (p->gx / 8);
         int parts = std::max(1, (4 * 152 + ny - 1) / ny);
-        parts = std::min(parts, (T + fpc - 1) / fpc);
+        parts = std::min(parts, (T + kRowB - 1) / kRowB);
         int per = (T + parts - 1) / parts;
-        per = (per + fpc - 1) / fpc * fpc;
+        per = (per + kRowB - 1) / kRowB * kRowB;
         p->frames_per_part = per;
         p->parts = (T + per - 1) / per;
     }
@@ -779,13 +773,12 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
     MRF_REQUIRE(p->nx <= 256, "subspace forms need nx <= 256");
     if (mode == 0) {
         const int G = p->gx;
-        const int fpc = kThreads / (G / 8);
-        dim3 grid(p->ny, (p->T + fpc - 1) / fpc);
-        const size_t sm = (size_t)(G + fpc * G + p->nx * K + fpc * K) * sizeof(float2);
+        dim3 grid(p->ny, (p->T + kRowB - 1) / kRowB);
+        const size_t sm = (size_t)(G + kRowB * (G + 1) + p->nx * K + kRowB * K) * sizeof(float2);
         MRF_DISPATCH_G(G, {
             MRF_PROPAGATE(set_smem(k_rows_fwd_expand<GG>, sm));
-            k_rows_fwd_expand<GG><<<grid, kThreads, sm, s>>>(alpha, phi, K, p->T, p->h1, p->inv_dx, p->inv_dy,
-                                                             p->nx, p->ny);
+            k_rows_fwd_expand<GG><<<grid, kRowThreads, sm, s>>>(alpha, phi, K, p->T, p->h1, p->inv_dx, p->inv_dy,
+                                                                p->nx, p->ny);
         });
         MRF_LAUNCHED_AS("k_rows_fwd_expand", s);
         return launch_cols_interp(p, p->h1, y, b, scale, s);
@@ -794,11 +787,11 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
     MRF_PROPAGATE(launch_rows_fwd(p, alpha, 1, K, K, p->sub_h1, s));
     {
         const int G = p->gy;
-        dim3 grid(p->nstrips, K);
-        const size_t sm = (size_t)(G + G * kStrip) * sizeof(float2);
+        dim3 grid(p->nstrips_a, K);
+        const size_t sm = tile_smem(G);
         MRF_DISPATCH_G(G, {
             MRF_PROPAGATE(set_smem(k_cols_store<GG>, sm));
-            k_cols_store<GG><<<grid, kThreads, sm, s>>>(p->sub_h1, p->sub_spec, p->ny);
+            k_cols_store<GG><<<grid, kColThreads, sm, s>>>(p->sub_h1, p->sub_spec, p->ny);
         });
         MRF_LAUNCHED_AS("k_cols_store", s);
     }
@@ -826,13 +819,13 @@ mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, i
     if (mode == 0) {
         MRF_PROPAGATE(launch_spread_cols(p, y, 0, 0, p->T, p->h1, s));
         const int G = p->gx;
-        const int fpc = kThreads / (G / 8);
         dim3 grid(p->ny, p->parts);
-        const size_t sm = (size_t)(G + fpc * G + fpc * K) * sizeof(float2);
+        const size_t sm = (size_t)(G + kRowB * (G + 1) + kRowB * K) * sizeof(float2);
         MRF_DISPATCH_G(G, {
             MRF_PROPAGATE(set_smem(k_rows_adj_reduce<GG>, sm));
-            k_rows_adj_reduce<GG><<<grid, kThreads, sm, s>>>(p->h1, phi, K, p->T, p->frames_per_part,
-                                                             p->sub_partial, p->inv_dx, p->inv_dy, p->nx, p->ny);
+            k_rows_adj_reduce<GG><<<grid, kRowThreads, sm, s>>>(p->h1, phi, K, p->T, p->frames_per_part,
+                                                                p->sub_partial, p->inv_dx, p->inv_dy, p->nx,
+                                                                p->ny);
         });
         MRF_LAUNCHED_AS("k_rows_adj_reduce", s);
         const size_t n = (size_t)p->ny * p->nx * K;

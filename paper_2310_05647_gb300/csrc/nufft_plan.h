@@ -5,16 +5,18 @@
 struct mrf_plan_s {
     int nx = 0, ny = 0, T = 0, ns = 0, os = 2, W = 4;
     int gx = 0, gy = 0;           // oversampled grid
-    int nstrips = 0;              // gx / 32 column strips
+    int sf = 29;                  // grid columns owned by a forward strip (32 - (W - 1))
+    int nstrips_f = 0;            // forward strips: ceil(gx / sf)
+    int nstrips_a = 0;            // adjoint strips: gx / 32
     int ngroups = 0;              // distinct per-frame trajectories
     float beta = 0.f;             // Kaiser-Bessel shape
     int parts = 1, frames_per_part = 1;  // frame split of the subspace adjoint reduction
     float* inv_dx = nullptr;      // [nx] 1 / psi_hat(x)
     float* inv_dy = nullptr;      // [ny]
-    int4* fwd_rec = nullptr;      // samples by (group, strip of first x node)
-    int* fwd_off = nullptr;       // [ngroups * nstrips + 1]
-    int4* adj_rec = nullptr;      // samples by (group, every strip they touch)
-    int* adj_off = nullptr;       // [ngroups * nstrips + 1]
+    int4* fwd_rec = nullptr;      // samples by (group, forward strip of the first x node)
+    int* fwd_off = nullptr;       // [ngroups * nstrips_f + 1]
+    int4* adj_rec = nullptr;      // samples by (group, every adjoint strip they touch)
+    int* adj_off = nullptr;       // [ngroups * nstrips_a + 1]
     int4* grec = nullptr;         // samples in (group, index) order
     int* group_of = nullptr;      // [T]
     int* gf_off = nullptr;        // [ngroups + 1] frames of each group (CSR)

@@ -317,24 +317,58 @@ __global__ void k_fill_reverse(const int* __restrict__ nbr, const float* __restr
     rw[at] = w[e];
 }
 
-// sort each reverse list by source (fixed summation order), degree of W = (K + K^T)/2
-__global__ void k_degree(const float* __restrict__ w, int np, int knn, const int* __restrict__ roff,
-                         int* __restrict__ rsrc, float* __restrict__ rw, float* __restrict__ deg) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= np) return;
+// Order each reverse list by source index (a fixed summation order) and
+// compute the degrees of W = (K + K^T)/2.  One block per target patch: the
+// sources of a list are distinct, so each one's rank is the number of set
+// bits below it in a bitmap of the list (prefix popcounts), which sorts the
+// list in O(np / 32 + length) per target regardless of hub sizes.
+__global__ void __launch_bounds__(256) k_degree(const float* __restrict__ w, int np, int knn,
+                                                const int* __restrict__ roff, const int* __restrict__ rsrc_in,
+                                                const float* __restrict__ rw_in, int* __restrict__ rsrc,
+                                                float* __restrict__ rw, float* __restrict__ deg) {
+    extern __shared__ unsigned bits[];              // [nw] bitmap, then [nw] prefix counts
+    const int nw = (np + 31) >> 5;
+    unsigned* pre = bits + nw;
+    const int j = blockIdx.x;
     const int b = roff[j], e = roff[j + 1];
-    for (int i = b + 1; i < e; ++i) {
-        const int s = rsrc[i];
-        const float x = rw[i];
-        int k = i - 1;
-        while (k >= b && rsrc[k] > s) { rsrc[k + 1] = rsrc[k]; rw[k + 1] = rw[k]; --k; }
-        rsrc[k + 1] = s;
-        rw[k + 1] = x;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) bits[i] = 0u;
+    __syncthreads();
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const int src = rsrc_in[i];
+        atomicOr(&bits[src >> 5], 1u << (src & 31));
     }
-    float d = 0.f;
-    for (int q = 0; q < knn; ++q) d += w[(size_t)j * knn + q];
-    for (int i = b; i < e; ++i) d += rw[i];
-    deg[j] = 0.5f * d;
+    __syncthreads();
+    // exclusive prefix of the popcounts (block-wide, chunked per thread)
+    __shared__ unsigned part[256];
+    const int per = (nw + blockDim.x - 1) / blockDim.x;
+    const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
+    unsigned acc = 0;
+    for (int i = w0; i < w1; ++i) acc += __popc(bits[i]);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned run = part[threadIdx.x] - acc;
+    for (int i = w0; i < w1; ++i) { pre[i] = run; run += __popc(bits[i]); }
+    __syncthreads();
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const int src = rsrc_in[i];
+        const unsigned word = bits[src >> 5] & ((1u << (src & 31)) - 1u);
+        const int at = b + (int)(pre[src >> 5] + __popc(word));
+        rsrc[at] = src;
+        rw[at] = rw_in[i];
+    }
+    __syncthreads();
+    // fixed-order sum: strided partial sums, then a fixed reduction tree
+    double d = 0.0;
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) d += rw[i];
+    if (threadIdx.x < knn) d += w[(size_t)j * knn + threadIdx.x];
+    d = block_sum(d);
+    if (threadIdx.x == 0) deg[j] = (float)(0.5 * d);
 }
 
 // lambda1 = lambda1^0 / max(L) (or times max(L) as printed)
@@ -578,7 +612,8 @@ struct mrf_recon_s {
     int* nbr = nullptr;
     unsigned* d2 = nullptr;
     float *w = nullptr, *rw = nullptr, *deg = nullptr;
-    int *rcnt = nullptr, *roff = nullptr, *rpos = nullptr, *rsrc = nullptr;
+    int *rcnt = nullptr, *roff = nullptr, *rpos = nullptr, *rsrc = nullptr, *rsrc_tmp = nullptr;
+    float* rw_tmp = nullptr;
     float* scal = nullptr;      // [0] sigma2, [1] lmax, [2] lam1, [3] scratch
     double* acc = nullptr;      // [0] ||r||^2, [1] trace, [2] nuclear, [3..4] dot
     double* cost = nullptr;     // [cap] cost history
@@ -642,9 +677,14 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
     MRF_LAUNCHED_AS("k_edge_weights", s);
     k_scan<<<1, 1024, 0, s>>>(R->rcnt, np, R->roff);
     MRF_LAUNCHED_AS("k_scan", s);
-    k_fill_reverse<<<(ne + 255) / 256, 256, 0, s>>>(R->nbr, R->w, ne, knn, R->roff, R->rpos, R->rsrc, R->rw);
+    k_fill_reverse<<<(ne + 255) / 256, 256, 0, s>>>(R->nbr, R->w, ne, knn, R->roff, R->rpos, R->rsrc_tmp,
+                                                   R->rw_tmp);
     MRF_LAUNCHED_AS("k_fill_reverse", s);
-    k_degree<<<(np + 127) / 128, 128, 0, s>>>(R->w, np, knn, R->roff, R->rsrc, R->rw, R->deg);
+    {
+        const size_t smd = sizeof(unsigned) * 2 * (size_t)((np + 31) / 32);
+        MRF_CUDA(cudaFuncSetAttribute(k_degree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
+        k_degree<<<np, 256, smd, s>>>(R->w, np, knn, R->roff, R->rsrc_tmp, R->rw_tmp, R->rsrc, R->rw, R->deg);
+    }
     MRF_LAUNCHED_AS("k_degree", s);
     k_max<<<1, 1024, 0, s>>>(R->deg, np, R->scal + 1);
     MRF_LAUNCHED_AS("k_max", s);
@@ -724,6 +764,8 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(dalloc(R, &R->w, (size_t)np * knn));
     MRF_PROPAGATE(dalloc(R, &R->rw, (size_t)np * knn));
     MRF_PROPAGATE(dalloc(R, &R->rsrc, (size_t)np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->rsrc_tmp, (size_t)np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->rw_tmp, (size_t)np * knn));
     MRF_PROPAGATE(dalloc(R, &R->deg, np));
     MRF_PROPAGATE(dalloc(R, &R->rcnt, np));
     MRF_PROPAGATE(dalloc(R, &R->rpos, np));
