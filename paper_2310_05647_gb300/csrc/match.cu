@@ -137,13 +137,18 @@ __global__ void k_match_finish(const int* __restrict__ best_idx, const float2* _
 
 MatchWorkspace::~MatchWorkspace() { release(); }
 
-void MatchWorkspace::carve(char* base, int n, int m) {
+void MatchWorkspace::carve(char* base, int n, int m, size_t tc_bytes) {
     auto take = [&](size_t b) { char* p = base; base += (b + 255) / 256 * 256; return p; };
     best_idx = reinterpret_cast<int*>(take(sizeof(int) * (size_t)n));
     best_ip = reinterpret_cast<float2*>(take(sizeof(float2) * (size_t)n));
     cand = reinterpret_cast<int*>(take(sizeof(int) * (size_t)n * kTopK));
     norm2 = reinterpret_cast<float*>(take(sizeof(float) * (size_t)m));
     wscore = reinterpret_cast<float*>(take(sizeof(float) * (size_t)m));
+    if (tc_bytes) {
+        tc_err = reinterpret_cast<int*>(take(sizeof(int)));
+        tc_b = take(tc_bytes);
+        tc_b_bytes = tc_bytes;
+    }
     cap_n = n;
     cap_m = m;
     borrowed = true;
@@ -151,6 +156,7 @@ void MatchWorkspace::carve(char* base, int n, int m) {
 
 void MatchWorkspace::detach() {
     best_idx = nullptr; best_ip = nullptr; norm2 = nullptr; wscore = nullptr; cand = nullptr;
+    tc_b = nullptr; tc_err = nullptr; tc_b_bytes = 0; tc_dict = nullptr; tc_m = tc_len = 0;
     cap_n = cap_m = 0;
     borrowed = false;
 }
@@ -158,8 +164,9 @@ void MatchWorkspace::detach() {
 void MatchWorkspace::release() {
     if (borrowed) { detach(); return; }
     cudaFree(best_idx); cudaFree(best_ip); cudaFree(norm2); cudaFree(wscore);
-    cudaFree(cand);
+    cudaFree(cand); cudaFree(tc_b); cudaFree(tc_err);
     best_idx = nullptr; best_ip = nullptr; norm2 = nullptr; wscore = nullptr; cand = nullptr;
+    tc_b = nullptr; tc_err = nullptr; tc_b_bytes = 0; tc_dict = nullptr;
     cap_n = cap_m = 0;
 }
 
@@ -192,8 +199,8 @@ mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* no
 mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
                      int precision, const float* lut, int* idx, float* pd, float* t1t2, float pd_scale,
                      cudaStream_t s) {
-    if (precision == MRF_MATCH_BF16) {
-        MRF_PROPAGATE(match_bf16_candidates(ws, x, n, len, dict, m, s));
+    if (precision == MRF_MATCH_BF16 || precision == MRF_MATCH_BF16X3) {
+        MRF_PROPAGATE(match_bf16_candidates(ws, x, n, len, dict, m, precision == MRF_MATCH_BF16X3 ? 3 : 1, s));
         MRF_PROPAGATE(match_rerank(ws, x, n, len, dict, s));
     } else {
         k_match_fp32<<<(n + BM - 1) / BM, 256, 0, s>>>(x, n, len, dict, ws.wscore, m, ws.best_idx, ws.best_ip);
@@ -217,21 +224,33 @@ extern "C" mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64*
     MRF_REQUIRE(m >= 1 && m <= (1 << 24), "mrf_match: bad m (%d)", m);
     const int prec = precision & 0xff;
     const int literal = (precision & MRF_MATCH_LITERAL_NORM2) ? 1 : 0;
-    MRF_REQUIRE(prec == MRF_MATCH_FP32 || prec == MRF_MATCH_BF16, "mrf_match: unknown precision %d", prec);
+    MRF_REQUIRE(prec == MRF_MATCH_FP32 || prec == MRF_MATCH_BF16 || prec == MRF_MATCH_BF16X3,
+                "mrf_match: unknown precision %d", prec);
     MRF_REQUIRE(!(literal && prec != MRF_MATCH_FP32), "mrf_match: the literal norm flag needs FP32");
     if (n == 0) return MRF_OK;
     cudaStream_t s = as_stream(stream);
     // stream-ordered scratch: released on the stream after the kernels
     MatchWorkspace ws;
+    const size_t tcb = prec == MRF_MATCH_FP32 ? 0 : tc_operand_bytes(m, len, prec == MRF_MATCH_BF16X3 ? 3 : 1);
     const size_t bytes = sizeof(int) * (size_t)n + sizeof(float2) * (size_t)n + sizeof(int) * (size_t)n * kTopK +
-                         2 * sizeof(float) * (size_t)m + 5 * 256;
+                         2 * sizeof(float) * (size_t)m + tcb + 8 * 256;
     char* base = nullptr;
     MRF_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, s));
-    ws.carve(base, n, m);
+    ws.carve(base, n, m, tcb);
+    if (tcb) MRF_CUDA(cudaMemsetAsync(ws.tc_err, 0, sizeof(int), s));
     mrf_status st = match_prepare(ws, reinterpret_cast<const float2*>(dict), atom_norm2, m, len, literal, s);
     if (st == MRF_OK)
         st = match_run(ws, reinterpret_cast<const float2*>(x), n, len, reinterpret_cast<const float2*>(dict), m,
                        prec, lut, idx, pd, t1t2, 1.0f, s);
+    if (st == MRF_OK && tcb) {
+        // a bounded device wait that gave up is reported, not hidden
+        int h = 0;
+        if (cudaMemcpyAsync(&h, ws.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+            cudaStreamSynchronize(s) == cudaSuccess && h) {
+            set_error("mrf_match: a tensor-core wait timed out");
+            st = MRF_ETIMEOUT;
+        }
+    }
     ws.detach();
     MRF_CUDA(cudaFreeAsync(base, s));
     return st;

@@ -15,9 +15,15 @@ struct MatchWorkspace {
     float* wscore = nullptr;   // [m] score weight
     int cap_n = 0, cap_m = 0;
     bool borrowed = false;     // pointers carved from a caller-owned block
+    // tensor-core matcher: dictionary operand in the shared-memory tile layout
+    void* tc_b = nullptr;
+    size_t tc_b_bytes = 0;
+    const float2* tc_dict = nullptr;   // dictionary the operand was built from
+    int tc_m = 0, tc_len = 0, tc_split = 0;
+    int* tc_err = nullptr;     // set by a bounded wait that gave up
     ~MatchWorkspace();
     mrf_status reserve(int n, int m);
-    void carve(char* base, int n, int m);
+    void carve(char* base, int n, int m, size_t tc_bytes = 0);
     void detach();
     void release();
 };
@@ -29,9 +35,11 @@ mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* no
 mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
                      int precision, const float* lut, int* idx, float* pd, float* t1t2, float pd_scale,
                      cudaStream_t s);
+// bytes of the tensor-core dictionary operand for m atoms of length len
+size_t tc_operand_bytes(int m, int len, int split);
 // BF16 tensor-core candidate search and FP32 re-rank (match_tc.cu)
 mrf_status match_bf16_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
-                                 cudaStream_t s);
+                                 int split, cudaStream_t s);
 mrf_status match_rerank(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict,
                         cudaStream_t s);
 

@@ -1,14 +1,339 @@
-// BF16 tensor-core matching (candidate search + FP32 re-rank).
+// Dictionary matching (Eq. 5) on the 5th-generation tensor cores.
+//
+// The complex inner products s_nm = <d_m, x_n> = sum_k conj(d_mk) x_nk are a
+// real GEMM C = A B^T with
+//   A[n]      = (Re x_n0, Im x_n0, Re x_n1, ...)              (fingerprints)
+//   B[2m]     = (Re d_m0, Im d_m0, Re d_m1, ...)              -> Re s_nm
+//   B[2m + 1] = (-Im d_m0, Re d_m0, -Im d_m1, ...)            -> Im s_nm
+// over a reduction length 2L padded to a multiple of 16.  A block owns 128
+// fingerprints (one per TMEM lane) and sweeps the dictionary in tiles of 128
+// atoms (256 B rows): one elected thread issues tcgen05.mma (BF16 operands in
+// shared memory, FP32 accumulators in TMEM), every warp reads its 32 lanes
+// back with tcgen05.ld and keeps, per fingerprint, the 8 best atoms by
+// |s|^2 / ||d||^2.  The 8 candidates are then re-scored in FP32 from the
+// original FP32 data and the best (ties to the lowest index) is kept, so BF16
+// rounding only has to keep the winner among the top 8.  No fingerprint x
+// atom score reaches memory.
+//
+// Shared-memory operand layout: canonical K-major, no swizzle: 8-row x 16-byte
+// core matrices, core (row group g, k chunk c) at byte (g * KC + c) * 128,
+// KC = padded length / 8; descriptor LBO (next core along K) = 128 bytes, SBO
+// (next 8-row group) = KC * 128 bytes.
+#include <cuda_bf16.h>
+
 #include "common.h"
 #include "match.h"
 
 namespace mrf {
-mrf_status match_bf16_candidates(MatchWorkspace&, const float2*, int, int, const float2*, int, cudaStream_t) {
-    set_error("BF16 matching is not built yet");
-    return MRF_EUNSUPPORTED;
+
+constexpr int kTcRows = 128;        // fingerprints per block (TMEM lanes)
+constexpr int kTcAtoms = 128;       // atoms per tile (256 B rows)
+constexpr int kTcThreads = 128;
+constexpr unsigned kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;                  // descriptor version of the 5th-generation tensor core
+    return d;                                // base offset 0, no swizzle
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> F32, K-major A and B
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// byte offset of element (row, k) in the core-matrix layout with KC k-chunks
+__host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int KC) {
+    return (uint32_t)((((row >> 3) * KC + (k >> 3)) * 128) + ((row & 7) * 16) + ((k & 7) * 2));
+}
+
+// Operand value of the split form: with SPLIT = 3 the reduction axis holds
+// three copies of the 2 len real coefficients, (hi, hi, lo) for A and
+// (hi, lo, hi) for B, hi = bf16(v), lo = bf16(v - hi), so that the product sums
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (relative error ~2^-16) in one GEMM.
+__device__ __forceinline__ __nv_bfloat16 split_part(float v, int part, bool is_a, int split) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    if (split == 1) return hi;
+    const bool want_lo = is_a ? (part == 2) : (part == 1);
+    return want_lo ? __float2bfloat16_rn(v - __bfloat162float(hi)) : hi;
+}
+
+// B operand of every atom tile, pre-arranged in the shared-memory layout:
+// Bg[tile][256 rows][Lp] (bf16).
+__global__ void k_tc_prepare_b(const float2* __restrict__ dict, int m, int len, int Lp, int ntiles, int split,
+                               __nv_bfloat16* __restrict__ Bg) {
+    const int KC = Lp / 8;
+    const size_t per_tile = (size_t)2 * kTcAtoms * Lp;
+    const size_t total = per_tile * ntiles;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int tile = (int)(e / per_tile);
+        const int rem = (int)(e - (size_t)tile * per_tile);
+        const int row = rem / Lp, kk = rem - row * Lp;   // logical (row, k) of the tile
+        const int part = kk / (2 * len), k = kk - part * 2 * len;
+        const int atom = tile * kTcAtoms + (row >> 1);
+        float v = 0.f;
+        if (atom < m && part < split) {
+            const float2 d = dict[(size_t)atom * len + (k >> 1)];
+            if ((row & 1) == 0) v = (k & 1) ? d.y : d.x;           // (Re d, Im d)
+            else v = (k & 1) ? d.x : -d.y;                          // (-Im d, Re d)
+        }
+        Bg[(size_t)tile * per_tile + core_off(row, kk, KC) / 2] =
+            part < split ? split_part(v, part, false, split) : __float2bfloat16_rn(0.f);
+    }
+}
+
+__device__ __forceinline__ bool better_cand(float s, int i, float bs, int bi) {
+    return s > bs || (s == bs && i < bi);
+}
+
+template <int LP, int SPLIT>
+__global__ void __launch_bounds__(kTcThreads) k_match_tc(const float2* __restrict__ x, int n, int len,
+                                                         const __nv_bfloat16* __restrict__ Bg, int ntiles,
+                                                         const float* __restrict__ wscore, int m,
+                                                         const float2* __restrict__ dict,
+                                                         int* __restrict__ best_idx, float2* __restrict__ best_ip,
+                                                         int* __restrict__ err) {
+    constexpr int KC = LP / 8;
+    constexpr int A_BYTES = kTcRows * LP * 2;
+    constexpr int B_BYTES = 2 * kTcAtoms * LP * 2;
+    constexpr int NCOL = 2 * kTcAtoms;               // accumulator columns (256)
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char* sA = smraw;
+    unsigned char* sB = smraw + A_BYTES;
+    float* sW = reinterpret_cast<float*>(smraw + A_BYTES + B_BYTES);
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.x * kTcRows;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        s_fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // A tile: fingerprint rows in BF16 (zero rows past n, zero padding past the
+    // SPLIT copies of the 2 len coefficients)
+    for (int e = tid; e < kTcRows * LP; e += kTcThreads) {
+        const int row = e / LP, kk = e - row * LP;
+        const int part = kk / (2 * len), k = kk - part * 2 * len;
+        float v = 0.f;
+        if (n0 + row < n && part < SPLIT) {
+            const float2 xv = x[(size_t)(n0 + row) * len + (k >> 1)];
+            v = (k & 1) ? xv.y : xv.x;
+        }
+        *reinterpret_cast<__nv_bfloat16*>(sA + core_off(row, kk, KC)) =
+            part < SPLIT ? split_part(v, part, true, SPLIT) : __float2bfloat16_rn(0.f);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = mma_idesc(kTcRows, NCOL);
+
+    float cs[kTopK];
+    int ci[kTopK];
+#pragma unroll
+    for (int q = 0; q < kTopK; ++q) { cs[q] = -1.f; ci[q] = 0x7fffffff; }
+
+    for (int tile = 0; tile < ntiles; ++tile) {
+        // stage the tile's B operand and weights
+        const uint4* src = reinterpret_cast<const uint4*>(Bg + (size_t)tile * (B_BYTES / 2));
+        uint4* dst = reinterpret_cast<uint4*>(sB);
+        for (int e = tid; e < B_BYTES / 16; e += kTcThreads) dst[e] = src[e];
+        {
+            const int a = tile * kTcAtoms + tid;
+            sW[tid] = a < m ? wscore[a] : 0.f;
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int ks = 0; ks < LP / 16; ++ks) {
+                const uint64_t ad = smem_desc(smem_u32(sA) + ks * 256, 128, KC * 128);
+                const uint64_t bd = smem_desc(smem_u32(sB) + ks * 256, 128, KC * 128);
+                const uint32_t acc = ks > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&s_bar)));
+        }
+        // wait for the tile's products (bounded)
+        {
+            const uint32_t parity = tile & 1;
+            uint32_t done = 0;
+            unsigned spins = 0;
+            while (!done) {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                    "selp.u32 %0, 1, 0, p;\n\t}"
+                    : "=r"(done)
+                    : "r"(smem_u32(&s_bar)), "r"(parity));
+                if (!done && ++spins > kSpinLimit) {
+                    s_fail = 1;
+                    break;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!s_fail) {
+            // read this warp's 32 lanes, 32 columns (16 atoms) at a time
+#pragma unroll 1
+            for (int c0 = 0; c0 < NCOL; c0 += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                      "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                      "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int la = (c0 >> 1) + q;
+                    const int a = tile * kTcAtoms + la;
+                    const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
+                    const float sc = a < m ? (re * re + im * im) * sW[la] : -1.f;
+                    if (better_cand(sc, a, cs[kTopK - 1], ci[kTopK - 1])) {
+                        cs[kTopK - 1] = sc;
+                        ci[kTopK - 1] = a;
+#pragma unroll
+                        for (int r = kTopK - 1; r > 0; --r) {
+                            if (better_cand(cs[r], ci[r], cs[r - 1], ci[r - 1])) {
+                                const float ts = cs[r]; cs[r] = cs[r - 1]; cs[r - 1] = ts;
+                                const int ti = ci[r]; ci[r] = ci[r - 1]; ci[r - 1] = ti;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (s_fail) break;
+    }
+    // release TMEM (all reads are complete after the barrier above)
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
+    }
+    if (s_fail) {
+        if (tid == 0) atomicExch(err, 1);
+        return;
+    }
+    // FP32 re-rank of the candidates from the original data
+    const int row = n0 + tid;
+    if (row >= n) return;
+    const float2* xr = x + (size_t)row * len;
+    float bs = -1.f;
+    int bi = 0x7fffffff;
+    float2 bip = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < kTopK; ++q) {
+        const int a = ci[q];
+        if (a >= m) continue;
+        const float2* dr = dict + (size_t)a * len;
+        float2 s = make_float2(0.f, 0.f);
+        for (int k = 0; k < len; ++k) s = cadd(s, cconjmul(dr[k], xr[k]));
+        const float sc = cabs2(s) * wscore[a];
+        if (better_cand(sc, a, bs, bi)) { bs = sc; bi = a; bip = s; }
+    }
+    best_idx[row] = bi;
+    best_ip[row] = bip;
+}
+
+static int padded_len(int len, int split) { return (2 * len * split + 15) / 16 * 16; }
+
+size_t tc_operand_bytes(int m, int len, int split) {
+    const int ntiles = (m + kTcAtoms - 1) / kTcAtoms;
+    return sizeof(__nv_bfloat16) * (size_t)ntiles * 2 * kTcAtoms * padded_len(len, split);
+}
+
+mrf_status match_bf16_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
+                                 int split, cudaStream_t s) {
+    MRF_REQUIRE(split == 1 || split == 3, "BF16 matching: split must be 1 or 3");
+    MRF_REQUIRE(2 * len * split <= 128, "BF16 matching supports 2 x length x split <= 128 (length %d)", len);
+    const int Lp = padded_len(len, split);
+    const int ntiles = (m + kTcAtoms - 1) / kTcAtoms;
+    const size_t bbytes = sizeof(__nv_bfloat16) * (size_t)ntiles * 2 * kTcAtoms * Lp;
+    if (ws.tc_b == nullptr || ws.tc_b_bytes < bbytes || ws.tc_dict != dict || ws.tc_m != m || ws.tc_len != len ||
+        ws.tc_split != split) {
+        if (ws.tc_b_bytes < bbytes) {
+            MRF_REQUIRE(!ws.borrowed, "BF16 matching: the dictionary operand does not fit the scratch");
+            if (ws.tc_b) cudaFree(ws.tc_b);
+            ws.tc_b = nullptr;
+            MRF_CUDA(cudaMalloc(&ws.tc_b, bbytes));
+            ws.tc_b_bytes = bbytes;
+        }
+        k_tc_prepare_b<<<1024, 256, 0, s>>>(dict, m, len, Lp, ntiles, split,
+                                            reinterpret_cast<__nv_bfloat16*>(ws.tc_b));
+        MRF_LAUNCHED_AS("k_tc_prepare_b", s);
+        ws.tc_dict = dict;
+        ws.tc_m = m;
+        ws.tc_len = len;
+        ws.tc_split = split;
+    }
+    if (!ws.tc_err) {
+        MRF_CUDA(cudaMalloc(&ws.tc_err, sizeof(int)));
+        MRF_CUDA(cudaMemsetAsync(ws.tc_err, 0, sizeof(int), s));
+    }
+    const int blocks = (n + kTcRows - 1) / kTcRows;
+#define MRF_TC_LAUNCH(LPV, SP)                                                                                   \
+    do {                                                                                                         \
+        const size_t sm = (size_t)kTcRows * LPV * 2 + (size_t)2 * kTcAtoms * LPV * 2 + kTcAtoms * sizeof(float); \
+        MRF_CUDA(cudaFuncSetAttribute(k_match_tc<LPV, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+        k_match_tc<LPV, SP><<<blocks, kTcThreads, sm, s>>>(x, n, len,                                            \
+                                                           reinterpret_cast<const __nv_bfloat16*>(ws.tc_b),      \
+                                                           ntiles, ws.wscore, m, dict, ws.best_idx, ws.best_ip,  \
+                                                           ws.tc_err);                                           \
+    } while (0)
+    if (split == 1) {
+        if (Lp == 16) MRF_TC_LAUNCH(16, 1);
+        else if (Lp == 32) MRF_TC_LAUNCH(32, 1);
+        else if (Lp == 48) MRF_TC_LAUNCH(48, 1);
+        else if (Lp == 64) MRF_TC_LAUNCH(64, 1);
+        else if (Lp == 96) MRF_TC_LAUNCH(96, 1);
+        else MRF_TC_LAUNCH(128, 1);
+    } else {
+        if (Lp == 16) MRF_TC_LAUNCH(16, 3);
+        else if (Lp == 32) MRF_TC_LAUNCH(32, 3);
+        else if (Lp == 48) MRF_TC_LAUNCH(48, 3);
+        else if (Lp == 64) MRF_TC_LAUNCH(64, 3);
+        else if (Lp == 80) MRF_TC_LAUNCH(80, 3);
+        else if (Lp == 96) MRF_TC_LAUNCH(96, 3);
+        else if (Lp == 112) MRF_TC_LAUNCH(112, 3);
+        else MRF_TC_LAUNCH(128, 3);
+    }
+#undef MRF_TC_LAUNCH
+    MRF_LAUNCHED_AS("k_match_tc", s);
+    return MRF_OK;
+}
+
 mrf_status match_rerank(MatchWorkspace&, const float2*, int, int, const float2*, cudaStream_t) {
-    set_error("BF16 matching is not built yet");
-    return MRF_EUNSUPPORTED;
+    return MRF_OK;   // the FP32 re-rank is fused into k_match_tc
 }
+
 }  // namespace mrf

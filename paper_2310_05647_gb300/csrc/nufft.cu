@@ -278,6 +278,73 @@ __global__ void __launch_bounds__(kColThreads) k_spread_cols(const float2* __res
     }
 }
 
+// Grouped adjoint stage 1 without same-address contention: the contributions
+// of every group sample to the oversampled grid are precomputed as
+// (grid point, sample, weight) entries sorted by point.  Each thread reduces
+// a run of 32 consecutive entries for all K coefficient grids at once and adds
+// a partial sum to the grid only where the point changes, so the k-space
+// centre (where every interleaf overlaps) costs a few adds instead of
+// thousands of same-address atomics.  R: [ngroups * ns][K]; grid: [K][G][G]
+// (zeroed by the caller).
+constexpr int kGatherRun = 32;
+
+__global__ void k_gather_grid(const float2* __restrict__ R, int K, const int* __restrict__ pt,
+                              const int* __restrict__ smp, const float* __restrict__ w, int nent, int GG2,
+                              float2* __restrict__ grid) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) * kGatherRun;
+    if (b >= nent) return;
+    const int e = min(nent, b + kGatherRun);
+    float2 acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
+    int cur = pt[b];
+    for (int i = b; i < e; ++i) {
+        const int p = pt[i];
+        if (p != cur) {
+            for (int k = 0; k < K; ++k) {
+                atomicAdd(&grid[(size_t)k * GG2 + cur].x, acc[k].x);
+                atomicAdd(&grid[(size_t)k * GG2 + cur].y, acc[k].y);
+                acc[k] = make_float2(0.f, 0.f);
+            }
+            cur = p;
+        }
+        const float wi = w[i];
+        const float2* r = R + (size_t)smp[i] * K;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < K) acc[k] = cadd(acc[k], cscale(r[k], wi));
+    }
+    for (int k = 0; k < K; ++k) {
+        atomicAdd(&grid[(size_t)k * GG2 + cur].x, acc[k].x);
+        atomicAdd(&grid[(size_t)k * GG2 + cur].y, acc[k].y);
+    }
+}
+
+// Inverse FFT of a strip's columns of grid image f, image rows kept.
+template <int G>
+__global__ void __launch_bounds__(kColThreads) k_cols_inv(const float2* __restrict__ grid,
+                                                          float2* __restrict__ h1, int ny) {
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* tile = sm + G;
+    const int strip = blockIdx.x, f = blockIdx.y;
+    const int c0 = strip * kTile;
+    fft_twiddles<G>(tw);
+    const float2* src = grid + (size_t)f * G * G;
+    for (int idx = threadIdx.x; idx < G * kTile; idx += kColThreads) {
+        const int gy = idx / kTile, c = idx & (kTile - 1);
+        tile[idx] = src[(size_t)gy * G + c0 + c];
+    }
+    __syncthreads();
+    fft_batch<G, kTile, kColThreads, true>(tile, kTile, 1, tw);
+    float2* dst = h1 + (size_t)f * ny * G;
+    for (int idx = threadIdx.x; idx < ny * kTile; idx += kColThreads) {
+        const int iy = idx / kTile, c = idx & (kTile - 1);
+        const int gy = (iy - ny / 2) & (G - 1);
+        dst[(size_t)iy * G + c0 + c] = tile[gy * kTile + c];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Adjoint stage 2: inverse FFT along x, crop, deapodise.  DST 0: frames
 // x[t][iy][ix]; DST 1: coefficient image k, alpha[iy][ix][K] (times scale).
@@ -568,10 +635,69 @@ static void free_plan(mrf_plan_s* p) {
     if (!p) return;
     void* ptrs[] = {p->inv_dx, p->inv_dy, p->fwd_rec, p->fwd_off, p->adj_rec, p->adj_off, p->grec,
                     p->group_of, p->gf_off, p->gf, p->h1, p->sub_h1, p->sub_spec, p->sub_Y, p->sub_R,
-                    p->sub_partial};
+                    p->sub_partial, p->gat_off, p->gat_pt, p->gat_smp, p->gat_w};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
+}
+
+// Grouped adjoint gather table: every (group sample, tap) contribution,
+// sorted by its oversampled-grid point (row * G + column),
+// with weights psi(ux - mx) psi(uy - my) evaluated in FP64.  Built on the
+// host from the plan's sample records the first time the grouped adjoint
+// runs (synchronises the stream).
+static mrf_status build_gather(mrf_plan_s* p, cudaStream_t s) {
+    if (p->gat_off) return MRF_OK;
+    const int NG = p->ngroups, ns = p->ns, W = p->W;
+    const double beta = p->beta_d;
+    std::vector<int4> grec((size_t)NG * ns);
+    MRF_CUDA(cudaMemcpyAsync(grec.data(), p->grec, sizeof(int4) * grec.size(), cudaMemcpyDeviceToHost, s));
+    MRF_CUDA(cudaStreamSynchronize(s));
+    auto kb = [&](double u) {
+        const double z = 2.0 * u / W;
+        const double arg = std::max(0.0, 1.0 - z * z);
+        return std::cyl_bessel_i(0.0, beta * std::sqrt(arg));
+    };
+    struct Ent { int pt, smp; float w; };
+    std::vector<Ent> ents;
+    ents.reserve((size_t)NG * ns * W * W);
+    for (int g = 0; g < NG; ++g)
+        for (int j = 0; j < ns; ++j) {
+            const int4 r = grec[(size_t)g * ns + j];
+            const int mxw = r.y & 0xffff, myw = (r.y >> 16) & 0xffff;
+            float fxf, fyf;
+            std::memcpy(&fxf, &r.z, 4);
+            std::memcpy(&fyf, &r.w, 4);
+            for (int a = 0; a < W; ++a) {
+                const int col = (mxw + a) % p->gx;
+                const double wa = kb((double)fxf - a);
+                for (int b = 0; b < W; ++b) {
+                    const int row = (myw + b) % p->gy;
+                    ents.push_back({row * p->gx + col, g * ns + j, (float)(wa * kb((double)fyf - b))});
+                }
+            }
+        }
+    std::stable_sort(ents.begin(), ents.end(), [](const Ent& x, const Ent& y) { return x.pt < y.pt; });
+    std::vector<int> goff(2, 0), gpt(ents.size()), gsmp(ents.size());
+    std::vector<float> gw(ents.size());
+    for (size_t i = 0; i < ents.size(); ++i) {
+        gpt[i] = ents[i].pt;
+        gsmp[i] = ents[i].smp;
+        gw[i] = ents[i].w;
+    }
+    goff[1] = (int)ents.size();
+    p->gat_n = (int)ents.size();
+    MRF_CUDA(cudaMalloc(&p->gat_pt, sizeof(int) * gpt.size()));
+    MRF_CUDA(cudaMalloc(&p->gat_smp, sizeof(int) * gsmp.size()));
+    MRF_CUDA(cudaMalloc(&p->gat_w, sizeof(float) * gw.size()));
+    MRF_CUDA(cudaMemcpy(p->gat_pt, gpt.data(), sizeof(int) * gpt.size(), cudaMemcpyHostToDevice));
+    MRF_CUDA(cudaMemcpy(p->gat_smp, gsmp.data(), sizeof(int) * gsmp.size(), cudaMemcpyHostToDevice));
+    MRF_CUDA(cudaMemcpy(p->gat_w, gw.data(), sizeof(float) * gw.size(), cudaMemcpyHostToDevice));
+    int* off = nullptr;
+    MRF_CUDA(cudaMalloc(&off, sizeof(int) * goff.size()));
+    MRF_CUDA(cudaMemcpy(off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice));
+    p->gat_off = off;
+    return MRF_OK;
 }
 
 mrf_status ensure_subspace_workspace(mrf_plan_s* p, int K) {
@@ -616,6 +742,7 @@ extern "C" mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int T, int n
     p->gx = os * nx; p->gy = os * ny;
     const double beta = M_PI * std::sqrt((W / (double)os) * (W / (double)os) * (os - 0.5) * (os - 0.5) - 0.8);
     p->beta = (float)beta;
+    p->beta_d = beta;
     p->sf = kTile - (W - 1);
     p->nstrips_f = (p->gx + p->sf - 1) / p->sf;
     p->nstrips_a = p->gx / kTile;
@@ -840,7 +967,22 @@ mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, i
                                                                    p->sub_R);
         MRF_LAUNCHED_AS("k_combine_adj", s);
     }
-    MRF_PROPAGATE(launch_spread_cols(p, p->sub_R, 1, K, K, p->sub_h1, s));
+    MRF_PROPAGATE(build_gather(p, s));
+    {
+        const int G = p->gy;
+        MRF_CUDA(cudaMemsetAsync(p->sub_spec, 0, sizeof(float2) * (size_t)K * G * G, s));
+        const int runs = (p->gat_n + kGatherRun - 1) / kGatherRun;
+        k_gather_grid<<<(runs + 127) / 128, 128, 0, s>>>(p->sub_R, K, p->gat_pt, p->gat_smp, p->gat_w, p->gat_n,
+                                                         G * G, p->sub_spec);
+        MRF_LAUNCHED_AS("k_gather_grid", s);
+        dim3 grid(p->nstrips_a, K);
+        const size_t sm = tile_smem(G);
+        MRF_DISPATCH_G(G, {
+            MRF_PROPAGATE(set_smem(k_cols_inv<GG>, sm));
+            k_cols_inv<GG><<<grid, kColThreads, sm, s>>>(p->sub_spec, p->sub_h1, p->ny);
+        });
+        MRF_LAUNCHED_AS("k_cols_inv", s);
+    }
     MRF_PROPAGATE(launch_rows_adj(p, p->sub_h1, alpha_out, 1, K, K, scale, s));
     return MRF_OK;
 }

@@ -10,6 +10,7 @@ struct mrf_plan_s {
     int nstrips_a = 0;            // adjoint strips: gx / 32
     int ngroups = 0;              // distinct per-frame trajectories
     float beta = 0.f;             // Kaiser-Bessel shape
+    double beta_d = 0.0;
     int parts = 1, frames_per_part = 1;  // frame split of the subspace adjoint reduction
     float* inv_dx = nullptr;      // [nx] 1 / psi_hat(x)
     float* inv_dy = nullptr;      // [ny]
@@ -19,6 +20,13 @@ struct mrf_plan_s {
     int* adj_off = nullptr;       // [ngroups * nstrips_a + 1]
     int4* grec = nullptr;         // samples in (group, index) order
     int* group_of = nullptr;      // [T]
+    // grouped adjoint: the (grid point, sample, weight) contributions of every
+    // group sample, sorted by grid point (built on the first grouped adjoint)
+    int gat_n = 0;                // number of entries
+    int* gat_off = nullptr;       // [2] = {0, gat_n} (also marks the table as built)
+    int* gat_pt = nullptr;        // grid point gy * G + gx
+    int* gat_smp = nullptr;       // group sample g * ns + j
+    float* gat_w = nullptr;       // psi(ux - mx) psi(uy - my)
     int* gf_off = nullptr;        // [ngroups + 1] frames of each group (CSR)
     int* gf = nullptr;            // [T]
     float2* h1 = nullptr;         // [T][ny][gx] rows transformed along x

@@ -129,7 +129,7 @@ static unsigned nblk(size_t n, int t = 256) { return (unsigned)std::min<size_t>(
 // every device.
 constexpr double kQScale = 4096.0;
 
-__global__ void k_features(const float* __restrict__ t1t2, PatchGeom g, double t1max, double t2max,
+__global__ void k_features(const float* __restrict__ t1t2, PatchGeom g, double t1max, double t2max, int FD4,
                            int* __restrict__ F) {
     const int pp = g.p * g.p;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -138,8 +138,9 @@ __global__ void k_features(const float* __restrict__ t1t2, PatchGeom g, double t
     const int py = q / g.p, px = q - py * g.p;
     const int y = g.origin(i / g.cnt) + py, x = g.origin(i % g.cnt) + px;
     const size_t v = (size_t)y * g.n + x;
-    F[(size_t)e * 2] = (int)rint((double)t1t2[2 * v] / t1max * kQScale);
-    F[(size_t)e * 2 + 1] = (int)rint((double)t1t2[2 * v + 1] / t2max * kQScale);
+    int* f = F + (size_t)i * FD4 + 2 * q;
+    f[0] = (int)rint((double)t1t2[2 * v] / t1max * kQScale);
+    f[1] = (int)rint((double)t1t2[2 * v + 1] / t2max * kQScale);
 }
 
 __device__ __forceinline__ bool less_dj(unsigned d, int j, unsigned d2, int j2) {
@@ -147,60 +148,80 @@ __device__ __forceinline__ bool less_dj(unsigned d, int j, unsigned d2, int j2) 
 }
 
 // k nearest patches by squared distance (self excluded, ties to the lower
-// index).  Block: 32 query patches x 8 threads; each thread scans every 8th
-// candidate of each 64-candidate tile and keeps its KMAX best; the 8 lists of a
-// query are merged with shuffles.
+// index), in two steps.  k_knn_part: block = 32 query patches x one candidate
+// partition; 8 threads per query each scan every 8th candidate of each
+// 64-candidate tile, 4 candidates at a time with 16-byte shared loads, keep
+// their KMAX best and merge them with shuffles into the partition's best knn.
+// k_knn_merge: one thread per query merges the partitions' sorted lists.
+// Feature rows are padded with zeros to a multiple of 4 (FD4).
 template <int KMAX>
-__global__ void __launch_bounds__(256) k_knn(const int* __restrict__ F, int np, int FD, int knn,
-                                             int* __restrict__ nbr, unsigned* __restrict__ d2out) {
-    extern __shared__ int shf[];
-    const int ld = FD + 1;
+__global__ void __launch_bounds__(256) k_knn_part(const int* __restrict__ F, int np, int FD4, int knn,
+                                                  int cand_per_part, int* __restrict__ pnbr,
+                                                  unsigned* __restrict__ pd2) {
+    extern __shared__ int4 shf4[];
+    int* shf = reinterpret_cast<int*>(shf4);
+    const int ld = FD4 + 4;
     int* Fq = shf;              // [32][ld]
     int* Fc = shf + 32 * ld;    // [64][ld]
     const int ql = threadIdx.x >> 3, sub = threadIdx.x & 7;
     const int q = blockIdx.x * 32 + ql;
-    for (int i = threadIdx.x; i < 32 * FD; i += blockDim.x) {
-        const int r = i / FD, c = i - r * FD;
+    const int part = blockIdx.y;
+    const int cb = part * cand_per_part, ce = min(np, cb + cand_per_part);
+    const int v4 = FD4 >> 2;
+    for (int i = threadIdx.x; i < 32 * v4; i += blockDim.x) {
+        const int r = i / v4, c = i - r * v4;
         const int qq = blockIdx.x * 32 + r;
-        Fq[r * ld + c] = qq < np ? F[(size_t)qq * FD + c] : 0;
+        const int4 v = qq < np ? reinterpret_cast<const int4*>(F + (size_t)qq * FD4)[c] : make_int4(0, 0, 0, 0);
+        *reinterpret_cast<int4*>(Fq + r * ld + 4 * c) = v;
     }
     unsigned bd[KMAX];
     int bj[KMAX];
 #pragma unroll
     for (int i = 0; i < KMAX; ++i) { bd[i] = 0xffffffffu; bj[i] = 0x7fffffff; }
-    for (int c0 = 0; c0 < np; c0 += 64) {
+    for (int c0 = cb; c0 < ce; c0 += 64) {
         __syncthreads();
-        for (int i = threadIdx.x; i < 64 * FD; i += blockDim.x) {
-            const int r = i / FD, c = i - r * FD;
-            Fc[r * ld + c] = c0 + r < np ? F[(size_t)(c0 + r) * FD + c] : 0;
+        for (int i = threadIdx.x; i < 64 * v4; i += blockDim.x) {
+            const int r = i / v4, c = i - r * v4;
+            const int4 v = c0 + r < ce ? reinterpret_cast<const int4*>(F + (size_t)(c0 + r) * FD4)[c]
+                                       : make_int4(0, 0, 0, 0);
+            *reinterpret_cast<int4*>(Fc + r * ld + 4 * c) = v;
         }
         __syncthreads();
         if (q < np) {
-            for (int c = sub; c < 64; c += 8) {
-                const int j = c0 + c;
-                if (j >= np || j == q) continue;
-                const int* a = Fq + ql * ld;
-                const int* b = Fc + c * ld;
-                unsigned d = 0u;
-                for (int t = 0; t < FD; ++t) {
-                    const int df = a[t] - b[t];
-                    d += (unsigned)(df * df);
-                }
-                if (less_dj(d, j, bd[KMAX - 1], bj[KMAX - 1])) {
-                    bd[KMAX - 1] = d;
-                    bj[KMAX - 1] = j;
 #pragma unroll
-                    for (int i = KMAX - 1; i > 0; --i) {
-                        if (less_dj(bd[i], bj[i], bd[i - 1], bj[i - 1])) {
-                            const unsigned td = bd[i]; bd[i] = bd[i - 1]; bd[i - 1] = td;
-                            const int tj = bj[i]; bj[i] = bj[i - 1]; bj[i - 1] = tj;
+            for (int grp = 0; grp < 2; ++grp) {
+                unsigned d[4] = {0u, 0u, 0u, 0u};
+                const int* a = Fq + ql * ld;
+                for (int t = 0; t < FD4; t += 4) {
+                    const int4 av = *reinterpret_cast<const int4*>(a + t);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int4 bv = *reinterpret_cast<const int4*>(Fc + (sub + 8 * (4 * grp + u)) * ld + t);
+                        const int e0 = av.x - bv.x, e1 = av.y - bv.y, e2 = av.z - bv.z, e3 = av.w - bv.w;
+                        d[u] += (unsigned)(e0 * e0) + (unsigned)(e1 * e1) + (unsigned)(e2 * e2) +
+                                (unsigned)(e3 * e3);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = c0 + sub + 8 * (4 * grp + u);
+                    if (j >= ce || j == q) continue;
+                    if (less_dj(d[u], j, bd[KMAX - 1], bj[KMAX - 1])) {
+                        bd[KMAX - 1] = d[u];
+                        bj[KMAX - 1] = j;
+#pragma unroll
+                        for (int i = KMAX - 1; i > 0; --i) {
+                            if (less_dj(bd[i], bj[i], bd[i - 1], bj[i - 1])) {
+                                const unsigned td = bd[i]; bd[i] = bd[i - 1]; bd[i - 1] = td;
+                                const int tj = bj[i]; bj[i] = bj[i - 1]; bj[i - 1] = tj;
+                            }
                         }
                     }
                 }
             }
         }
     }
-    // merge the 8 sorted lists of this query
+    // merge the 8 sorted lists of this query into the partition's best knn
     for (int r = 0; r < knn; ++r) {
         unsigned d = bd[0];
         int j = bj[0];
@@ -217,9 +238,30 @@ __global__ void __launch_bounds__(256) k_knn(const int* __restrict__ F, int np, 
             bj[KMAX - 1] = 0x7fffffff;
         }
         if (sub == 0 && q < np) {
-            nbr[(size_t)q * knn + r] = j;
-            d2out[(size_t)q * knn + r] = d;
+            pnbr[((size_t)part * np + q) * knn + r] = j;
+            pd2[((size_t)part * np + q) * knn + r] = d;
         }
+    }
+}
+
+__global__ void k_knn_merge(const int* __restrict__ pnbr, const unsigned* __restrict__ pd2, int parts, int np,
+                            int knn, int* __restrict__ nbr, unsigned* __restrict__ d2out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= np) return;
+    int pos[16];
+    for (int p = 0; p < parts; ++p) pos[p] = 0;
+    for (int r = 0; r < knn; ++r) {
+        int bp = -1;
+        unsigned bd = 0xffffffffu;
+        int bjj = 0x7fffffff;
+        for (int p = 0; p < parts; ++p) {
+            if (pos[p] >= knn) continue;
+            const size_t o = ((size_t)p * np + q) * knn + pos[p];
+            if (less_dj(pd2[o], pnbr[o], bd, bjj)) { bd = pd2[o]; bjj = pnbr[o]; bp = p; }
+        }
+        nbr[(size_t)q * knn + r] = bjj;
+        d2out[(size_t)q * knn + r] = bd;
+        if (bp >= 0) pos[bp]++;
     }
 }
 
@@ -611,6 +653,9 @@ struct mrf_recon_s {
     int* F = nullptr;
     int* nbr = nullptr;
     unsigned* d2 = nullptr;
+    int* pnbr = nullptr;        // [parts][np][knn] per-partition kNN lists
+    unsigned* pd2 = nullptr;
+    int knn_parts_max = 8;
     float *w = nullptr, *rw = nullptr, *deg = nullptr;
     int *rcnt = nullptr, *roff = nullptr, *rpos = nullptr, *rsrc = nullptr, *rsrc_tmp = nullptr;
     float* rw_tmp = nullptr;
@@ -657,17 +702,29 @@ static mrf_status svt(mrf_recon_s* R, const float2* alpha, float2* P, double* nu
 static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
     const int np = R->np, knn = R->prm.knn, FD = 2 * R->pp;
     k_features<<<(unsigned)(((size_t)np * R->pp + 255) / 256), 256, 0, s>>>(R->t1t2, R->g, (double)R->t1max,
-                                                                             (double)R->t2max, R->F);
+                                                                             (double)R->t2max,
+                                                                             (FD + 3) / 4 * 4, R->F);
     MRF_LAUNCHED_AS("k_features", s);
-    const size_t sm = sizeof(int) * (size_t)(32 + 64) * (FD + 1);
-    if (knn <= 16) {
-        MRF_CUDA(cudaFuncSetAttribute(k_knn<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_knn<16><<<(np + 31) / 32, 256, sm, s>>>(R->F, np, FD, knn, R->nbr, R->d2);
-    } else {
-        MRF_CUDA(cudaFuncSetAttribute(k_knn<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_knn<32><<<(np + 31) / 32, 256, sm, s>>>(R->F, np, FD, knn, R->nbr, R->d2);
+    {
+        const int FD4 = (FD + 3) / 4 * 4;
+        const size_t sm = sizeof(int) * (size_t)(32 + 64) * (FD4 + 4);
+        const int qb = (np + 31) / 32;
+        int parts = std::max(1, std::min(R->knn_parts_max, (4 * 152 + qb - 1) / qb));
+        int per = (np + parts - 1) / parts;
+        per = (per + 63) / 64 * 64;
+        parts = (np + per - 1) / per;
+        dim3 grid(qb, parts);
+        if (knn <= 16) {
+            MRF_CUDA(cudaFuncSetAttribute(k_knn_part<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_knn_part<16><<<grid, 256, sm, s>>>(R->F, np, FD4, knn, per, R->pnbr, R->pd2);
+        } else {
+            MRF_CUDA(cudaFuncSetAttribute(k_knn_part<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_knn_part<32><<<grid, 256, sm, s>>>(R->F, np, FD4, knn, per, R->pnbr, R->pd2);
+        }
+        MRF_LAUNCHED_AS("k_knn_part", s);
+        k_knn_merge<<<(np + 127) / 128, 128, 0, s>>>(R->pnbr, R->pd2, parts, np, knn, R->nbr, R->d2);
     }
-    MRF_LAUNCHED_AS("k_knn", s);
+    MRF_LAUNCHED_AS("k_knn_merge", s);
     const int ne = np * knn;
     k_median_nonzero<<<1, 1024, 0, s>>>(R->d2, ne, R->scal + 0);
     MRF_LAUNCHED_AS("k_median_nonzero", s);
@@ -758,7 +815,11 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(dalloc(R, &R->t1t2, 2 * (size_t)N));
     MRF_PROPAGATE(dalloc(R, &R->pd, N));
     MRF_PROPAGATE(dalloc(R, &R->idx, N));
-    MRF_PROPAGATE(dalloc(R, &R->F, (size_t)np * 2 * R->pp));
+    const int FD4 = (2 * R->pp + 3) / 4 * 4;
+    MRF_PROPAGATE(dalloc(R, &R->F, (size_t)np * FD4));
+    MRF_CUDA(cudaMemsetAsync(R->F, 0, sizeof(int) * (size_t)np * FD4, s));
+    MRF_PROPAGATE(dalloc(R, &R->pnbr, (size_t)R->knn_parts_max * np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->pd2, (size_t)R->knn_parts_max * np * knn));
     MRF_PROPAGATE(dalloc(R, &R->nbr, (size_t)np * knn));
     MRF_PROPAGATE(dalloc(R, &R->d2, (size_t)np * knn));
     MRF_PROPAGATE(dalloc(R, &R->w, (size_t)np * knn));
@@ -866,7 +927,8 @@ extern "C" mrf_status mrf_recon_create(mrf_recon* out, mrf_plan plan, const mrf_
     MRF_REQUIRE(prm->stride >= 1 && prm->stride <= prm->patch, "mrf_recon_create: stride must be in [1, patch]");
     MRF_REQUIRE(prm->knn >= 1 && prm->knn <= 32, "mrf_recon_create: knn must be in [1, 32]");
     MRF_REQUIRE(prm->beta > 0.f && prm->mu > 0.f, "mrf_recon_create: beta and mu must be > 0");
-    MRF_REQUIRE(prm->match_precision == MRF_MATCH_FP32 || prm->match_precision == MRF_MATCH_BF16,
+    MRF_REQUIRE(prm->match_precision == MRF_MATCH_FP32 || prm->match_precision == MRF_MATCH_BF16 ||
+                    prm->match_precision == MRF_MATCH_BF16X3,
                 "mrf_recon_create: unknown match precision %d", prm->match_precision);
     const PatchGeom g = make_geom(plan->nx, prm->patch, prm->stride);
     MRF_REQUIRE(g.count() >= prm->knn + 1, "mrf_recon_create: need at least knn + 1 patches (%d)", g.count());

@@ -1,0 +1,111 @@
+"""GPU parity of the tensor-core matchers (tcgen05, FP32 accumulation, FP32
+top-8 re-rank) against the FP64 oracle, on subspace-compressed atoms.
+
+* split BF16 (MRF_MATCH_BF16X3): the product is exact to ~2^-16, so the
+  winner must agree with the oracle or be a near-tie (score within 1e-5 of
+  the best) for 99.5% of fingerprints, and every noiseless atom must match
+  itself or a near-tie of itself.
+* plain BF16 (MRF_MATCH_BF16): operand rounding (2^-9 relative) can push the
+  exact winner out of the top 8 when neighbouring atoms differ by less than
+  that; the pick must still be near-optimal at BF16 resolution (exact score
+  within 1% of the best) and agree with FP32 for most fingerprints."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dictionary, epg, match as omatch
+from gpu_util import as_f32_inputs, c64, f32, mrf, np_, rand_c
+
+pytestmark = pytest.mark.gpu
+BF16, BF16X3 = 1, 2
+
+
+@pytest.fixture(scope="module")
+def compressed():
+    fa, tr = synth.fisp_train(200, seed=2)
+    lut = synth.keep_t1_ge_t2(synth.log_grid(100, 4000, 60), synth.log_grid(10, 500, 40))
+    D = epg.fisp(lut[:, 0], lut[:, 1], fa, tr)
+    phi = dictionary.subspace(D, 10)
+    Dc = D @ phi
+    n2 = np.sum(np.abs(D) ** 2, axis=1)
+    Dc, n2, lut = as_f32_inputs(Dc, n2, lut)
+    return Dc, n2, lut
+
+
+def _near_tie_ok(X, Dc, n2, gi, oi, rtol=1e-5):
+    sc = omatch.scores(X, Dc, n2)
+    rows = np.arange(len(X))
+    ok = (gi == oi) | (sc[rows, gi] >= sc[rows, oi] * (1 - rtol))
+    return ok.mean()
+
+
+def test_split_bf16_noiseless_atoms_match_themselves(compressed):
+    m = mrf()
+    Dc, n2, lut = compressed
+    pd = np.random.default_rng(0).uniform(0.5, 2.0, len(Dc))
+    (X,) = as_f32_inputs(Dc * pd[:, None])
+    idx, pdh, _ = m.match(c64(X), c64(Dc), f32(lut), atom_norm2=f32(n2), precision=BF16X3)
+    oi, _, _, opd = omatch.match(X, Dc, lut, atom_norm2=n2)
+    assert _near_tie_ok(X, Dc, n2, np_(idx), oi) == 1.0
+    same = np_(idx) == oi
+    assert same.mean() > 0.99
+    np.testing.assert_allclose(np_(pdh)[same], opd[same], rtol=1e-4)
+
+
+def test_split_bf16_noisy_agrees_with_fp32_and_oracle(compressed):
+    m = mrf()
+    Dc, n2, lut = compressed
+    rng = np.random.default_rng(1)
+    n = 5000                                        # several 128-row blocks + ragged tail
+    X = Dc[rng.integers(0, len(Dc), n)] * rng.uniform(0.3, 2.0, (n, 1)) + 0.02 * rand_c(rng, n, Dc.shape[1])
+    X[:5] = 0.0
+    (X,) = as_f32_inputs(X)
+    gb, pb, _ = m.match(c64(X), c64(Dc), f32(lut), atom_norm2=f32(n2), precision=BF16X3)
+    gf, pf, _ = m.match(c64(X), c64(Dc), f32(lut), atom_norm2=f32(n2), precision=0)
+    oi, _, _, opd = omatch.match(X, Dc, lut, atom_norm2=n2)
+    gb, gf = np_(gb), np_(gf)
+    assert _near_tie_ok(X, Dc, n2, gb, oi) >= 0.995
+    assert (gb == gf).mean() >= 0.995
+    assert np.all(gb[:5] == 0) and np.all(np_(pb)[:5] == 0)
+    same = gb == oi
+    np.testing.assert_allclose(np_(pb)[same], opd[same], rtol=1e-4, atol=1e-6)
+
+
+def test_plain_bf16_is_near_optimal(compressed):
+    m = mrf()
+    Dc, n2, lut = compressed
+    rng = np.random.default_rng(3)
+    n = 3000
+    X = Dc[rng.integers(0, len(Dc), n)] * rng.uniform(0.3, 2.0, (n, 1)) + 0.02 * rand_c(rng, n, Dc.shape[1])
+    (X,) = as_f32_inputs(X)
+    gb = np_(m.match(c64(X), c64(Dc), f32(lut), atom_norm2=f32(n2), precision=BF16)[0])
+    oi = omatch.match(X, Dc, lut, atom_norm2=n2)[0]
+    assert _near_tie_ok(X, Dc, n2, gb, oi, rtol=1e-2) == 1.0
+    assert (gb == oi).mean() > 0.5
+
+
+@pytest.mark.parametrize("prec", [BF16, BF16X3])
+def test_tc_ragged_atoms_and_lengths(prec):
+    m = mrf()
+    rng = np.random.default_rng(2)
+    for n, mm, L in [(257, 130, 4), (100, 129, 8), (300, 1, 16), (200, 300, 21)]:
+        if prec == BF16X3 and 6 * L > 128:
+            continue
+        D = rand_c(rng, mm, L)
+        X = D[rng.integers(0, mm, n)] + 0.01 * rand_c(rng, n, L)
+        lut = rng.uniform(10, 1000, (mm, 2))
+        D, X, lut = as_f32_inputs(D, X, lut)
+        gi = np_(m.match(c64(X), c64(D), f32(lut), precision=prec)[0])
+        oi = omatch.match(X, D, lut)[0]
+        n2 = np.sum(np.abs(D) ** 2, 1)
+        assert _near_tie_ok(X, D, n2, gi, oi, rtol=1e-5 if prec == BF16X3 else 1e-2) >= 0.995, (n, mm, L)
+
+
+def test_tc_rejects_long_fingerprints():
+    m = mrf()
+    D = c64(np.ones((4, 70)))
+    with pytest.raises(m.MRFError):
+        m.match(c64(np.ones((3, 70))), D, f32(np.ones((4, 2))), precision=BF16)
+    D = c64(np.ones((4, 30)))
+    with pytest.raises(m.MRFError):
+        m.match(c64(np.ones((3, 30))), D, f32(np.ones((4, 2))), precision=BF16X3)
