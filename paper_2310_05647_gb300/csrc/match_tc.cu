@@ -6,14 +6,15 @@
 //   B[2m]     = (Re d_m0, Im d_m0, Re d_m1, ...)              -> Re s_nm
 //   B[2m + 1] = (-Im d_m0, Re d_m0, -Im d_m1, ...)            -> Im s_nm
 // over a reduction length 2L padded to a multiple of 16.  A block owns 128
-// fingerprints (one per TMEM lane) and sweeps the dictionary in tiles of 128
-// atoms (256 B rows): one elected thread issues tcgen05.mma (BF16 operands in
-// shared memory, FP32 accumulators in TMEM), every warp reads its 32 lanes
-// back with tcgen05.ld and keeps, per fingerprint, the 8 best atoms by
-// |s|^2 / ||d||^2.  The 8 candidates are then re-scored in FP32 from the
-// original FP32 data and the best (ties to the lowest index) is kept, so BF16
-// rounding only has to keep the winner among the top 8.  No fingerprint x
-// atom score reaches memory.
+// fingerprints (one per TMEM lane) and sweeps the dictionary in tiles of 64
+// atoms (128 B rows): one elected thread issues tcgen05.mma (BF16 operands in
+// shared memory, FP32 accumulators in TMEM, two accumulator buffers so the
+// next tile's products overlap the scoring of this one), every warp reads its
+// 32 lanes back with tcgen05.ld and keeps, per fingerprint, the best atoms by
+// |s|^2 / ||d||^2 (8 for plain BF16, 4 for the split form).  The candidates
+// are then re-scored in FP32 from the original FP32 data and the best (ties to
+// the lowest index) is kept, so BF16 rounding only has to keep the winner
+// among the candidates.  No fingerprint x atom score reaches memory.
 //
 // Shared-memory operand layout: canonical K-major, no swizzle: 8-row x 16-byte
 // core matrices, core (row group g, k chunk c) at byte (g * KC + c) * 128,
@@ -27,8 +28,8 @@
 namespace mrf {
 
 constexpr int kTcRows = 128;        // fingerprints per block (TMEM lanes)
-constexpr int kTcAtoms = 128;       // atoms per tile (256 B rows)
-constexpr int kTcThreads = 128;
+constexpr int kTcAtoms = 64;        // atoms per tile (128 B rows, N = 128)
+constexpr int kTcThreads = 256;       // 8 warps: two per TMEM lane quarter
 constexpr unsigned kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -93,7 +94,32 @@ __device__ __forceinline__ bool better_cand(float s, int i, float bs, int bi) {
     return s > bs || (s == bs && i < bi);
 }
 
-template <int LP, int SPLIT>
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+// bounded wait on an mbarrier phase; returns false if it gave up
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    unsigned spins = 0;
+    while (!done) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity));
+        if (!done && ++spins > kSpinLimit) return false;
+    }
+    return true;
+}
+
+// Pipelined sweep: tiles of kTcAtoms atoms; two accumulator buffers in TMEM
+// and two B buffers in shared memory.  While the block scores tile i, the
+// tensor core computes tile i + 1 and tile i + 2 is copied in (cp.async).
+template <int LP, int SPLIT, int TOPK>
 __global__ void __launch_bounds__(kTcThreads) k_match_tc(const float2* __restrict__ x, int n, int len,
                                                          const __nv_bfloat16* __restrict__ Bg, int ntiles,
                                                          const float* __restrict__ wscore, int m,
@@ -102,29 +128,51 @@ __global__ void __launch_bounds__(kTcThreads) k_match_tc(const float2* __restric
                                                          int* __restrict__ err) {
     constexpr int KC = LP / 8;
     constexpr int A_BYTES = kTcRows * LP * 2;
-    constexpr int B_BYTES = 2 * kTcAtoms * LP * 2;
-    constexpr int NCOL = 2 * kTcAtoms;               // accumulator columns (256)
+    constexpr int B_BYTES = 2 * kTcAtoms * LP * 2;   // one tile: 2 rows per atom
+    constexpr int NCOL = 2 * kTcAtoms;               // accumulator columns per buffer
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* sA = smraw;
-    unsigned char* sB = smraw + A_BYTES;
-    float* sW = reinterpret_cast<float*>(smraw + A_BYTES + B_BYTES);
+    unsigned char* sB0 = smraw + A_BYTES;            // two B buffers
+    float* sW = reinterpret_cast<float*>(smraw + A_BYTES + 2 * B_BYTES);   // [2][kTcAtoms]
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ int s_fail;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int lq = warp & 3;                         // TMEM lane quarter this warp may read
+    const int half = warp >> 2;                      // which half of each tile's columns it scores
     const int n0 = blockIdx.x * kTcRows;
+    __shared__ float s_ms[kTcRows][TOPK];
+    __shared__ int s_mi[kTcRows][TOPK];
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(NCOL));
+                     "r"(2 * NCOL));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         s_fail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    auto stage_b = [&](int tile, int buf) {          // cp.async the tile's B operand
+        const char* src = reinterpret_cast<const char*>(Bg + (size_t)tile * (B_BYTES / 2));
+        const uint32_t dst = smem_u32(sB0 + buf * B_BYTES);
+        for (int e = tid; e < B_BYTES / 16; e += kTcThreads) cp_async16(dst + 16 * e, src + 16 * e);
+    };
+    auto stage_w = [&](int tile, int buf) {          // cp.async the tile's score weights, close the group
+        for (int e = tid; e < kTcAtoms / 4; e += kTcThreads) {
+            const int a = tile * kTcAtoms + 4 * e;
+            if (a + 3 < m) cp_async16(smem_u32(sW + buf * kTcAtoms + 4 * e), wscore + a);
+            else
+                for (int q = 0; q < 4; ++q) sW[buf * kTcAtoms + 4 * e + q] = a + q < m ? wscore[a + q] : 0.f;
+        }
+        cp_async_commit();
+    };
+    auto stage = [&](int tile, int buf) { stage_b(tile, buf); stage_w(tile, buf); };
+    stage(0, 0);
+    if (ntiles > 1) stage(1, 1);
     // A tile: fingerprint rows in BF16 (zero rows past n, zero padding past the
     // SPLIT copies of the 2 len coefficients)
     for (int e = tid; e < kTcRows * LP; e += kTcThreads) {
@@ -138,68 +186,62 @@ __global__ void __launch_bounds__(kTcThreads) k_match_tc(const float2* __restric
         *reinterpret_cast<__nv_bfloat16*>(sA + core_off(row, kk, KC)) =
             part < SPLIT ? split_part(v, part, true, SPLIT) : __float2bfloat16_rn(0.f);
     }
+    const uint32_t idesc = mma_idesc(kTcRows, NCOL);
+    auto issue = [&](int tile) {                     // thread 0 only
+        const int buf = tile & 1;
+        const uint32_t tm = s_tmem + (uint32_t)(buf * NCOL);
+        const uint32_t bbase = smem_u32(sB0 + buf * B_BYTES);
+#pragma unroll
+        for (int ks = 0; ks < LP / 16; ++ks) {
+            const uint64_t ad = smem_desc(smem_u32(sA) + ks * 256, 128, KC * 128);
+            const uint64_t bd = smem_desc(bbase + ks * 256, 128, KC * 128);
+            const uint32_t acc = ks > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tm),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&s_bar[buf])));
+    };
+    // tile 0 ready -> first MMA
+    if (ntiles > 1) cp_async_wait<1>(); else cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = s_tmem;
-    const uint32_t idesc = mma_idesc(kTcRows, NCOL);
+    if (tid == 0) issue(0);
 
-    float cs[kTopK];
-    int ci[kTopK];
+    float cs[TOPK];
+    int ci[TOPK];
 #pragma unroll
-    for (int q = 0; q < kTopK; ++q) { cs[q] = -1.f; ci[q] = 0x7fffffff; }
+    for (int q = 0; q < TOPK; ++q) { cs[q] = -1.f; ci[q] = 0x7fffffff; }
 
     for (int tile = 0; tile < ntiles; ++tile) {
-        // stage the tile's B operand and weights
-        const uint4* src = reinterpret_cast<const uint4*>(Bg + (size_t)tile * (B_BYTES / 2));
-        uint4* dst = reinterpret_cast<uint4*>(sB);
-        for (int e = tid; e < B_BYTES / 16; e += kTcThreads) dst[e] = src[e];
-        {
-            const int a = tile * kTcAtoms + tid;
-            sW[tid] = a < m ? wscore[a] : 0.f;
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-            for (int ks = 0; ks < LP / 16; ++ks) {
-                const uint64_t ad = smem_desc(smem_u32(sA) + ks * 256, 128, KC * 128);
-                const uint64_t bd = smem_desc(smem_u32(sB) + ks * 256, 128, KC * 128);
-                const uint32_t acc = ks > 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&s_bar)));
-        }
-        // wait for the tile's products (bounded)
-        {
-            const uint32_t parity = tile & 1;
-            uint32_t done = 0;
-            unsigned spins = 0;
-            while (!done) {
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                    "selp.u32 %0, 1, 0, p;\n\t}"
-                    : "=r"(done)
-                    : "r"(smem_u32(&s_bar)), "r"(parity));
-                if (!done && ++spins > kSpinLimit) {
-                    s_fail = 1;
-                    break;
-                }
+        const int buf = tile & 1;
+        // next tile: its B copy landed -> launch its MMA into the other buffer
+        if (tile + 1 < ntiles) {
+            cp_async_wait<0>();
+            asm volatile("fence.proxy.async.shared::cta;");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                issue(tile + 1);
             }
         }
+        // this tile's products
+        if (!wait_parity(smem_u32(&s_bar[buf]), (tile >> 1) & 1)) s_fail = 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
+        // B buffer `buf` is free again: prefetch tile + 2's operand into it (its
+        // weights follow once this tile's scores no longer need the buffer)
+        if (tile + 2 < ntiles) stage_b(tile + 2, buf);
         if (!s_fail) {
-            // read this warp's 32 lanes, 32 columns (16 atoms) at a time
+            const float* w = sW + buf * kTcAtoms;
 #pragma unroll 1
-            for (int c0 = 0; c0 < NCOL; c0 += 32) {
+            for (int c0 = half * (NCOL / 2); c0 < (half + 1) * (NCOL / 2); c0 += 32) {
                 uint32_t v[32];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                const uint32_t taddr = s_tmem + (uint32_t)(buf * NCOL) + ((uint32_t)(lq * 32) << 16) +
+                                       (uint32_t)c0;
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -211,48 +253,83 @@ __global__ void __launch_bounds__(kTcThreads) k_match_tc(const float2* __restric
                       "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
+                float sc[16];
+                bool any = false;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int la = (c0 >> 1) + q;
-                    const int a = tile * kTcAtoms + la;
                     const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
-                    const float sc = a < m ? (re * re + im * im) * sW[la] : -1.f;
-                    if (better_cand(sc, a, cs[kTopK - 1], ci[kTopK - 1])) {
-                        cs[kTopK - 1] = sc;
-                        ci[kTopK - 1] = a;
+                    sc[q] = tile * kTcAtoms + la < m ? (re * re + im * im) * w[la] : -1.f;
+                    any |= sc[q] >= cs[TOPK - 1];
+                }
+                if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
-                        for (int r = kTopK - 1; r > 0; --r) {
-                            if (better_cand(cs[r], ci[r], cs[r - 1], ci[r - 1])) {
-                                const float ts = cs[r]; cs[r] = cs[r - 1]; cs[r - 1] = ts;
-                                const int ti = ci[r]; ci[r] = ci[r - 1]; ci[r - 1] = ti;
+                    for (int q = 0; q < 16; ++q) {
+                        const int a = tile * kTcAtoms + (c0 >> 1) + q;
+                        if (better_cand(sc[q], a, cs[TOPK - 1], ci[TOPK - 1])) {
+                            cs[TOPK - 1] = sc[q];
+                            ci[TOPK - 1] = a;
+#pragma unroll
+                            for (int r = TOPK - 1; r > 0; --r) {
+                                if (better_cand(cs[r], ci[r], cs[r - 1], ci[r - 1])) {
+                                    const float ts = cs[r]; cs[r] = cs[r - 1]; cs[r - 1] = ts;
+                                    const int ti = ci[r]; ci[r] = ci[r - 1]; ci[r - 1] = ti;
+                                }
                             }
                         }
                     }
                 }
             }
         }
+        // every warp is done with accumulator `buf` and weights `buf` before
+        // either is overwritten
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
+        if (tile + 2 < ntiles) stage_w(tile + 2, buf);
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (s_fail) break;
     }
-    // release TMEM (all reads are complete after the barrier above)
+    cp_async_wait<0>();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(2 * NCOL));
     }
     if (s_fail) {
         if (tid == 0) atomicExch(err, 1);
         return;
     }
+    // merge the two column halves' candidate lists of each fingerprint
+    const int lrow = lq * 32 + (tid & 31);
+    if (half == 1) {
+#pragma unroll
+        for (int q = 0; q < TOPK; ++q) { s_ms[lrow][q] = cs[q]; s_mi[lrow][q] = ci[q]; }
+    }
+    __syncthreads();
+    if (half == 1) return;
+#pragma unroll
+    for (int q = 0; q < TOPK; ++q) {
+        const float sc = s_ms[lrow][q];
+        const int a = s_mi[lrow][q];
+        if (better_cand(sc, a, cs[TOPK - 1], ci[TOPK - 1])) {
+            cs[TOPK - 1] = sc;
+            ci[TOPK - 1] = a;
+#pragma unroll
+            for (int r = TOPK - 1; r > 0; --r) {
+                if (better_cand(cs[r], ci[r], cs[r - 1], ci[r - 1])) {
+                    const float ts = cs[r]; cs[r] = cs[r - 1]; cs[r - 1] = ts;
+                    const int ti = ci[r]; ci[r] = ci[r - 1]; ci[r - 1] = ti;
+                }
+            }
+        }
+    }
     // FP32 re-rank of the candidates from the original data
-    const int row = n0 + tid;
+    const int row = n0 + lrow;
     if (row >= n) return;
     const float2* xr = x + (size_t)row * len;
     float bs = -1.f;
     int bi = 0x7fffffff;
     float2 bip = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < kTopK; ++q) {
+    for (int q = 0; q < TOPK; ++q) {
         const int a = ci[q];
         if (a >= m) continue;
         const float2* dr = dict + (size_t)a * len;
@@ -303,12 +380,15 @@ mrf_status match_bf16_candidates(MatchWorkspace& ws, const float2* x, int n, int
     const int blocks = (n + kTcRows - 1) / kTcRows;
 #define MRF_TC_LAUNCH(LPV, SP)                                                                                   \
     do {                                                                                                         \
-        const size_t sm = (size_t)kTcRows * LPV * 2 + (size_t)2 * kTcAtoms * LPV * 2 + kTcAtoms * sizeof(float); \
-        MRF_CUDA(cudaFuncSetAttribute(k_match_tc<LPV, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-        k_match_tc<LPV, SP><<<blocks, kTcThreads, sm, s>>>(x, n, len,                                            \
-                                                           reinterpret_cast<const __nv_bfloat16*>(ws.tc_b),      \
-                                                           ntiles, ws.wscore, m, dict, ws.best_idx, ws.best_ip,  \
-                                                           ws.tc_err);                                           \
+        constexpr int TK = SP == 3 ? 4 : kTopK;                                                                  \
+        const size_t sm = (size_t)kTcRows * LPV * 2 + (size_t)2 * 2 * kTcAtoms * LPV * 2 +                       \
+                          2 * kTcAtoms * sizeof(float);                                                           \
+        MRF_CUDA(cudaFuncSetAttribute(k_match_tc<LPV, SP, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                      (int)sm));                                                                 \
+        k_match_tc<LPV, SP, TK><<<blocks, kTcThreads, sm, s>>>(x, n, len,                                        \
+                                                               reinterpret_cast<const __nv_bfloat16*>(ws.tc_b),  \
+                                                               ntiles, ws.wscore, m, dict, ws.best_idx,          \
+                                                               ws.best_ip, ws.tc_err);                           \
     } while (0)
     if (split == 1) {
         if (Lp == 16) MRF_TC_LAUNCH(16, 1);
