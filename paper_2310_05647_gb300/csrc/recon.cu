@@ -463,9 +463,14 @@ __global__ void __launch_bounds__(128) k_graph_blocks(const float2* __restrict__
 // B = A V the orthogonalised columns.  R rows per lane, KP >= K columns (the
 // extra columns are zero and stay zero).
 // --------------------------------------------------------------------------
+// Vio (nullable) holds each patch's right singular vectors [np][KP][KP]: with
+// warm != 0 the sweep starts from A V_prev (the previous iterate's basis, so
+// the columns are nearly orthogonal and few sweeps are needed); the final V
+// is stored back.  The SVD computed is the same either way.
 template <int R, int KP>
 __global__ void __launch_bounds__(128) k_svt(const float2* __restrict__ alpha, PatchGeom g, int K, float tau,
-                                             float2* __restrict__ P, double* __restrict__ nuc) {
+                                             float2* __restrict__ P, double* __restrict__ nuc,
+                                             float2* __restrict__ Vio, int warm) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= g.count()) return;
@@ -484,6 +489,34 @@ __global__ void __launch_bounds__(128) k_svt(const float2* __restrict__ alpha, P
     float2 v[KP];
 #pragma unroll
     for (int k = 0; k < KP; ++k) v[k] = make_float2(lane == k ? 1.f : 0.f, 0.f);
+    float2* Vp = Vio ? Vio + (size_t)j * KP * KP : nullptr;
+    if (Vp && warm) {
+        // v = row `lane` of V_prev; a <- a V_prev (row i of V_prev from lane i)
+        if (lane < KP) {
+#pragma unroll
+            for (int k = 0; k < KP; ++k) v[k] = Vp[lane * KP + k];
+        }
+        float2 na[R][KP];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k = 0; k < KP; ++k) na[r][k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                float2 vik;
+                vik.x = __shfl_sync(0xffffffffu, v[k].x, i);
+                vik.y = __shfl_sync(0xffffffffu, v[k].y, i);
+#pragma unroll
+                for (int r = 0; r < R; ++r) na[r][k] = cadd(na[r][k], cmul(a[r][i], vik));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k = 0; k < KP; ++k) a[r][k] = na[r][k];
+    }
     for (int sweep = 0; sweep < 30; ++sweep) {
         float off = 0.f;
 #pragma unroll
@@ -537,6 +570,10 @@ __global__ void __launch_bounds__(128) k_svt(const float2* __restrict__ alpha, P
         f[k] = sg > tau ? (sg - tau) / sg : 0.f;
     }
     if (nuc && lane == 0) atomicAdd(nuc, (double)nsum);
+    if (Vp && lane < KP) {
+#pragma unroll
+        for (int k = 0; k < KP; ++k) Vp[lane * KP + k] = v[k];
+    }
     if (!P) return;
     // P[row][k] = sum_j B[row][j] f_j conj(V[k][j]); row k of V lives in lane k
     for (int k = 0; k < K; ++k) {
@@ -663,6 +700,8 @@ struct mrf_recon_s {
     double* acc = nullptr;      // [0] ||r||^2, [1] trace, [2] nuclear, [3..4] dot
     double* cost = nullptr;     // [cap] cost history
     int cost_cap = 0, iters_done = 0;
+    float2* svt_v = nullptr;    // [np][svt_kp][svt_kp] right singular vectors of the last SVT
+    int svt_kp = 0, svt_warm = 0;
     std::vector<void*> owned;
 };
 
@@ -686,15 +725,29 @@ static mrf_status svt(mrf_recon_s* R, const float2* alpha, float2* P, double* nu
     const int rows = R->pp;
     const unsigned blocks = (unsigned)((R->np + 3) / 4);
     const float tau = 1.0f / R->prm.beta;
-#define MRF_SVT(RR, KK) k_svt<RR, KK><<<blocks, 128, 0, s>>>(alpha, R->g, K, tau, P, nuc)
-    const int KP = K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : 16;
+    const int warm = R->svt_warm;
+#define MRF_SVT(RR, KK) k_svt<RR, KK><<<blocks, 128, 0, s>>>(alpha, R->g, K, tau, P, nuc, R->svt_v, warm)
+    const int KP = R->svt_kp;
     if (rows <= 64) {
-        if (KP == 4) MRF_SVT(2, 4); else if (KP == 8) MRF_SVT(2, 8); else if (KP == 12) MRF_SVT(2, 12); else MRF_SVT(2, 16);
+        switch (KP) {
+            case 4: MRF_SVT(2, 4); break;
+            case 8: MRF_SVT(2, 8); break;
+            case 10: MRF_SVT(2, 10); break;
+            case 12: MRF_SVT(2, 12); break;
+            default: MRF_SVT(2, 16); break;
+        }
     } else {
-        if (KP == 4) MRF_SVT(4, 4); else if (KP == 8) MRF_SVT(4, 8); else if (KP == 12) MRF_SVT(4, 12); else MRF_SVT(4, 16);
+        switch (KP) {
+            case 4: MRF_SVT(4, 4); break;
+            case 8: MRF_SVT(4, 8); break;
+            case 10: MRF_SVT(4, 10); break;
+            case 12: MRF_SVT(4, 12); break;
+            default: MRF_SVT(4, 16); break;
+        }
     }
 #undef MRF_SVT
     MRF_LAUNCHED_AS("k_svt", s);
+    R->svt_warm = 1;
     return MRF_OK;
 }
 
@@ -833,6 +886,8 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(dalloc(R, &R->roff, np + 1));
     MRF_PROPAGATE(dalloc(R, &R->scal, 8));
     MRF_PROPAGATE(dalloc(R, &R->acc, 8));
+    R->svt_kp = K <= 4 ? 4 : K <= 8 ? 8 : K == 10 ? 10 : K <= 12 ? 12 : 16;
+    MRF_PROPAGATE(dalloc(R, &R->svt_v, (size_t)np * R->svt_kp * R->svt_kp));
     R->cost_cap = 1024;
     MRF_PROPAGATE(dalloc(R, &R->cost, R->cost_cap));
     MRF_PROPAGATE(R->mws.reserve(N, R->m));
