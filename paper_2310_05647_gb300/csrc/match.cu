@@ -193,6 +193,7 @@ mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* no
                          int literal, cudaStream_t s) {
     k_match_weights<<<(m + 255) / 256, 256, 0, s>>>(dict, norm2_in, m, len, literal, ws.norm2, ws.wscore);
     MRF_LAUNCHED_AS("k_match_weights", s);
+    ws.tc_dict = nullptr;   // the tensor-core operand carries the weights: rebuild it
     return MRF_OK;
 }
 

@@ -67,9 +67,11 @@ __device__ __forceinline__ __nv_bfloat16 split_part(float v, int part, bool is_a
 }
 
 // B operand of every atom tile, pre-arranged in the shared-memory layout:
-// Bg[tile][256 rows][Lp] (bf16).
-__global__ void k_tc_prepare_b(const float2* __restrict__ dict, int m, int len, int Lp, int ntiles, int split,
-                               __nv_bfloat16* __restrict__ Bg) {
+// Bg[tile][2 kTcAtoms rows][Lp] (bf16), each atom scaled by the square root of
+// its score weight so that the score is the plain |product|^2; padding atoms
+// are zero rows.
+__global__ void k_tc_prepare_b(const float2* __restrict__ dict, const float* __restrict__ wscore, int m, int len,
+                               int Lp, int ntiles, int split, __nv_bfloat16* __restrict__ Bg) {
     const int KC = Lp / 8;
     const size_t per_tile = (size_t)2 * kTcAtoms * Lp;
     const size_t total = per_tile * ntiles;
@@ -84,6 +86,7 @@ __global__ void k_tc_prepare_b(const float2* __restrict__ dict, int m, int len, 
             const float2 d = dict[(size_t)atom * len + (k >> 1)];
             if ((row & 1) == 0) v = (k & 1) ? d.y : d.x;           // (Re d, Im d)
             else v = (k & 1) ? d.x : -d.y;                          // (-Im d, Re d)
+            v *= sqrtf(wscore[atom]);                               // |s|^2 w = |<sqrt(w) d, x>|^2
         }
         Bg[(size_t)tile * per_tile + core_off(row, kk, KC) / 2] =
             part < split ? split_part(v, part, false, split) : __float2bfloat16_rn(0.f);
@@ -116,34 +119,56 @@ __device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
     return true;
 }
 
-// Pipelined sweep: tiles of kTcAtoms atoms; two accumulator buffers in TMEM
-// and two B buffers in shared memory.  While the block scores tile i, the
-// tensor core computes tile i + 1 and tile i + 2 is copied in (cp.async).
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+}
+
+// Warp-specialised sweep over tiles of kTcAtoms atoms.  Warp 8 (producer):
+// streams each tile's B operand into a 4-stage shared ring with one bulk copy
+// (mbarrier transaction count) and issues the tile's MMAs into one of two TMEM
+// accumulator buffers.  Warps 0-7 (consumers, two per TMEM lane quarter, one
+// column half each): wait for a buffer, copy it to registers, hand it back to
+// the producer, then score.  Every wait is bounded; a wait that gives up sets
+// the error word and the block stops.
+constexpr int kTcStages = 4;
+constexpr int kTcConsumers = 8;
+
 template <int LP, int SPLIT, int TOPK>
-__global__ void __launch_bounds__(kTcThreads) k_match_tc(const float2* __restrict__ x, int n, int len,
-                                                         const __nv_bfloat16* __restrict__ Bg, int ntiles,
-                                                         const float* __restrict__ wscore, int m,
-                                                         const float2* __restrict__ dict,
-                                                         int* __restrict__ best_idx, float2* __restrict__ best_ip,
-                                                         int* __restrict__ err) {
+__global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __restrict__ x, int n, int len,
+                                                              const __nv_bfloat16* __restrict__ Bg, int ntiles,
+                                                              const float* __restrict__ wscore, int m,
+                                                              const float2* __restrict__ dict,
+                                                              int* __restrict__ best_idx,
+                                                              float2* __restrict__ best_ip, int* __restrict__ err) {
     constexpr int KC = LP / 8;
     constexpr int A_BYTES = kTcRows * LP * 2;
     constexpr int B_BYTES = 2 * kTcAtoms * LP * 2;   // one tile: 2 rows per atom
     constexpr int NCOL = 2 * kTcAtoms;               // accumulator columns per buffer
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* sA = smraw;
-    unsigned char* sB0 = smraw + A_BYTES;            // two B buffers
-    float* sW = reinterpret_cast<float*>(smraw + A_BYTES + 2 * B_BYTES);   // [2][kTcAtoms]
+    unsigned char* sB = smraw + A_BYTES;             // [kTcStages][B_BYTES]
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t s_bfull[kTcStages], s_bempty[kTcStages], s_afull[2], s_aempty[2];
     __shared__ int s_fail;
-
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int lq = warp & 3;                         // TMEM lane quarter this warp may read
-    const int half = warp >> 2;                      // which half of each tile's columns it scores
-    const int n0 = blockIdx.x * kTcRows;
     __shared__ float s_ms[kTcRows][TOPK];
     __shared__ int s_mi[kTcRows][TOPK];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.x * kTcRows;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -152,30 +177,19 @@ __global__ void __launch_bounds__(kTcThreads) k_match_tc(const float2* __restric
     }
     if (tid == 0) {
         s_fail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[1])));
+        for (int q = 0; q < kTcStages; ++q) {
+            mbar_init(smem_u32(&s_bfull[q]), 1);
+            mbar_init(smem_u32(&s_bempty[q]), 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(smem_u32(&s_afull[q]), 1);
+            mbar_init(smem_u32(&s_aempty[q]), kTcConsumers);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    auto stage_b = [&](int tile, int buf) {          // cp.async the tile's B operand
-        const char* src = reinterpret_cast<const char*>(Bg + (size_t)tile * (B_BYTES / 2));
-        const uint32_t dst = smem_u32(sB0 + buf * B_BYTES);
-        for (int e = tid; e < B_BYTES / 16; e += kTcThreads) cp_async16(dst + 16 * e, src + 16 * e);
-    };
-    auto stage_w = [&](int tile, int buf) {          // cp.async the tile's score weights, close the group
-        for (int e = tid; e < kTcAtoms / 4; e += kTcThreads) {
-            const int a = tile * kTcAtoms + 4 * e;
-            if (a + 3 < m) cp_async16(smem_u32(sW + buf * kTcAtoms + 4 * e), wscore + a);
-            else
-                for (int q = 0; q < 4; ++q) sW[buf * kTcAtoms + 4 * e + q] = a + q < m ? wscore[a + q] : 0.f;
-        }
-        cp_async_commit();
-    };
-    auto stage = [&](int tile, int buf) { stage_b(tile, buf); stage_w(tile, buf); };
-    stage(0, 0);
-    if (ntiles > 1) stage(1, 1);
     // A tile: fingerprint rows in BF16 (zero rows past n, zero padding past the
     // SPLIT copies of the 2 len coefficients)
-    for (int e = tid; e < kTcRows * LP; e += kTcThreads) {
+    for (int e = tid; e < kTcRows * LP; e += blockDim.x) {
         const int row = e / LP, kk = e - row * LP;
         const int part = kk / (2 * len), k = kk - part * 2 * len;
         float v = 0.f;
@@ -186,124 +200,144 @@ __global__ void __launch_bounds__(kTcThreads) k_match_tc(const float2* __restric
         *reinterpret_cast<__nv_bfloat16*>(sA + core_off(row, kk, KC)) =
             part < SPLIT ? split_part(v, part, true, SPLIT) : __float2bfloat16_rn(0.f);
     }
-    const uint32_t idesc = mma_idesc(kTcRows, NCOL);
-    auto issue = [&](int tile) {                     // thread 0 only
-        const int buf = tile & 1;
-        const uint32_t tm = s_tmem + (uint32_t)(buf * NCOL);
-        const uint32_t bbase = smem_u32(sB0 + buf * B_BYTES);
-#pragma unroll
-        for (int ks = 0; ks < LP / 16; ++ks) {
-            const uint64_t ad = smem_desc(smem_u32(sA) + ks * 256, 128, KC * 128);
-            const uint64_t bd = smem_desc(bbase + ks * 256, 128, KC * 128);
-            const uint32_t acc = ks > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tm),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&s_bar[buf])));
-    };
-    // tile 0 ready -> first MMA
-    if (ntiles > 1) cp_async_wait<1>(); else cp_async_wait<0>();
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) issue(0);
+    const uint32_t tmem = s_tmem;
 
     float cs[TOPK];
     int ci[TOPK];
 #pragma unroll
     for (int q = 0; q < TOPK; ++q) { cs[q] = -1.f; ci[q] = 0x7fffffff; }
 
-    for (int tile = 0; tile < ntiles; ++tile) {
-        const int buf = tile & 1;
-        // next tile: its B copy landed -> launch its MMA into the other buffer
-        if (tile + 1 < ntiles) {
-            cp_async_wait<0>();
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncthreads();
-            if (tid == 0) {
+    if (warp == kTcConsumers) {
+        // ------------------------------ producer ------------------------------
+        if (lane == 0) {
+            const uint32_t idesc = mma_idesc(kTcRows, NCOL);
+            auto load = [&](int tile) {
+                const int st = tile % kTcStages;
+                const uint32_t bar = smem_u32(&s_bfull[st]);
+                mbar_expect_tx(bar, B_BYTES);
+                bulk_g2s(smem_u32(sB + st * B_BYTES), Bg + (size_t)tile * (B_BYTES / 2), B_BYTES, bar);
+            };
+            for (int t = 0; t < kTcStages && t < ntiles; ++t) load(t);
+            for (int tile = 0; tile < ntiles && !s_fail; ++tile) {
+                const int st = tile % kTcStages, buf = tile & 1;
+                if (!wait_parity(smem_u32(&s_bfull[st]), (tile / kTcStages) & 1)) { s_fail = 1; break; }
+                if (tile >= 2 && !wait_parity(smem_u32(&s_aempty[buf]), ((tile >> 1) - 1) & 1)) {
+                    s_fail = 1;
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                issue(tile + 1);
+                const uint32_t tm = tmem + (uint32_t)(buf * NCOL);
+                const uint32_t bbase = smem_u32(sB + st * B_BYTES);
+#pragma unroll
+                for (int ks = 0; ks < LP / 16; ++ks) {
+                    const uint64_t ad = smem_desc(smem_u32(sA) + ks * 256, 128, KC * 128);
+                    const uint64_t bd = smem_desc(bbase + ks * 256, 128, KC * 128);
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tm),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+                mma_commit(smem_u32(&s_afull[buf]));
+                mma_commit(smem_u32(&s_bempty[st]));
+                // refill the stage of the previous tile once its MMA has read it
+                const int prev = tile - 1;
+                if (prev >= 0 && prev + kTcStages < ntiles) {
+                    const int ps = prev % kTcStages;
+                    if (!wait_parity(smem_u32(&s_bempty[ps]), (prev / kTcStages) & 1)) { s_fail = 1; break; }
+                    load(prev + kTcStages);
+                }
+            }
+            // the last tiles' MMAs must finish before the block releases TMEM
+            if (!s_fail && ntiles > 0) {
+                const int last = ntiles - 1;
+                if (!wait_parity(smem_u32(&s_bempty[last % kTcStages]), (last / kTcStages) & 1)) s_fail = 1;
             }
         }
-        // this tile's products
-        if (!wait_parity(smem_u32(&s_bar[buf]), (tile >> 1) & 1)) s_fail = 1;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // B buffer `buf` is free again: prefetch tile + 2's operand into it (its
-        // weights follow once this tile's scores no longer need the buffer)
-        if (tile + 2 < ntiles) stage_b(tile + 2, buf);
-        if (!s_fail) {
-            const float* w = sW + buf * kTcAtoms;
-#pragma unroll 1
-            for (int c0 = half * (NCOL / 2); c0 < (half + 1) * (NCOL / 2); c0 += 32) {
-                uint32_t v[32];
-                const uint32_t taddr = s_tmem + (uint32_t)(buf * NCOL) + ((uint32_t)(lq * 32) << 16) +
-                                       (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-                      "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-                      "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                float sc[16];
-                bool any = false;
+        __syncwarp();
+    } else {
+        // ------------------------------ consumers -----------------------------
+        const int lq = warp & 3, half = warp >> 2;
+        for (int tile = 0; tile < ntiles; ++tile) {
+            const int buf = tile & 1;
+            if (!wait_parity(smem_u32(&s_afull[buf]), (tile >> 1) & 1)) { s_fail = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            uint32_t v[64];
+            const uint32_t taddr = tmem + (uint32_t)(buf * NCOL) + ((uint32_t)(lq * 32) << 16) +
+                                   (uint32_t)(half * (NCOL / 2));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                  "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                  "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                  "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]),
+                  "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]),
+                  "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]),
+                  "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]), "=r"(v[57]),
+                  "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+                : "r"(taddr + 32u));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            // the accumulator is in registers: hand the buffer back
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&s_aempty[buf]));
+            // A lane meets its atoms in increasing index order, so "strictly
+            // greater score" ranks a newcomer below equal earlier atoms: the
+            // list stays the top TOPK by (score, then lowest index).  The list
+            // settles slowly (a newcomer enters with probability ~TOPK / atoms
+            // seen), so the insertion runs only when some lane of the warp
+            // needs it.
+            const int a0 = tile * kTcAtoms + half * (kTcAtoms / 2);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int la = (c0 >> 1) + q;
-                    const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
-                    sc[q] = tile * kTcAtoms + la < m ? (re * re + im * im) * w[la] : -1.f;
-                    any |= sc[q] >= cs[TOPK - 1];
-                }
-                if (__any_sync(0xffffffffu, any)) {
+            for (int q = 0; q < 32; ++q) {
+                const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
+                const float sc = fmaf(re, re, im * im);
+                const bool in = sc > cs[TOPK - 1];
+                if (__any_sync(0xffffffffu, in)) {
+                    if (in) { cs[TOPK - 1] = sc; ci[TOPK - 1] = a0 + q; }
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int a = tile * kTcAtoms + (c0 >> 1) + q;
-                        if (better_cand(sc[q], a, cs[TOPK - 1], ci[TOPK - 1])) {
-                            cs[TOPK - 1] = sc[q];
-                            ci[TOPK - 1] = a;
-#pragma unroll
-                            for (int r = TOPK - 1; r > 0; --r) {
-                                if (better_cand(cs[r], ci[r], cs[r - 1], ci[r - 1])) {
-                                    const float ts = cs[r]; cs[r] = cs[r - 1]; cs[r - 1] = ts;
-                                    const int ti = ci[r]; ci[r] = ci[r - 1]; ci[r - 1] = ti;
-                                }
-                            }
+                    for (int r = TOPK - 1; r > 0; --r) {
+                        if (cs[r] > cs[r - 1]) {
+                            const float ts = cs[r]; cs[r] = cs[r - 1]; cs[r - 1] = ts;
+                            const int ti = ci[r]; ci[r] = ci[r - 1]; ci[r - 1] = ti;
                         }
                     }
                 }
             }
+            if (s_fail) break;
         }
-        // every warp is done with accumulator `buf` and weights `buf` before
-        // either is overwritten
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        if (tile + 2 < ntiles) stage_w(tile + 2, buf);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (s_fail) break;
     }
-    cp_async_wait<0>();
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(2 * NCOL));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * NCOL));
     }
     if (s_fail) {
         if (tid == 0) atomicExch(err, 1);
         return;
     }
+    if (warp >= kTcConsumers) return;
     // merge the two column halves' candidate lists of each fingerprint
-    const int lrow = lq * 32 + (tid & 31);
+    const int lq = warp & 3, half = warp >> 2;
+    const int lrow = lq * 32 + lane;
     if (half == 1) {
 #pragma unroll
         for (int q = 0; q < TOPK; ++q) { s_ms[lrow][q] = cs[q]; s_mi[lrow][q] = ci[q]; }
     }
-    __syncthreads();
+    asm volatile("bar.sync 1, %0;" ::"n"(kTcThreads));     // consumer warps only
     if (half == 1) return;
 #pragma unroll
     for (int q = 0; q < TOPK; ++q) {
@@ -365,7 +399,7 @@ mrf_status match_bf16_candidates(MatchWorkspace& ws, const float2* x, int n, int
             MRF_CUDA(cudaMalloc(&ws.tc_b, bbytes));
             ws.tc_b_bytes = bbytes;
         }
-        k_tc_prepare_b<<<1024, 256, 0, s>>>(dict, m, len, Lp, ntiles, split,
+        k_tc_prepare_b<<<1024, 256, 0, s>>>(dict, ws.wscore, m, len, Lp, ntiles, split,
                                             reinterpret_cast<__nv_bfloat16*>(ws.tc_b));
         MRF_LAUNCHED_AS("k_tc_prepare_b", s);
         ws.tc_dict = dict;
@@ -381,11 +415,10 @@ mrf_status match_bf16_candidates(MatchWorkspace& ws, const float2* x, int n, int
 #define MRF_TC_LAUNCH(LPV, SP)                                                                                   \
     do {                                                                                                         \
         constexpr int TK = SP == 3 ? 4 : kTopK;                                                                  \
-        const size_t sm = (size_t)kTcRows * LPV * 2 + (size_t)2 * 2 * kTcAtoms * LPV * 2 +                       \
-                          2 * kTcAtoms * sizeof(float);                                                           \
+        const size_t sm = (size_t)kTcRows * LPV * 2 + (size_t)kTcStages * 2 * kTcAtoms * LPV * 2;                \
         MRF_CUDA(cudaFuncSetAttribute(k_match_tc<LPV, SP, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                       (int)sm));                                                                 \
-        k_match_tc<LPV, SP, TK><<<blocks, kTcThreads, sm, s>>>(x, n, len,                                        \
+        k_match_tc<LPV, SP, TK><<<blocks, kTcThreads + 32, sm, s>>>(x, n, len,                                   \
                                                                reinterpret_cast<const __nv_bfloat16*>(ws.tc_b),  \
                                                                ntiles, ws.wscore, m, dict, ws.best_idx,          \
                                                                ws.best_ip, ws.tc_err);                           \
