@@ -170,6 +170,21 @@ mrf_status mrf_match_noalloc(const mrf_c64* x, int n, int len, const mrf_c64* di
                              const float* atom_norm2, const float* lut, int m, int precision,
                              int* idx, float* pd, float* t1t2, mrf_stream stream);
 
+/* Patch graph of Eq. 7, kept sparse: for every row i of the integer patch
+ * vectors F, the knn rows j != i with the smallest squared distance
+ * sum_k (F_ik - F_jk)^2 over the first fd entries, in ascending order, ties
+ * to the lower j.  The distances are exact integers (Algorithm 1 builds F as
+ * the 12-bit fixed point rint(4096 T / Tmax) of the matched T1 and T2 maps
+ * over each patch, so tied distances are common and break alike everywhere).
+ * F: dev int32 [np][ld], 0 <= F <= 4096, ld >= fd and a multiple of 4, the
+ * entries fd <= k < ld zero.  nbr: dev int32 [np][knn]; d2: dev uint32
+ * [np][knn].  Needs 1 <= knn <= 32, np > knn, 1 <= fd <= 255.  Scratch is
+ * allocated and freed by the call, which synchronises the stream to report
+ * a feature outside [0, 4096] (MRF_EINVAL) or a device wait that gave up
+ * (MRF_ETIMEOUT). */
+mrf_status mrf_patch_knn(const int* F, int np, int fd, int ld, int knn, int* nbr, unsigned* d2,
+                         mrf_stream stream);
+
 /* ------------------------------------------------------------------------
  * Algorithm 1 (MS-LLR).  The iterate is held in the temporal subspace,
  * X = alpha Phi^H with alpha dev [ny][nx][K]; the problem is posed over

@@ -8,8 +8,8 @@ not been built.
 """
 from .api import (MRFError, NufftPlan, Recon, ReconParams, dict_subspace, epg_fisp, launch_count, match,
                   nufft_adjoint, nufft_adjoint_subspace, nufft_forward, nufft_forward_subspace,
-                  nufft_plan, profile_enable, profile_mark, profile_read)
+                  nufft_plan, patch_knn, profile_enable, profile_mark, profile_read)
 
 __all__ = ["MRFError", "NufftPlan", "Recon", "ReconParams", "dict_subspace", "epg_fisp", "match",
            "nufft_adjoint", "nufft_adjoint_subspace", "nufft_forward", "nufft_forward_subspace",
-           "nufft_plan", "launch_count", "profile_enable", "profile_mark", "profile_read"]
+           "nufft_plan", "patch_knn", "launch_count", "profile_enable", "profile_mark", "profile_read"]

@@ -39,6 +39,7 @@ SIGNATURES = {
     "mrf_dict_subspace": (i32, [vp, i32, i32, i32, vp, vp, vp, vp]),
     "mrf_match": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp, vp]),
     "mrf_match_noalloc": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp, vp]),
+    "mrf_patch_knn": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),
     "mrf_recon_create": (i32, [C.POINTER(vp), vp, C.POINTER(ReconParams), vp, i32, vp, vp, vp, i32, vp, vp]),
     "mrf_recon_iter": (i32, [vp, i32, f64p, vp]),
     "mrf_recon_maps": (i32, [vp, vp, vp, vp, vp, vp]),

@@ -157,6 +157,18 @@ def match(x, D, lut, atom_norm2=None, precision=MATCH_FP32):
     return idx, pd, t1t2
 
 
+def patch_knn(F, knn, fd=None):
+    """(nbr [np, knn] int32, d2 [np, knn] int32 holding uint32 bits) of the
+    integer patch vectors F [np, ld] (entries past fd zero, ld % 4 == 0)."""
+    _check(F, "F", torch.int32)
+    npatch, ld = F.shape
+    fd = ld if fd is None else int(fd)
+    nbr = torch.empty((npatch, knn), dtype=torch.int32, device=F.device)
+    d2 = torch.empty((npatch, knn), dtype=torch.int32, device=F.device)
+    _lib.call("mrf_patch_knn", _ptr(F), npatch, fd, ld, int(knn), _ptr(nbr), _ptr(d2), _stream())
+    return nbr, d2
+
+
 # ---------------------------------------------------------------------------
 # Algorithm 1
 # ---------------------------------------------------------------------------

@@ -24,37 +24,13 @@
 
 #include "common.h"
 #include "match.h"
+#include "tc5.cuh"
 
 namespace mrf {
 
 constexpr int kTcRows = 128;        // fingerprints per block (TMEM lanes)
 constexpr int kTcAtoms = 64;        // atoms per tile (128 B rows, N = 128)
 constexpr int kTcThreads = 256;       // 8 warps: two per TMEM lane quarter
-constexpr unsigned kSpinLimit = 1u << 26;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;                  // descriptor version of the 5th-generation tensor core
-    return d;                                // base offset 0, no swizzle
-}
-
-// kind::f16 instruction descriptor: BF16 x BF16 -> F32, K-major A and B
-__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// byte offset of element (row, k) in the core-matrix layout with KC k-chunks
-__host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int KC) {
-    return (uint32_t)((((row >> 3) * KC + (k >> 3)) * 128) + ((row & 7) * 16) + ((k & 7) * 2));
-}
-
 // Operand value of the split form: with SPLIT = 3 the reduction axis holds
 // three copies of the 2 len real coefficients, (hi, hi, lo) for A and
 // (hi, lo, hi) for B, hi = bf16(v), lo = bf16(v - hi), so that the product sums
@@ -95,46 +71,6 @@ __global__ void k_tc_prepare_b(const float2* __restrict__ dict, const float* __r
 
 __device__ __forceinline__ bool better_cand(float s, int i, float bs, int bi) {
     return s > bs || (s == bs && i < bi);
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
-
-// bounded wait on an mbarrier phase; returns false if it gave up
-__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
-    uint32_t done = 0;
-    unsigned spins = 0;
-    while (!done) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity));
-        if (!done && ++spins > kSpinLimit) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
 }
 
 // Warp-specialised sweep over tiles of kTcAtoms atoms.  Warp 8 (producer):
@@ -215,10 +151,12 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
         // ------------------------------ producer ------------------------------
         if (lane == 0) {
             const uint32_t idesc = mma_idesc(kTcRows, NCOL);
+            int loaded = 0, mmas = 0;   // tiles whose copy / whose MMAs were issued
             auto load = [&](int tile) {
                 const int st = tile % kTcStages;
                 const uint32_t bar = smem_u32(&s_bfull[st]);
                 mbar_expect_tx(bar, B_BYTES);
+                loaded = tile + 1;
                 bulk_g2s(smem_u32(sB + st * B_BYTES), Bg + (size_t)tile * (B_BYTES / 2), B_BYTES, bar);
             };
             for (int t = 0; t < kTcStages && t < ntiles; ++t) load(t);
@@ -242,6 +180,7 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tm),
                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
                 }
+                mmas = tile + 1;
                 mma_commit(smem_u32(&s_afull[buf]));
                 mma_commit(smem_u32(&s_bempty[st]));
                 // refill the stage of the previous tile once its MMA has read it
@@ -252,11 +191,15 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
                     load(prev + kTcStages);
                 }
             }
-            // the last tiles' MMAs must finish before the block releases TMEM
-            if (!s_fail && ntiles > 0) {
-                const int last = ntiles - 1;
+            // every issued MMA and copy must finish before the block reuses shared
+            // memory or releases TMEM, also when a wait gave up (bounded again)
+            if (mmas > 0) {
+                const int last = mmas - 1;
                 if (!wait_parity(smem_u32(&s_bempty[last % kTcStages]), (last / kTcStages) & 1)) s_fail = 1;
             }
+            if (s_fail)
+                for (int t = mmas; t < loaded; ++t)
+                    wait_parity(smem_u32(&s_bfull[t % kTcStages]), (t / kTcStages) & 1);
         }
         __syncwarp();
     } else {

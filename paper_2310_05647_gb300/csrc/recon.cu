@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "common.h"
+#include "knn.h"
 #include "match.h"
 #include "nufft_plan.h"
 
@@ -141,128 +142,6 @@ __global__ void k_features(const float* __restrict__ t1t2, PatchGeom g, double t
     int* f = F + (size_t)i * FD4 + 2 * q;
     f[0] = (int)rint((double)t1t2[2 * v] / t1max * kQScale);
     f[1] = (int)rint((double)t1t2[2 * v + 1] / t2max * kQScale);
-}
-
-__device__ __forceinline__ bool less_dj(unsigned d, int j, unsigned d2, int j2) {
-    return d < d2 || (d == d2 && j < j2);
-}
-
-// k nearest patches by squared distance (self excluded, ties to the lower
-// index), in two steps.  k_knn_part: block = 32 query patches x one candidate
-// partition; 8 threads per query each scan every 8th candidate of each
-// 64-candidate tile, 4 candidates at a time with 16-byte shared loads, keep
-// their KMAX best and merge them with shuffles into the partition's best knn.
-// k_knn_merge: one thread per query merges the partitions' sorted lists.
-// Feature rows are padded with zeros to a multiple of 4 (FD4).
-template <int KMAX>
-__global__ void __launch_bounds__(256) k_knn_part(const int* __restrict__ F, int np, int FD4, int knn,
-                                                  int cand_per_part, int* __restrict__ pnbr,
-                                                  unsigned* __restrict__ pd2) {
-    extern __shared__ int4 shf4[];
-    int* shf = reinterpret_cast<int*>(shf4);
-    const int ld = FD4 + 4;
-    int* Fq = shf;              // [32][ld]
-    int* Fc = shf + 32 * ld;    // [64][ld]
-    const int ql = threadIdx.x >> 3, sub = threadIdx.x & 7;
-    const int q = blockIdx.x * 32 + ql;
-    const int part = blockIdx.y;
-    const int cb = part * cand_per_part, ce = min(np, cb + cand_per_part);
-    const int v4 = FD4 >> 2;
-    for (int i = threadIdx.x; i < 32 * v4; i += blockDim.x) {
-        const int r = i / v4, c = i - r * v4;
-        const int qq = blockIdx.x * 32 + r;
-        const int4 v = qq < np ? reinterpret_cast<const int4*>(F + (size_t)qq * FD4)[c] : make_int4(0, 0, 0, 0);
-        *reinterpret_cast<int4*>(Fq + r * ld + 4 * c) = v;
-    }
-    unsigned bd[KMAX];
-    int bj[KMAX];
-#pragma unroll
-    for (int i = 0; i < KMAX; ++i) { bd[i] = 0xffffffffu; bj[i] = 0x7fffffff; }
-    for (int c0 = cb; c0 < ce; c0 += 64) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 64 * v4; i += blockDim.x) {
-            const int r = i / v4, c = i - r * v4;
-            const int4 v = c0 + r < ce ? reinterpret_cast<const int4*>(F + (size_t)(c0 + r) * FD4)[c]
-                                       : make_int4(0, 0, 0, 0);
-            *reinterpret_cast<int4*>(Fc + r * ld + 4 * c) = v;
-        }
-        __syncthreads();
-        if (q < np) {
-#pragma unroll
-            for (int grp = 0; grp < 2; ++grp) {
-                unsigned d[4] = {0u, 0u, 0u, 0u};
-                const int* a = Fq + ql * ld;
-                for (int t = 0; t < FD4; t += 4) {
-                    const int4 av = *reinterpret_cast<const int4*>(a + t);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int4 bv = *reinterpret_cast<const int4*>(Fc + (sub + 8 * (4 * grp + u)) * ld + t);
-                        const int e0 = av.x - bv.x, e1 = av.y - bv.y, e2 = av.z - bv.z, e3 = av.w - bv.w;
-                        d[u] += (unsigned)(e0 * e0) + (unsigned)(e1 * e1) + (unsigned)(e2 * e2) +
-                                (unsigned)(e3 * e3);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = c0 + sub + 8 * (4 * grp + u);
-                    if (j >= ce || j == q) continue;
-                    if (less_dj(d[u], j, bd[KMAX - 1], bj[KMAX - 1])) {
-                        bd[KMAX - 1] = d[u];
-                        bj[KMAX - 1] = j;
-#pragma unroll
-                        for (int i = KMAX - 1; i > 0; --i) {
-                            if (less_dj(bd[i], bj[i], bd[i - 1], bj[i - 1])) {
-                                const unsigned td = bd[i]; bd[i] = bd[i - 1]; bd[i - 1] = td;
-                                const int tj = bj[i]; bj[i] = bj[i - 1]; bj[i - 1] = tj;
-                            }
-                        }
-                    }
-                }
-            }
-        }
-    }
-    // merge the 8 sorted lists of this query into the partition's best knn
-    for (int r = 0; r < knn; ++r) {
-        unsigned d = bd[0];
-        int j = bj[0];
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-            const unsigned d2 = __shfl_xor_sync(0xffffffffu, d, o);
-            const int j2 = __shfl_xor_sync(0xffffffffu, j, o);
-            if (less_dj(d2, j2, d, j)) { d = d2; j = j2; }
-        }
-        if (bj[0] == j) {
-#pragma unroll
-            for (int i = 0; i < KMAX - 1; ++i) { bd[i] = bd[i + 1]; bj[i] = bj[i + 1]; }
-            bd[KMAX - 1] = 0xffffffffu;
-            bj[KMAX - 1] = 0x7fffffff;
-        }
-        if (sub == 0 && q < np) {
-            pnbr[((size_t)part * np + q) * knn + r] = j;
-            pd2[((size_t)part * np + q) * knn + r] = d;
-        }
-    }
-}
-
-__global__ void k_knn_merge(const int* __restrict__ pnbr, const unsigned* __restrict__ pd2, int parts, int np,
-                            int knn, int* __restrict__ nbr, unsigned* __restrict__ d2out) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= np) return;
-    int pos[16];
-    for (int p = 0; p < parts; ++p) pos[p] = 0;
-    for (int r = 0; r < knn; ++r) {
-        int bp = -1;
-        unsigned bd = 0xffffffffu;
-        int bjj = 0x7fffffff;
-        for (int p = 0; p < parts; ++p) {
-            if (pos[p] >= knn) continue;
-            const size_t o = ((size_t)p * np + q) * knn + pos[p];
-            if (less_dj(pd2[o], pnbr[o], bd, bjj)) { bd = pd2[o]; bjj = pnbr[o]; bp = p; }
-        }
-        nbr[(size_t)q * knn + r] = bjj;
-        d2out[(size_t)q * knn + r] = bd;
-        if (bp >= 0) pos[bp]++;
-    }
 }
 
 // sigma^2 = median of the non-zero kNN squared distances (1 if none), by a
@@ -690,9 +569,7 @@ struct mrf_recon_s {
     int* F = nullptr;
     int* nbr = nullptr;
     unsigned* d2 = nullptr;
-    int* pnbr = nullptr;        // [parts][np][knn] per-partition kNN lists
-    unsigned* pd2 = nullptr;
-    int knn_parts_max = 8;
+    mrf::KnnWorkspace knn;      // kNN scratch (operand tiles, per-partition lists)
     float *w = nullptr, *rw = nullptr, *deg = nullptr;
     int *rcnt = nullptr, *roff = nullptr, *rpos = nullptr, *rsrc = nullptr, *rsrc_tmp = nullptr;
     float* rw_tmp = nullptr;
@@ -758,26 +635,7 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
                                                                              (double)R->t2max,
                                                                              (FD + 3) / 4 * 4, R->F);
     MRF_LAUNCHED_AS("k_features", s);
-    {
-        const int FD4 = (FD + 3) / 4 * 4;
-        const size_t sm = sizeof(int) * (size_t)(32 + 64) * (FD4 + 4);
-        const int qb = (np + 31) / 32;
-        int parts = std::max(1, std::min(R->knn_parts_max, (4 * 152 + qb - 1) / qb));
-        int per = (np + parts - 1) / parts;
-        per = (per + 63) / 64 * 64;
-        parts = (np + per - 1) / per;
-        dim3 grid(qb, parts);
-        if (knn <= 16) {
-            MRF_CUDA(cudaFuncSetAttribute(k_knn_part<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_knn_part<16><<<grid, 256, sm, s>>>(R->F, np, FD4, knn, per, R->pnbr, R->pd2);
-        } else {
-            MRF_CUDA(cudaFuncSetAttribute(k_knn_part<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_knn_part<32><<<grid, 256, sm, s>>>(R->F, np, FD4, knn, per, R->pnbr, R->pd2);
-        }
-        MRF_LAUNCHED_AS("k_knn_part", s);
-        k_knn_merge<<<(np + 127) / 128, 128, 0, s>>>(R->pnbr, R->pd2, parts, np, knn, R->nbr, R->d2);
-    }
-    MRF_LAUNCHED_AS("k_knn_merge", s);
+    MRF_PROPAGATE(knn_run(R->knn, R->F, np, FD, (FD + 3) / 4 * 4, knn, R->nbr, R->d2, s));
     const int ne = np * knn;
     k_median_nonzero<<<1, 1024, 0, s>>>(R->d2, ne, R->scal + 0);
     MRF_LAUNCHED_AS("k_median_nonzero", s);
@@ -871,8 +729,7 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     const int FD4 = (2 * R->pp + 3) / 4 * 4;
     MRF_PROPAGATE(dalloc(R, &R->F, (size_t)np * FD4));
     MRF_CUDA(cudaMemsetAsync(R->F, 0, sizeof(int) * (size_t)np * FD4, s));
-    MRF_PROPAGATE(dalloc(R, &R->pnbr, (size_t)R->knn_parts_max * np * knn));
-    MRF_PROPAGATE(dalloc(R, &R->pd2, (size_t)R->knn_parts_max * np * knn));
+    MRF_PROPAGATE(R->knn.reserve(np, 2 * R->pp, knn));
     MRF_PROPAGATE(dalloc(R, &R->nbr, (size_t)np * knn));
     MRF_PROPAGATE(dalloc(R, &R->d2, (size_t)np * knn));
     MRF_PROPAGATE(dalloc(R, &R->w, (size_t)np * knn));
