@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default="plain,chosen")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["mrf256_t1000", "mrf256_t100"],
+                    help="mrf256_t100: the same image with 100 frames, for small profiling captures")
     return ap.parse_args()
 
 
@@ -487,7 +489,9 @@ def run_ours(args, dist):
 
 
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = args.workload
     dist = Dist()
     try:
         if args.impl == "reference":

@@ -318,56 +318,50 @@ __global__ void __launch_bounds__(kKnThreads + 32) k_knn_tc(const int* __restric
             const unsigned nbl = jb + lane < ce ? (unsigned)__ldg(nrm + jb + lane) : 0u;
             if (!wait_parity(smem_u32(&s_afull[buf]), (tile >> 1) & 1)) { s_fail = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            uint32_t v[64];
             const uint32_t taddr = tmem + (uint32_t)(buf * NCOL) + ((uint32_t)(lq * 32) << 16) +
                                    (uint32_t)(half * (NCOL / 2));
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                  "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-                  "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-                  "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]),
-                  "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]),
-                  "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]),
-                  "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]), "=r"(v[57]),
-                  "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
-                : "r"(taddr + 32u));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&s_aempty[buf]));
             // A lane meets its candidates in increasing index order, so a strict
             // "less" keeps equal earlier candidates ahead: the list is the best
-            // KN by (distance, then lowest index).
+            // KN by (distance, then lowest index).  The accumulator is read in
+            // four groups of 8 candidates (a small loop body for the
+            // instruction cache); the buffer goes back to the producer after
+            // the last group.
+#pragma unroll 1
+            for (int grp = 0; grp < 4; ++grp) {
+                uint32_t v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr + 16u * (uint32_t)grp));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int j = jb + q;
-                const int ch = __float2int_rn(__uint_as_float(v[2 * q]));
-                const int cl = __float2int_rn(__uint_as_float(v[2 * q + 1]));
-                const unsigned nb = __shfl_sync(0xffffffffu, nbl, q);
-                unsigned d = nq + nb - 2u * (unsigned)(32 * ch + cl);
-                if (j >= ce || j == qrow) d = 0xffffffffu;
-                const bool in = d < bd[KN - 1];
-                if (__any_sync(0xffffffffu, in)) {
-                    if (in) { bd[KN - 1] = d; bj[KN - 1] = j; }
+                for (int u = 0; u < 8; ++u) {
+                    const int q = 8 * grp + u;
+                    const int j = jb + q;
+                    const int ch = __float2int_rn(__uint_as_float(v[2 * u]));
+                    const int cl = __float2int_rn(__uint_as_float(v[2 * u + 1]));
+                    const unsigned nb = __shfl_sync(0xffffffffu, nbl, q);
+                    unsigned d = nq + nb - 2u * (unsigned)(32 * ch + cl);
+                    if (j >= ce || j == qrow) d = 0xffffffffu;
+                    const bool in = d < bd[KN - 1];
+                    if (__any_sync(0xffffffffu, in)) {
+                        if (in) { bd[KN - 1] = d; bj[KN - 1] = j; }
 #pragma unroll
-                    for (int r = KN - 1; r > 0; --r) {
-                        if (bd[r] < bd[r - 1]) {
-                            const unsigned td = bd[r]; bd[r] = bd[r - 1]; bd[r - 1] = td;
-                            const int tj = bj[r]; bj[r] = bj[r - 1]; bj[r - 1] = tj;
+                        for (int r = KN - 1; r > 0; --r) {
+                            if (bd[r] < bd[r - 1]) {
+                                const unsigned td = bd[r]; bd[r] = bd[r - 1]; bd[r - 1] = td;
+                                const int tj = bj[r]; bj[r] = bj[r - 1]; bj[r - 1] = tj;
+                            }
                         }
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&s_aempty[buf]));
             if (s_fail) break;
         }
     }

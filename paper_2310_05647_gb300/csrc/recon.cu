@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(128) k_graph_blocks(const float2* __restrict__
 // the columns are nearly orthogonal and few sweeps are needed); the final V
 // is stored back.  The SVD computed is the same either way.
 template <int R, int KP>
-__global__ void __launch_bounds__(128) k_svt(const float2* __restrict__ alpha, PatchGeom g, int K, float tau,
+__global__ void __launch_bounds__(128, (R <= 2 && KP <= 10) ? 4 : 1) k_svt(const float2* __restrict__ alpha, PatchGeom g, int K, float tau,
                                              float2* __restrict__ P, double* __restrict__ nuc,
                                              float2* __restrict__ Vio, int warm) {
     const int lane = threadIdx.x & 31;
@@ -396,46 +396,108 @@ __global__ void __launch_bounds__(128) k_svt(const float2* __restrict__ alpha, P
 #pragma unroll
             for (int k = 0; k < KP; ++k) a[r][k] = na[r][k];
     }
+    // Parallel cyclic order (circle schedule): a sweep is KP - 1 rounds of
+    // KP / 2 disjoint column pairs that together pair every two columns once;
+    // rotations of disjoint pairs commute, so a round reduces its pairs' inner
+    // products together (one shuffle tree for all of them) and then rotates.  A pair is rotated while its normalised
+    // off-diagonal |gamma| / (|a_p| |a_q|) exceeds kJacobiTol (a few times the
+    // FP32 rounding of a p^2-term inner product: below it a rotation only
+    // moves rounding noise); a sweep without rotations ends the loop, and so
+    // does a sweep whose rotations were all below kJacobiQuad (cyclic Jacobi
+    // converges quadratically: what such a sweep leaves is of order
+    // kJacobiQuad^2 < kJacobiTol).  Column norms are recomputed exactly at each
+    // sweep and updated in closed form after each rotation
+    // (|a_p|^2 -= t |gamma|, |a_q|^2 += t |gamma|).
+    constexpr float kJacobiTol = 2e-6f;
+    constexpr float kJacobiQuad = 3e-4f;
+    constexpr int NP = KP / 2;
     for (int sweep = 0; sweep < 30; ++sweep) {
-        float off = 0.f;
+        float n2[KP];
 #pragma unroll
-        for (int p = 0; p < KP - 1; ++p) {
+        for (int k = 0; k < KP; ++k) {
+            n2[k] = 0.f;
 #pragma unroll
-            for (int q = p + 1; q < KP; ++q) {
-                float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+            for (int r = 0; r < R; ++r) n2[k] += cabs2(a[r][k]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < KP; ++k) n2[k] += __shfl_xor_sync(0xffffffffu, n2[k], o);
+        bool rotated = false, large = false;
+        // Round rd pairs the register positions (i, KP - 1 - i); between rounds
+        // the columns at positions 1 .. KP - 1 shift down by one (position 0
+        // stays), which is the circle schedule with the data moved instead of
+        // the indices: the loop body is one round (small enough for the
+        // instruction cache) and after KP - 1 rounds every column is back in
+        // its position.
+#pragma unroll 1
+        for (int rd = 0; rd < KP - 1; ++rd) {
+            float gr[NP], gi[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const int p = i, q = KP - 1 - i;
+                gr[i] = 0.f;
+                gi[i] = 0.f;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    al += cabs2(a[r][p]);
-                    be += cabs2(a[r][q]);
                     const float2 t = cconjmul(a[r][p], a[r][q]);
-                    gr += t.x;
-                    gi += t.y;
+                    gr[i] += t.x;
+                    gi[i] += t.y;
                 }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                gr = warp_sum(gr);
-                gi = warp_sum(gi);
-                const float gabs = sqrtf(gr * gr + gi * gi);
-                const float nrm = sqrtf(al * be);
-                if (gabs > 1e-30f && gabs > 1e-7f * nrm) {
-                    off = fmaxf(off, gabs / nrm);
-                    const float zeta = (be - al) / (2.f * gabs);
-                    const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                    const float c = rsqrtf(1.f + t * t), s = c * t;
-                    const float2 ph = make_float2(gr / gabs, -gi / gabs);   // conj(gamma) / |gamma|
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    gr[i] += __shfl_xor_sync(0xffffffffu, gr[i], o);
+                    gi[i] += __shfl_xor_sync(0xffffffffu, gi[i], o);
+                }
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const int p = i, q = KP - 1 - i;
+                const float al = n2[p], be = n2[q];
+                const float g2 = gr[i] * gr[i] + gi[i] * gi[i];
+                if (g2 > 1e-36f && g2 > kJacobiTol * kJacobiTol * al * be) {
+                    rotated = true;
+                    large |= g2 > kJacobiQuad * kJacobiQuad * al * be;
+                    const float ig = rsqrtf(g2), gabs = g2 * ig;
+                    // t: the root of t^2 + 2 zeta t - 1 = 0 of smaller magnitude,
+                    // zeta = (|a_q|^2 - |a_p|^2) / (2 |gamma|)
+                    const float d = be - al;
+                    const float t = __fdividef(2.f * gabs, d + copysignf(sqrtf(d * d + 4.f * g2), d));
+                    const float c = rsqrtf(1.f + t * t), sn = c * t;
+                    const float2 ph = make_float2(gr[i] * ig, -gi[i] * ig);   // conj(gamma) / |gamma|
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const float2 ap = a[r][p], aq = cmul(a[r][q], ph);
-                        a[r][p] = csub(cscale(ap, c), cscale(aq, s));
-                        a[r][q] = cadd(cscale(ap, s), cscale(aq, c));
+                        a[r][p] = csub(cscale(ap, c), cscale(aq, sn));
+                        a[r][q] = cadd(cscale(ap, sn), cscale(aq, c));
                     }
                     const float2 vp = v[p], vq = cmul(v[q], ph);
-                    v[p] = csub(cscale(vp, c), cscale(vq, s));
-                    v[q] = cadd(cscale(vp, s), cscale(vq, c));
+                    v[p] = csub(cscale(vp, c), cscale(vq, sn));
+                    v[q] = cadd(cscale(vp, sn), cscale(vq, c));
+                    n2[p] = al - t * gabs;
+                    n2[q] = be + t * gabs;
                 }
             }
+            // shift positions 1 .. KP - 1 down by one
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 first = a[r][1];
+#pragma unroll
+                for (int k = 1; k < KP - 1; ++k) a[r][k] = a[r][k + 1];
+                a[r][KP - 1] = first;
+            }
+            {
+                const float2 first = v[1];
+                const float nf = n2[1];
+#pragma unroll
+                for (int k = 1; k < KP - 1; ++k) { v[k] = v[k + 1]; n2[k] = n2[k + 1]; }
+                v[KP - 1] = first;
+                n2[KP - 1] = nf;
+            }
         }
-        if (off < 2e-7f) break;
+        if (!rotated || !large) break;
     }
     float f[KP];
     float nsum = 0.f;

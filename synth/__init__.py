@@ -65,6 +65,13 @@ WORKLOADS = {
     "mrf256_t1000": Workload("mrf256_t1000", n=256, frames=1000, ns=2048, interleaves=48,
                              t1_range=(100.0, 4000.0), t2_range=(10.0, 500.0),
                              n_t1=100, n_t2=60, rank=10),
+    # The same image, patch grid, dictionary and interleaf pattern with 100
+    # frames: the per-image kernels (matching, kNN, SVT, graph term) have the
+    # shapes of the 1000-frame workload at a tenth of the device memory, for
+    # small profiling captures.
+    "mrf256_t100": Workload("mrf256_t100", n=256, frames=100, ns=2048, interleaves=48,
+                            t1_range=(100.0, 4000.0), t2_range=(10.0, 500.0),
+                            n_t1=100, n_t2=60, rank=10),
 }
 
 
