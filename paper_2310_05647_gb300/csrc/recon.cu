@@ -300,35 +300,79 @@ __global__ void k_lambda(const float* __restrict__ lmax, float lam1_0, int liter
 
 // (Q(X) L)_j = deg_j Q_j - 1/2 sum_{i in N(j)} w_ji Q_i - 1/2 sum_{i: j in N(i)} w_ij Q_i,
 // written per patch (QL nullable) and/or accumulated into Tr(Q L Q^H).
-__global__ void __launch_bounds__(128) k_graph_blocks(const float2* __restrict__ alpha, PatchGeom g, int K,
-                                                      const int* __restrict__ nbr, const float* __restrict__ w,
-                                                      int knn, const int* __restrict__ roff,
-                                                      const int* __restrict__ rsrc, const float* __restrict__ rw,
-                                                      const float* __restrict__ deg, float2* __restrict__ QL,
-                                                      double* __restrict__ trace) {
+// One block per patch j, each thread up to kGbElems of its p x p x K
+// coefficients (consecutive threads read consecutive coefficients of a
+// neighbour's patch rows).  The neighbour list (forward kNN entries, then
+// the reverse list) is staged in shared memory kGbChunk entries at a time as
+// (offset of the neighbour patch's first coefficient, w / 2), so the inner
+// loop is one gather and two FMAs per coefficient and neighbour.
+constexpr int kGbThreads = 128;
+constexpr int kGbElems = 8;
+constexpr int kGbChunk = 256;
+
+__global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __restrict__ alpha, PatchGeom g, int K,
+                                                             const int* __restrict__ nbr,
+                                                             const float* __restrict__ w, int knn,
+                                                             const int* __restrict__ roff,
+                                                             const int* __restrict__ rsrc,
+                                                             const float* __restrict__ rw,
+                                                             const float* __restrict__ deg,
+                                                             float2* __restrict__ QL, double* __restrict__ trace) {
+    __shared__ int s_off[kGbChunk];
+    __shared__ float s_w[kGbChunk];
     const int j = blockIdx.x;
     const int pK = g.p * K;
     const int ne = g.p * pK;
     const int jy = g.origin(j / g.cnt), jx = g.origin(j % g.cnt);
     const float dj = deg[j];
     const int rb = roff[j], re = roff[j + 1];
+    const int nq = knn + (re - rb);
     double tr = 0.0;
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        const int py = e / pK, rem = e - py * pK;      // rem = px * K + k
-        const float2 a = alpha[((size_t)(jy + py) * g.n + jx) * K + rem];
-        float2 v = cscale(a, dj);
-        for (int q = 0; q < knn; ++q) {
-            const int i = nbr[(size_t)j * knn + q];
-            const float2 b = alpha[((size_t)(g.origin(i / g.cnt) + py) * g.n + g.origin(i % g.cnt)) * K + rem];
-            v = csub(v, cscale(b, 0.5f * w[(size_t)j * knn + q]));
+    for (int e0 = 0; e0 < ne; e0 += kGbThreads * kGbElems) {
+        int off[kGbElems];
+        float2 a[kGbElems], v[kGbElems];
+#pragma unroll
+        for (int u = 0; u < kGbElems; ++u) {
+            const int e = e0 + threadIdx.x + u * kGbThreads;
+            const int py = e / pK, rem = e - py * pK;      // rem = px * K + k
+            off[u] = e < ne ? py * g.n * K + rem : -1;
+            a[u] = e < ne ? alpha[((size_t)jy * g.n + jx) * K + off[u]] : make_float2(0.f, 0.f);
+            v[u] = cscale(a[u], dj);
         }
-        for (int q = rb; q < re; ++q) {
-            const int i = rsrc[q];
-            const float2 b = alpha[((size_t)(g.origin(i / g.cnt) + py) * g.n + g.origin(i % g.cnt)) * K + rem];
-            v = csub(v, cscale(b, 0.5f * rw[q]));
+        for (int c0 = 0; c0 < nq; c0 += kGbChunk) {
+            const int cn = min(kGbChunk, nq - c0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < cn; t += kGbThreads) {
+                const int q = c0 + t;
+                int i;
+                float wq;
+                if (q < knn) { i = nbr[(size_t)j * knn + q]; wq = w[(size_t)j * knn + q]; }
+                else { i = rsrc[rb + q - knn]; wq = rw[rb + q - knn]; }
+                s_off[t] = (g.origin(i / g.cnt) * g.n + g.origin(i % g.cnt)) * K;
+                s_w[t] = 0.5f * wq;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int t = 0; t < cn; ++t) {
+                const float2* src = alpha + s_off[t];
+                const float wt = s_w[t];
+#pragma unroll
+                for (int u = 0; u < kGbElems; ++u) {
+                    if (off[u] >= 0) {
+                        const float2 b = src[off[u]];
+                        v[u].x -= wt * b.x;
+                        v[u].y -= wt * b.y;
+                    }
+                }
+            }
         }
-        if (QL) QL[(size_t)j * ne + e] = v;
-        if (trace) tr += (double)a.x * v.x + (double)a.y * v.y;
+#pragma unroll
+        for (int u = 0; u < kGbElems; ++u) {
+            if (off[u] < 0) continue;
+            const int e = e0 + threadIdx.x + u * kGbThreads;
+            if (QL) QL[(size_t)j * ne + e] = v[u];
+            if (trace) tr += (double)a[u].x * v[u].x + (double)a[u].y * v[u].y;
+        }
     }
     if (trace) {
         tr = block_sum(tr);
@@ -730,7 +774,7 @@ static mrf_status match_maps(mrf_recon_s* R, cudaStream_t s) {
 }
 
 static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s) {
-    k_graph_blocks<<<R->np, 128, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc, R->rw,
+    k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc, R->rw,
                                          R->deg, QL, trace);
     MRF_LAUNCHED_AS("k_graph_blocks", s);
     return MRF_OK;
