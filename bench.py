@@ -210,6 +210,8 @@ def algorithmic_work(kernel, inp):
     T, n, ns, K, G = w.frames, w.n, w.ns, w.rank, w.os * w.n
     M = inp["atoms"]
     frame_h1 = n * G * 8                          # one frame's half-oversampled intermediate
+    cnt = (n - w.patch) // w.stride + 1 + (1 if (n - w.patch) % w.stride else 0)
+    npatch = cnt * cnt
     ngroups = w.interleaves or T
     table = {
         # per-frame subspace expansion: coefficients (L2-resident, read once) + H1 write
@@ -226,6 +228,13 @@ def algorithmic_work(kernel, inp):
         "k_match_fp32": ("alu", 8.0 * n * n * M * K),
         # tensor-core matching (split BF16): real GEMM 2 x N x (2 M) x (3 x 2 K) issued
         "k_match_tc": ("tensor", 2.0 * n * n * (2 * M) * (3 * 2 * K)),
+        # exact patch kNN: FP16 GEMM of the np query vectors against 2 np candidate
+        # rows (h, l) over the 2 p^2 = 128 entries
+        "k_knn_tc": ("tensor", 2.0 * npatch * (2 * npatch) * (2 * w.patch ** 2)),
+        # SVT: each patch block read once and written once, V read and written
+        "k_svt": ("hbm", npatch * (2 * w.patch ** 2 * K * 8 + 2 * K * K * 8)),
+        # graph term: the coefficient image read once, Q(X) L written per patch
+        "k_graph_blocks": ("hbm", n * n * K * 8 + npatch * w.patch ** 2 * K * 8),
     }
     return table.get(kernel)
 
@@ -262,12 +271,67 @@ def time_variant(variant, inp, steps, warmup, dist):
     prof = mrf.profile_read()
     mrf.profile_enable(False)
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    # The timed region is far shorter than the sampler's 200 ms period: keep the
+    # same iteration running for a sustained window and sample clocks there too.
+    # (Untimed: it only checks the clocks the timed steps ran under.)
+    with Clocks(torch.cuda.current_device()) as clk2:
+        t0 = time.time()
+        while time.time() - t0 < 1.5:
+            for _ in range(20):
+                flush.zero_()
+                rec.iterate(1)
+            torch.cuda.synchronize()
+    clocks = merge_clocks(clk.summary(), clk2.summary(), 1e3 * (time.time() - t0))
     t1, t2, pd, _ = rec.maps()
     maps = [t.cpu().numpy() for t in (t1, t2, pd)]
     info = rec.info()
+    alpha = rec.alpha().clone()
     del rec
-    return dict(ms=ms, launches=launches, profile=prof, clocks=clk.summary(),
-                nrmse=nrmse(inp["truth"], maps), info=info, maps=maps)
+    return dict(ms=ms, launches=launches, profile=prof, clocks=clocks,
+                nrmse=nrmse(inp["truth"], maps), info=info, maps=maps, alpha=alpha)
+
+
+def merge_clocks(timed, sustained, sustained_ms):
+    """Clock record of the timed steps plus the sustained window that follows them."""
+    out = dict(sustained)
+    out["samples_timed_region"] = timed.get("samples", 0)
+    out["sm_mhz_timed_region"] = timed.get("sm_mhz")
+    out["reasons"] = sorted(set(timed.get("reasons", [])) | set(sustained.get("reasons", [])))
+    out["window"] = (f"median over a {sustained_ms:.0f} ms window of the same iteration loop run right after "
+                     f"the timed steps (the timed region itself is shorter than the 200 ms sampling period)")
+    return out
+
+
+def precision_variants(inp, alpha, reps=5):
+    """Match the final iterate with every matching precision: per-call device time,
+    index agreement and T1/T2/PD NRMSE against the FP32 exhaustive result."""
+    import numpy as np
+    import torch
+
+    import paper_2310_05647_gb300 as mrf
+    from paper_2310_05647_gb300.api import MATCH_BF16, MATCH_BF16X3, MATCH_FP8, MATCH_FP32
+
+    w = inp["w"]
+    x = alpha.reshape(w.n * w.n, w.rank).contiguous()
+    out, ref = {}, None
+    for name, prec in (("fp32", MATCH_FP32), ("bf16x3", MATCH_BF16X3), ("bf16", MATCH_BF16), ("fp8", MATCH_FP8)):
+        res = mrf.match(x, inp["comp"], inp["lut"], atom_norm2=inp["n2"], precision=prec)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(reps):
+            res = mrf.match(x, inp["comp"], inp["lut"], atom_norm2=inp["n2"], precision=prec)
+        ev[1].record()
+        torch.cuda.synchronize()
+        idx, pd, t1t2 = (t.cpu().numpy() for t in res)
+        maps = (t1t2[:, 0], t1t2[:, 1], pd)
+        if ref is None:
+            ref = (idx, maps)
+        err = {nm: float(np.linalg.norm(maps[i] - ref[1][i]) / max(np.linalg.norm(ref[1][i]), 1e-30))
+               for i, nm in enumerate(("t1", "t2", "pd"))}
+        out[name] = {"ms_per_match": ev[0].elapsed_time(ev[1]) / reps,
+                     "index_agreement_vs_fp32": float((idx == ref[0]).mean()), "nrmse_vs_fp32": err}
+    return out
 
 
 def e2e_chosen(inp, iters, reps=2):
@@ -473,6 +537,12 @@ def run_ours(args, dist):
         line["chosen_vs_plain_nrmse"] = {nm: float(np.sqrt(np.sum((b[i][mask] - a[i][mask]) ** 2) /
                                                            np.sum(a[i][mask] ** 2)))
                                          for i, nm in enumerate(("t1", "t2", "pd"))}
+    if "chosen" in res:
+        line["precision_variants"] = {
+            "what": "matching of the chosen run's final iterate (256^2 fingerprints x %d atoms, K = %d): device "
+                    "ms per mrf_match call, index agreement and map NRMSE vs FP32 exhaustive matching"
+                    % (inp["atoms"], w.rank),
+            **precision_variants(inp, res["chosen"]["alpha"])}
     if not args.no_e2e:
         sec, h2d, d2h = e2e_chosen(inp, w.iters)
         sec = dist.max(sec)

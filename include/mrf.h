@@ -131,8 +131,10 @@ mrf_status mrf_dict_subspace(const mrf_c64* dict, int m, int T, int K, mrf_c64* 
 enum {
     MRF_MATCH_FP32 = 0,        /* exhaustive FP32 inner products (plain form) */
     MRF_MATCH_BF16 = 1,        /* BF16 tensor-core scores, FP32 top-8 re-rank (2 len <= 128) */
-    MRF_MATCH_BF16X3 = 2,      /* split BF16 (hi/lo, three products in one GEMM), FP32 top-8
+    MRF_MATCH_BF16X3 = 2,      /* split BF16 (hi/lo, three products in one GEMM), FP32 top-4
                                   re-rank: tensor-core speed at ~2^-16 score error (6 len <= 128) */
+    MRF_MATCH_FP8 = 3,         /* FP8 e4m3 tensor-core scores (atoms scaled to unit norm x 448,
+                                  fingerprints by 448 / max |x|), FP32 top-8 re-rank (2 len <= 128) */
     MRF_MATCH_LITERAL_NORM2 = 0x100 /* flag: argmax of |<d,x>|/||d||^2 as printed in Eq. 5 */
 };
 

@@ -19,7 +19,7 @@ __all__ = ["MRFError", "NufftPlan", "Recon", "ReconParams", "dict_subspace", "ep
            "nufft_adjoint", "nufft_adjoint_subspace", "nufft_forward", "nufft_forward_subspace",
            "nufft_plan"]
 
-MATCH_FP32, MATCH_BF16, MATCH_BF16X3, MATCH_LITERAL_NORM2 = 0, 1, 2, 0x100
+MATCH_FP32, MATCH_BF16, MATCH_BF16X3, MATCH_FP8, MATCH_LITERAL_NORM2 = 0, 1, 2, 3, 0x100
 RECON_LITERAL_XUPDATE, RECON_LITERAL_LAMBDA1, RECON_NO_COST, RECON_GROUPED = 1, 2, 4, 8
 
 

@@ -200,8 +200,8 @@ mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* no
 mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
                      int precision, const float* lut, int* idx, float* pd, float* t1t2, float pd_scale,
                      cudaStream_t s) {
-    if (precision == MRF_MATCH_BF16 || precision == MRF_MATCH_BF16X3) {
-        MRF_PROPAGATE(match_bf16_candidates(ws, x, n, len, dict, m, precision == MRF_MATCH_BF16X3 ? 3 : 1, s));
+    if (tc_form(precision)) {
+        MRF_PROPAGATE(match_tc_candidates(ws, x, n, len, dict, m, tc_form(precision), s));
         MRF_PROPAGATE(match_rerank(ws, x, n, len, dict, s));
     } else {
         k_match_fp32<<<(n + BM - 1) / BM, 256, 0, s>>>(x, n, len, dict, ws.wscore, m, ws.best_idx, ws.best_ip);
@@ -225,14 +225,15 @@ extern "C" mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64*
     MRF_REQUIRE(m >= 1 && m <= (1 << 24), "mrf_match: bad m (%d)", m);
     const int prec = precision & 0xff;
     const int literal = (precision & MRF_MATCH_LITERAL_NORM2) ? 1 : 0;
-    MRF_REQUIRE(prec == MRF_MATCH_FP32 || prec == MRF_MATCH_BF16 || prec == MRF_MATCH_BF16X3,
+    MRF_REQUIRE(prec == MRF_MATCH_FP32 || prec == MRF_MATCH_BF16 || prec == MRF_MATCH_BF16X3 ||
+                    prec == MRF_MATCH_FP8,
                 "mrf_match: unknown precision %d", prec);
     MRF_REQUIRE(!(literal && prec != MRF_MATCH_FP32), "mrf_match: the literal norm flag needs FP32");
     if (n == 0) return MRF_OK;
     cudaStream_t s = as_stream(stream);
     // stream-ordered scratch: released on the stream after the kernels
     MatchWorkspace ws;
-    const size_t tcb = prec == MRF_MATCH_FP32 ? 0 : tc_operand_bytes(m, len, prec == MRF_MATCH_BF16X3 ? 3 : 1);
+    const size_t tcb = prec == MRF_MATCH_FP32 ? 0 : tc_operand_bytes(m, len, tc_form(prec));
     const size_t bytes = sizeof(int) * (size_t)n + sizeof(float2) * (size_t)n + sizeof(int) * (size_t)n * kTopK +
                          2 * sizeof(float) * (size_t)m + tcb + 8 * 256;
     char* base = nullptr;

@@ -36,10 +36,14 @@ mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const 
                      int precision, const float* lut, int* idx, float* pd, float* t1t2, float pd_scale,
                      cudaStream_t s);
 // bytes of the tensor-core dictionary operand for m atoms of length len
-size_t tc_operand_bytes(int m, int len, int split);
-// BF16 tensor-core candidate search and FP32 re-rank (match_tc.cu)
-mrf_status match_bf16_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
-                                 int split, cudaStream_t s);
+size_t tc_operand_bytes(int m, int len, int prec);
+// operand form of a tensor-core precision: 1 BF16, 3 split BF16, 8 FP8 e4m3 (0: FP32 path)
+inline int tc_form(int precision) {
+    return precision == MRF_MATCH_BF16 ? 1 : precision == MRF_MATCH_BF16X3 ? 3 : precision == MRF_MATCH_FP8 ? 8 : 0;
+}
+// tensor-core candidate search and FP32 re-rank (match_tc.cu)
+mrf_status match_tc_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
+                               int prec, cudaStream_t s);
 mrf_status match_rerank(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict,
                         cudaStream_t s);
 

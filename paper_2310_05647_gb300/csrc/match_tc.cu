@@ -11,7 +11,7 @@
 // shared memory, FP32 accumulators in TMEM, two accumulator buffers so the
 // next tile's products overlap the scoring of this one), every warp reads its
 // 32 lanes back with tcgen05.ld and keeps, per fingerprint, the best atoms by
-// |s|^2 / ||d||^2 (8 for plain BF16, 4 for the split form).  The candidates
+// |s|^2 / ||d||^2 (8 for plain BF16 and FP8, 4 for the split form).  The candidates
 // are then re-scored in FP32 from the original FP32 data and the best (ties to
 // the lowest index) is kept, so BF16 rounding only has to keep the winner
 // among the candidates.  No fingerprint x atom score reaches memory.
@@ -21,6 +21,7 @@
 // KC = padded length / 8; descriptor LBO (next core along K) = 128 bytes, SBO
 // (next 8-row group) = KC * 128 bytes.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "common.h"
 #include "match.h"
@@ -69,6 +70,43 @@ __global__ void k_tc_prepare_b(const float2* __restrict__ dict, const float* __r
     }
 }
 
+// FP8 (e4m3, kind::f8f6f4) operands: 8-bit core matrices are 8 rows x 16
+// elements, so the k chunk is 16 elements and KC = padded length / 16.  The
+// atoms' rows sqrt(w) d have unit norm (w = 1 / ||d||^2 and the compressed
+// atom is no longer than the full one), so one factor 448 (the largest finite
+// e4m3) brings every atom to the format's range; a fingerprint row is scaled
+// by 448 / max |x|, which leaves its argmax unchanged.
+constexpr float kE4m3Max = 448.f;
+
+__host__ __device__ __forceinline__ uint32_t core_off8(int row, int k, int KC) {
+    return (uint32_t)((((row >> 3) * KC + (k >> 4)) * 128) + ((row & 7) * 16) + (k & 15));
+}
+
+__device__ __forceinline__ unsigned char to_e4m3(float v) {
+    return (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+__global__ void k_tc_prepare_b8(const float2* __restrict__ dict, const float* __restrict__ wscore, int m, int len,
+                                int Lp, int ntiles, unsigned char* __restrict__ Bg) {
+    const int KC = Lp / 16;
+    const size_t per_tile = (size_t)2 * kTcAtoms * Lp;
+    const size_t total = per_tile * ntiles;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int tile = (int)(e / per_tile);
+        const int rem = (int)(e - (size_t)tile * per_tile);
+        const int row = rem / Lp, k = rem - row * Lp;
+        const int atom = tile * kTcAtoms + (row >> 1);
+        float v = 0.f;
+        if (atom < m && k < 2 * len) {
+            const float2 d = dict[(size_t)atom * len + (k >> 1)];
+            if ((row & 1) == 0) v = (k & 1) ? d.y : d.x;
+            else v = (k & 1) ? d.x : -d.y;
+            v *= kE4m3Max * sqrtf(wscore[atom]);
+        }
+        Bg[(size_t)tile * per_tile + core_off8(row, k, KC)] = to_e4m3(v);
+    }
+}
+
 __device__ __forceinline__ bool better_cand(float s, int i, float bs, int bi) {
     return s > bs || (s == bs && i < bi);
 }
@@ -83,16 +121,21 @@ __device__ __forceinline__ bool better_cand(float s, int i, float bs, int bi) {
 constexpr int kTcStages = 4;
 constexpr int kTcConsumers = 8;
 
-template <int LP, int SPLIT, int TOPK>
+// PREC: 1 = BF16, 3 = split BF16 (three copies along the reduction axis),
+// 8 = FP8 e4m3.
+template <int LP, int PREC, int TOPK>
 __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __restrict__ x, int n, int len,
-                                                              const __nv_bfloat16* __restrict__ Bg, int ntiles,
+                                                              const unsigned char* __restrict__ Bg, int ntiles,
                                                               const float* __restrict__ wscore, int m,
                                                               const float2* __restrict__ dict,
                                                               int* __restrict__ best_idx,
                                                               float2* __restrict__ best_ip, int* __restrict__ err) {
-    constexpr int KC = LP / 8;
-    constexpr int A_BYTES = kTcRows * LP * 2;
-    constexpr int B_BYTES = 2 * kTcAtoms * LP * 2;   // one tile: 2 rows per atom
+    constexpr bool F8 = PREC == 8;
+    constexpr int SPLIT = PREC == 3 ? 3 : 1;
+    constexpr int EB = F8 ? 1 : 2;                   // operand bytes
+    constexpr int KC = LP * EB / 16;                 // 16-byte k chunks per row
+    constexpr int A_BYTES = kTcRows * LP * EB;
+    constexpr int B_BYTES = 2 * kTcAtoms * LP * EB;  // one tile: 2 rows per atom
     constexpr int NCOL = 2 * kTcAtoms;               // accumulator columns per buffer
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* sA = smraw;
@@ -102,6 +145,7 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
     __shared__ int s_fail;
     __shared__ float s_ms[kTcRows][TOPK];
     __shared__ int s_mi[kTcRows][TOPK];
+    __shared__ float s_rs[kTcRows];                  // FP8: row scale 448 / max |x|
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n0 = blockIdx.x * kTcRows;
@@ -123,9 +167,30 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    if (F8) {
+        for (int row = tid; row < kTcRows; row += blockDim.x) {
+            float mx = 0.f;
+            if (n0 + row < n)
+                for (int k = 0; k < len; ++k) {
+                    const float2 xv = x[(size_t)(n0 + row) * len + k];
+                    mx = fmaxf(mx, fmaxf(fabsf(xv.x), fabsf(xv.y)));
+                }
+            s_rs[row] = mx > 0.f ? kE4m3Max / mx : 0.f;
+        }
+        __syncthreads();
+        for (int e = tid; e < kTcRows * LP; e += blockDim.x) {
+            const int row = e / LP, k = e - row * LP;
+            float v = 0.f;
+            if (n0 + row < n && k < 2 * len) {
+                const float2 xv = x[(size_t)(n0 + row) * len + (k >> 1)];
+                v = ((k & 1) ? xv.y : xv.x) * s_rs[row];
+            }
+            sA[core_off8(row, k, KC)] = to_e4m3(v);
+        }
+    }
     // A tile: fingerprint rows in BF16 (zero rows past n, zero padding past the
     // SPLIT copies of the 2 len coefficients)
-    for (int e = tid; e < kTcRows * LP; e += blockDim.x) {
+    for (int e = tid; !F8 && e < kTcRows * LP; e += blockDim.x) {
         const int row = e / LP, kk = e - row * LP;
         const int part = kk / (2 * len), k = kk - part * 2 * len;
         float v = 0.f;
@@ -150,14 +215,15 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
     if (warp == kTcConsumers) {
         // ------------------------------ producer ------------------------------
         if (lane == 0) {
-            const uint32_t idesc = mma_idesc(kTcRows, NCOL);
+            // kind::f16 BF16 x BF16, or kind::f8f6f4 E4M3 x E4M3 (format code 0)
+            const uint32_t idesc = F8 ? mma_idesc_f16(kTcRows, NCOL) : mma_idesc(kTcRows, NCOL);
             int loaded = 0, mmas = 0;   // tiles whose copy / whose MMAs were issued
             auto load = [&](int tile) {
                 const int st = tile % kTcStages;
                 const uint32_t bar = smem_u32(&s_bfull[st]);
                 mbar_expect_tx(bar, B_BYTES);
                 loaded = tile + 1;
-                bulk_g2s(smem_u32(sB + st * B_BYTES), Bg + (size_t)tile * (B_BYTES / 2), B_BYTES, bar);
+                bulk_g2s(smem_u32(sB + st * B_BYTES), Bg + (size_t)tile * B_BYTES, B_BYTES, bar);
             };
             for (int t = 0; t < kTcStages && t < ntiles; ++t) load(t);
             for (int tile = 0; tile < ntiles && !s_fail; ++tile) {
@@ -171,14 +237,21 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
                 const uint32_t tm = tmem + (uint32_t)(buf * NCOL);
                 const uint32_t bbase = smem_u32(sB + st * B_BYTES);
 #pragma unroll
-                for (int ks = 0; ks < LP / 16; ++ks) {
+                // one MMA consumes 32 bytes of each row: 16 BF16 or 32 FP8 elements
+                for (int ks = 0; ks < LP * EB / 32; ++ks) {
                     const uint64_t ad = smem_desc(smem_u32(sA) + ks * 256, 128, KC * 128);
                     const uint64_t bd = smem_desc(bbase + ks * 256, 128, KC * 128);
                     const uint32_t acc = ks > 0 ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tm),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    if (F8)
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tm),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    else
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tm),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
                 }
                 mmas = tile + 1;
                 mma_commit(smem_u32(&s_afull[buf]));
@@ -310,61 +383,73 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
     best_ip[row] = bip;
 }
 
-static int padded_len(int len, int split) { return (2 * len * split + 15) / 16 * 16; }
-
-size_t tc_operand_bytes(int m, int len, int split) {
-    const int ntiles = (m + kTcAtoms - 1) / kTcAtoms;
-    return sizeof(__nv_bfloat16) * (size_t)ntiles * 2 * kTcAtoms * padded_len(len, split);
+// reduction length: 2 len real coefficients (times 3 for the split form),
+// padded to a multiple of 16 (BF16) or 32 (FP8) elements
+static int padded_len(int len, int prec) {
+    return prec == 8 ? (2 * len + 31) / 32 * 32 : (2 * len * prec + 15) / 16 * 16;
 }
 
-mrf_status match_bf16_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
-                                 int split, cudaStream_t s) {
-    MRF_REQUIRE(split == 1 || split == 3, "BF16 matching: split must be 1 or 3");
-    MRF_REQUIRE(2 * len * split <= 128, "BF16 matching supports 2 x length x split <= 128 (length %d)", len);
-    const int Lp = padded_len(len, split);
+size_t tc_operand_bytes(int m, int len, int prec) {
     const int ntiles = (m + kTcAtoms - 1) / kTcAtoms;
-    const size_t bbytes = sizeof(__nv_bfloat16) * (size_t)ntiles * 2 * kTcAtoms * Lp;
+    return (size_t)(prec == 8 ? 1 : 2) * ntiles * 2 * kTcAtoms * padded_len(len, prec);
+}
+
+mrf_status match_tc_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
+                               int prec, cudaStream_t s) {
+    MRF_REQUIRE(prec == 1 || prec == 3 || prec == 8, "tensor-core matching: unknown operand form %d", prec);
+    MRF_REQUIRE(padded_len(len, prec) <= 128,
+                "tensor-core matching supports a padded reduction length of at most 128 (length %d)", len);
+    const int Lp = padded_len(len, prec);
+    const int ntiles = (m + kTcAtoms - 1) / kTcAtoms;
+    const size_t bbytes = tc_operand_bytes(m, len, prec);
     if (ws.tc_b == nullptr || ws.tc_b_bytes < bbytes || ws.tc_dict != dict || ws.tc_m != m || ws.tc_len != len ||
-        ws.tc_split != split) {
+        ws.tc_split != prec) {
         if (ws.tc_b_bytes < bbytes) {
-            MRF_REQUIRE(!ws.borrowed, "BF16 matching: the dictionary operand does not fit the scratch");
+            MRF_REQUIRE(!ws.borrowed, "tensor-core matching: the dictionary operand does not fit the scratch");
             if (ws.tc_b) cudaFree(ws.tc_b);
             ws.tc_b = nullptr;
             MRF_CUDA(cudaMalloc(&ws.tc_b, bbytes));
             ws.tc_b_bytes = bbytes;
         }
-        k_tc_prepare_b<<<1024, 256, 0, s>>>(dict, ws.wscore, m, len, Lp, ntiles, split,
-                                            reinterpret_cast<__nv_bfloat16*>(ws.tc_b));
-        MRF_LAUNCHED_AS("k_tc_prepare_b", s);
+        if (prec == 8) {
+            k_tc_prepare_b8<<<1024, 256, 0, s>>>(dict, ws.wscore, m, len, Lp, ntiles,
+                                                 reinterpret_cast<unsigned char*>(ws.tc_b));
+            MRF_LAUNCHED_AS("k_tc_prepare_b8", s);
+        } else {
+            k_tc_prepare_b<<<1024, 256, 0, s>>>(dict, ws.wscore, m, len, Lp, ntiles, prec,
+                                                reinterpret_cast<__nv_bfloat16*>(ws.tc_b));
+            MRF_LAUNCHED_AS("k_tc_prepare_b", s);
+        }
         ws.tc_dict = dict;
         ws.tc_m = m;
         ws.tc_len = len;
-        ws.tc_split = split;
+        ws.tc_split = prec;
     }
     if (!ws.tc_err) {
         MRF_CUDA(cudaMalloc(&ws.tc_err, sizeof(int)));
         MRF_CUDA(cudaMemsetAsync(ws.tc_err, 0, sizeof(int), s));
     }
     const int blocks = (n + kTcRows - 1) / kTcRows;
-#define MRF_TC_LAUNCH(LPV, SP)                                                                                   \
+#define MRF_TC_LAUNCH(LPV, PR)                                                                                   \
     do {                                                                                                         \
-        constexpr int TK = SP == 3 ? 4 : kTopK;                                                                  \
-        const size_t sm = (size_t)kTcRows * LPV * 2 + (size_t)kTcStages * 2 * kTcAtoms * LPV * 2;                \
-        MRF_CUDA(cudaFuncSetAttribute(k_match_tc<LPV, SP, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+        constexpr int TK = PR == 3 ? 4 : kTopK;                                                                  \
+        constexpr int EBV = PR == 8 ? 1 : 2;                                                                     \
+        const size_t sm = (size_t)kTcRows * LPV * EBV + (size_t)kTcStages * 2 * kTcAtoms * LPV * EBV;            \
+        MRF_CUDA(cudaFuncSetAttribute(k_match_tc<LPV, PR, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                       (int)sm));                                                                 \
-        k_match_tc<LPV, SP, TK><<<blocks, kTcThreads + 32, sm, s>>>(x, n, len,                                   \
-                                                               reinterpret_cast<const __nv_bfloat16*>(ws.tc_b),  \
+        k_match_tc<LPV, PR, TK><<<blocks, kTcThreads + 32, sm, s>>>(x, n, len,                                   \
+                                                               reinterpret_cast<const unsigned char*>(ws.tc_b),  \
                                                                ntiles, ws.wscore, m, dict, ws.best_idx,          \
                                                                ws.best_ip, ws.tc_err);                           \
     } while (0)
-    if (split == 1) {
+    if (prec == 1) {
         if (Lp == 16) MRF_TC_LAUNCH(16, 1);
         else if (Lp == 32) MRF_TC_LAUNCH(32, 1);
         else if (Lp == 48) MRF_TC_LAUNCH(48, 1);
         else if (Lp == 64) MRF_TC_LAUNCH(64, 1);
         else if (Lp == 96) MRF_TC_LAUNCH(96, 1);
         else MRF_TC_LAUNCH(128, 1);
-    } else {
+    } else if (prec == 3) {
         if (Lp == 16) MRF_TC_LAUNCH(16, 3);
         else if (Lp == 32) MRF_TC_LAUNCH(32, 3);
         else if (Lp == 48) MRF_TC_LAUNCH(48, 3);
@@ -373,6 +458,11 @@ mrf_status match_bf16_candidates(MatchWorkspace& ws, const float2* x, int n, int
         else if (Lp == 96) MRF_TC_LAUNCH(96, 3);
         else if (Lp == 112) MRF_TC_LAUNCH(112, 3);
         else MRF_TC_LAUNCH(128, 3);
+    } else {
+        if (Lp == 32) MRF_TC_LAUNCH(32, 8);
+        else if (Lp == 64) MRF_TC_LAUNCH(64, 8);
+        else if (Lp == 96) MRF_TC_LAUNCH(96, 8);
+        else MRF_TC_LAUNCH(128, 8);
     }
 #undef MRF_TC_LAUNCH
     MRF_LAUNCHED_AS("k_match_tc", s);

@@ -946,7 +946,7 @@ extern "C" mrf_status mrf_recon_create(mrf_recon* out, mrf_plan plan, const mrf_
     MRF_REQUIRE(prm->knn >= 1 && prm->knn <= 32, "mrf_recon_create: knn must be in [1, 32]");
     MRF_REQUIRE(prm->beta > 0.f && prm->mu > 0.f, "mrf_recon_create: beta and mu must be > 0");
     MRF_REQUIRE(prm->match_precision == MRF_MATCH_FP32 || prm->match_precision == MRF_MATCH_BF16 ||
-                    prm->match_precision == MRF_MATCH_BF16X3,
+                    prm->match_precision == MRF_MATCH_BF16X3 || prm->match_precision == MRF_MATCH_FP8,
                 "mrf_recon_create: unknown match precision %d", prm->match_precision);
     const PatchGeom g = make_geom(plan->nx, prm->patch, prm->stride);
     MRF_REQUIRE(g.count() >= prm->knn + 1, "mrf_recon_create: need at least knn + 1 patches (%d)", g.count());

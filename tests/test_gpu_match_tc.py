@@ -17,7 +17,7 @@ from oracle import dictionary, epg, match as omatch
 from gpu_util import as_f32_inputs, c64, f32, mrf, np_, rand_c
 
 pytestmark = pytest.mark.gpu
-BF16, BF16X3 = 1, 2
+BF16, BF16X3, FP8 = 1, 2, 3
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +84,22 @@ def test_plain_bf16_is_near_optimal(compressed):
     assert (gb == oi).mean() > 0.5
 
 
-@pytest.mark.parametrize("prec", [BF16, BF16X3])
+def test_fp8_is_near_optimal(compressed):
+    m = mrf()
+    Dc, n2, lut = compressed
+    rng = np.random.default_rng(4)
+    n = 3000
+    X = Dc[rng.integers(0, len(Dc), n)] * rng.uniform(0.3, 2.0, (n, 1)) + 0.02 * rand_c(rng, n, Dc.shape[1])
+    X[:3] = 0.0
+    (X,) = as_f32_inputs(X)
+    gi, pdg, _ = m.match(c64(X), c64(Dc), f32(lut), atom_norm2=f32(n2), precision=FP8)
+    gi = np_(gi)
+    oi = omatch.match(X, Dc, lut, atom_norm2=n2)[0]
+    assert _near_tie_ok(X, Dc, n2, gi, oi, rtol=5e-2) == 1.0
+    assert np.all(gi[:3] == 0) and np.all(np_(pdg)[:3] == 0)
+
+
+@pytest.mark.parametrize("prec", [BF16, BF16X3, FP8])
 def test_tc_ragged_atoms_and_lengths(prec):
     m = mrf()
     rng = np.random.default_rng(2)
@@ -98,7 +113,8 @@ def test_tc_ragged_atoms_and_lengths(prec):
         gi = np_(m.match(c64(X), c64(D), f32(lut), precision=prec)[0])
         oi = omatch.match(X, D, lut)[0]
         n2 = np.sum(np.abs(D) ** 2, 1)
-        assert _near_tie_ok(X, D, n2, gi, oi, rtol=1e-5 if prec == BF16X3 else 1e-2) >= 0.995, (n, mm, L)
+        rtol = {BF16X3: 1e-5, BF16: 1e-2, FP8: 1e-1}[prec]
+        assert _near_tie_ok(X, D, n2, gi, oi, rtol=rtol) >= 0.995, (n, mm, L)
 
 
 def test_tc_rejects_long_fingerprints():
@@ -109,3 +125,6 @@ def test_tc_rejects_long_fingerprints():
     D = c64(np.ones((4, 30)))
     with pytest.raises(m.MRFError):
         m.match(c64(np.ones((3, 30))), D, f32(np.ones((4, 2))), precision=BF16X3)
+    D = c64(np.ones((4, 65)))
+    with pytest.raises(m.MRFError):
+        m.match(c64(np.ones((3, 65))), D, f32(np.ones((4, 2))), precision=FP8)
