@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default="plain,chosen")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched-serving measurement")
     ap.add_argument("--workload", default=WORKLOAD, choices=["mrf256_t1000", "mrf256_t100"],
                     help="mrf256_t100: the same image with 100 frames, for small profiling captures")
     return ap.parse_args()
@@ -334,6 +335,90 @@ def precision_variants(inp, alpha, reps=5):
     return out
 
 
+def serving(seed=0, slices=16, iters=10, rounds=10):
+    """Batched serving: `slices` slices of uneven size (grid 128^2 or 256^2, T in
+    {500, 750, 1000}, 1-3 spiral arms per frame, seeded draws) sharing one atom
+    grid, each compressed in its own frame count's subspace.  Throughput and
+    request latency of the batched loop (one CUDA graph launch per iteration
+    of all slices) against the same slices iterated one after another."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2310_05647_gb300 as mrf
+    from paper_2310_05647_gb300.api import MATCH_BF16X3, RECON_GROUPED, RECON_NO_COST
+
+    w = synth.WORKLOADS[WORKLOAD]
+    rng = np.random.default_rng(1000 + seed)
+    dev = torch.device("cuda")
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    fa, tr = synth.fisp_train(1000, seed=w.tr_seed)
+    lut = synth.workload_grid(w)
+    lut_d = f32(lut)
+    D = mrf.epg_fisp(lut_d, f32(fa), f32(tr))
+    comp = {}
+    for T in (500, 750, 1000):
+        comp[T] = mrf.dict_subspace(D[:, :T].contiguous(), w.rank)
+    del D
+    cfg, recons, keep = [], [], []
+    for i in range(slices):
+        n = int(rng.choice([128, 256]))
+        T = int(rng.choice([500, 750, 1000]))
+        per = int(rng.integers(1, 4))
+        cfg.append({"n": n, "frames": T, "arms_per_frame": per})
+        t1, t2, pd, mask, label = synth.phantom(n, seed=100 + i)
+        pairs = np.stack([np.maximum(t1.ravel(), 1.0), np.maximum(t2.ravel(), 1.0)], -1)
+        S = mrf.epg_fisp(f32(pairs), f32(fa[:T]), f32(tr[:T]))
+        X = (S * f32((pd * mask).ravel()).to(torch.complex64)[:, None]).T.contiguous().view(T, n, n)
+        del S
+        plan = mrf.nufft_plan(n, n, f32(synth.spiral_trajectory(n, T, w.ns, w.interleaves, per_frame=per)))
+        b = mrf.nufft_forward(plan, X)
+        del X
+        sig = math.sqrt(float((b.abs() ** 2).mean()) * 10 ** (-w.snr_db / 10))
+        g = torch.Generator(device=dev)
+        g.manual_seed(2000 + i)
+        b = (b + torch.complex(torch.randn(b.shape, generator=g, device=dev),
+                               torch.randn(b.shape, generator=g, device=dev)) * (sig / math.sqrt(2.0))).contiguous()
+        phi, cmp_, n2 = comp[T]
+        p = mrf.ReconParams(patch=w.patch, stride=w.stride, knn=w.knn, flags=RECON_GROUPED | RECON_NO_COST,
+                            match_precision=MATCH_BF16X3)
+        recons.append(mrf.Recon(plan, p, phi, cmp_, n2, lut_d, b))
+        keep.append((plan, b))
+    torch.cuda.synchronize()
+    # unbatched: every slice's iterations issued one slice after another
+    for r in recons:
+        r.iterate(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in recons:
+        r.iterate(iters)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    batch = mrf.Batch(recons)
+    l0 = mrf.launch_count()
+    batch.iterate(2)                      # one eager iteration + the captured one
+    per_iter_kernels = (mrf.launch_count() - l0) // 2
+    lat = []
+    for _ in range(rounds):
+        t0 = time.perf_counter()
+        batch.iterate(iters)              # synchronises
+        lat.append(time.perf_counter() - t0)
+    tuning = [r.plan.gather_tuning() for r in recons]
+    maps_ok = all(bool(torch.isfinite(r.maps()[0]).all()) for r in recons)
+    del batch
+    tot = sum(lat)
+    return {"what": f"{slices} slices, {iters} iterations per request; grids from {{128^2, 256^2}} (192^2 needs a "
+                    f"non-power-of-two FFT, not built), T from {{500, 750, 1000}}, 1-3 arms of {w.ns} samples per "
+                    f"frame, shared {len(lut)}-atom grid, split-BF16 matching, no cost terms",
+            "slices": cfg,
+            "throughput_slice_iters_per_s": slices * iters * rounds / tot,
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+                           "rounds": rounds},
+            "unbatched_slice_iters_per_s": slices * iters / seq_s,
+            "kernels_per_batched_iteration": per_iter_kernels,
+            "gather_tuning_run_threads": tuning, "maps_finite": maps_ok}
+
+
 def e2e_chosen(inp, iters, reps=2):
     """End to end through the public API: pinned host k-space in, host maps out."""
     import torch
@@ -543,6 +628,8 @@ def run_ours(args, dist):
                     "ms per mrf_match call, index agreement and map NRMSE vs FP32 exhaustive matching"
                     % (inp["atoms"], w.rank),
             **precision_variants(inp, res["chosen"]["alpha"])}
+    if not args.no_serving and dist.world == 1:
+        line["serving"] = serving(seed=dist.rank)
     if not args.no_e2e:
         sec, h2d, d2h = e2e_chosen(inp, w.iters)
         sec = dist.max(sec)

@@ -45,6 +45,7 @@ typedef struct { float re, im; } mrf_c64;
 typedef void* mrf_stream;                 /* cudaStream_t */
 typedef struct mrf_plan_s* mrf_plan;       /* NUFFT plan (opaque) */
 typedef struct mrf_recon_s* mrf_recon;     /* Algorithm 1 state (opaque) */
+typedef struct mrf_batch_s* mrf_batch;     /* batch of slices advanced together (opaque) */
 
 /* Last error message of the calling thread ("" if none). */
 const char* mrf_last_error(void);
@@ -70,6 +71,11 @@ int mrf_abi_version(void);
 mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int nframes, int ns,
                           const float* traj, int os, int kb_width, mrf_stream stream);
 mrf_status mrf_nufft_destroy(mrf_plan plan);
+
+/* Tile shape the spread autotuner chose for the grouped adjoint's gather
+ * kernel (entries reduced per thread, threads per block), timed on this
+ * plan's own table on its first grouped adjoint; 0, 0 before that call. */
+mrf_status mrf_nufft_gather_tuning(mrf_plan plan, int* run, int* threads);
 
 /* y = A x over all frames.  x: dev [nframes][ny][nx] mrf_c64;
  * y: dev [nframes][ns] mrf_c64 (overwritten). */
@@ -241,6 +247,36 @@ mrf_status mrf_recon_alpha(mrf_recon r, mrf_c64* alpha, mrf_stream stream);
 mrf_status mrf_recon_info(mrf_recon r, double* a_norm, double* x_scale, double* lam1,
                           double* sigma2, mrf_stream stream);
 mrf_status mrf_recon_destroy(mrf_recon r);
+
+/* ------------------------------------------------------------------------
+ * Batched serving (not in the paper: a deployment form of Algorithm 1).
+ * A batch advances count independent slices together: each slice is an
+ * mrf_recon with its own NUFFT plan (sizes, frames and trajectories may
+ * differ) and the same atom count m, rank K and match precision (slices with
+ * different frame counts carry the dictionary compressed in their own
+ * subspace).  Per iteration the slices' operator,
+ * graph, X-update and SVT steps run concurrently on one stream each, the
+ * matching of every slice's fingerprints is one tensor-core launch (FP32
+ * precision: one launch per slice), then the slices rebuild their graphs
+ * concurrently.  Costs are not computed in batch mode.
+ * ---------------------------------------------------------------------- */
+/* recons: host array of count handles (1 <= count <= 64), owned by the
+ * caller; destroy the batch before any of them.  Synchronises `stream`. */
+mrf_status mrf_batch_create(mrf_batch* out, const mrf_recon* recons, int count, mrf_stream stream);
+/* n_iters iterations of every slice.  The first call runs one iteration
+ * directly and captures the next into a CUDA graph (so it must not be made
+ * inside a stream capture); every later iteration is one graph launch.  The
+ * call synchronises `stream` and returns MRF_ETIMEOUT when a bounded device
+ * wait gave up (the results are then not valid) and MRF_EINVAL when a patch
+ * feature left its fixed-point range.  Maps: mrf_recon_maps per slice. */
+mrf_status mrf_batch_iter(mrf_batch b, int n_iters, mrf_stream stream);
+mrf_status mrf_batch_destroy(mrf_batch b);
+
+/* Self-test of the bounded device wait used by the tensor-core kernels: one
+ * thread polls an mbarrier phase that nothing completes, gives up after
+ * `polls` polls (1 <= polls <= 65536) and raises the error word; the call
+ * returns MRF_ETIMEOUT with a message, and the context stays usable. */
+mrf_status mrf_wait_selftest(int polls, mrf_stream stream);
 
 /* ------------------------------------------------------------------------
  * Tracing.  Not part of the method: launch accounting and per-kernel timing

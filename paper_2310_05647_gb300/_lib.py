@@ -39,7 +39,12 @@ SIGNATURES = {
     "mrf_dict_subspace": (i32, [vp, i32, i32, i32, vp, vp, vp, vp]),
     "mrf_match": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp, vp]),
     "mrf_match_noalloc": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp, vp]),
+    "mrf_nufft_gather_tuning": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
     "mrf_patch_knn": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),
+    "mrf_batch_create": (i32, [C.POINTER(vp), C.POINTER(vp), i32, vp]),
+    "mrf_batch_iter": (i32, [vp, i32, vp]),
+    "mrf_batch_destroy": (i32, [vp]),
+    "mrf_wait_selftest": (i32, [i32, vp]),
     "mrf_recon_create": (i32, [C.POINTER(vp), vp, C.POINTER(ReconParams), vp, i32, vp, vp, vp, i32, vp, vp]),
     "mrf_recon_iter": (i32, [vp, i32, f64p, vp]),
     "mrf_recon_maps": (i32, [vp, vp, vp, vp, vp, vp]),

@@ -61,6 +61,12 @@ class NufftPlan:
         _lib.call("mrf_nufft_plan", C.byref(h), nx, ny, self.T, self.ns, _ptr(traj), os, kb_width, _stream())
         self.handle = h
 
+    def gather_tuning(self):
+        """(entries per thread, threads per block) the spread autotuner chose; (0, 0) before tuning."""
+        run, thr = C.c_int(0), C.c_int(0)
+        _lib.call("mrf_nufft_gather_tuning", self.handle, C.byref(run), C.byref(thr))
+        return run.value, thr.value
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:
@@ -245,6 +251,39 @@ class Recon:
             except Exception:
                 pass
             self.handle = None
+
+
+class Batch:
+    """Owner of an mrf_batch: slices (Recon objects with their own plans and one
+    shared dictionary) advanced together; every iteration after the first is
+    one CUDA graph launch.  Keeps the Recon objects alive."""
+
+    def __init__(self, recons):
+        recons = list(recons)
+        if not recons:
+            raise ValueError("a batch needs at least one slice")
+        self.recons = recons
+        arr = (C.c_void_p * len(recons))(*[r.handle.value for r in recons])
+        h = C.c_void_p()
+        _lib.call("mrf_batch_create", C.byref(h), arr, len(recons), _stream())
+        self.handle = h
+
+    def iterate(self, n=1):
+        _lib.call("mrf_batch_iter", self.handle, int(n), _stream())
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.call("mrf_batch_destroy", h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def wait_selftest(polls=1000):
+    """Run the bounded-wait self-test; raises MRFError (status MRF_ETIMEOUT) as designed."""
+    _lib.call("mrf_wait_selftest", int(polls), _stream())
 
 
 # ---------------------------------------------------------------------------

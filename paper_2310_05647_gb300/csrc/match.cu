@@ -207,6 +207,11 @@ mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const 
         k_match_fp32<<<(n + BM - 1) / BM, 256, 0, s>>>(x, n, len, dict, ws.wscore, m, ws.best_idx, ws.best_ip);
         MRF_LAUNCHED_AS("k_match_fp32", s);
     }
+    return match_finish(ws, n, lut, idx, pd, t1t2, pd_scale, s);
+}
+
+mrf_status match_finish(MatchWorkspace& ws, int n, const float* lut, int* idx, float* pd, float* t1t2,
+                        float pd_scale, cudaStream_t s) {
     k_match_finish<<<(n + 255) / 256, 256, 0, s>>>(ws.best_idx, ws.best_ip, n, ws.norm2, lut, idx, pd, t1t2,
                                                    pd_scale);
     MRF_LAUNCHED_AS("k_match_finish", s);

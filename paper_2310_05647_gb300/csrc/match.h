@@ -41,6 +41,29 @@ size_t tc_operand_bytes(int m, int len, int prec);
 inline int tc_form(int precision) {
     return precision == MRF_MATCH_BF16 ? 1 : precision == MRF_MATCH_BF16X3 ? 3 : precision == MRF_MATCH_FP8 ? 8 : 0;
 }
+// one slice of a batched tensor-core matching launch: fingerprint blocks
+// block0 .. block0 + ceil(n / 128) - 1 of the launch belong to this slice,
+// matched against the slice's own dictionary operand (same m, length and
+// precision for every slice of a launch)
+struct TcSlice {
+    const float2* x;
+    int n;
+    int block0;
+    int* best_idx;
+    float2* best_ip;
+    const unsigned char* Bg;     // tensor-core operand of the slice's dictionary
+    const float* wscore;         // score weights
+    const float2* dict;          // FP32 dictionary (re-rank)
+};
+// build (or reuse) the tensor-core operand of dict in ws
+mrf_status tc_prepare_operand(MatchWorkspace& ws, const float2* dict, int m, int len, int prec, cudaStream_t s);
+// winners of every slice of a batch in one launch; every slice's operand must
+// have been prepared (tc_prepare_operand); ws supplies the error word
+mrf_status match_tc_batch(MatchWorkspace& ws, const TcSlice* d_slices, int nslices, int total_blocks, int len,
+                          int m, int prec, cudaStream_t s);
+// idx / pd / t1t2 of n fingerprints from ws.best_idx / ws.best_ip
+mrf_status match_finish(MatchWorkspace& ws, int n, const float* lut, int* idx, float* pd, float* t1t2,
+                        float pd_scale, cudaStream_t s);
 // tensor-core candidate search and FP32 re-rank (match_tc.cu)
 mrf_status match_tc_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
                                int prec, cudaStream_t s);

@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
                                                               const float* __restrict__ wscore, int m,
                                                               const float2* __restrict__ dict,
                                                               int* __restrict__ best_idx,
-                                                              float2* __restrict__ best_ip, int* __restrict__ err) {
+                                                              float2* __restrict__ best_ip, int* __restrict__ err,
+                                                              const TcSlice* __restrict__ slices, int nslices) {
     constexpr bool F8 = PREC == 8;
     constexpr int SPLIT = PREC == 3 ? 3 : 1;
     constexpr int EB = F8 ? 1 : 2;                   // operand bytes
@@ -148,7 +149,21 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
     __shared__ float s_rs[kTcRows];                  // FP8: row scale 448 / max |x|
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n0 = blockIdx.x * kTcRows;
+    int n0 = blockIdx.x * kTcRows;
+    if (nslices > 0) {
+        // batched launch: the block's slice is the last one starting at or before it
+        int si = 0;
+        for (int q = 1; q < nslices; ++q)
+            if (slices[q].block0 <= (int)blockIdx.x) si = q;
+        x = slices[si].x;
+        n = slices[si].n;
+        best_idx = slices[si].best_idx;
+        best_ip = slices[si].best_ip;
+        Bg = slices[si].Bg;
+        wscore = slices[si].wscore;
+        dict = slices[si].dict;
+        n0 = ((int)blockIdx.x - slices[si].block0) * kTcRows;
+    }
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -394,8 +409,23 @@ size_t tc_operand_bytes(int m, int len, int prec) {
     return (size_t)(prec == 8 ? 1 : 2) * ntiles * 2 * kTcAtoms * padded_len(len, prec);
 }
 
+static mrf_status tc_launch(MatchWorkspace& ws, const float2* x, int n, int blocks, const TcSlice* slices,
+                            int nslices, int len, const float2* dict, int m, int prec, cudaStream_t s);
+
 mrf_status match_tc_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
                                int prec, cudaStream_t s) {
+    return tc_launch(ws, x, n, (n + kTcRows - 1) / kTcRows, nullptr, 0, len, dict, m, prec, s);
+}
+
+mrf_status match_tc_batch(MatchWorkspace& ws, const TcSlice* d_slices, int nslices, int total_blocks, int len,
+                          int m, int prec, cudaStream_t s) {
+    MRF_REQUIRE(d_slices && nslices >= 1, "batched matching: empty slice table");
+    MRF_REQUIRE(ws.tc_b && ws.tc_m == m && ws.tc_len == len && ws.tc_split == prec,
+                "batched matching: the operands were not prepared");
+    return tc_launch(ws, nullptr, 0, total_blocks, d_slices, nslices, len, nullptr, m, prec, s);
+}
+
+mrf_status tc_prepare_operand(MatchWorkspace& ws, const float2* dict, int m, int len, int prec, cudaStream_t s) {
     MRF_REQUIRE(prec == 1 || prec == 3 || prec == 8, "tensor-core matching: unknown operand form %d", prec);
     MRF_REQUIRE(padded_len(len, prec) <= 128,
                 "tensor-core matching supports a padded reduction length of at most 128 (length %d)", len);
@@ -429,7 +459,15 @@ mrf_status match_tc_candidates(MatchWorkspace& ws, const float2* x, int n, int l
         MRF_CUDA(cudaMalloc(&ws.tc_err, sizeof(int)));
         MRF_CUDA(cudaMemsetAsync(ws.tc_err, 0, sizeof(int), s));
     }
-    const int blocks = (n + kTcRows - 1) / kTcRows;
+    return MRF_OK;
+}
+
+static mrf_status tc_launch(MatchWorkspace& ws, const float2* x, int n, int blocks, const TcSlice* slices,
+                            int nslices, int len, const float2* dict, int m, int prec, cudaStream_t s) {
+    if (!slices) MRF_PROPAGATE(tc_prepare_operand(ws, dict, m, len, prec, s));
+    const int Lp = padded_len(len, prec);
+    const int ntiles = (m + kTcAtoms - 1) / kTcAtoms;
+    if (blocks == 0) return MRF_OK;
 #define MRF_TC_LAUNCH(LPV, PR)                                                                                   \
     do {                                                                                                         \
         constexpr int TK = PR == 3 ? 4 : kTopK;                                                                  \
@@ -440,7 +478,7 @@ mrf_status match_tc_candidates(MatchWorkspace& ws, const float2* x, int n, int l
         k_match_tc<LPV, PR, TK><<<blocks, kTcThreads + 32, sm, s>>>(x, n, len,                                   \
                                                                reinterpret_cast<const unsigned char*>(ws.tc_b),  \
                                                                ntiles, ws.wscore, m, dict, ws.best_idx,          \
-                                                               ws.best_ip, ws.tc_err);                           \
+                                                               ws.best_ip, ws.tc_err, slices, nslices);          \
     } while (0)
     if (prec == 1) {
         if (Lp == 16) MRF_TC_LAUNCH(16, 1);
@@ -474,3 +512,40 @@ mrf_status match_rerank(MatchWorkspace&, const float2*, int, int, const float2*,
 }
 
 }  // namespace mrf
+
+namespace mrf {
+
+// One thread polls phase 0 of an mbarrier that nothing arrives on: the wait
+// gives up after `limit` polls and raises the error word, like every bounded
+// wait of the tensor-core kernels.
+__global__ void k_wait_selftest(unsigned limit, int* __restrict__ err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !wait_parity(smem_u32(&bar), 0, limit)) atomicExch(err, 2);
+}
+
+}  // namespace mrf
+
+extern "C" mrf_status mrf_wait_selftest(int polls, mrf_stream stream) {
+    using namespace mrf;
+    MRF_REQUIRE(polls >= 1 && polls <= 65536, "mrf_wait_selftest: polls must be in [1, 65536]");
+    cudaStream_t s = as_stream(stream);
+    int* err = nullptr;
+    MRF_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&err), sizeof(int), s));
+    MRF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    k_wait_selftest<<<1, 32, 0, s>>>((unsigned)polls, err);
+    MRF_LAUNCHED_AS("k_wait_selftest", s);
+    int h = 0;
+    MRF_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRF_CUDA(cudaFreeAsync(err, s));
+    MRF_CUDA(cudaStreamSynchronize(s));
+    if (h == 2) {
+        set_error("mrf_wait_selftest: the device wait gave up after %d polls", polls);
+        return MRF_ETIMEOUT;
+    }
+    return MRF_OK;
+}

@@ -281,19 +281,19 @@ __global__ void __launch_bounds__(kColThreads) k_spread_cols(const float2* __res
 // Grouped adjoint stage 1 without same-address contention: the contributions
 // of every group sample to the oversampled grid are precomputed as
 // (grid point, sample, weight) entries sorted by point.  Each thread reduces
-// a run of 32 consecutive entries for all K coefficient grids at once and adds
-// a partial sum to the grid only where the point changes, so the k-space
+// a run of RUN consecutive entries for all K coefficient grids at once and
+// adds a partial sum to the grid only where the point changes, so the k-space
 // centre (where every interleaf overlaps) costs a few adds instead of
 // thousands of same-address atomics.  R: [ngroups * ns][K]; grid: [K][G][G]
-// (zeroed by the caller).
-constexpr int kGatherRun = 32;
-
+// (zeroed by the caller).  The run length and block size are tuned per plan
+// (tune_gather): longer runs mean fewer atomics, shorter runs more parallelism.
+template <int RUN>
 __global__ void k_gather_grid(const float2* __restrict__ R, int K, const int* __restrict__ pt,
                               const int* __restrict__ smp, const float* __restrict__ w, int nent, int GG2,
                               float2* __restrict__ grid) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) * kGatherRun;
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) * RUN;
     if (b >= nent) return;
-    const int e = min(nent, b + kGatherRun);
+    const int e = min(nent, b + RUN);
     float2 acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -700,6 +700,65 @@ static mrf_status build_gather(mrf_plan_s* p, cudaStream_t s) {
     return MRF_OK;
 }
 
+static mrf_status launch_gather(const mrf_plan_s* p, int run, int threads, int K, cudaStream_t s) {
+    const int runs = (p->gat_n + run - 1) / run;
+    const unsigned blocks = (unsigned)((runs + threads - 1) / threads);
+    const int GG2 = p->gy * p->gx;
+#define MRF_GATHER(RV) \
+    k_gather_grid<RV><<<blocks, threads, 0, s>>>(p->sub_R, K, p->gat_pt, p->gat_smp, p->gat_w, p->gat_n, GG2, p->sub_spec)
+    switch (run) {
+        case 8: MRF_GATHER(8); break;
+        case 16: MRF_GATHER(16); break;
+        case 64: MRF_GATHER(64); break;
+        default: MRF_GATHER(32); break;
+    }
+#undef MRF_GATHER
+    MRF_LAUNCHED_AS("k_gather_grid", s);
+    return MRF_OK;
+}
+
+// Spread tile-shape autotuner: time every (run length, block size) of
+// k_gather_grid on this plan's own gather table and K, keep the fastest.
+// Runs once per plan and K, on the first grouped adjoint (which already
+// synchronises to build the table); the candidates add into sub_spec, which
+// the caller clears afterwards.
+static mrf_status tune_gather(mrf_plan_s* p, int K, cudaStream_t s) {
+    if (p->gat_tuned_K == K) return MRF_OK;
+    static const int runs[] = {8, 16, 32, 64};
+    static const int threads[] = {128, 256};
+    cudaEvent_t e0, e1;
+    MRF_CUDA(cudaEventCreate(&e0));
+    MRF_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int brun = 32, bthr = 128;
+    mrf_status st = MRF_OK;
+    for (int r : runs)
+        for (int t : threads) {
+            st = launch_gather(p, r, t, K, s);          // warm-up
+            for (int rep = 0; st == MRF_OK && rep < 3; ++rep) {
+                if (rep == 0 && cudaEventRecord(e0, s) != cudaSuccess) st = MRF_ECUDA;
+                if (st == MRF_OK) st = launch_gather(p, r, t, K, s);
+            }
+            float ms = 0.f;
+            if (st != MRF_OK || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                if (st == MRF_OK) {
+                    set_error("gather autotuner: timing failed");
+                    st = MRF_ECUDA;
+                }
+                break;
+            }
+            if (ms < best) { best = ms; brun = r; bthr = t; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MRF_OK) return st;
+    p->gat_run = brun;
+    p->gat_threads = bthr;
+    p->gat_tuned_K = K;
+    return MRF_OK;
+}
+
 mrf_status ensure_subspace_workspace(mrf_plan_s* p, int K) {
     if (p->sub_K >= K) return MRF_OK;
     const int Kc = 16;
@@ -871,6 +930,13 @@ fail:
     return e == cudaErrorMemoryAllocation ? MRF_ENOMEM : MRF_ECUDA;
 }
 
+extern "C" mrf_status mrf_nufft_gather_tuning(mrf_plan p, int* run, int* threads) {
+    MRF_REQUIRE(p && run && threads, "mrf_nufft_gather_tuning: NULL argument");
+    *run = p->gat_tuned_K ? p->gat_run : 0;
+    *threads = p->gat_tuned_K ? p->gat_threads : 0;
+    return MRF_OK;
+}
+
 extern "C" mrf_status mrf_nufft_destroy(mrf_plan p) {
     free_plan(p);
     return MRF_OK;
@@ -968,13 +1034,11 @@ mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, i
         MRF_LAUNCHED_AS("k_combine_adj", s);
     }
     MRF_PROPAGATE(build_gather(p, s));
+    MRF_PROPAGATE(tune_gather(p, K, s));
     {
         const int G = p->gy;
         MRF_CUDA(cudaMemsetAsync(p->sub_spec, 0, sizeof(float2) * (size_t)K * G * G, s));
-        const int runs = (p->gat_n + kGatherRun - 1) / kGatherRun;
-        k_gather_grid<<<(runs + 127) / 128, 128, 0, s>>>(p->sub_R, K, p->gat_pt, p->gat_smp, p->gat_w, p->gat_n,
-                                                         G * G, p->sub_spec);
-        MRF_LAUNCHED_AS("k_gather_grid", s);
+        MRF_PROPAGATE(launch_gather(p, p->gat_run, p->gat_threads, K, s));
         dim3 grid(p->nstrips_a, K);
         const size_t sm = tile_smem(G);
         MRF_DISPATCH_G(G, {

@@ -27,6 +27,9 @@ struct mrf_plan_s {
     int* gat_pt = nullptr;        // grid point gy * G + gx
     int* gat_smp = nullptr;       // group sample g * ns + j
     float* gat_w = nullptr;       // psi(ux - mx) psi(uy - my)
+    int gat_run = 32;             // tuned entries per thread of k_gather_grid
+    int gat_threads = 128;        // tuned block size of k_gather_grid
+    int gat_tuned_K = 0;          // K the tuning was done for (0: not tuned)
     int* gf_off = nullptr;        // [ngroups + 1] frames of each group (CSR)
     int* gf = nullptr;            // [T]
     float2* h1 = nullptr;         // [T][ny][gx] rows transformed along x

@@ -780,11 +780,11 @@ static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStre
     return MRF_OK;
 }
 
-// one iteration of the loop body (stream-ordered, capturable)
-static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
+// the steps of one iteration before the matching step (stream-ordered,
+// capturable); the cost terms only when cost is set
+static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t s) {
     const size_t NK = (size_t)R->N * R->K;
     const float inv_a = (float)(1.0 / R->a);
-    const bool cost = !(R->prm.flags & MRF_RECON_NO_COST);
     MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, s));
     MRF_PROPAGATE(graph_pass(R, R->QL, nullptr, s));
     const float c = R->prm.mu * R->prm.lam2 * R->prm.beta;
@@ -803,6 +803,12 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
         k_cost<<<1, 1, 0, s>>>(R->acc, R->scal + 2, R->prm.lam2, R->cost + (it % R->cost_cap));
         MRF_LAUNCHED_AS("k_cost", s);
     }
+    return MRF_OK;
+}
+
+// one iteration of the loop body (stream-ordered, capturable)
+static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
+    MRF_PROPAGATE(iteration_pre(R, it, !(R->prm.flags & MRF_RECON_NO_COST), s));
     MRF_PROPAGATE(match_maps(R, s));
     MRF_PROPAGATE(build_graph(R, s));
     return MRF_OK;
@@ -1024,5 +1030,203 @@ extern "C" mrf_status mrf_recon_info(mrf_recon R, double* a_norm, double* x_scal
 
 extern "C" mrf_status mrf_recon_destroy(mrf_recon R) {
     free_recon(R);
+    return MRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched serving: S independent slices (their own plans and sizes, one
+// shared dictionary) advanced together.  One batched iteration forks the
+// slices' pre-matching steps onto one stream each, matches every slice's
+// fingerprints in a single tensor-core launch (a slice table maps the
+// launch's blocks to slices), and forks again for the per-slice matching
+// epilogue and graph rebuild.  The first mrf_batch_iter runs one iteration
+// eagerly (lazy tables, the spread autotuner, the warm SVT state) and then
+// captures the fork/join sequence into a CUDA graph that every later
+// iteration replays with one launch.
+// ---------------------------------------------------------------------------
+struct mrf_batch_s {
+    std::vector<mrf_recon_s*> R;
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ev;
+    cudaEvent_t fork = nullptr, fork2 = nullptr;
+    cudaStream_t cs = nullptr;      // the batch's own stream (the one captured; joined to the caller's)
+    cudaEvent_t entry = nullptr, exit = nullptr;
+    mrf::TcSlice* d_slices = nullptr;
+    int total_blocks = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int* d_err = nullptr;           // gathered error words (filled by batch_check)
+};
+
+namespace mrf {
+
+static void free_batch(mrf_batch_s* B) {
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    for (cudaStream_t t : B->st) cudaStreamDestroy(t);
+    for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
+    if (B->fork) cudaEventDestroy(B->fork);
+    if (B->fork2) cudaEventDestroy(B->fork2);
+    if (B->entry) cudaEventDestroy(B->entry);
+    if (B->exit) cudaEventDestroy(B->exit);
+    if (B->cs) cudaStreamDestroy(B->cs);
+    cudaFree(B->d_slices);
+    delete B;
+}
+
+static mrf_status batch_iteration(mrf_batch_s* B, cudaStream_t s) {
+    const int S = (int)B->R.size();
+    mrf_recon_s* R0 = B->R[0];
+    const int form = tc_form(R0->prm.match_precision);
+    MRF_CUDA(cudaEventRecord(B->fork, s));
+    for (int i = 0; i < S; ++i) {
+        MRF_CUDA(cudaStreamWaitEvent(B->st[i], B->fork, 0));
+        MRF_PROPAGATE(iteration_pre(B->R[i], 0, false, B->st[i]));
+        MRF_CUDA(cudaEventRecord(B->ev[i], B->st[i]));
+    }
+    for (int i = 0; i < S; ++i) MRF_CUDA(cudaStreamWaitEvent(s, B->ev[i], 0));
+    if (form) MRF_PROPAGATE(match_tc_batch(R0->mws, B->d_slices, S, B->total_blocks, R0->K, R0->m, form, s));
+    MRF_CUDA(cudaEventRecord(B->fork2, s));
+    for (int i = 0; i < S; ++i) {
+        mrf_recon_s* R = B->R[i];
+        MRF_CUDA(cudaStreamWaitEvent(B->st[i], B->fork2, 0));
+        if (form) MRF_PROPAGATE(match_finish(R->mws, R->N, R->lut, R->idx, R->pd, R->t1t2, 1.0f, B->st[i]));
+        else MRF_PROPAGATE(match_maps(R, B->st[i]));      // FP32: one exhaustive launch per slice
+        MRF_PROPAGATE(build_graph(R, B->st[i]));
+        MRF_CUDA(cudaEventRecord(B->ev[i], B->st[i]));
+    }
+    for (int i = 0; i < S; ++i) MRF_CUDA(cudaStreamWaitEvent(s, B->ev[i], 0));
+    return MRF_OK;
+}
+
+// error words of the batch's bounded device waits and range checks
+static mrf_status batch_check(mrf_batch_s* B, cudaStream_t s) {
+    std::vector<const int*> src;
+    for (mrf_recon_s* R : B->R) {
+        if (R->mws.tc_err) src.push_back(R->mws.tc_err);
+        if (R->knn.err) src.push_back(R->knn.err);
+    }
+    std::vector<int> h(src.size(), 0);
+    for (size_t i = 0; i < src.size(); ++i)
+        MRF_CUDA(cudaMemcpyAsync(&h[i], src[i], sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRF_CUDA(cudaStreamSynchronize(s));
+    for (int v : h) {
+        if (v == 2) {
+            set_error("mrf_batch_iter: a bounded device wait gave up");
+            return MRF_ETIMEOUT;
+        }
+        if (v == 1) {
+            set_error("mrf_batch_iter: a patch feature left [0, 4096]");
+            return MRF_EINVAL;
+        }
+    }
+    return MRF_OK;
+}
+
+}  // namespace mrf
+
+extern "C" mrf_status mrf_batch_create(mrf_batch* out, const mrf_recon* recons, int count, mrf_stream stream) {
+    MRF_REQUIRE(out && recons, "mrf_batch_create: NULL argument");
+    MRF_REQUIRE(count >= 1 && count <= 64, "mrf_batch_create: count must be in [1, 64] (got %d)", count);
+    *out = nullptr;
+    mrf_recon_s* R0 = recons[0];
+    MRF_REQUIRE(R0 != nullptr, "mrf_batch_create: NULL recon 0");
+    for (int i = 0; i < count; ++i) {
+        mrf_recon_s* R = recons[i];
+        MRF_REQUIRE(R != nullptr, "mrf_batch_create: NULL recon %d", i);
+        MRF_REQUIRE(R->m == R0->m && R->K == R0->K && R->prm.match_precision == R0->prm.match_precision,
+                    "mrf_batch_create: slice %d differs from slice 0 in atoms, K or match precision", i);
+        for (int j = 0; j < i; ++j)
+            MRF_REQUIRE(R != recons[j] && R->plan != recons[j]->plan,
+                        "mrf_batch_create: slices %d and %d share a recon or a NUFFT plan", j, i);
+    }
+    cudaStream_t s = as_stream(stream);
+    const int form = mrf::tc_form(R0->prm.match_precision);
+    for (int i = 0; form && i < count; ++i)
+        MRF_PROPAGATE(mrf::tc_prepare_operand(recons[i]->mws, recons[i]->dict_c, R0->m, R0->K, form, s));
+    auto* B = new mrf_batch_s();
+    std::vector<mrf::TcSlice> table;
+    for (int i = 0; i < count; ++i) {
+        mrf_recon_s* R = recons[i];
+        B->R.push_back(R);
+        table.push_back({R->alpha, R->N, B->total_blocks, R->mws.best_idx, R->mws.best_ip,
+                         static_cast<const unsigned char*>(R->mws.tc_b), R->mws.wscore, R->dict_c});
+        B->total_blocks += (R->N + 127) / 128;
+    }
+    mrf_status st = MRF_OK;
+    auto fail = [&](const char* what, cudaError_t e) {
+        set_error("mrf_batch_create: %s failed: %s", what, cudaGetErrorString(e));
+        st = MRF_ECUDA;
+    };
+    cudaError_t e = cudaMalloc(&B->d_slices, sizeof(mrf::TcSlice) * table.size());
+    if (e != cudaSuccess) fail("cudaMalloc", e);
+    if (st == MRF_OK) {
+        e = cudaMemcpyAsync(B->d_slices, table.data(), sizeof(mrf::TcSlice) * table.size(), cudaMemcpyHostToDevice,
+                            s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) fail("slice table upload", e);
+    }
+    for (int i = 0; st == MRF_OK && i < count; ++i) {
+        cudaStream_t t;
+        cudaEvent_t ev;
+        e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { fail("cudaStreamCreateWithFlags", e); break; }
+        B->st.push_back(t);
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) { fail("cudaEventCreateWithFlags", e); break; }
+        B->ev.push_back(ev);
+    }
+    if (st == MRF_OK && ((e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming)) != cudaSuccess ||
+                         (e = cudaEventCreateWithFlags(&B->fork2, cudaEventDisableTiming)) != cudaSuccess ||
+                         (e = cudaEventCreateWithFlags(&B->entry, cudaEventDisableTiming)) != cudaSuccess ||
+                         (e = cudaEventCreateWithFlags(&B->exit, cudaEventDisableTiming)) != cudaSuccess))
+        fail("cudaEventCreateWithFlags", e);
+    if (st == MRF_OK && (e = cudaStreamCreateWithFlags(&B->cs, cudaStreamNonBlocking)) != cudaSuccess)
+        fail("cudaStreamCreateWithFlags", e);
+    if (st != MRF_OK) {
+        free_batch(B);
+        return st;
+    }
+    *out = B;
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_batch_iter(mrf_batch B, int n_iters, mrf_stream stream) {
+    MRF_REQUIRE(B != nullptr, "mrf_batch_iter: NULL batch");
+    MRF_REQUIRE(n_iters >= 0, "mrf_batch_iter: n_iters must be >= 0");
+    if (n_iters == 0) return MRF_OK;
+    // the work runs on the batch's own stream (the legacy default stream
+    // cannot be captured), ordered after and before the caller's stream
+    const cudaStream_t caller = as_stream(stream);
+    const cudaStream_t s = B->cs;
+    MRF_CUDA(cudaEventRecord(B->entry, caller));
+    MRF_CUDA(cudaStreamWaitEvent(s, B->entry, 0));
+    const int total = n_iters;
+    if (!B->exec) {
+        MRF_PROPAGATE(batch_iteration(B, s));           // eager: lazy tables, autotuning, warm SVT state
+        --n_iters;
+        MRF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        const mrf_status st = batch_iteration(B, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st != MRF_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (st != MRF_OK) return st;
+            set_error("mrf_batch_iter: stream capture failed: %s", cudaGetErrorString(e));
+            return MRF_ECUDA;
+        }
+        B->graph = g;
+        MRF_CUDA(cudaGraphInstantiate(&B->exec, g, 0));
+    }
+    for (int i = 0; i < n_iters; ++i) MRF_CUDA(cudaGraphLaunch(B->exec, s));
+    for (mrf_recon_s* R : B->R) R->iters_done += total;
+    MRF_CUDA(cudaEventRecord(B->exit, s));
+    MRF_CUDA(cudaStreamWaitEvent(caller, B->exit, 0));
+    return batch_check(B, s);
+}
+
+extern "C" mrf_status mrf_batch_destroy(mrf_batch B) {
+    mrf::free_batch(B);
     return MRF_OK;
 }

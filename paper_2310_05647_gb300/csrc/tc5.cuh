@@ -41,8 +41,9 @@ __host__ __device__ __forceinline__ uint32_t core_off(int row, int k, int KC) {
     return (uint32_t)((((row >> 3) * KC + (k >> 3)) * 128) + ((row & 7) * 16) + ((k & 7) * 2));
 }
 
-// bounded wait on an mbarrier phase; returns false if it gave up
-__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
+// bounded wait on an mbarrier phase; returns false if it gave up after
+// `limit` polls
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity, unsigned limit = kSpinLimit) {
     uint32_t done = 0;
     unsigned spins = 0;
     while (!done) {
@@ -51,7 +52,7 @@ __device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
             : "r"(bar), "r"(parity));
-        if (!done && ++spins > kSpinLimit) return false;
+        if (!done && ++spins > limit) return false;
     }
     return true;
 }

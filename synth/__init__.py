@@ -146,20 +146,25 @@ def spiral_interleaf(n: int, ns: int, n_interleaves: int = 48):
     return np.pi * tau ** 2 * np.exp(1j * 2 * np.pi * n_turns * tau)
 
 
-def spiral_trajectory(n: int, frames: int, ns: int, interleaves: int):
-    """k-space sample positions [frames, ns, 2] as (kx, ky) in radians/voxel.
+def spiral_trajectory(n: int, frames: int, ns: int, interleaves: int, per_frame: int = 1):
+    """k-space sample positions [frames, per_frame * ns, 2] as (kx, ky) in radians/voxel.
 
     interleaves == 0: frame t is the base arm rotated by t golden angles.
-    interleaves == P: frame t uses arm (t mod P), rotated by 2 pi (t mod P)/P.
+    interleaves == P: frame t uses arms (t per_frame + j) mod P, j < per_frame,
+    arm a rotated by 2 pi a / P, concatenated.
     Coordinates are wrapped into [-pi, pi).
     """
     arm = spiral_interleaf(n, ns, 48 if interleaves == 0 else interleaves)
     t = np.arange(frames)
     if interleaves == 0:
+        if per_frame != 1:
+            raise ValueError("golden-angle frames carry one arm each")
         rot = t * GOLDEN_ANGLE
+        k = arm[None, :] * np.exp(1j * rot)[:, None]
     else:
-        rot = 2 * np.pi * (t % interleaves) / interleaves
-    k = arm[None, :] * np.exp(1j * rot)[:, None]
+        arms = (t[:, None] * per_frame + np.arange(per_frame)[None, :]) % interleaves     # [frames, per_frame]
+        rot = 2 * np.pi * arms / interleaves
+        k = (arm[None, None, :] * np.exp(1j * rot)[:, :, None]).reshape(frames, per_frame * ns)
     out = np.stack([k.real, k.imag], axis=-1)
     out = np.mod(out + np.pi, 2 * np.pi) - np.pi
     return out

@@ -1,0 +1,142 @@
+"""Batched serving: slices of uneven sizes advanced together (one matching
+launch for all slices, CUDA-graph replay after the first iteration) must
+follow each slice's own recon; the bounded device wait must report
+MRF_ETIMEOUT and leave the context usable; the spread autotuner must pick
+one of its candidates without changing the grouped adjoint's result.
+
+Batched and solo runs are two runs of the same FP32 computation whose
+atomic accumulations (grouped gather, power-iteration norms) add in a
+different order; near-tie matching flips then move the graph, so the
+coefficient images agree to 5e-4 rather than to rounding."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import c64, f32, mrf, np_, rand_c, rel
+
+pytestmark = pytest.mark.gpu
+
+T, NS, IL, K = 60, 256, 6, 6
+SIDES = (64, 32, 128)
+
+
+def _shared():
+    m = mrf()
+    fa, tr = synth.fisp_train(T, seed=2)
+    lut = synth.keep_t1_ge_t2(synth.log_grid(250, 3000, 24), synth.log_grid(25, 350, 16))
+    D = m.epg_fisp(f32(lut), f32(fa), f32(tr))
+    phi, comp, n2 = m.dict_subspace(D, K)
+    return dict(fa=f32(fa), tr=f32(tr), lut=f32(lut), phi=phi, comp=comp, n2=n2)
+
+
+def _slice(sh, n, seed):
+    m = mrf()
+    t1, t2, pd, mask, label = synth.phantom(n, seed=seed)
+    pairs = np.stack([np.maximum(t1.ravel(), 1.0), np.maximum(t2.ravel(), 1.0)], -1)
+    S = m.epg_fisp(f32(pairs), sh["fa"], sh["tr"])
+    X = (S * c64((pd * mask).ravel())[:, None]).T.contiguous().view(T, n, n)
+    plan = m.nufft_plan(n, n, f32(synth.spiral_trajectory(n, T, NS, IL).astype(np.float32)))
+    b = m.nufft_forward(plan, X)
+    return plan, b
+
+
+def _recon(sh, plan, b, prec=2):
+    m = mrf()
+    p = m.ReconParams(patch=8, stride=4, knn=4, flags=8 | 4, match_precision=prec)   # grouped, no cost
+    return m.Recon(plan, p, sh["phi"], sh["comp"], sh["n2"], sh["lut"], b)
+
+
+@pytest.mark.parametrize("prec", [2, 0])
+def test_batch_follows_each_slice(prec):
+    m = mrf()
+    sh = _shared()
+    slices = [_slice(sh, n, seed=i) for i, n in enumerate(SIDES)]
+    solo = [_recon(sh, plan, b, prec) for plan, b in slices]
+    # the batch needs plans of its own (the grouped operator keeps its workspace in the plan)
+    batched = [_recon(sh, _slice(sh, n, seed=i)[0], b, prec) for i, (n, (_, b)) in enumerate(zip(SIDES, slices))]
+    batch = m.Batch(batched)
+    for r in solo:
+        r.iterate(3)
+    batch.iterate(3)                      # eager first iteration, then graph replays
+    for a, c in zip(solo, batched):
+        assert rel(np_(c.alpha()), np_(a.alpha())) < 5e-4
+        ia, ic = np_(a.maps()[3]), np_(c.maps()[3])
+        assert (ia == ic).mean() > 0.99
+    for r in solo:
+        r.iterate(2)
+    batch.iterate(2)                      # graph replays only
+    for a, c in zip(solo, batched):
+        assert rel(np_(c.alpha()), np_(a.alpha())) < 1e-3
+        assert np.all(np.isfinite(np_(c.maps()[0])))
+
+
+def test_batch_slices_with_different_frame_counts():
+    """Each frame count carries the shared atoms compressed in its own subspace."""
+    m = mrf()
+    fa, tr = synth.fisp_train(T, seed=2)
+    lut = synth.keep_t1_ge_t2(synth.log_grid(250, 3000, 24), synth.log_grid(25, 350, 16))
+    D = m.epg_fisp(f32(lut), f32(fa), f32(tr))
+    solo, batched = [], []
+    for i, (n, frames, per) in enumerate(((64, T, 1), (32, 40, 2), (128, 50, 3))):
+        Dt = D[:, :frames].contiguous()
+        phi, comp, n2 = m.dict_subspace(Dt, K)
+        sh = dict(fa=f32(fa[:frames]), tr=f32(tr[:frames]), lut=f32(lut), phi=phi, comp=comp, n2=n2)
+        t1, t2, pd, mask, _ = synth.phantom(n, seed=i)
+        pairs = np.stack([np.maximum(t1.ravel(), 1.0), np.maximum(t2.ravel(), 1.0)], -1)
+        S = m.epg_fisp(f32(pairs), sh["fa"], sh["tr"])
+        X = (S * c64((pd * mask).ravel())[:, None]).T.contiguous().view(frames, n, n)
+        k = f32(synth.spiral_trajectory(n, frames, NS, IL, per_frame=per).astype(np.float32))
+        plan = m.nufft_plan(n, n, k)
+        b = m.nufft_forward(plan, X)
+        solo.append(_recon(sh, plan, b))
+        batched.append(_recon(sh, m.nufft_plan(n, n, k), b))
+    batch = m.Batch(batched)
+    for r in solo:
+        r.iterate(3)
+    batch.iterate(3)
+    for a, c in zip(solo, batched):
+        assert rel(np_(c.alpha()), np_(a.alpha())) < 5e-4
+        assert (np_(a.maps()[3]) == np_(c.maps()[3])).mean() > 0.99
+
+
+def test_batch_rejects_shared_plan_and_other_atom_counts():
+    m = mrf()
+    sh = _shared()
+    plan, b = _slice(sh, 64, seed=0)
+    r1, r2 = _recon(sh, plan, b), _recon(sh, plan, b)
+    with pytest.raises(m.MRFError):
+        m.Batch([r1, r2])
+    fewer = dict(sh, comp=sh["comp"][:-3].contiguous(), n2=sh["n2"][:-3].contiguous(), lut=sh["lut"][:-3].contiguous())
+    plan2, b2 = _slice(sh, 64, seed=1)
+    with pytest.raises(m.MRFError):
+        m.Batch([r1, _recon(fewer, plan2, b2)])
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    m = mrf()
+    with pytest.raises(m.MRFError) as e:
+        m.wait_selftest(1000)
+    assert e.value.status == 4            # MRF_ETIMEOUT
+    rng = np.random.default_rng(0)
+    D = rand_c(rng, 40, 6)
+    X = D[rng.integers(0, 40, 300)]
+    idx = np_(m.match(c64(X), c64(D), f32(rng.uniform(10, 100, (40, 2))), precision=2)[0])
+    assert idx.shape == (300,) and idx.min() >= 0 and idx.max() < 40
+
+
+def test_gather_autotuner_choice_and_result():
+    m = mrf()
+    n = 64
+    k = synth.spiral_trajectory(n, T, NS, IL).astype(np.float32)
+    plan = m.nufft_plan(n, n, f32(k))
+    assert plan.gather_tuning() == (0, 0)
+    rng = np.random.default_rng(1)
+    phi, _ = np.linalg.qr(rand_c(rng, T, K))
+    phi_d = c64(phi)
+    y = c64(rand_c(rng, T, NS))
+    a_grouped = m.nufft_adjoint_subspace(plan, y, phi_d, 1.0, mode=1)
+    run, thr = plan.gather_tuning()
+    assert run in (8, 16, 32, 64) and thr in (128, 256)
+    a_frames = m.nufft_adjoint_subspace(plan, y, phi_d, 1.0, mode=0)
+    assert rel(np_(a_grouped), np_(a_frames)) < 1e-4
