@@ -221,3 +221,26 @@ def paper_grid():
     t2 = np.concatenate([np.arange(20, 101, 5), np.arange(110, 201, 10),
                          np.arange(300, 1901, 200)]).astype(np.float64)
     return t1, t2
+
+
+# ----------------------------------------------------------------------------
+# Draws of the learned matcher's training set (random numbers only; the
+# arithmetic that turns them into fingerprints runs in the library)
+# ----------------------------------------------------------------------------
+def mlp_training_draws(n: int, K: int, seed: int, t1_range=(100.0, 4000.0), t2_range=(10.0, 500.0),
+                       pd_range=(0.2, 1.2), snr_db_range=(20.0, 40.0)):
+    """(t1t2 [n, 2], rho [n], snr_db [n], noise [n, K] complex): T1 and T2
+    log-uniform over their ranges with T1 >= T2 (rejection), PD and SNR
+    uniform, complex Gaussian noise of unit variance per coefficient."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((0, 2))
+    while len(out) < n:
+        m = 2 * (n - len(out)) + 16
+        t1 = np.exp(rng.uniform(np.log(t1_range[0]), np.log(t1_range[1]), m))
+        t2 = np.exp(rng.uniform(np.log(t2_range[0]), np.log(t2_range[1]), m))
+        keep = t1 >= t2
+        out = np.concatenate([out, np.stack([t1[keep], t2[keep]], -1)])[:n]
+    rho = rng.uniform(pd_range[0], pd_range[1], n)
+    snr = rng.uniform(snr_db_range[0], snr_db_range[1], n)
+    noise = (rng.standard_normal((n, K)) + 1j * rng.standard_normal((n, K))) / np.sqrt(2.0)
+    return out, rho, snr, noise
