@@ -46,6 +46,7 @@ typedef void* mrf_stream;                 /* cudaStream_t */
 typedef struct mrf_plan_s* mrf_plan;       /* NUFFT plan (opaque) */
 typedef struct mrf_recon_s* mrf_recon;     /* Algorithm 1 state (opaque) */
 typedef struct mrf_batch_s* mrf_batch;     /* batch of slices advanced together (opaque) */
+typedef struct mrf_mlp_s* mrf_mlp;         /* learned matcher network (opaque) */
 
 /* Last error message of the calling thread ("" if none). */
 const char* mrf_last_error(void);
@@ -194,6 +195,50 @@ mrf_status mrf_patch_knn(const int* F, int np, int fd, int ld, int knn, int* nbr
                          mrf_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Learned matcher.  The paper's related work (Section I) cites replacing
+ * dictionary matching by a fully connected network that maps a fingerprint
+ * to its tissue parameters; this is that network for the subspace form:
+ * 20 inputs (the K = 10 complex coefficients divided by their norm, as
+ * (Re, Im) pairs) -> 3 x 256 GELU (exact erf form) -> 3 outputs
+ * (u1, u2, u3): log T1 and log T2 mapped from [log Tmin, log Tmax] onto
+ * [-1, 1], and PD per unit input norm divided by pd_scale.  Parameters are
+ * packed per layer as W [out][in] row-major, then b [out] (137731 floats).
+ * The products use a BF16 copy of the FP32 master weights (refreshed by
+ * every Adam step); biases, activations and accumulation are FP32.
+ * ---------------------------------------------------------------------- */
+/* params: host float [137731]; decode: host float [5] = (t1min, t1max,
+ * t2min, t2max, pd_scale); max_batch: rows of the largest training batch.
+ * Synchronises the device. */
+mrf_status mrf_mlp_create(mrf_mlp* out, const float* params, int nparams, const float* decode,
+                          int max_batch);
+mrf_status mrf_mlp_destroy(mrf_mlp net);
+/* Host copies of the FP32 master parameters and (nullable) of the BF16
+ * values the products use, widened to float.  Synchronises the device. */
+mrf_status mrf_mlp_get_params(mrf_mlp net, float* params, float* params_bf16);
+/* Loss L = 1/(2B) sum (y - t)^2 of B rows x: dev [B][20] against targets t:
+ * dev [B][3], and its gradient with respect to the parameters as used (BF16
+ * weights, FP32 biases): grad dev [137731], loss dev [1] (nullable). */
+mrf_status mrf_mlp_grad(mrf_mlp net, const float* x, const float* t, int B, float* grad, float* loss,
+                        mrf_stream stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * gradient of one batch; loss dev [1] nullable. */
+mrf_status mrf_mlp_train_step(mrf_mlp net, const float* x, const float* t, int B, float lr, float* loss,
+                              mrf_stream stream);
+/* y: dev [n][3] network outputs for x: dev [n][20]. */
+mrf_status mrf_mlp_infer(mrf_mlp net, const float* x, int n, float* y, mrf_stream stream);
+/* Training fingerprints from noiseless signals sig: dev [n][T] of the drawn
+ * (T1, T2) (t1t2: dev [n][2]), PD rho: dev [n], SNR in dB snr_db: dev [n]
+ * and unit-variance complex noise: dev [n][K]: alpha = rho sig Phi + sigma
+ * noise with sigma^2 = ||rho sig Phi||^2 / K 10^(-snr/10); x: dev [n][2K] =
+ * alpha / ||alpha|| as (Re, Im); y: dev [n][3] the encoded targets with PD
+ * per unit norm rho / ||alpha||.  phi: dev [T][K]; ranges: host [5] as the
+ * decode constants above. */
+mrf_status mrf_mlp_training_set(const mrf_c64* sig, const float* t1t2, const float* rho,
+                                const float* snr_db, const mrf_c64* noise, int n, int T,
+                                const mrf_c64* phi, int K, const float* ranges, float* x, float* y,
+                                mrf_stream stream);
+
+/* ------------------------------------------------------------------------
  * Algorithm 1 (MS-LLR).  The iterate is held in the temporal subspace,
  * X = alpha Phi^H with alpha dev [ny][nx][K]; the problem is posed over
  * X in S (Eq. 11, 13), so X^0 = P_S(A^H b).  Per iteration:
@@ -210,7 +255,10 @@ enum {
     MRF_RECON_LITERAL_XUPDATE = 1,  /* Eq. 19 as printed: divide by 1 + mu lambda2 beta */
     MRF_RECON_LITERAL_LAMBDA1 = 2,  /* lambda1 = lambda1^0 * max(L) as printed */
     MRF_RECON_NO_COST = 4,          /* skip the cost evaluation */
-    MRF_RECON_GROUPED = 8           /* data term through the grouped subspace operator */
+    MRF_RECON_GROUPED = 8,          /* data term through the grouped subspace operator */
+    MRF_RECON_LEARNED = 16          /* maps from the learned matcher (params.mlp, K = 10); fingerprints
+                                       it maps outside the dictionary's T1/T2 box, or to T1 < T2, are
+                                       matched exhaustively instead (needs a tensor-core precision) */
 };
 
 typedef struct {
@@ -220,7 +268,8 @@ typedef struct {
     float pd_target;                /* PD scale of the matched initial maps (100) */
     float a_norm, x_scale;          /* > 0: use these instead of deriving a, gamma */
     int flags;                      /* MRF_RECON_* */
-    int match_precision;            /* MRF_MATCH_FP32 or MRF_MATCH_BF16 */
+    int match_precision;            /* MRF_MATCH_*: the matcher (and the learned matcher's fallback) */
+    mrf_mlp mlp;                    /* with MRF_RECON_LEARNED: the trained network (borrowed) */
 } mrf_recon_params;
 
 /* Create the loop state and run Algorithm 1's initialisation (X^0, M^0,

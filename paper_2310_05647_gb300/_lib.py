@@ -22,7 +22,7 @@ class ReconParams(C.Structure):
     _fields_ = [("mu", f32), ("lam1_0", f32), ("lam2", f32), ("beta", f32),
                 ("patch", i32), ("stride", i32), ("knn", i32), ("power_iters", i32),
                 ("pd_target", f32), ("a_norm", f32), ("x_scale", f32),
-                ("flags", i32), ("match_precision", i32)]
+                ("flags", i32), ("match_precision", i32), ("mlp", vp)]
 
 
 # name -> (restype, argtypes); every entry point declared in include/mrf.h
@@ -45,6 +45,13 @@ SIGNATURES = {
     "mrf_batch_iter": (i32, [vp, i32, vp]),
     "mrf_batch_destroy": (i32, [vp]),
     "mrf_wait_selftest": (i32, [i32, vp]),
+    "mrf_mlp_create": (i32, [C.POINTER(vp), vp, i32, vp, i32]),
+    "mrf_mlp_destroy": (i32, [vp]),
+    "mrf_mlp_get_params": (i32, [vp, vp, vp]),
+    "mrf_mlp_grad": (i32, [vp, vp, vp, i32, vp, vp, vp]),
+    "mrf_mlp_train_step": (i32, [vp, vp, vp, i32, f32, vp, vp]),
+    "mrf_mlp_infer": (i32, [vp, vp, i32, vp, vp]),
+    "mrf_mlp_training_set": (i32, [vp, vp, vp, vp, vp, i32, i32, vp, i32, vp, vp, vp, vp]),
     "mrf_recon_create": (i32, [C.POINTER(vp), vp, C.POINTER(ReconParams), vp, i32, vp, vp, vp, i32, vp, vp]),
     "mrf_recon_iter": (i32, [vp, i32, f64p, vp]),
     "mrf_recon_maps": (i32, [vp, vp, vp, vp, vp, vp]),

@@ -20,7 +20,7 @@ __all__ = ["MRFError", "NufftPlan", "Recon", "ReconParams", "dict_subspace", "ep
            "nufft_plan"]
 
 MATCH_FP32, MATCH_BF16, MATCH_BF16X3, MATCH_FP8, MATCH_LITERAL_NORM2 = 0, 1, 2, 3, 0x100
-RECON_LITERAL_XUPDATE, RECON_LITERAL_LAMBDA1, RECON_NO_COST, RECON_GROUPED = 1, 2, 4, 8
+RECON_LITERAL_XUPDATE, RECON_LITERAL_LAMBDA1, RECON_NO_COST, RECON_GROUPED, RECON_LEARNED = 1, 2, 4, 8, 16
 
 
 def _stream():
@@ -193,9 +193,132 @@ class ReconParams:
     x_scale: float = 0.0
     flags: int = 0
     match_precision: int = MATCH_FP32
+    mlp: object = None          # Mlp for RECON_LEARNED (kept alive by the Recon)
 
     def as_c(self):
-        return _lib.ReconParams(*[getattr(self, f.name) for f in fields(self)])
+        vals = [getattr(self, f.name) for f in fields(self) if f.name != "mlp"]
+        return _lib.ReconParams(*vals, self.mlp.handle.value if self.mlp is not None else None)
+
+
+class Mlp:
+    """Owner of an mrf_mlp: the learned matcher's 20-256-256-256-3 GELU network."""
+
+    N_PARAMS = 137731
+
+    def __init__(self, params, decode, max_batch=1024):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.N_PARAMS:
+            raise ValueError(f"expected {self.N_PARAMS} parameters")
+        d = np.ascontiguousarray(decode, dtype=np.float32)
+        self.decode = tuple(float(v) for v in d)
+        self.max_batch = int(max_batch)
+        h = C.c_void_p()
+        _lib.call("mrf_mlp_create", C.byref(h), p.ctypes.data, p.size, d.ctypes.data, self.max_batch)
+        self.handle = h
+
+    def params(self):
+        """(FP32 master parameters, BF16 values used in the products) as NumPy arrays."""
+        import numpy as np
+        a = np.empty(self.N_PARAMS, np.float32)
+        b = np.empty(self.N_PARAMS, np.float32)
+        _lib.call("mrf_mlp_get_params", self.handle, a.ctypes.data, b.ctypes.data)
+        return a, b
+
+    def grad(self, x, t):
+        _check(x, "x", torch.float32)
+        _check(t, "t", torch.float32, (x.shape[0], 3))
+        g = torch.empty(self.N_PARAMS, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _lib.call("mrf_mlp_grad", self.handle, _ptr(x), _ptr(t), x.shape[0], _ptr(g), _ptr(loss), _stream())
+        return g, loss
+
+    def train_step(self, x, t, lr, loss=None):
+        _lib.call("mrf_mlp_train_step", self.handle, _ptr(x), _ptr(t), x.shape[0], float(lr), _ptr(loss),
+                  _stream())
+
+    def infer(self, x):
+        _check(x, "x", torch.float32)
+        y = torch.empty((x.shape[0], 3), dtype=torch.float32, device=x.device)
+        _lib.call("mrf_mlp_infer", self.handle, _ptr(x), x.shape[0], _ptr(y), _stream())
+        return y
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.call("mrf_mlp_destroy", h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def mlp_training_set(sig, t1t2, rho, snr_db, noise, phi, ranges):
+    """(x [n, 2K], y [n, 3]) training fingerprints from noiseless signals sig [n, T]."""
+    import numpy as np
+    n, T = sig.shape
+    K = phi.shape[1]
+    _check(sig, "sig", torch.complex64)
+    _check(t1t2, "t1t2", torch.float32, (n, 2))
+    _check(rho, "rho", torch.float32, (n,))
+    _check(snr_db, "snr_db", torch.float32, (n,))
+    _check(noise, "noise", torch.complex64, (n, K))
+    _check(phi, "phi", torch.complex64, (T, K))
+    r = np.ascontiguousarray(ranges, dtype=np.float32)
+    x = torch.empty((n, 2 * K), dtype=torch.float32, device=sig.device)
+    y = torch.empty((n, 3), dtype=torch.float32, device=sig.device)
+    _lib.call("mrf_mlp_training_set", _ptr(sig), _ptr(t1t2), _ptr(rho), _ptr(snr_db), _ptr(noise), n, T, _ptr(phi),
+              K, r.ctypes.data, _ptr(x), _ptr(y), _stream())
+    return x, y
+
+
+def train_matcher(params0, draws, fa_deg, tr_ms, phi, ranges, epochs=3, batch=1024, lr=(1e-3, 1e-5), chunk=65536,
+                  perm_seed=0):
+    """Train the learned matcher on fingerprints synthesised on the GPU.
+
+    draws = (t1t2 [n, 2], rho [n], snr_db [n], noise [n, K] complex) as NumPy
+    arrays (the caller's random draws); params0: initial packed parameters.
+    The set is simulated chunk by chunk (EPG signals, subspace projection,
+    noise, normalisation) and kept on the device; training runs `epochs`
+    passes of Adam over shuffled batches with a cosine decay from lr[0] to
+    lr[1].  Returns (Mlp, per-epoch mean batch losses)."""
+    import math
+    import numpy as np
+    t1t2, rho, snr, noise = draws
+    n = t1t2.shape[0]
+    dev = phi.device
+    xs, ys = [], []
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        tt = torch.tensor(np.ascontiguousarray(t1t2[c0:c1]), dtype=torch.float32, device=dev)
+        sig = epg_fisp(tt, fa_deg, tr_ms)
+        x, y = mlp_training_set(sig, tt, torch.tensor(rho[c0:c1], dtype=torch.float32, device=dev),
+                                torch.tensor(snr[c0:c1], dtype=torch.float32, device=dev),
+                                torch.tensor(np.ascontiguousarray(noise[c0:c1]), dtype=torch.complex64, device=dev),
+                                phi, ranges)
+        xs.append(x)
+        ys.append(y)
+        del sig
+    X, Y = torch.cat(xs), torch.cat(ys)
+    net = Mlp(params0, ranges, max_batch=batch)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(perm_seed)
+    steps = epochs * (n // batch)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    acc = torch.zeros(1, dtype=torch.float64, device=dev)
+    history, step = [], 0
+    for _ in range(epochs):
+        perm = torch.randperm(n, generator=gen, device=dev)
+        acc.zero_()
+        for b0 in range(0, n - batch + 1, batch):
+            idx = perm[b0:b0 + batch]
+            xb, yb = X[idx].contiguous(), Y[idx].contiguous()
+            rate = lr[1] + 0.5 * (lr[0] - lr[1]) * (1.0 + math.cos(math.pi * step / max(steps - 1, 1)))
+            net.train_step(xb, yb, rate, loss)
+            acc += loss
+            step += 1
+        history.append(float(acc) / (n // batch))
+    return net, history
 
 
 class Recon:
@@ -210,7 +333,7 @@ class Recon:
         _check(lut, "lut", torch.float32, (m, 2))
         _check(b, "b", torch.complex64, (plan.T, plan.ns))
         self.plan, self.K = plan, K
-        self._keep = (phi, dict_c, atom_norm2, lut, b)      # the C object borrows these
+        self._keep = (phi, dict_c, atom_norm2, lut, b, params.mlp)      # the C object borrows these
         self._params = params.as_c()
         h = C.c_void_p()
         _lib.call("mrf_recon_create", C.byref(h), plan.handle, C.byref(self._params), _ptr(phi), K, _ptr(dict_c),

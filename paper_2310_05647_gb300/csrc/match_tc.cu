@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
         wscore = slices[si].wscore;
         dict = slices[si].dict;
         n0 = ((int)blockIdx.x - slices[si].block0) * kTcRows;
+        if (n0 >= n) return;    // a launch sized for more rows than the slice holds (n written on the device)
     }
 
     if (warp == 0) {

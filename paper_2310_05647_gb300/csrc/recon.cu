@@ -23,6 +23,7 @@
 #include "common.h"
 #include "knn.h"
 #include "match.h"
+#include "mlp.h"
 #include "nufft_plan.h"
 
 namespace mrf {
@@ -685,6 +686,12 @@ struct mrf_recon_s {
     int cost_cap = 0, iters_done = 0;
     float2* svt_v = nullptr;    // [np][svt_kp][svt_kp] right singular vectors of the last SVT
     int svt_kp = 0, svt_warm = 0;
+    // learned matcher (MRF_RECON_LEARNED)
+    float t1min = 0.f, t2min = 0.f;
+    float *mlp_x = nullptr, *mlp_norm = nullptr, *mlp_y = nullptr;
+    int *fb_list = nullptr, *fb_count = nullptr;
+    float2* fb_x = nullptr;
+    mrf::TcSlice* fb_table = nullptr;
     std::vector<void*> owned;
 };
 
@@ -773,6 +780,77 @@ static mrf_status match_maps(mrf_recon_s* R, cudaStream_t s) {
                      R->pd, R->t1t2, 1.0f, s);
 }
 
+// Learned matcher: decode the network outputs into maps; a fingerprint
+// mapped outside the dictionary's [T1min, T1max] x [T2min, T2max] box, to
+// T1 < T2, or to a non-finite value joins the fallback list (matched
+// exhaustively next).  idx = -1 marks a learned (off-grid) map value.
+__global__ void k_learned_decode(const float* __restrict__ y, const float* __restrict__ norm, int n, float t1min,
+                                 float t1max, float t2min, float t2max, float pd_scale, float lt1, float lt1r,
+                                 float lt2, float lt2r, float* __restrict__ t1t2, float* __restrict__ pd,
+                                 int* __restrict__ idx, int* __restrict__ list, int* __restrict__ count) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const float t1 = expf(lt1 + 0.5f * (y[3 * v] + 1.f) * lt1r);
+    const float t2 = expf(lt2 + 0.5f * (y[3 * v + 1] + 1.f) * lt2r);
+    const float r = y[3 * v + 2] * pd_scale * norm[v];
+    const bool ok = t1 >= t1min && t1 <= t1max && t2 >= t2min && t2 <= t2max && t1 >= t2 && isfinite(r);
+    t1t2[2 * v] = ok ? t1 : 0.f;
+    t1t2[2 * v + 1] = ok ? t2 : 0.f;
+    pd[v] = ok ? fmaxf(r, 0.f) : 0.f;
+    idx[v] = -1;
+    if (!ok) list[atomicAdd(count, 1)] = v;
+}
+
+// compact the fallback fingerprints and give the matcher's slice its row count
+__global__ void k_fallback_gather(const float2* __restrict__ alpha, int K, const int* __restrict__ list,
+                                  const int* __restrict__ count, float2* __restrict__ xc, TcSlice* __restrict__ table) {
+    const int c = *count;
+    const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (e == 0) table->n = c;
+    if (e >= (size_t)c * K) return;
+    const int i = (int)(e / K), k = (int)(e - (size_t)i * K);
+    xc[e] = alpha[(size_t)list[i] * K + k];
+}
+
+__global__ void k_fallback_scatter(const int* __restrict__ list, const int* __restrict__ count,
+                                   const int* __restrict__ best_idx, const float2* __restrict__ best_ip,
+                                   const float* __restrict__ norm2, const float* __restrict__ lut,
+                                   float* __restrict__ t1t2, float* __restrict__ pd, int* __restrict__ idx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *count) return;
+    const int v = list[i], k = best_idx[i];
+    const float n2 = norm2[k];
+    idx[v] = k;
+    t1t2[2 * v] = lut[2 * k];
+    t1t2[2 * v + 1] = lut[2 * k + 1];
+    pd[v] = n2 > 0.f ? fmaxf(best_ip[i].x / n2, 0.f) : 0.f;
+}
+
+static mrf_status learned_maps(mrf_recon_s* R, cudaStream_t s) {
+    const int N = R->N;
+    const float* dec = mlp_decode(R->prm.mlp);
+    MRF_PROPAGATE(mlp_features(R->alpha, N, R->mlp_x, R->mlp_norm, s));
+    MRF_PROPAGATE(mlp_infer(R->prm.mlp, R->mlp_x, N, R->mlp_y, s));
+    MRF_CUDA(cudaMemsetAsync(R->fb_count, 0, sizeof(int), s));
+    const float lt1 = logf(dec[0]), lt1r = logf(dec[1]) - lt1, lt2 = logf(dec[2]), lt2r = logf(dec[3]) - lt2;
+    k_learned_decode<<<(N + 255) / 256, 256, 0, s>>>(R->mlp_y, R->mlp_norm, N, R->t1min, R->t1max, R->t2min,
+                                                     R->t2max, dec[4], lt1, lt1r, lt2, lt2r, R->t1t2, R->pd,
+                                                     R->idx, R->fb_list, R->fb_count);
+    MRF_LAUNCHED_AS("k_learned_decode", s);
+    const size_t NK = (size_t)N * R->K;
+    k_fallback_gather<<<(unsigned)((NK + 255) / 256), 256, 0, s>>>(R->alpha, R->K, R->fb_list, R->fb_count,
+                                                                    R->fb_x, R->fb_table);
+    MRF_LAUNCHED_AS("k_fallback_gather", s);
+    // exhaustive matching of the fallback list: a launch sized for all N rows,
+    // blocks past the list's (device-side) length return at once
+    MRF_PROPAGATE(match_tc_batch(R->mws, R->fb_table, 1, (N + 127) / 128, R->K, R->m,
+                                 tc_form(R->prm.match_precision), s));
+    k_fallback_scatter<<<(N + 255) / 256, 256, 0, s>>>(R->fb_list, R->fb_count, R->mws.best_idx, R->mws.best_ip,
+                                                       R->mws.norm2, R->lut, R->t1t2, R->pd, R->idx);
+    MRF_LAUNCHED_AS("k_fallback_scatter", s);
+    return MRF_OK;
+}
+
 static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s) {
     k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc, R->rw,
                                          R->deg, QL, trace);
@@ -809,7 +887,8 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
 // one iteration of the loop body (stream-ordered, capturable)
 static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     MRF_PROPAGATE(iteration_pre(R, it, !(R->prm.flags & MRF_RECON_NO_COST), s));
-    MRF_PROPAGATE(match_maps(R, s));
+    if (R->prm.flags & MRF_RECON_LEARNED) MRF_PROPAGATE(learned_maps(R, s));
+    else MRF_PROPAGATE(match_maps(R, s));
     MRF_PROPAGATE(build_graph(R, s));
     return MRF_OK;
 }
@@ -862,15 +941,34 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(R->mws.reserve(N, R->m));
     MRF_PROPAGATE(ensure_subspace_workspace(p, K));
     MRF_PROPAGATE(match_prepare(R->mws, R->dict_c, R->atom_norm2, R->m, K, 0, s));
+    if (R->prm.flags & MRF_RECON_LEARNED) {
+        // network inputs/outputs and the fallback list with its one-slice table
+        const int form = tc_form(R->prm.match_precision);
+        MRF_PROPAGATE(tc_prepare_operand(R->mws, R->dict_c, R->m, K, form, s));
+        MRF_PROPAGATE(dalloc(R, &R->mlp_x, (size_t)N * kMlpIn));
+        MRF_PROPAGATE(dalloc(R, &R->mlp_norm, (size_t)N));
+        MRF_PROPAGATE(dalloc(R, &R->mlp_y, (size_t)N * kMlpOut));
+        MRF_PROPAGATE(dalloc(R, &R->fb_list, (size_t)N));
+        MRF_PROPAGATE(dalloc(R, &R->fb_count, 1));
+        MRF_PROPAGATE(dalloc(R, &R->fb_x, (size_t)N * K));
+        MRF_PROPAGATE(dalloc(R, &R->fb_table, 1));
+        const TcSlice t{R->fb_x, 0, 0, R->mws.best_idx, R->mws.best_ip,
+                        static_cast<const unsigned char*>(R->mws.tc_b), R->mws.wscore, R->dict_c};
+        MRF_CUDA(cudaMemcpyAsync(R->fb_table, &t, sizeof(t), cudaMemcpyHostToDevice, s));
+        MRF_CUDA(cudaStreamSynchronize(s));
+    }
     // t1max, t2max of the look-up table
     {
         std::vector<float> lut((size_t)R->m * 2);
         MRF_CUDA(cudaMemcpyAsync(lut.data(), R->lut, lut.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
         MRF_CUDA(cudaStreamSynchronize(s));
         R->t1max = R->t2max = 0.f;
+        R->t1min = R->t2min = 3.4e38f;
         for (int i = 0; i < R->m; ++i) {
             R->t1max = std::max(R->t1max, lut[2 * i]);
             R->t2max = std::max(R->t2max, lut[2 * i + 1]);
+            R->t1min = std::min(R->t1min, lut[2 * i]);
+            R->t2min = std::min(R->t2min, lut[2 * i + 1]);
         }
         if (!(R->t1max > 0.f)) R->t1max = 1.f;
         if (!(R->t2max > 0.f)) R->t2max = 1.f;
@@ -954,6 +1052,10 @@ extern "C" mrf_status mrf_recon_create(mrf_recon* out, mrf_plan plan, const mrf_
     MRF_REQUIRE(prm->match_precision == MRF_MATCH_FP32 || prm->match_precision == MRF_MATCH_BF16 ||
                     prm->match_precision == MRF_MATCH_BF16X3 || prm->match_precision == MRF_MATCH_FP8,
                 "mrf_recon_create: unknown match precision %d", prm->match_precision);
+    MRF_REQUIRE(!(prm->flags & MRF_RECON_LEARNED) ||
+                    (prm->mlp && K == 10 && mrf::tc_form(prm->match_precision) != 0),
+                "mrf_recon_create: the learned matcher needs params.mlp, K = 10 and a tensor-core precision "
+                "for its fallback");
     const PatchGeom g = make_geom(plan->nx, prm->patch, prm->stride);
     MRF_REQUIRE(g.count() >= prm->knn + 1, "mrf_recon_create: need at least knn + 1 patches (%d)", g.count());
     auto* R = new mrf_recon_s();
@@ -1137,6 +1239,8 @@ extern "C" mrf_status mrf_batch_create(mrf_batch* out, const mrf_recon* recons, 
         MRF_REQUIRE(R != nullptr, "mrf_batch_create: NULL recon %d", i);
         MRF_REQUIRE(R->m == R0->m && R->K == R0->K && R->prm.match_precision == R0->prm.match_precision,
                     "mrf_batch_create: slice %d differs from slice 0 in atoms, K or match precision", i);
+        MRF_REQUIRE(!(R->prm.flags & MRF_RECON_LEARNED),
+                    "mrf_batch_create: slice %d uses the learned matcher (not batched)", i);
         for (int j = 0; j < i; ++j)
             MRF_REQUIRE(R != recons[j] && R->plan != recons[j]->plan,
                         "mrf_batch_create: slices %d and %d share a recon or a NUFFT plan", j, i);

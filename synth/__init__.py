@@ -244,3 +244,14 @@ def mlp_training_draws(n: int, K: int, seed: int, t1_range=(100.0, 4000.0), t2_r
     snr = rng.uniform(snr_db_range[0], snr_db_range[1], n)
     noise = (rng.standard_normal((n, K)) + 1j * rng.standard_normal((n, K))) / np.sqrt(2.0)
     return out, rho, snr, noise
+
+
+def mlp_init_params(seed: int, sizes=(20, 256, 256, 256, 3)):
+    """Initial packed parameters of the learned matcher (per layer W [out][in],
+    then b [out]): W uniform in +-sqrt(6 / in), b = 0."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, o in zip(sizes[:-1], sizes[1:]):
+        lim = np.sqrt(6.0 / i)
+        out += [rng.uniform(-lim, lim, o * i), np.zeros(o)]
+    return np.concatenate(out)
