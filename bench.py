@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--variants", default="plain,chosen")
+    ap.add_argument("--variants", default="plain,chosen,learned")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched-serving measurement")
     ap.add_argument("--workload", default=WORKLOAD, choices=["mrf256_t1000", "mrf256_t100"],
                     help="mrf256_t100: the same image with 100 frames, for small profiling captures")
@@ -185,13 +185,43 @@ def make_inputs(seed):
                 atoms=int(lut.shape[0]))
 
 
-def params_for(variant, w):
+def params_for(variant, w, mlp=None):
+    """plain: frame-by-frame operator, FP32 exhaustive matching; chosen: grouped
+    operator, split-BF16 tensor-core matching; learned: chosen with the learned
+    matcher (exhaustive split-BF16 fallback)."""
     import paper_2310_05647_gb300 as mrf
-    from paper_2310_05647_gb300.api import RECON_GROUPED
+    from paper_2310_05647_gb300.api import RECON_GROUPED, RECON_LEARNED
     from paper_2310_05647_gb300.api import MATCH_BF16X3, MATCH_FP32
-    flags = RECON_GROUPED if variant == "chosen" else 0
-    prec = MATCH_BF16X3 if variant == "chosen" else MATCH_FP32
-    return mrf.ReconParams(patch=w.patch, stride=w.stride, knn=w.knn, flags=flags, match_precision=prec)
+    flags = {"plain": 0, "chosen": RECON_GROUPED, "learned": RECON_GROUPED | RECON_LEARNED}[variant]
+    prec = MATCH_FP32 if variant == "plain" else MATCH_BF16X3
+    return mrf.ReconParams(patch=w.patch, stride=w.stride, knn=w.knn, flags=flags, match_precision=prec,
+                           mlp=mlp if variant == "learned" else None)
+
+
+def train_learned(inp, n_train=2_000_000, epochs=3, seed=0):
+    """The learned matcher for this workload: 2M noisy EPG fingerprints of the
+    workload's sequence (T1, T2 over the dictionary's ranges, SNR 20-40 dB),
+    simulated and trained on the GPU."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2310_05647_gb300 as mrf
+
+    w = inp["w"]
+    fa, tr = synth.fisp_train(w.frames, seed=w.tr_seed)
+    n2 = inp["n2"].cpu().numpy()
+    ranges = (w.t1_range[0], w.t1_range[1], w.t2_range[0], w.t2_range[1], float(1.0 / np.median(np.sqrt(n2))))
+    draws = synth.mlp_training_draws(n_train, w.rank, seed=3000 + seed, t1_range=w.t1_range, t2_range=w.t2_range)
+    dev = torch.device("cuda")
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net, hist = mrf.train_matcher(synth.mlp_init_params(4000 + seed), draws, f32(fa), f32(tr), inp["phi"], ranges,
+                                  epochs=epochs, batch=1024)
+    torch.cuda.synchronize()
+    return net, {"fingerprints": n_train, "epochs": epochs, "batch": 1024, "seconds": time.perf_counter() - t0,
+                 "loss_per_epoch": hist}
 
 
 def nrmse(truth, maps):
@@ -247,7 +277,8 @@ def time_variant(variant, inp, steps, warmup, dist):
     import paper_2310_05647_gb300 as mrf
 
     w = inp["w"]
-    rec = mrf.Recon(inp["plan"], params_for(variant, w), inp["phi"], inp["comp"], inp["n2"], inp["lut"], inp["b"])
+    rec = mrf.Recon(inp["plan"], params_for(variant, w, inp.get("mlp")), inp["phi"], inp["comp"], inp["n2"],
+                    inp["lut"], inp["b"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")    # 256 MiB > L2
     for _ in range(warmup):
         flush.zero_()
@@ -283,13 +314,14 @@ def time_variant(variant, inp, steps, warmup, dist):
                 rec.iterate(1)
             torch.cuda.synchronize()
     clocks = merge_clocks(clk.summary(), clk2.summary(), 1e3 * (time.time() - t0))
-    t1, t2, pd, _ = rec.maps()
+    t1, t2, pd, idx = rec.maps()
     maps = [t.cpu().numpy() for t in (t1, t2, pd)]
+    fallback = float((idx >= 0).float().mean())
     info = rec.info()
     alpha = rec.alpha().clone()
     del rec
     return dict(ms=ms, launches=launches, profile=prof, clocks=clocks,
-                nrmse=nrmse(inp["truth"], maps), info=info, maps=maps, alpha=alpha)
+                nrmse=nrmse(inp["truth"], maps), info=info, maps=maps, alpha=alpha, fallback=fallback)
 
 
 def merge_clocks(timed, sustained, sustained_ms):
@@ -563,6 +595,9 @@ def run_ours(args, dist):
     inp = make_inputs(seed=dist.rank)
     w = inp["w"]
     variants = [v for v in args.variants.split(",") if v]
+    training = None
+    if "learned" in variants:
+        inp["mlp"], training = train_learned(inp, seed=dist.rank)
     res = {}
     for v in variants:
         res[v] = time_variant(v, inp, args.steps, args.warmup, dist)
@@ -615,6 +650,17 @@ def run_ours(args, dist):
                                                                 key=lambda kv: -kv[1][0])[:8]}}
                          for v in res},
             "roofline": roof, "kernels": kernels, "clocks": r["clocks"], "gpu_launches": r["launches"]}
+    if "learned" in res:
+        import numpy as np
+        lv = line["variants"]["learned"]
+        lv["training"] = training
+        lv["fallback_fraction"] = res["learned"]["fallback"]
+        if "chosen" in res:
+            a, b = res["chosen"]["maps"], res["learned"]["maps"]
+            mask = inp["truth"][3]
+            lv["nrmse_vs_exhaustive_judge"] = {nm: float(np.sqrt(np.sum((b[i][mask] - a[i][mask]) ** 2) /
+                                                                 np.sum(a[i][mask] ** 2)))
+                                               for i, nm in enumerate(("t1", "t2", "pd"))}
     if "plain" in res and "chosen" in res:
         import numpy as np
         a, b = res["plain"]["maps"], res["chosen"]["maps"]

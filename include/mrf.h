@@ -226,6 +226,13 @@ mrf_status mrf_mlp_train_step(mrf_mlp net, const float* x, const float* t, int B
                               mrf_stream stream);
 /* y: dev [n][3] network outputs for x: dev [n][20]. */
 mrf_status mrf_mlp_infer(mrf_mlp net, const float* x, int n, float* y, mrf_stream stream);
+/* Inference engine: tensor_cores = 1 (default) runs tcgen05 BF16 products
+ * with every layer's input rounded to BF16; 0 runs the SIMT kernel with FP32
+ * activations. */
+mrf_status mrf_mlp_set_engine(mrf_mlp net, int tensor_cores);
+/* MRF_ETIMEOUT if a bounded device wait of the tensor-core inference gave up
+ * (synchronises `stream`). */
+mrf_status mrf_mlp_check(mrf_mlp net, mrf_stream stream);
 /* Training fingerprints from noiseless signals sig: dev [n][T] of the drawn
  * (T1, T2) (t1t2: dev [n][2]), PD rho: dev [n], SNR in dB snr_db: dev [n]
  * and unit-variance complex noise: dev [n][K]: alpha = rho sig Phi + sigma

@@ -72,12 +72,26 @@ def gelu_grad(z):
     return cdf + z * pdf
 
 
-def forward(theta, X, sizes=SIZES):
-    """(y [B, 3], cache): cache holds every layer's input and pre-activation."""
+def round_bf16(v):
+    """Round to the nearest bfloat16 (8 significant bits, ties to even), via
+    the float32 value: the upper 16 bits of its IEEE encoding after adding
+    0x7fff plus the lowest kept bit.  Finite inputs only."""
+    f = np.asarray(v, np.float64).astype(np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(theta, X, sizes=SIZES, act_bf16=False):
+    """(y [B, 3], cache): cache holds every layer's input and pre-activation.
+    act_bf16: every layer's input rounded to bfloat16 (the tensor-core
+    inference, whose operands are BF16)."""
     layers = unpack(theta, sizes)
     h = np.asarray(X, np.float64)
     cache = []
     for li, (W, b) in enumerate(layers):
+        if act_bf16:
+            h = round_bf16(h)
         z = h @ W.T + b
         cache.append((h, z))
         h = gelu(z) if li < len(layers) - 1 else z

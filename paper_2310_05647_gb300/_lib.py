@@ -51,6 +51,8 @@ SIGNATURES = {
     "mrf_mlp_grad": (i32, [vp, vp, vp, i32, vp, vp, vp]),
     "mrf_mlp_train_step": (i32, [vp, vp, vp, i32, f32, vp, vp]),
     "mrf_mlp_infer": (i32, [vp, vp, i32, vp, vp]),
+    "mrf_mlp_set_engine": (i32, [vp, i32]),
+    "mrf_mlp_check": (i32, [vp, vp]),
     "mrf_mlp_training_set": (i32, [vp, vp, vp, vp, vp, i32, i32, vp, i32, vp, vp, vp, vp]),
     "mrf_recon_create": (i32, [C.POINTER(vp), vp, C.POINTER(ReconParams), vp, i32, vp, vp, vp, i32, vp, vp]),
     "mrf_recon_iter": (i32, [vp, i32, f64p, vp]),

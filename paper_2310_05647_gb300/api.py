@@ -237,6 +237,12 @@ class Mlp:
         _lib.call("mrf_mlp_train_step", self.handle, _ptr(x), _ptr(t), x.shape[0], float(lr), _ptr(loss),
                   _stream())
 
+    def set_engine(self, tensor_cores=True):
+        _lib.call("mrf_mlp_set_engine", self.handle, 1 if tensor_cores else 0)
+
+    def check(self):
+        _lib.call("mrf_mlp_check", self.handle, _stream())
+
     def infer(self, x):
         _check(x, "x", torch.float32)
         y = torch.empty((x.shape[0], 3), dtype=torch.float32, device=x.device)

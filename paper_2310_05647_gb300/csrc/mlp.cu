@@ -15,11 +15,13 @@
 // row-major, then b [out].  Loss 1 / (2B) sum (y - t)^2.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "common.h"
 #include "mlp.h"
+#include "tc5.cuh"
 
 namespace mrf {
 
@@ -238,6 +240,188 @@ __global__ void __launch_bounds__(kMlpHidden) k_mlp_infer(InferParams P, const f
     }
 }
 
+// Tensor-core inference (tcgen05, BF16 operands, FP32 accumulators in TMEM).
+// A block owns 128 fingerprints per tile (one per TMEM lane) and loops over
+// tiles.  The layer input sits in shared memory as the MMA's A operand
+// ([128][K] BF16, canonical K-major core matrices); each layer's weights
+// [N][K] arrive with one bulk copy (pre-arranged in the same layout), the
+// 128 x N product lands in TMEM (N = 256, or 16 for the 3 padded outputs),
+// and 8 warps (two per lane quarter, one column half each) add the bias,
+// apply GELU and write the next layer's input back as BF16.  The next
+// layer's weights are requested as soon as the current products are done,
+// so the copy overlaps the epilogue.  Every wait is bounded.
+constexpr int kTcMlpRows = 128;
+constexpr int kTcMlpWarps = 8;
+constexpr int kL0K = 32;                   // the 20 inputs padded to two MMA k-steps
+constexpr int kOutN = 16;                  // the 3 outputs padded to the smallest N
+constexpr int kWBytes = kMlpHidden * kMlpHidden * 2;        // largest weight operand
+constexpr int kABytes = kTcMlpRows * kMlpHidden * 2;
+
+struct TcInferParams {
+    const unsigned char* w[kLayers];       // pre-arranged BF16 operands
+    int wbytes[kLayers];
+    const float* b[kLayers];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__global__ void __launch_bounds__(32 * kTcMlpWarps) k_mlp_infer_tc(TcInferParams P, const float* __restrict__ x,
+                                                                   int n, float* __restrict__ y,
+                                                                   int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char* sA = smraw;                 // layer input [128][K]
+    unsigned char* sW = smraw + kABytes;       // layer weights [N][K]
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_wbar, s_mbar;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lq = warp & 3, half = warp >> 2;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kMlpHidden));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        s_fail = 0;
+        mbar_init(smem_u32(&s_wbar), 1);
+        mbar_init(smem_u32(&s_mbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+    uint32_t wphase = 0, mphase = 0;
+    int pending_w = 0;                         // weight copies issued and not yet waited for
+    int pending_m = 0;                         // products committed and not yet seen complete
+    const int ntiles = (n + kTcMlpRows - 1) / kTcMlpRows;
+    auto load_w = [&](int l) {
+        const uint32_t bar = smem_u32(&s_wbar);
+        mbar_expect_tx(bar, (uint32_t)P.wbytes[l]);
+        bulk_g2s(smem_u32(sW), P.w[l], (uint32_t)P.wbytes[l], bar);
+    };
+    if (tid == 0 && blockIdx.x < ntiles) { load_w(0); pending_w = 1; }
+    for (int tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
+        const int r0 = tile * kTcMlpRows;
+        // layer-0 input: 20 features per row, padded to 32, rows past n zero
+        for (int e = tid; e < kTcMlpRows * kL0K / 2; e += blockDim.x) {
+            const int row = e / (kL0K / 2), k = 2 * (e - row * (kL0K / 2));
+            float a = 0.f, b = 0.f;
+            if (r0 + row < n && k < kMlpIn) {
+                a = x[(size_t)(r0 + row) * kMlpIn + k];
+                b = x[(size_t)(r0 + row) * kMlpIn + k + 1];
+            }
+            *reinterpret_cast<uint32_t*>(sA + core_off(row, k, kL0K / 8)) = pack_bf16x2(a, b);
+        }
+        for (int l = 0; l < kLayers; ++l) {
+            const int K = l == 0 ? kL0K : kMlpHidden;
+            const int N = l == kLayers - 1 ? kOutN : kMlpHidden;
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tid == 0) {
+                if (!wait_parity(smem_u32(&s_wbar), wphase)) s_fail = 1;
+                wphase ^= 1;
+                pending_w = 0;
+                if (!s_fail) {
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t idesc = mma_idesc(kTcMlpRows, N);
+                    for (int ks = 0; ks < K / 16; ++ks) {
+                        const uint64_t ad = smem_desc(smem_u32(sA) + ks * 256, 128, (K / 8) * 128);
+                        const uint64_t bd = smem_desc(smem_u32(sW) + ks * 256, 128, (K / 8) * 128);
+                        const uint32_t acc = ks > 0 ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                    mma_commit(smem_u32(&s_mbar));
+                    if (!wait_parity(smem_u32(&s_mbar), mphase)) { s_fail = 1; pending_m = 1; }
+                    // the weights and the layer input are free: request the next weights
+                    const int nl = l + 1 < kLayers ? l + 1 : 0;
+                    const bool more = l + 1 < kLayers || tile + (int)gridDim.x < ntiles;
+                    if (!s_fail && more) { load_w(nl); pending_w = 1; }
+                }
+                mphase ^= 1;
+            }
+            __syncthreads();
+            if (s_fail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int row = lq * 32 + lane;
+            const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16);
+            if (l < kLayers - 1) {
+                // bias + GELU of this warp's 128 columns, written back as the next input
+#pragma unroll 1
+                for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+                    uint32_t v[32];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                        : "r"(tl + (uint32_t)c0));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    const float* bias = P.b[l] + c0;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        uint4 q;
+                        q.x = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 0]) + __ldg(bias + 8 * g + 0)),
+                                          gelu(__uint_as_float(v[8 * g + 1]) + __ldg(bias + 8 * g + 1)));
+                        q.y = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 2]) + __ldg(bias + 8 * g + 2)),
+                                          gelu(__uint_as_float(v[8 * g + 3]) + __ldg(bias + 8 * g + 3)));
+                        q.z = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 4]) + __ldg(bias + 8 * g + 4)),
+                                          gelu(__uint_as_float(v[8 * g + 5]) + __ldg(bias + 8 * g + 5)));
+                        q.w = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 6]) + __ldg(bias + 8 * g + 6)),
+                                          gelu(__uint_as_float(v[8 * g + 7]) + __ldg(bias + 8 * g + 7)));
+                        *reinterpret_cast<uint4*>(sA + core_off(row, c0 + 8 * g, kMlpHidden / 8)) = q;
+                    }
+                }
+            } else if (half == 0) {
+                uint32_t v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(tl));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (r0 + row < n)
+#pragma unroll
+                    for (int j = 0; j < kMlpOut; ++j)
+                        y[(size_t)(r0 + row) * kMlpOut + j] = __uint_as_float(v[j]) + __ldg(P.b[l] + j);
+            }
+        }
+    }
+    // after a failed wait: a copy or products still in flight must end before exit
+    if (tid == 0 && pending_w) wait_parity(smem_u32(&s_wbar), wphase);
+    if (tid == 0 && pending_m) wait_parity(smem_u32(&s_mbar), mphase ^ 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMlpHidden));
+    if (s_fail && tid == 0) atomicExch(err, 2);
+}
+
+// weight operand of layer l in the shared-memory layout: row = output unit
+// (N rows, zero past the layer's outputs), k = input (zero past its inputs)
+__global__ void k_mlp_prepare_tc(const __nv_bfloat16* __restrict__ W, int out, int in, int N, int K,
+                                 __nv_bfloat16* __restrict__ dst) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * K) return;
+    const int r = e / K, k = e - r * K;
+    const __nv_bfloat16 v = (r < out && k < in) ? W[(size_t)r * in + k] : __float2bfloat16_rn(0.f);
+    dst[core_off(r, k, K / 8) / 2] = v;
+}
+
 // Training set: one warp per fingerprint.  alpha = rho sig Phi + sigma noise
 // with sigma^2 = ||rho sig Phi||^2 / K 10^(-snr / 10); x = alpha / ||alpha||
 // as (Re, Im); y = (u1, u2, rho / ||alpha|| / pd_scale) with u the log T maps
@@ -336,10 +520,22 @@ struct mrf_mlp_s {
     float *d0 = nullptr, *d1 = nullptr;
     long long step = 0;
     bool wt_fresh = false;
+    unsigned char* wtc = nullptr;   // tensor-core weight operands, layer by layer
+    bool tensor_cores = true;       // inference on tcgen05 (false: the SIMT kernel)
+    int* err = nullptr;             // set when a bounded device wait gave up
     float decode[5] = {};
 };
 
 namespace mrf {
+
+// operand sizes (bytes) of the tensor-core inference per layer
+static int tc_rows(int l) { return l == kLayers - 1 ? kOutN : kMlpHidden; }
+static int tc_k(int l) { return l == 0 ? kL0K : kMlpHidden; }
+static size_t tc_offset(int l) {
+    size_t at = 0;
+    for (int i = 0; i < l; ++i) at += (size_t)tc_rows(i) * tc_k(i) * 2;
+    return at;
+}
 
 static mrf_status refresh_transposed(mrf_mlp_s* N, cudaStream_t s) {
     if (N->wt_fresh) return MRF_OK;
@@ -347,8 +543,30 @@ static mrf_status refresh_transposed(mrf_mlp_s* N, cudaStream_t s) {
         const int out = kSizes[l + 1], in = kSizes[l];
         k_transpose_w<<<(out * in + 255) / 256, 256, 0, s>>>(N->wb + N->L.w[l], out, in, N->wt + N->L.w[l]);
         MRF_LAUNCHED_AS("k_transpose_w", s);
+        const int R = tc_rows(l), K = tc_k(l);
+        k_mlp_prepare_tc<<<(R * K + 255) / 256, 256, 0, s>>>(
+            N->wb + N->L.w[l], out, in, R, K, reinterpret_cast<__nv_bfloat16*>(N->wtc + tc_offset(l)));
+        MRF_LAUNCHED_AS("k_mlp_prepare_tc", s);
     }
     N->wt_fresh = true;
+    return MRF_OK;
+}
+
+static mrf_status mlp_infer_tc(mrf_mlp_s* N, const float* x, int n, float* y, cudaStream_t s) {
+    TcInferParams P;
+    for (int l = 0; l < kLayers; ++l) {
+        P.w[l] = N->wtc + tc_offset(l);
+        P.wbytes[l] = tc_rows(l) * tc_k(l) * 2;
+        P.b[l] = N->w + N->L.b[l];
+    }
+    const size_t sm = (size_t)kABytes + kWBytes;
+    MRF_CUDA(cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int tiles = (n + kTcMlpRows - 1) / kTcMlpRows;
+    int dev = 0, sms = 152;
+    MRF_CUDA(cudaGetDevice(&dev));
+    MRF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    k_mlp_infer_tc<<<std::min(tiles, sms), 32 * kTcMlpWarps, sm, s>>>(P, x, n, y, N->err);
+    MRF_LAUNCHED_AS("k_mlp_infer_tc", s);
     return MRF_OK;
 }
 
@@ -356,6 +574,7 @@ mrf_status mlp_infer(mrf_mlp_s* N, const float* x, int n, float* y, cudaStream_t
     MRF_REQUIRE(N && x && y && n >= 0, "mlp_infer: bad arguments");
     if (n == 0) return MRF_OK;
     MRF_PROPAGATE(refresh_transposed(N, s));
+    if (N->tensor_cores) return mlp_infer_tc(N, x, n, y, s);
     InferParams P;
     for (int l = 0; l < kLayers; ++l) {
         P.wt[l] = N->wt + N->L.w[l];
@@ -447,6 +666,9 @@ extern "C" mrf_status mrf_mlp_create(mrf_mlp* out, const float* params, int npar
     A(reinterpret_cast<void**>(&N->m), sizeof(float) * P);
     A(reinterpret_cast<void**>(&N->v), sizeof(float) * P);
     A(reinterpret_cast<void**>(&N->ws), sizeof(float) * per_row * max_batch);
+    A(reinterpret_cast<void**>(&N->wtc), tc_offset(kLayers));
+    A(reinterpret_cast<void**>(&N->err), sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(N->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(N->w, params, sizeof(float) * P, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(N->m, 0, sizeof(float) * P);
     if (e == cudaSuccess) e = cudaMemset(N->v, 0, sizeof(float) * P);
@@ -457,7 +679,7 @@ extern "C" mrf_status mrf_mlp_create(mrf_mlp* out, const float* params, int npar
     if (e != cudaSuccess) {
         set_error("mrf_mlp_create: %s", cudaGetErrorString(e));
         cudaFree(N->w); cudaFree(N->wb); cudaFree(N->wt); cudaFree(N->g); cudaFree(N->m); cudaFree(N->v);
-        cudaFree(N->ws);
+        cudaFree(N->ws); cudaFree(N->wtc); cudaFree(N->err);
         delete N;
         return MRF_ECUDA;
     }
@@ -478,7 +700,7 @@ extern "C" mrf_status mrf_mlp_create(mrf_mlp* out, const float* params, int npar
 extern "C" mrf_status mrf_mlp_destroy(mrf_mlp N) {
     if (!N) return MRF_OK;
     cudaFree(N->w); cudaFree(N->wb); cudaFree(N->wt); cudaFree(N->g); cudaFree(N->m); cudaFree(N->v);
-    cudaFree(N->ws);
+    cudaFree(N->ws); cudaFree(N->wtc); cudaFree(N->err);
     delete N;
     return MRF_OK;
 }
@@ -526,6 +748,25 @@ extern "C" mrf_status mrf_mlp_train_step(mrf_mlp N, const float* x, const float*
 
 extern "C" mrf_status mrf_mlp_infer(mrf_mlp N, const float* x, int n, float* y, mrf_stream stream) {
     return mlp_infer(N, x, n, y, as_stream(stream));
+}
+
+extern "C" mrf_status mrf_mlp_set_engine(mrf_mlp N, int tensor_cores) {
+    MRF_REQUIRE(N, "mrf_mlp_set_engine: NULL network");
+    N->tensor_cores = tensor_cores != 0;
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_mlp_check(mrf_mlp N, mrf_stream stream) {
+    MRF_REQUIRE(N, "mrf_mlp_check: NULL network");
+    int h = 0;
+    cudaStream_t s = as_stream(stream);
+    MRF_CUDA(cudaMemcpyAsync(&h, N->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRF_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        set_error("mrf_mlp: a tensor-core wait timed out");
+        return MRF_ETIMEOUT;
+    }
+    return MRF_OK;
 }
 
 extern "C" mrf_status mrf_mlp_training_set(const mrf_c64* sig, const float* t1t2, const float* rho,

@@ -94,13 +94,24 @@ def test_training_set_matches_oracle():
 
 
 def test_inference_matches_oracle_forward():
+    """SIMT engine: FP32 activations.  Tensor-core engine: each layer's input
+    rounded to BF16 (the oracle rounds the same way, from its FP64 values, so
+    an activation can land one BF16 step apart: 2^-8 relative, rarely)."""
     net = _net(6)
     rng = np.random.default_rng(7)
-    n = 1000                                                  # several 32-row blocks and a ragged tail
-    x = rng.standard_normal((n, 20)).astype(np.float32)
-    y = np_(net.infer(f32(x)))
-    yo, _ = omlp.forward(_used_params(net), x.astype(np.float64))
-    assert rel(y, yo) < 1e-4
+    theta = _used_params(net)
+    for n in (1000, 128 * 152 * 2 + 77):                      # ragged tails; more tiles than SMs
+        x = rng.standard_normal((n, 20)).astype(np.float32)
+        net.set_engine(tensor_cores=False)
+        y = np_(net.infer(f32(x)))
+        yo, _ = omlp.forward(theta, x.astype(np.float64))
+        assert rel(y, yo) < 1e-4
+        net.set_engine(tensor_cores=True)
+        yt = np_(net.infer(f32(x)))
+        net.check()
+        yb, _ = omlp.forward(theta, x.astype(np.float64), act_bf16=True)
+        assert rel(yt, yb) < 2e-3
+        assert rel(yt, yo) < 2e-2
 
 
 def _small_problem(T=200, K=10):

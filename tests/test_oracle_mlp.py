@@ -120,3 +120,15 @@ def test_noiseless_training_targets_recover_pd():
     np.testing.assert_allclose(y[:, 2], 1.0 / np.linalg.norm(sig @ phi, axis=1), rtol=1e-12)
     a = sig @ phi
     np.testing.assert_allclose(x[:, 0::2] + 1j * x[:, 1::2], a / np.linalg.norm(a, axis=1)[:, None], rtol=1e-12)
+
+
+def test_round_bf16():
+    # exactly representable values (8 significant bits) are unchanged
+    exact = np.array([1.0, -2.5, 0.15625, 3.0 * 2 ** -20, 255.0, -0.0])
+    np.testing.assert_array_equal(mlp.round_bf16(exact), exact)
+    # halfway cases go to the even neighbour: 1 + 2^-8 lies between 1 and 1 + 2^-7
+    assert mlp.round_bf16(np.array([1.0 + 2 ** -8]))[0] == 1.0
+    assert mlp.round_bf16(np.array([1.0 + 3 * 2 ** -8]))[0] == 1.0 + 2 ** -6
+    # otherwise the relative error is at most the unit roundoff 2^-8 (8 significant bits)
+    v = np.random.default_rng(8).standard_normal(10000) * 10.0
+    assert np.max(np.abs(mlp.round_bf16(v) - v) / np.abs(v)) <= 2 ** -8 * (1 + 1e-6)
