@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(256) k_match_fp32(const float2* __restrict__ x
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+        __syncthreads();   // every warp is done with the previous tile's weights
         if (threadIdx.x < BN) ws[threadIdx.x] = (a0 + threadIdx.x < m) ? wscore[a0 + threadIdx.x] : 0.f;
         for (int k0 = 0; k0 < len; k0 += BK) {
 #pragma unroll
