@@ -246,12 +246,13 @@ __global__ void __launch_bounds__(kMlpHidden) k_mlp_infer(InferParams P, const f
 // ([128][K] BF16, canonical K-major core matrices); each layer's weights
 // [N][K] arrive with one bulk copy (pre-arranged in the same layout), the
 // 128 x N product lands in TMEM (N = 256, or 16 for the 3 padded outputs),
-// and 8 warps (two per lane quarter, one column half each) add the bias,
-// apply GELU and write the next layer's input back as BF16.  The next
+// and 16 warps (four per lane quarter, one column quarter each) add the
+// bias (staged in shared memory), apply GELU and write the next layer's input
+// back as BF16.  The next
 // layer's weights are requested as soon as the current products are done,
 // so the copy overlaps the epilogue.  Every wait is bounded.
 constexpr int kTcMlpRows = 128;
-constexpr int kTcMlpWarps = 8;
+constexpr int kTcMlpWarps = 16;
 constexpr int kL0K = 32;                   // the 20 inputs padded to two MMA k-steps
 constexpr int kOutN = 16;                  // the 3 outputs padded to the smallest N
 constexpr int kWBytes = kMlpHidden * kMlpHidden * 2;        // largest weight operand
@@ -277,8 +278,12 @@ __global__ void __launch_bounds__(32 * kTcMlpWarps) k_mlp_infer_tc(TcInferParams
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_wbar, s_mbar;
     __shared__ int s_fail;
+    __shared__ float s_bias[kLayers - 1][kMlpHidden + 4];   // hidden biases, then the outputs' at [2][256..]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lq = warp & 3, half = warp >> 2;
+    const int lq = warp & 3, quarter = warp >> 2;
+    for (int e = tid; e < (kLayers - 1) * kMlpHidden; e += blockDim.x)
+        s_bias[e / kMlpHidden][e % kMlpHidden] = P.b[e / kMlpHidden][e % kMlpHidden];
+    if (tid < kMlpOut) s_bias[kLayers - 2][kMlpHidden + tid] = P.b[kLayers - 1][tid];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(kMlpHidden));
@@ -354,9 +359,9 @@ __global__ void __launch_bounds__(32 * kTcMlpWarps) k_mlp_infer_tc(TcInferParams
             const int row = lq * 32 + lane;
             const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16);
             if (l < kLayers - 1) {
-                // bias + GELU of this warp's 128 columns, written back as the next input
+                // bias + GELU of this warp's 64 columns, written back as the next input
 #pragma unroll 1
-                for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+                for (int c0 = quarter * 64; c0 < quarter * 64 + 64; c0 += 32) {
                     uint32_t v[32];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -369,22 +374,22 @@ __global__ void __launch_bounds__(32 * kTcMlpWarps) k_mlp_infer_tc(TcInferParams
                           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                         : "r"(tl + (uint32_t)c0));
                     asm volatile("tcgen05.wait::ld.sync.aligned;");
-                    const float* bias = P.b[l] + c0;
+                    const float* bias = s_bias[l] + c0;
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         uint4 q;
-                        q.x = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 0]) + __ldg(bias + 8 * g + 0)),
-                                          gelu(__uint_as_float(v[8 * g + 1]) + __ldg(bias + 8 * g + 1)));
-                        q.y = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 2]) + __ldg(bias + 8 * g + 2)),
-                                          gelu(__uint_as_float(v[8 * g + 3]) + __ldg(bias + 8 * g + 3)));
-                        q.z = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 4]) + __ldg(bias + 8 * g + 4)),
-                                          gelu(__uint_as_float(v[8 * g + 5]) + __ldg(bias + 8 * g + 5)));
-                        q.w = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 6]) + __ldg(bias + 8 * g + 6)),
-                                          gelu(__uint_as_float(v[8 * g + 7]) + __ldg(bias + 8 * g + 7)));
+                        q.x = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 0]) + bias[8 * g + 0]),
+                                          gelu(__uint_as_float(v[8 * g + 1]) + bias[8 * g + 1]));
+                        q.y = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 2]) + bias[8 * g + 2]),
+                                          gelu(__uint_as_float(v[8 * g + 3]) + bias[8 * g + 3]));
+                        q.z = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 4]) + bias[8 * g + 4]),
+                                          gelu(__uint_as_float(v[8 * g + 5]) + bias[8 * g + 5]));
+                        q.w = pack_bf16x2(gelu(__uint_as_float(v[8 * g + 6]) + bias[8 * g + 6]),
+                                          gelu(__uint_as_float(v[8 * g + 7]) + bias[8 * g + 7]));
                         *reinterpret_cast<uint4*>(sA + core_off(row, c0 + 8 * g, kMlpHidden / 8)) = q;
                     }
                 }
-            } else if (half == 0) {
+            } else if (quarter == 0) {
                 uint32_t v[16];
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(32 * kTcMlpWarps) k_mlp_infer_tc(TcInferParams
                 if (r0 + row < n)
 #pragma unroll
                     for (int j = 0; j < kMlpOut; ++j)
-                        y[(size_t)(r0 + row) * kMlpOut + j] = __uint_as_float(v[j]) + __ldg(P.b[l] + j);
+                        y[(size_t)(r0 + row) * kMlpOut + j] = __uint_as_float(v[j]) + s_bias[kLayers - 2][kMlpHidden + j];
             }
         }
     }
