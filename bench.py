@@ -235,6 +235,16 @@ def nrmse(truth, maps):
     return out
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu --set full capture of the kernel as it stands, on the same launch
+# shape (the matcher's shape, 65536 fingerprints x 5441 atoms x K = 10, does
+# not depend on the frame count; captured on the 100-frame workload).  An
+# entry must be dropped whenever its kernel changes.
+MEASURED_TRAFFIC = {
+    "k_match_tc": (6705920, "ncu --set full, mrf256_t100 workload, launch shape of the full workload"),
+}
+
+
 # algorithmic bytes (HBM-bound kernels) or flops (ALU-bound) per launch
 def algorithmic_work(kernel, inp):
     w = inp["w"]
@@ -621,7 +631,9 @@ def run_ours(args, dist):
             peak = peaks.get("bf16_tflops_sustained", 1716.1)
             ach = work[1] / (kms * 1e-3) / 1e12
             roof = {"kernel": kname, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "peak_source": "of measured (bf16 sustained)", "traffic": None,
+                    "frac": ach / peak, "peak_source": "of measured (bf16 sustained)",
+                    "traffic": MEASURED_TRAFFIC.get(kname, (None,))[0],
+                    "traffic_source": MEASURED_TRAFFIC.get(kname, (None, None))[1],
                     "algorithmic_flops_per_launch": work[1], "ms_per_launch": kms}
         elif work and work[0] == "alu":
             peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
