@@ -313,6 +313,12 @@ def time_variant(variant, inp, steps, warmup, dist):
     prof = mrf.profile_read()
     mrf.profile_enable(False)
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    # results after warm-up + the timed steps (read before the clock window below)
+    t1, t2, pd, idx = rec.maps()
+    maps = [t.cpu().numpy() for t in (t1, t2, pd)]
+    fallback = float((idx >= 0).float().mean())
+    info = rec.info()
+    alpha = rec.alpha().clone()
     # The timed region is far shorter than the sampler's 200 ms period: keep the
     # same iteration running for a sustained window and sample clocks there too.
     # (Untimed: it only checks the clocks the timed steps ran under.)
@@ -324,11 +330,6 @@ def time_variant(variant, inp, steps, warmup, dist):
                 rec.iterate(1)
             torch.cuda.synchronize()
     clocks = merge_clocks(clk.summary(), clk2.summary(), 1e3 * (time.time() - t0))
-    t1, t2, pd, idx = rec.maps()
-    maps = [t.cpu().numpy() for t in (t1, t2, pd)]
-    fallback = float((idx >= 0).float().mean())
-    info = rec.info()
-    alpha = rec.alpha().clone()
     del rec
     return dict(ms=ms, launches=launches, profile=prof, clocks=clocks,
                 nrmse=nrmse(inp["truth"], maps), info=info, maps=maps, alpha=alpha, fallback=fallback)
