@@ -303,6 +303,20 @@ mrf_status mrf_recon_alpha(mrf_recon r, mrf_c64* alpha, mrf_stream stream);
 mrf_status mrf_recon_info(mrf_recon r, double* a_norm, double* x_scale, double* lam1,
                           double* sigma2, mrf_stream stream);
 mrf_status mrf_recon_destroy(mrf_recon r);
+/* Checkpoint / resume.  A checkpoint is a host byte buffer holding the loop
+ * state the next iteration reads (coefficient images, residual, SVT output
+ * and right singular vectors, maps, cost history, iteration count) and the
+ * scales a and gamma.  checkpoint_size gives its length; checkpoint fills it
+ * (synchronises).  restore loads it into an object created with the same
+ * plan geometry, K, patch/graph parameters, dictionary and data, and with
+ * params.a_norm and params.x_scale set to the saved a and gamma (from
+ * mrf_recon_info of the saved object) so that the scaled data agree;
+ * MRF_EINVAL otherwise.  The graph and lambda1 are rebuilt from the restored
+ * maps; iterations then continue as if uninterrupted (synchronises). */
+mrf_status mrf_recon_checkpoint_size(mrf_recon r, size_t* bytes);
+mrf_status mrf_recon_checkpoint(mrf_recon r, void* buf, size_t bytes, mrf_stream stream);
+mrf_status mrf_recon_restore(mrf_recon r, const void* buf, size_t bytes, mrf_stream stream);
+
 
 /* ------------------------------------------------------------------------
  * Batched serving (not in the paper: a deployment form of Algorithm 1).

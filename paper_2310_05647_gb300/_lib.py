@@ -54,6 +54,9 @@ SIGNATURES = {
     "mrf_mlp_set_engine": (i32, [vp, i32]),
     "mrf_mlp_check": (i32, [vp, vp]),
     "mrf_mlp_training_set": (i32, [vp, vp, vp, vp, vp, i32, i32, vp, i32, vp, vp, vp, vp]),
+    "mrf_recon_checkpoint_size": (i32, [vp, C.POINTER(C.c_size_t)]),
+    "mrf_recon_checkpoint": (i32, [vp, vp, C.c_size_t, vp]),
+    "mrf_recon_restore": (i32, [vp, vp, C.c_size_t, vp]),
     "mrf_recon_create": (i32, [C.POINTER(vp), vp, C.POINTER(ReconParams), vp, i32, vp, vp, vp, i32, vp, vp]),
     "mrf_recon_iter": (i32, [vp, i32, f64p, vp]),
     "mrf_recon_maps": (i32, [vp, vp, vp, vp, vp, vp]),

@@ -367,6 +367,20 @@ class Recon:
         _lib.call("mrf_recon_alpha", self.handle, _ptr(a), _stream())
         return a
 
+    def checkpoint(self):
+        """The loop state as a NumPy uint8 array (see mrf_recon_checkpoint)."""
+        import numpy as np
+        n = C.c_size_t(0)
+        _lib.call("mrf_recon_checkpoint_size", self.handle, C.byref(n))
+        buf = np.empty(n.value, np.uint8)
+        _lib.call("mrf_recon_checkpoint", self.handle, buf.ctypes.data, n.value, _stream())
+        return buf
+
+    def restore(self, buf):
+        import numpy as np
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _lib.call("mrf_recon_restore", self.handle, buf.ctypes.data, buf.size, _stream())
+
     def info(self):
         vals = [C.c_double() for _ in range(4)]
         _lib.call("mrf_recon_info", self.handle, *[C.byref(v) for v in vals], _stream())

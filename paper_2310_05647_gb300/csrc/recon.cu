@@ -17,6 +17,7 @@
 // and the singular values of Q_i(X) (p^2 x T) equal those of Q_i(alpha)
 // (p^2 x K) because Phi has orthonormal columns.
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <vector>
 
@@ -1132,6 +1133,116 @@ extern "C" mrf_status mrf_recon_info(mrf_recon R, double* a_norm, double* x_scal
 
 extern "C" mrf_status mrf_recon_destroy(mrf_recon R) {
     free_recon(R);
+    return MRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume of the loop state.  A checkpoint holds what the next
+// iteration reads and the graph cannot be rebuilt without: the coefficient
+// images, the residual, the SVT output P and its right singular vectors (warm
+// start), the maps, the cost history, the iteration count and the scales a
+// and gamma (a header checks that the restoring object has the same shape and
+// scales).  The graph, sigma^2 and lambda1 are rebuilt from the restored maps.
+// ---------------------------------------------------------------------------
+namespace mrf {
+
+struct CkptHeader {
+    uint32_t magic, version;
+    int32_t N, K, np, pp, kp, m, iters_done, svt_warm, cost_cap, pad;
+    int64_t nr;
+    double a, gamma;
+};
+constexpr uint32_t kCkptMagic = 0x4d524643u;   // "MRFC"
+
+struct CkptPart {
+    void* dev;
+    size_t bytes;
+};
+
+static std::vector<CkptPart> ckpt_parts(mrf_recon_s* R) {
+    const size_t NK = (size_t)R->N * R->K, nr = (size_t)R->plan->T * R->plan->ns;
+    return {{R->alpha, sizeof(float2) * NK},
+            {R->r, sizeof(float2) * nr},
+            {R->P, sizeof(float2) * (size_t)R->np * R->pp * R->K},
+            {R->svt_v, sizeof(float2) * (size_t)R->np * R->svt_kp * R->svt_kp},
+            {R->t1t2, sizeof(float) * 2 * (size_t)R->N},
+            {R->pd, sizeof(float) * (size_t)R->N},
+            {R->idx, sizeof(int) * (size_t)R->N},
+            {R->cost, sizeof(double) * (size_t)R->cost_cap}};
+}
+
+static size_t ckpt_bytes(mrf_recon_s* R) {
+    size_t b = sizeof(CkptHeader);
+    for (const CkptPart& p : ckpt_parts(R)) b += p.bytes;
+    return b;
+}
+
+static CkptHeader ckpt_header(mrf_recon_s* R) {
+    CkptHeader h{};
+    h.magic = kCkptMagic;
+    h.version = 1;
+    h.N = R->N; h.K = R->K; h.np = R->np; h.pp = R->pp; h.kp = R->svt_kp; h.m = R->m;
+    h.iters_done = R->iters_done; h.svt_warm = R->svt_warm; h.cost_cap = R->cost_cap;
+    h.nr = (int64_t)R->plan->T * R->plan->ns;
+    h.a = R->a;
+    h.gamma = R->gamma;
+    return h;
+}
+
+}  // namespace mrf
+
+extern "C" mrf_status mrf_recon_checkpoint_size(mrf_recon R, size_t* bytes) {
+    MRF_REQUIRE(R && bytes, "mrf_recon_checkpoint_size: NULL argument");
+    *bytes = mrf::ckpt_bytes(R);
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_recon_checkpoint(mrf_recon R, void* buf, size_t bytes, mrf_stream stream) {
+    using namespace mrf;
+    MRF_REQUIRE(R && buf, "mrf_recon_checkpoint: NULL argument");
+    MRF_REQUIRE(bytes >= ckpt_bytes(R), "mrf_recon_checkpoint: buffer of %zu bytes, need %zu", bytes,
+                ckpt_bytes(R));
+    cudaStream_t s = as_stream(stream);
+    const CkptHeader h = ckpt_header(R);
+    char* out = static_cast<char*>(buf);
+    std::memcpy(out, &h, sizeof(h));
+    size_t at = sizeof(h);
+    for (const CkptPart& p : ckpt_parts(R)) {
+        MRF_CUDA(cudaMemcpyAsync(out + at, p.dev, p.bytes, cudaMemcpyDeviceToHost, s));
+        at += p.bytes;
+    }
+    MRF_CUDA(cudaStreamSynchronize(s));
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_recon_restore(mrf_recon R, const void* buf, size_t bytes, mrf_stream stream) {
+    using namespace mrf;
+    MRF_REQUIRE(R && buf, "mrf_recon_restore: NULL argument");
+    MRF_REQUIRE(bytes >= sizeof(CkptHeader), "mrf_recon_restore: buffer too small");
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    const CkptHeader mine = ckpt_header(R);
+    MRF_REQUIRE(h.magic == kCkptMagic && h.version == 1, "mrf_recon_restore: not a checkpoint of this library");
+    MRF_REQUIRE(h.N == mine.N && h.K == mine.K && h.np == mine.np && h.pp == mine.pp && h.kp == mine.kp &&
+                    h.m == mine.m && h.nr == mine.nr && h.cost_cap == mine.cost_cap,
+                "mrf_recon_restore: the checkpoint's shape (N %d, K %d, patches %d, atoms %d) differs from this "
+                "object's (N %d, K %d, patches %d, atoms %d)", h.N, h.K, h.np, h.m, mine.N, mine.K, mine.np, mine.m);
+    MRF_REQUIRE(std::fabs(h.a - mine.a) <= 1e-6 * std::fabs(h.a) &&
+                    std::fabs(h.gamma - mine.gamma) <= 1e-6 * std::fabs(h.gamma),
+                "mrf_recon_restore: scales differ (a %g vs %g, gamma %g vs %g); create the object with "
+                "params.a_norm and params.x_scale set to the saved a and gamma", h.a, mine.a, h.gamma, mine.gamma);
+    MRF_REQUIRE(bytes >= ckpt_bytes(R), "mrf_recon_restore: truncated checkpoint");
+    cudaStream_t s = as_stream(stream);
+    const char* in = static_cast<const char*>(buf);
+    size_t at = sizeof(h);
+    for (const CkptPart& p : ckpt_parts(R)) {
+        MRF_CUDA(cudaMemcpyAsync(p.dev, in + at, p.bytes, cudaMemcpyHostToDevice, s));
+        at += p.bytes;
+    }
+    R->iters_done = h.iters_done;
+    R->svt_warm = h.svt_warm;
+    MRF_PROPAGATE(build_graph(R, s));
+    MRF_CUDA(cudaStreamSynchronize(s));
     return MRF_OK;
 }
 
