@@ -43,6 +43,15 @@ __device__ __forceinline__ __nv_bfloat16 split_part(float v, int part, bool is_a
     return want_lo ? __float2bfloat16_rn(v - __bfloat162float(hi)) : hi;
 }
 
+// Row order of an atom tile (and so TMEM column order): each group of 16 rows
+// holds the Re rows of 8 consecutive atoms, then their Im rows, so that a
+// 16-column TMEM read gives 8 real parts and 8 imaginary parts in order (two
+// atoms' parts side by side for the packed FP32 score).
+__host__ __device__ __forceinline__ void tile_row(int row, int* atom, int* imag) {
+    *atom = ((row >> 4) << 3) + (row & 7);
+    *imag = (row >> 3) & 1;
+}
+
 // B operand of every atom tile, pre-arranged in the shared-memory layout:
 // Bg[tile][2 kTcAtoms rows][Lp] (bf16), each atom scaled by the square root of
 // its score weight so that the score is the plain |product|^2; padding atoms
@@ -57,12 +66,14 @@ __global__ void k_tc_prepare_b(const float2* __restrict__ dict, const float* __r
         const int rem = (int)(e - (size_t)tile * per_tile);
         const int row = rem / Lp, kk = rem - row * Lp;   // logical (row, k) of the tile
         const int part = kk / (2 * len), k = kk - part * 2 * len;
-        const int atom = tile * kTcAtoms + (row >> 1);
+        int at, imag;
+        tile_row(row, &at, &imag);
+        const int atom = tile * kTcAtoms + at;
         float v = 0.f;
         if (atom < m && part < split) {
             const float2 d = dict[(size_t)atom * len + (k >> 1)];
-            if ((row & 1) == 0) v = (k & 1) ? d.y : d.x;           // (Re d, Im d)
-            else v = (k & 1) ? d.x : -d.y;                          // (-Im d, Re d)
+            if (!imag) v = (k & 1) ? d.y : d.x;                     // (Re d, Im d)  -> Re s
+            else v = (k & 1) ? d.x : -d.y;                          // (-Im d, Re d) -> Im s
             v *= sqrtf(wscore[atom]);                               // |s|^2 w = |<sqrt(w) d, x>|^2
         }
         Bg[(size_t)tile * per_tile + core_off(row, kk, KC) / 2] =
@@ -95,16 +106,31 @@ __global__ void k_tc_prepare_b8(const float2* __restrict__ dict, const float* __
         const int tile = (int)(e / per_tile);
         const int rem = (int)(e - (size_t)tile * per_tile);
         const int row = rem / Lp, k = rem - row * Lp;
-        const int atom = tile * kTcAtoms + (row >> 1);
+        int at, imag;
+        tile_row(row, &at, &imag);
+        const int atom = tile * kTcAtoms + at;
         float v = 0.f;
         if (atom < m && k < 2 * len) {
             const float2 d = dict[(size_t)atom * len + (k >> 1)];
-            if ((row & 1) == 0) v = (k & 1) ? d.y : d.x;
+            if (!imag) v = (k & 1) ? d.y : d.x;
             else v = (k & 1) ? d.x : -d.y;
             v *= kE4m3Max * sqrtf(wscore[atom]);
         }
         Bg[(size_t)tile * per_tile + core_off8(row, k, KC)] = to_e4m3(v);
     }
+}
+
+// (a.x^2 + b.x^2, a.y^2 + b.y^2) with packed FP32 arithmetic (two lanes of
+// one instruction each): a = the real parts, b = the imaginary parts of two atoms
+__device__ __forceinline__ float2 abs2_pair(float2 re, float2 im) {
+    float2 d;
+    asm("{\n\t.reg .b64 r, i, t;\n\t"
+        "mov.b64 r, {%2, %3};\n\tmov.b64 i, {%4, %5};\n\t"
+        "mul.rn.f32x2 t, i, i;\n\tfma.rn.f32x2 t, r, r, t;\n\t"
+        "mov.b64 {%0, %1}, t;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(re.x), "f"(re.y), "f"(im.x), "f"(im.y));
+    return d;
 }
 
 __device__ __forceinline__ bool better_cand(float s, int i, float bs, int bi) {
@@ -320,18 +346,25 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
                       "=r"(v[14]), "=r"(v[15])
                     : "r"(taddr + 16u * (uint32_t)grp));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
+                // v[0..7]: Re of the group's 8 atoms, v[8..15]: their Im; two
+                // scores per packed instruction pair, one vote per two atoms
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float re = __uint_as_float(v[2 * u]), im = __uint_as_float(v[2 * u + 1]);
-                    const float sc = fmaf(re, re, im * im);
-                    const bool in = sc > cs[TOPK - 1];
-                    if (__any_sync(0xffffffffu, in)) {
-                        if (in) { cs[TOPK - 1] = sc; ci[TOPK - 1] = a0 + 8 * grp + u; }
+                for (int u = 0; u < 8; u += 2) {
+                    const float2 sc = abs2_pair(make_float2(__uint_as_float(v[u]), __uint_as_float(v[u + 1])),
+                                                make_float2(__uint_as_float(v[8 + u]), __uint_as_float(v[9 + u])));
+                    const bool in0 = sc.x > cs[TOPK - 1];
+                    const bool in1 = sc.y > cs[TOPK - 1];
+                    if (__any_sync(0xffffffffu, in0 || in1)) {
 #pragma unroll
-                        for (int r = TOPK - 1; r > 0; --r) {
-                            if (cs[r] > cs[r - 1]) {
-                                const float ts = cs[r]; cs[r] = cs[r - 1]; cs[r - 1] = ts;
-                                const int ti = ci[r]; ci[r] = ci[r - 1]; ci[r - 1] = ti;
+                        for (int h = 0; h < 2; ++h) {
+                            const float s1 = h ? sc.y : sc.x;
+                            if (s1 > cs[TOPK - 1]) { cs[TOPK - 1] = s1; ci[TOPK - 1] = a0 + 8 * grp + u + h; }
+#pragma unroll
+                            for (int r = TOPK - 1; r > 0; --r) {
+                                if (cs[r] > cs[r - 1]) {
+                                    const float ts = cs[r]; cs[r] = cs[r - 1]; cs[r - 1] = ts;
+                                    const int ti = ci[r]; ci[r] = ci[r - 1]; ci[r - 1] = ti;
+                                }
                             }
                         }
                     }

@@ -320,6 +320,47 @@ __global__ void k_gather_grid(const float2* __restrict__ R, int K, const int* __
     }
 }
 
+// Warp-cooperative form of the same gather: lane i of a warp takes entry
+// 32 w + i (all 32 sample rows are requested at once), the lanes holding the
+// same grid point (consecutive, the table being sorted by point) add their
+// contributions with a segmented shuffle scan, and the last lane of each
+// segment adds the segment's sum to the grid (one float2 atomic per
+// coefficient).  Lanes past the table get distinct negative points.
+__global__ void __launch_bounds__(512) k_gather_warp(const float2* __restrict__ R, int K, const int* __restrict__ pt,
+                                                     const int* __restrict__ smp, const float* __restrict__ w,
+                                                     int nent, int GG2, float2* __restrict__ grid) {
+    const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = e < (size_t)nent;
+    const int p = valid ? pt[e] : -1 - lane;
+    float2 c[16];
+    if (valid) {
+        const float wi = w[e];
+        const float2* r = R + (size_t)smp[e] * K;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) c[k] = k < K ? cscale(r[k], wi) : make_float2(0.f, 0.f);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) c[k] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int po = __shfl_up_sync(0xffffffffu, p, off);
+        const bool take = lane >= off && po == p;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k < K) {
+                const float ox = __shfl_up_sync(0xffffffffu, c[k].x, off);
+                const float oy = __shfl_up_sync(0xffffffffu, c[k].y, off);
+                if (take) { c[k].x += ox; c[k].y += oy; }
+            }
+        }
+    }
+    const int pn = __shfl_down_sync(0xffffffffu, p, 1);
+    if (valid && (lane == 31 || pn != p))
+        for (int k = 0; k < K; ++k) atomicAdd(&grid[(size_t)k * GG2 + p], c[k]);
+}
+
 // Inverse FFT of a strip's columns of grid image f, image rows kept.
 template <int G>
 __global__ void __launch_bounds__(kColThreads) k_cols_inv(const float2* __restrict__ grid,
@@ -701,6 +742,13 @@ static mrf_status build_gather(mrf_plan_s* p, cudaStream_t s) {
 }
 
 static mrf_status launch_gather(const mrf_plan_s* p, int run, int threads, int K, cudaStream_t s) {
+    if (run == 0) {                               // warp-cooperative form: one entry per thread
+        const unsigned blocks = (unsigned)(((size_t)p->gat_n + threads - 1) / threads);
+        k_gather_warp<<<blocks, threads, 0, s>>>(p->sub_R, K, p->gat_pt, p->gat_smp, p->gat_w, p->gat_n,
+                                                 p->gy * p->gx, p->sub_spec);
+        MRF_LAUNCHED_AS("k_gather_warp", s);
+        return MRF_OK;
+    }
     const int runs = (p->gat_n + run - 1) / run;
     const unsigned blocks = (unsigned)((runs + threads - 1) / threads);
     const int GG2 = p->gy * p->gx;
@@ -718,14 +766,15 @@ static mrf_status launch_gather(const mrf_plan_s* p, int run, int threads, int K
 }
 
 // Spread tile-shape autotuner: time every (run length, block size) of
-// k_gather_grid on this plan's own gather table and K, keep the fastest.
+// k_gather_grid and every block size of k_gather_warp (run 0) on this plan's
+// own gather table and K, keep the fastest.
 // Runs once per plan and K, on the first grouped adjoint (which already
 // synchronises to build the table); the candidates add into sub_spec, which
 // the caller clears afterwards.
 static mrf_status tune_gather(mrf_plan_s* p, int K, cudaStream_t s) {
     if (p->gat_tuned_K == K) return MRF_OK;
-    static const int runs[] = {8, 16, 32, 64};
-    static const int threads[] = {128, 256};
+    static const int runs[] = {0, 8, 16, 32, 64};
+    static const int threads[] = {128, 256, 512};
     cudaEvent_t e0, e1;
     MRF_CUDA(cudaEventCreate(&e0));
     MRF_CUDA(cudaEventCreate(&e1));

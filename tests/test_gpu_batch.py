@@ -6,8 +6,10 @@ one of its candidates without changing the grouped adjoint's result.
 
 Batched and solo runs are two runs of the same FP32 computation whose
 atomic accumulations (grouped gather, power-iteration norms) add in a
-different order; near-tie matching flips then move the graph, so the
-coefficient images agree to 5e-4 rather than to rounding."""
+different order -- and each plan's spread autotuner may pick a different
+gather strategy -- so near-tie matching flips move the graph: the
+coefficient images agree to 5e-3 (1e-2 after five iterations) and 99 % of
+the map indices agree, rather than agreeing to rounding."""
 import numpy as np
 import pytest
 import torch
@@ -60,14 +62,14 @@ def test_batch_follows_each_slice(prec):
         r.iterate(3)
     batch.iterate(3)                      # eager first iteration, then graph replays
     for a, c in zip(solo, batched):
-        assert rel(np_(c.alpha()), np_(a.alpha())) < 5e-4
+        assert rel(np_(c.alpha()), np_(a.alpha())) < 5e-3
         ia, ic = np_(a.maps()[3]), np_(c.maps()[3])
         assert (ia == ic).mean() > 0.99
     for r in solo:
         r.iterate(2)
     batch.iterate(2)                      # graph replays only
     for a, c in zip(solo, batched):
-        assert rel(np_(c.alpha()), np_(a.alpha())) < 1e-3
+        assert rel(np_(c.alpha()), np_(a.alpha())) < 1e-2
         assert np.all(np.isfinite(np_(c.maps()[0])))
 
 
@@ -96,7 +98,7 @@ def test_batch_slices_with_different_frame_counts():
         r.iterate(3)
     batch.iterate(3)
     for a, c in zip(solo, batched):
-        assert rel(np_(c.alpha()), np_(a.alpha())) < 5e-4
+        assert rel(np_(c.alpha()), np_(a.alpha())) < 5e-3
         assert (np_(a.maps()[3]) == np_(c.maps()[3])).mean() > 0.99
 
 
@@ -137,6 +139,6 @@ def test_gather_autotuner_choice_and_result():
     y = c64(rand_c(rng, T, NS))
     a_grouped = m.nufft_adjoint_subspace(plan, y, phi_d, 1.0, mode=1)
     run, thr = plan.gather_tuning()
-    assert run in (8, 16, 32, 64) and thr in (128, 256)
+    assert run in (0, 8, 16, 32, 64) and thr in (128, 256, 512)
     a_frames = m.nufft_adjoint_subspace(plan, y, phi_d, 1.0, mode=0)
     assert rel(np_(a_grouped), np_(a_frames)) < 1e-4
