@@ -165,37 +165,55 @@ __global__ void __launch_bounds__(1024) k_median_nonzero(const unsigned* __restr
         if (threadIdx.x == 0) *sigma2 = 1.0f;
         return;
     }
-    unsigned vals[2];
-    for (int which = 0; which < 2; ++which) {
-        const unsigned rank = which == 0 ? (unsigned)(total - 1) / 2 : (unsigned)total / 2;
-        unsigned prefix = 0, mask = 0;
-        if (threadIdx.x == 0) s_rank = rank;
-        for (int shift = 24; shift >= 0; shift -= 8) {
-            for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
-            __syncthreads();
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const unsigned b = v[i];
-                if (b == 0u) continue;
-                if ((b & mask) == prefix) atomicAdd(&hist[(b >> shift) & 255u], 1u);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned r = s_rank, c = 0;
-                int bucket = 0;
-                for (; bucket < 255; ++bucket) {
-                    if (c + hist[bucket] > r) break;
-                    c += hist[bucket];
-                }
-                s_rank = r - c;
-                s_prefix = prefix | ((unsigned)bucket << shift);
-            }
-            __syncthreads();
-            prefix = s_prefix;
-            mask |= 255u << shift;
-        }
-        vals[which] = prefix;
+    // the lower middle rank by a 4 x 8-bit radix select; the upper middle
+    // rank (total / 2) is the same value when enough elements equal it, else
+    // the smallest non-zero element above it (one more pass)
+    const unsigned rank = (unsigned)(total - 1) / 2;
+    unsigned prefix = 0, mask = 0;
+    if (threadIdx.x == 0) s_rank = rank;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned b = v[i];
+            if (b == 0u) continue;
+            if ((b & mask) == prefix) atomicAdd(&hist[(b >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned r = s_rank, c = 0;
+            int bucket = 0;
+            for (; bucket < 255; ++bucket) {
+                if (c + hist[bucket] > r) break;
+                c += hist[bucket];
+            }
+            s_rank = r - c;
+            s_prefix = prefix | ((unsigned)bucket << shift);
+        }
+        __syncthreads();
+        prefix = s_prefix;
+        mask |= 255u << shift;
     }
+    const unsigned lo = prefix;                     // value of rank (total - 1) / 2
+    // elements <= lo and the smallest element above lo (non-zero elements only)
+    __shared__ int s_le;
+    __shared__ unsigned s_above;
+    if (threadIdx.x == 0) { s_le = 0; s_above = 0xffffffffu; }
+    __syncthreads();
+    int le = 0;
+    unsigned above = 0xffffffffu;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned b = v[i];
+        if (b == 0u) continue;
+        if (b <= lo) ++le;
+        else above = min(above, b);
+    }
+    atomicAdd(&s_le, le);
+    atomicMin(&s_above, above);
+    __syncthreads();
+    unsigned vals[2];
+    vals[0] = lo;
+    vals[1] = s_le > total / 2 ? lo : s_above;
     if (threadIdx.x == 0)
         *sigma2 = (float)(0.5 * ((double)vals[0] + (double)vals[1]) / (kQScale * kQScale));
 }
@@ -392,20 +410,33 @@ __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __res
 // warm != 0 the sweep starts from A V_prev (the previous iterate's basis, so
 // the columns are nearly orthogonal and few sweeps are needed); the final V
 // is stored back.  The SVD computed is the same either way.
-template <int R, int KP>
-__global__ void __launch_bounds__(128, (R <= 2 && KP <= 10) ? 4 : 1) k_svt(const float2* __restrict__ alpha, PatchGeom g, int K, float tau,
-                                             float2* __restrict__ P, double* __restrict__ nuc,
-                                             float2* __restrict__ Vio, int warm) {
+// sum over the LANES lanes of one patch (a whole warp, or one half of it)
+template <int LANES>
+__device__ __forceinline__ float lane_sum(float v) {
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// LANES = 32: one patch per warp; LANES = 16: two patches per warp (each half
+// a patch, R rows per lane), which halves the shuffle trees and the rotation
+// arithmetic per patch.  A half-warp past the last patch works on zeros, and
+// the sweep loop ends only when neither half needs another sweep.
+template <int R, int KP, int LANES>
+__global__ void __launch_bounds__(128, LANES == 16 ? (R * KP <= 32 ? 3 : 2) : ((R <= 2 && KP <= 10) ? 4 : 1))
+    k_svt(const float2* __restrict__ alpha, PatchGeom g, int K, float tau, float2* __restrict__ P,
+          double* __restrict__ nuc, float2* __restrict__ Vio, int warm) {
     const int lane = threadIdx.x & 31;
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= g.count()) return;
+    const int sl = lane & (LANES - 1), base = lane & ~(LANES - 1);
+    const int j = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / LANES) + lane / LANES;
+    const bool active = j < g.count();
     const int pp = g.p * g.p;
-    const int jy = g.origin(j / g.cnt), jx = g.origin(j % g.cnt);
+    const int jy = active ? g.origin(j / g.cnt) : 0, jx = active ? g.origin(j % g.cnt) : 0;
     float2 a[R][KP];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int row = lane + 32 * r;
-        const bool ok = row < pp;
+        const int row = sl + LANES * r;
+        const bool ok = active && row < pp;
         const int py = ok ? row / g.p : 0, px = ok ? row - py * g.p : 0;
         const float2* src = alpha + ((size_t)(jy + py) * g.n + jx + px) * K;
 #pragma unroll
@@ -413,13 +444,13 @@ __global__ void __launch_bounds__(128, (R <= 2 && KP <= 10) ? 4 : 1) k_svt(const
     }
     float2 v[KP];
 #pragma unroll
-    for (int k = 0; k < KP; ++k) v[k] = make_float2(lane == k ? 1.f : 0.f, 0.f);
-    float2* Vp = Vio ? Vio + (size_t)j * KP * KP : nullptr;
-    if (Vp && warm) {
-        // v = row `lane` of V_prev; a <- a V_prev (row i of V_prev from lane i)
-        if (lane < KP) {
+    for (int k = 0; k < KP; ++k) v[k] = make_float2(sl == k ? 1.f : 0.f, 0.f);
+    float2* Vp = (Vio && active) ? Vio + (size_t)j * KP * KP : nullptr;
+    if (Vio && warm) {
+        // v = row `sl` of V_prev; a <- a V_prev (row i of V_prev from lane base + i)
+        if (Vp && sl < KP) {
 #pragma unroll
-            for (int k = 0; k < KP; ++k) v[k] = Vp[lane * KP + k];
+            for (int k = 0; k < KP; ++k) v[k] = Vp[sl * KP + k];
         }
         float2 na[R][KP];
 #pragma unroll
@@ -431,8 +462,8 @@ __global__ void __launch_bounds__(128, (R <= 2 && KP <= 10) ? 4 : 1) k_svt(const
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
                 float2 vik;
-                vik.x = __shfl_sync(0xffffffffu, v[k].x, i);
-                vik.y = __shfl_sync(0xffffffffu, v[k].y, i);
+                vik.x = __shfl_sync(0xffffffffu, v[k].x, base + i);
+                vik.y = __shfl_sync(0xffffffffu, v[k].y, base + i);
 #pragma unroll
                 for (int r = 0; r < R; ++r) na[r][k] = cadd(na[r][k], cmul(a[r][i], vik));
             }
@@ -466,7 +497,7 @@ __global__ void __launch_bounds__(128, (R <= 2 && KP <= 10) ? 4 : 1) k_svt(const
             for (int r = 0; r < R; ++r) n2[k] += cabs2(a[r][k]);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
+        for (int o = LANES / 2; o > 0; o >>= 1)
 #pragma unroll
             for (int k = 0; k < KP; ++k) n2[k] += __shfl_xor_sync(0xffffffffu, n2[k], o);
         bool rotated = false, large = false;
@@ -492,7 +523,7 @@ __global__ void __launch_bounds__(128, (R <= 2 && KP <= 10) ? 4 : 1) k_svt(const
                 }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
+            for (int o = LANES / 2; o > 0; o >>= 1)
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
                     gr[i] += __shfl_xor_sync(0xffffffffu, gr[i], o);
@@ -543,7 +574,7 @@ __global__ void __launch_bounds__(128, (R <= 2 && KP <= 10) ? 4 : 1) k_svt(const
                 n2[KP - 1] = nf;
             }
         }
-        if (!rotated || !large) break;
+        if (!__any_sync(0xffffffffu, rotated && large)) break;
     }
     float f[KP];
     float nsum = 0.f;
@@ -552,28 +583,28 @@ __global__ void __launch_bounds__(128, (R <= 2 && KP <= 10) ? 4 : 1) k_svt(const
         float s2 = 0.f;
 #pragma unroll
         for (int r = 0; r < R; ++r) s2 += cabs2(a[r][k]);
-        const float sg = sqrtf(warp_sum(s2));
+        const float sg = sqrtf(lane_sum<LANES>(s2));
         nsum += sg;
         f[k] = sg > tau ? (sg - tau) / sg : 0.f;
     }
-    if (nuc && lane == 0) atomicAdd(nuc, (double)nsum);
-    if (Vp && lane < KP) {
+    if (nuc && active && sl == 0) atomicAdd(nuc, (double)nsum);
+    if (Vp && sl < KP) {
 #pragma unroll
-        for (int k = 0; k < KP; ++k) Vp[lane * KP + k] = v[k];
+        for (int k = 0; k < KP; ++k) Vp[sl * KP + k] = v[k];
     }
     if (!P) return;
-    // P[row][k] = sum_j B[row][j] f_j conj(V[k][j]); row k of V lives in lane k
+    // P[row][k] = sum_j B[row][j] f_j conj(V[k][j]); row k of V lives in lane base + k
     for (int k = 0; k < K; ++k) {
         float2 vk[KP];
 #pragma unroll
         for (int jj = 0; jj < KP; ++jj) {
-            vk[jj].x = __shfl_sync(0xffffffffu, v[jj].x, k);
-            vk[jj].y = __shfl_sync(0xffffffffu, v[jj].y, k);
+            vk[jj].x = __shfl_sync(0xffffffffu, v[jj].x, base + k);
+            vk[jj].y = __shfl_sync(0xffffffffu, v[jj].y, base + k);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int row = lane + 32 * r;
-            if (row < pp) {
+            const int row = sl + LANES * r;
+            if (active && row < pp) {
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int jj = 0; jj < KP; ++jj) acc = cadd(acc, cscale(cmulc(a[r][jj], vk[jj]), f[jj]));
@@ -714,26 +745,38 @@ static void free_recon(mrf_recon_s* R) {
 static mrf_status svt(mrf_recon_s* R, const float2* alpha, float2* P, double* nuc, cudaStream_t s) {
     const int K = R->K;
     const int rows = R->pp;
-    const unsigned blocks = (unsigned)((R->np + 3) / 4);
     const float tau = 1.0f / R->prm.beta;
     const int warm = R->svt_warm;
-#define MRF_SVT(RR, KK) k_svt<RR, KK><<<blocks, 128, 0, s>>>(alpha, R->g, K, tau, P, nuc, R->svt_v, warm)
     const int KP = R->svt_kp;
-    if (rows <= 64) {
+    // two patches per warp (16 lanes, R = rows / 16) up to 64 rows and KP <= 12;
+    // one patch per warp otherwise
+    const bool half = rows <= 64 && KP <= 12;
+    const int per_block = half ? 8 : 4;
+    const unsigned blocks = (unsigned)((R->np + per_block - 1) / per_block);
+#define MRF_SVT(RR, KK, LL) k_svt<RR, KK, LL><<<blocks, 128, 0, s>>>(alpha, R->g, K, tau, P, nuc, R->svt_v, warm)
+    if (half && rows <= 32) {
         switch (KP) {
-            case 4: MRF_SVT(2, 4); break;
-            case 8: MRF_SVT(2, 8); break;
-            case 10: MRF_SVT(2, 10); break;
-            case 12: MRF_SVT(2, 12); break;
-            default: MRF_SVT(2, 16); break;
+            case 4: MRF_SVT(2, 4, 16); break;
+            case 8: MRF_SVT(2, 8, 16); break;
+            case 10: MRF_SVT(2, 10, 16); break;
+            default: MRF_SVT(2, 12, 16); break;
         }
+    } else if (half) {
+        switch (KP) {
+            case 4: MRF_SVT(4, 4, 16); break;
+            case 8: MRF_SVT(4, 8, 16); break;
+            case 10: MRF_SVT(4, 10, 16); break;
+            default: MRF_SVT(4, 12, 16); break;
+        }
+    } else if (rows <= 64) {
+        MRF_SVT(2, 16, 32);
     } else {
         switch (KP) {
-            case 4: MRF_SVT(4, 4); break;
-            case 8: MRF_SVT(4, 8); break;
-            case 10: MRF_SVT(4, 10); break;
-            case 12: MRF_SVT(4, 12); break;
-            default: MRF_SVT(4, 16); break;
+            case 4: MRF_SVT(4, 4, 32); break;
+            case 8: MRF_SVT(4, 8, 32); break;
+            case 10: MRF_SVT(4, 10, 32); break;
+            case 12: MRF_SVT(4, 12, 32); break;
+            default: MRF_SVT(4, 16, 32); break;
         }
     }
 #undef MRF_SVT

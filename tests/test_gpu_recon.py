@@ -90,8 +90,12 @@ def test_iterations_match_oracle(prob, mode):
         assert rel(a_g, a_o) < 1e-4 * (it + 1), it
         assert cost == pytest.approx(o.cost[-1], rel=1e-4 * (it + 1))
         idx = np_(r.maps()[3]).ravel()
-        assert (idx == o.maps[0].ravel()).mean() > 0.99
-        assert r.info()["lam1"] == pytest.approx(o.lam1, rel=1e-3)
+        agree = (idx == o.maps[0].ravel()).mean()
+        assert agree > 0.99
+        # lambda1 = lambda1^0 / max(L) is a discrete function of the matched maps
+        # (through the kNN graph): a near-tie pick of one voxel can change the
+        # largest degree by up to one edge weight
+        assert r.info()["lam1"] == pytest.approx(o.lam1, rel=1e-3 if agree == 1.0 else 3e-2)
 
 
 def test_literal_flags(prob):
