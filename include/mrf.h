@@ -263,9 +263,13 @@ enum {
     MRF_RECON_LITERAL_LAMBDA1 = 2,  /* lambda1 = lambda1^0 * max(L) as printed */
     MRF_RECON_NO_COST = 4,          /* skip the cost evaluation */
     MRF_RECON_GROUPED = 8,          /* data term through the grouped subspace operator */
-    MRF_RECON_LEARNED = 16          /* maps from the learned matcher (params.mlp, K = 10); fingerprints
+    MRF_RECON_LEARNED = 16,         /* maps from the learned matcher (params.mlp, K = 10); fingerprints
                                        it maps outside the dictionary's T1/T2 box, or to T1 < T2, are
                                        matched exhaustively instead (needs a tensor-core precision) */
+    MRF_RECON_SERIAL = 32           /* run an iteration's steps one after another on the caller's
+                                       stream (default: the forward operator, the SVT and matching +
+                                       graph rebuild run concurrently on internal streams, joined into
+                                       the caller's stream; same results) */
 };
 
 typedef struct {

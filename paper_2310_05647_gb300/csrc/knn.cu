@@ -337,23 +337,31 @@ __global__ void __launch_bounds__(kKnThreads + 32) k_knn_tc(const int* __restric
                       "=r"(v[14]), "=r"(v[15])
                     : "r"(taddr + 16u * (uint32_t)grp));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
+                // one vote per two candidates; the pair's insertions stay
+                // predicated per lane and in index order
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int q = 8 * grp + u;
-                    const int j = jb + q;
-                    const int ch = __float2int_rn(__uint_as_float(v[2 * u]));
-                    const int cl = __float2int_rn(__uint_as_float(v[2 * u + 1]));
-                    const unsigned nb = __shfl_sync(0xffffffffu, nbl, q);
-                    unsigned d = nq + nb - 2u * (unsigned)(32 * ch + cl);
-                    if (j >= ce || j == qrow) d = 0xffffffffu;
-                    const bool in = d < bd[KN - 1];
-                    if (__any_sync(0xffffffffu, in)) {
-                        if (in) { bd[KN - 1] = d; bj[KN - 1] = j; }
+                for (int u = 0; u < 8; u += 2) {
+                    unsigned d[2];
 #pragma unroll
-                        for (int r = KN - 1; r > 0; --r) {
-                            if (bd[r] < bd[r - 1]) {
-                                const unsigned td = bd[r]; bd[r] = bd[r - 1]; bd[r - 1] = td;
-                                const int tj = bj[r]; bj[r] = bj[r - 1]; bj[r - 1] = tj;
+                    for (int h = 0; h < 2; ++h) {
+                        const int q = 8 * grp + u + h;
+                        const int j = jb + q;
+                        const int ch = __float2int_rn(__uint_as_float(v[2 * (u + h)]));
+                        const int cl = __float2int_rn(__uint_as_float(v[2 * (u + h) + 1]));
+                        const unsigned nb = __shfl_sync(0xffffffffu, nbl, q);
+                        d[h] = nq + nb - 2u * (unsigned)(32 * ch + cl);
+                        if (j >= ce || j == qrow) d[h] = 0xffffffffu;
+                    }
+                    if (__any_sync(0xffffffffu, d[0] < bd[KN - 1] || d[1] < bd[KN - 1])) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (d[h] < bd[KN - 1]) { bd[KN - 1] = d[h]; bj[KN - 1] = jb + 8 * grp + u + h; }
+#pragma unroll
+                            for (int r = KN - 1; r > 0; --r) {
+                                if (bd[r] < bd[r - 1]) {
+                                    const unsigned td = bd[r]; bd[r] = bd[r - 1]; bd[r - 1] = td;
+                                    const int tj = bj[r]; bj[r] = bj[r - 1]; bj[r - 1] = tj;
+                                }
                             }
                         }
                     }

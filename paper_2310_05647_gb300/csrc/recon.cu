@@ -320,17 +320,97 @@ __global__ void k_lambda(const float* __restrict__ lmax, float lam1_0, int liter
 
 // (Q(X) L)_j = deg_j Q_j - 1/2 sum_{i in N(j)} w_ji Q_i - 1/2 sum_{i: j in N(i)} w_ij Q_i,
 // written per patch (QL nullable) and/or accumulated into Tr(Q L Q^H).
-// One block per patch j, each thread up to kGbElems of its p x p x K
-// coefficients (consecutive threads read consecutive coefficients of a
-// neighbour's patch rows).  The neighbour list (forward kNN entries, then
-// the reverse list) is staged in shared memory kGbChunk entries at a time as
-// (offset of the neighbour patch's first coefficient, w / 2), so the inner
-// loop is one gather and two FMAs per coefficient and neighbour.
+// One block per patch j; each thread takes kGbPairs pairs of consecutive
+// coefficients of its p x p x K block (K even: a pair is one aligned 16-byte
+// load from every neighbour patch; consecutive threads read consecutive
+// pairs of a neighbour's patch rows).  The neighbour list (forward kNN
+// entries, then the reverse list) is staged in shared memory kGbChunk entries
+// at a time as (offset of the neighbour patch's first coefficient, w / 2), so
+// the inner loop is one gather and four FMAs per pair and neighbour.
 constexpr int kGbThreads = 128;
-constexpr int kGbElems = 8;
+constexpr int kGbPairs = 4;
 constexpr int kGbChunk = 256;
 
 __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __restrict__ alpha, PatchGeom g, int K,
+                                                             const int* __restrict__ nbr,
+                                                             const float* __restrict__ w, int knn,
+                                                             const int* __restrict__ roff,
+                                                             const int* __restrict__ rsrc,
+                                                             const float* __restrict__ rw,
+                                                             const float* __restrict__ deg,
+                                                             float2* __restrict__ QL, double* __restrict__ trace) {
+    __shared__ int s_off[kGbChunk];
+    __shared__ float s_w[kGbChunk];
+    const int j = blockIdx.x;
+    const int pK = g.p * K;
+    const int ne = g.p * pK;                       // even: K is even
+    const int jy = g.origin(j / g.cnt), jx = g.origin(j % g.cnt);
+    const float dj = deg[j];
+    const int rb = roff[j], re = roff[j + 1];
+    const int nq = knn + (re - rb);
+    double tr = 0.0;
+    for (int e0 = 0; e0 < ne; e0 += 2 * kGbThreads * kGbPairs) {
+        int off[kGbPairs];
+        float4 a[kGbPairs], v[kGbPairs];
+#pragma unroll
+        for (int u = 0; u < kGbPairs; ++u) {
+            const int e = e0 + 2 * (threadIdx.x + u * kGbThreads);
+            const int py = e / pK, rem = e - py * pK;      // rem = px * K + k, even
+            off[u] = e < ne ? py * g.n * K + rem : -1;
+            a[u] = e < ne ? *reinterpret_cast<const float4*>(alpha + ((size_t)jy * g.n + jx) * K + off[u])
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[u] = make_float4(a[u].x * dj, a[u].y * dj, a[u].z * dj, a[u].w * dj);
+        }
+        for (int c0 = 0; c0 < nq; c0 += kGbChunk) {
+            const int cn = min(kGbChunk, nq - c0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < cn; t += kGbThreads) {
+                const int q = c0 + t;
+                int i;
+                float wq;
+                if (q < knn) { i = nbr[(size_t)j * knn + q]; wq = w[(size_t)j * knn + q]; }
+                else { i = rsrc[rb + q - knn]; wq = rw[rb + q - knn]; }
+                s_off[t] = (g.origin(i / g.cnt) * g.n + g.origin(i % g.cnt)) * K;
+                s_w[t] = 0.5f * wq;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int t = 0; t < cn; ++t) {
+                const float2* src = alpha + s_off[t];
+                const float wt = s_w[t];
+#pragma unroll
+                for (int u = 0; u < kGbPairs; ++u) {
+                    if (off[u] >= 0) {
+                        const float4 b = *reinterpret_cast<const float4*>(src + off[u]);
+                        v[u].x -= wt * b.x;
+                        v[u].y -= wt * b.y;
+                        v[u].z -= wt * b.z;
+                        v[u].w -= wt * b.w;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kGbPairs; ++u) {
+            if (off[u] < 0) continue;
+            const int e = e0 + 2 * (threadIdx.x + u * kGbThreads);
+            if (QL) *reinterpret_cast<float4*>(QL + (size_t)j * ne + e) = v[u];
+            if (trace)
+                tr += (double)a[u].x * v[u].x + (double)a[u].y * v[u].y + (double)a[u].z * v[u].z +
+                      (double)a[u].w * v[u].w;
+        }
+    }
+    if (trace) {
+        tr = block_sum(tr);
+        if (threadIdx.x == 0) atomicAdd(trace, tr);
+    }
+}
+
+// Odd K: the same computation one coefficient at a time (the pair loads of
+// k_graph_blocks need K even for alignment and for pairs within a voxel).
+constexpr int kGbElems = 8;
+
+__global__ void __launch_bounds__(kGbThreads) k_graph_blocks_odd(const float2* __restrict__ alpha, PatchGeom g, int K,
                                                              const int* __restrict__ nbr,
                                                              const float* __restrict__ w, int knn,
                                                              const int* __restrict__ roff,
@@ -724,6 +804,9 @@ struct mrf_recon_s {
     int *fb_list = nullptr, *fb_count = nullptr;
     float2* fb_x = nullptr;
     mrf::TcSlice* fb_table = nullptr;
+    // concurrency inside one iteration: two side streams and their events
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t ev[5] = {};
     std::vector<void*> owned;
 };
 
@@ -738,6 +821,10 @@ static mrf_status dalloc(mrf_recon_s* R, T** p, size_t n) {
 
 static void free_recon(mrf_recon_s* R) {
     if (!R) return;
+    for (cudaStream_t t : R->side)
+        if (t) cudaStreamDestroy(t);
+    for (cudaEvent_t e : R->ev)
+        if (e) cudaEventDestroy(e);
     for (void* p : R->owned) cudaFree(p);
     delete R;
 }
@@ -896,8 +983,12 @@ static mrf_status learned_maps(mrf_recon_s* R, cudaStream_t s) {
 }
 
 static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s) {
-    k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc, R->rw,
-                                         R->deg, QL, trace);
+    if (R->K % 2 == 0)
+        k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc,
+                                                    R->rw, R->deg, QL, trace);
+    else
+        k_graph_blocks_odd<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff,
+                                                        R->rsrc, R->rw, R->deg, QL, trace);
     MRF_LAUNCHED_AS("k_graph_blocks", s);
     return MRF_OK;
 }
@@ -928,12 +1019,74 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
     return MRF_OK;
 }
 
-// one iteration of the loop body (stream-ordered, capturable)
+// One iteration of the loop body, with its independent steps on three
+// streams (stream-ordered, ends joined into s):
+//   s:       adjoint -> (join) X update -> forward -> |r|^2 -> (join) cost
+//   side[1]: graph term Q(X)L (needs the previous graph) ............ ^ join
+//   side[0]:                     SVT of the new iterate -> P, sum sigma
+//   side[1]:                     cost trace -> matching -> graph rebuild
+// The forward operator, the SVT and the matching all read only the new
+// iterate; the graph rebuild only the new maps; the accumulators they add
+// to are distinct slots.
 static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
-    MRF_PROPAGATE(iteration_pre(R, it, !(R->prm.flags & MRF_RECON_NO_COST), s));
-    if (R->prm.flags & MRF_RECON_LEARNED) MRF_PROPAGATE(learned_maps(R, s));
-    else MRF_PROPAGATE(match_maps(R, s));
-    MRF_PROPAGATE(build_graph(R, s));
+    const bool cost = !(R->prm.flags & MRF_RECON_NO_COST);
+    if (R->prm.flags & MRF_RECON_SERIAL) {
+        // the same steps one after another on s
+        MRF_PROPAGATE(iteration_pre(R, it, cost, s));
+        if (R->prm.flags & MRF_RECON_LEARNED) MRF_PROPAGATE(learned_maps(R, s));
+        else MRF_PROPAGATE(match_maps(R, s));
+        return build_graph(R, s);
+    }
+    const size_t NK = (size_t)R->N * R->K;
+    const float inv_a = (float)(1.0 / R->a);
+    cudaStream_t sb = R->side[0], sc = R->side[1];
+    // (profiler marks after each cross-stream wait: a side stream's next kernel
+    // is charged from the point its inputs are ready)
+    auto mark = [](cudaStream_t t) { mrf_profile_mark(reinterpret_cast<mrf_stream>(t)); };
+    MRF_CUDA(cudaEventRecord(R->ev[0], s));
+    MRF_CUDA(cudaStreamWaitEvent(sc, R->ev[0], 0));
+    mark(sc);
+    MRF_PROPAGATE(graph_pass(R, R->QL, nullptr, sc));
+    MRF_CUDA(cudaEventRecord(R->ev[1], sc));
+    MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, s));
+    MRF_CUDA(cudaStreamWaitEvent(s, R->ev[1], 0));
+    mark(s);
+    const float c = R->prm.mu * R->prm.lam2 * R->prm.beta;
+    k_xupdate<<<(unsigned)((NK + 255) / 256), 256, 0, s>>>(
+        R->alpha, R->grad, R->QL, R->P, R->g, R->K, R->prm.mu, c, R->scal + 2,
+        (R->prm.flags & MRF_RECON_LITERAL_XUPDATE) ? 1 : 0, nullptr);
+    MRF_LAUNCHED_AS("k_xupdate", s);
+    if (cost) MRF_CUDA(cudaMemsetAsync(R->acc, 0, 3 * sizeof(double), s));
+    MRF_CUDA(cudaEventRecord(R->ev[2], s));                  // the new iterate
+    MRF_CUDA(cudaStreamWaitEvent(sb, R->ev[2], 0));
+    MRF_CUDA(cudaStreamWaitEvent(sc, R->ev[2], 0));
+    mark(sb);
+    mark(sc);
+    MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, sb));
+    MRF_CUDA(cudaEventRecord(R->ev[3], sb));
+    if (cost) {
+        MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, sc));   // trace with the current graph
+        // the cost weighs the trace with this iteration's lambda1, which the
+        // graph rebuild below replaces: keep a copy for k_cost
+        MRF_CUDA(cudaMemcpyAsync(R->scal + 4, R->scal + 2, sizeof(float), cudaMemcpyDeviceToDevice, sc));
+    }
+    if (R->prm.flags & MRF_RECON_LEARNED) MRF_PROPAGATE(learned_maps(R, sc));
+    else MRF_PROPAGATE(match_maps(R, sc));
+    MRF_PROPAGATE(build_graph(R, sc));
+    MRF_CUDA(cudaEventRecord(R->ev[4], sc));
+    MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, s));
+    if (cost) {
+        const size_t nr = (size_t)R->plan->T * R->plan->ns;
+        k_norm2_acc<<<nblk(nr), 256, 0, s>>>(R->r, nr, R->acc + 0);
+        MRF_LAUNCHED_AS("k_norm2_acc", s);
+    }
+    MRF_CUDA(cudaStreamWaitEvent(s, R->ev[3], 0));
+    MRF_CUDA(cudaStreamWaitEvent(s, R->ev[4], 0));
+    mark(s);
+    if (cost) {
+        k_cost<<<1, 1, 0, s>>>(R->acc, R->scal + 4, R->prm.lam2, R->cost + (it % R->cost_cap));
+        MRF_LAUNCHED_AS("k_cost", s);
+    }
     return MRF_OK;
 }
 
@@ -1105,6 +1258,15 @@ extern "C" mrf_status mrf_recon_create(mrf_recon* out, mrf_plan plan, const mrf_
     auto* R = new mrf_recon_s();
     R->plan = plan;
     R->prm = *prm;
+    for (cudaStream_t& t : R->side)
+        if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess) t = nullptr;
+    for (cudaEvent_t& e : R->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) e = nullptr;
+    if (!R->side[0] || !R->side[1] || !R->ev[0] || !R->ev[1] || !R->ev[2] || !R->ev[3] || !R->ev[4]) {
+        free_recon(R);
+        set_error("mrf_recon_create: could not create the loop's streams and events");
+        return MRF_ECUDA;
+    }
     R->K = K;
     R->m = m;
     R->N = plan->nx * plan->ny;

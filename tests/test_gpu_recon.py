@@ -37,12 +37,12 @@ def prob():
     return problem()
 
 
-def gpu_recon(pr, mode=0, **kw):
+def gpu_recon(pr, mode=0, extra_flags=0, **kw):
     m = mrf()
     plan = m.nufft_plan(pr["n"], pr["n"], f32(pr["k"]))
     dc = pr["D"] @ pr["phi"]
     n2 = np.sum(np.abs(pr["D"]) ** 2, axis=1)
-    params = m.ReconParams(patch=8, stride=4, knn=4, flags=(8 if mode else 0), **kw)
+    params = m.ReconParams(patch=8, stride=4, knn=4, flags=(8 if mode else 0) | extra_flags, **kw)
     return m.Recon(plan, params, c64(pr["phi"]), c64(dc), f32(n2), f32(pr["lut"]), c64(pr["b"]))
 
 
@@ -87,7 +87,9 @@ def test_iterations_match_oracle(prob, mode):
         o.iterate()
         cost = r.iterate(1, costs=True)[0]
         a_g, a_o = np_(r.alpha()), alpha_of(o)
-        assert rel(a_g, a_o) < 1e-4 * (it + 1), it
+        # the grouped adjoint adds its gather with float atomics in a run-dependent
+        # order; near-tie matching amplifies that through the graph
+        assert rel(a_g, a_o) < (3e-4 if mode else 1e-4) * (it + 1), it
         assert cost == pytest.approx(o.cost[-1], rel=1e-4 * (it + 1))
         idx = np_(r.maps()[3]).ravel()
         agree = (idx == o.maps[0].ravel()).mean()
@@ -138,3 +140,28 @@ def test_recon_rejects_bad_params(prob):
         params = m.ReconParams(**{**dict(patch=8, stride=4, knn=4), **bad})
         with pytest.raises(m.MRFError):
             m.Recon(plan, params, c64(prob["phi"]), c64(dc), f32(n2), f32(prob["lut"]), c64(prob["b"]))
+
+
+def test_odd_rank_iteration_matches_oracle():
+    """K = 5: the graph term's odd-K path (pair loads need K even)."""
+    pr = problem(K=5)
+    o = oracle_recon(pr)
+    r = gpu_recon(pr, 1, a_norm=o.a, x_scale=o.gamma)
+    o.iterate()
+    r.iterate(1)
+    assert rel(np_(r.alpha()), alpha_of(o)) < 1e-4
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_serial_and_concurrent_iterations_agree(prob, mode):
+    """MRF_RECON_SERIAL runs the same steps on one stream; the default runs
+    the forward operator, the SVT and matching + graph rebuild concurrently.
+    Two runs agree up to the order of the grouped gather's atomic additions,
+    amplified through near-tie matching as in the oracle parity test."""
+    o = oracle_recon(prob)
+    rs = gpu_recon(prob, mode, a_norm=o.a, x_scale=o.gamma)
+    rc = gpu_recon(prob, mode, extra_flags=32, a_norm=o.a, x_scale=o.gamma)
+    cs = rs.iterate(3, costs=True)
+    cc = rc.iterate(3, costs=True)
+    assert rel(np_(rc.alpha()), np_(rs.alpha())) < 1e-3
+    np.testing.assert_allclose(cc, cs, rtol=1e-4)
