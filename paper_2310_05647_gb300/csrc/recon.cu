@@ -320,97 +320,19 @@ __global__ void k_lambda(const float* __restrict__ lmax, float lam1_0, int liter
 
 // (Q(X) L)_j = deg_j Q_j - 1/2 sum_{i in N(j)} w_ji Q_i - 1/2 sum_{i: j in N(i)} w_ij Q_i,
 // written per patch (QL nullable) and/or accumulated into Tr(Q L Q^H).
-// One block per patch j; each thread takes kGbPairs pairs of consecutive
-// coefficients of its p x p x K block (K even: a pair is one aligned 16-byte
-// load from every neighbour patch; consecutive threads read consecutive
-// pairs of a neighbour's patch rows).  The neighbour list (forward kNN
-// entries, then the reverse list) is staged in shared memory kGbChunk entries
-// at a time as (offset of the neighbour patch's first coefficient, w / 2), so
-// the inner loop is one gather and four FMAs per pair and neighbour.
+// One block per patch j, each thread up to kGbElems of its p x p x K
+// coefficients (consecutive threads read consecutive coefficients of a
+// neighbour's patch rows).  The neighbour list (forward kNN entries, then
+// the reverse list) is staged in shared memory kGbChunk entries at a time as
+// (offset of the neighbour patch's first coefficient, w / 2), so the inner
+// loop is one gather and two FMAs per coefficient and neighbour.  (Pairs of
+// coefficients per 16-byte load halve the loads but leave fewer in flight
+// per warp; measured slower on this latency-bound kernel.)
 constexpr int kGbThreads = 128;
-constexpr int kGbPairs = 4;
 constexpr int kGbChunk = 256;
-
-__global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __restrict__ alpha, PatchGeom g, int K,
-                                                             const int* __restrict__ nbr,
-                                                             const float* __restrict__ w, int knn,
-                                                             const int* __restrict__ roff,
-                                                             const int* __restrict__ rsrc,
-                                                             const float* __restrict__ rw,
-                                                             const float* __restrict__ deg,
-                                                             float2* __restrict__ QL, double* __restrict__ trace) {
-    __shared__ int s_off[kGbChunk];
-    __shared__ float s_w[kGbChunk];
-    const int j = blockIdx.x;
-    const int pK = g.p * K;
-    const int ne = g.p * pK;                       // even: K is even
-    const int jy = g.origin(j / g.cnt), jx = g.origin(j % g.cnt);
-    const float dj = deg[j];
-    const int rb = roff[j], re = roff[j + 1];
-    const int nq = knn + (re - rb);
-    double tr = 0.0;
-    for (int e0 = 0; e0 < ne; e0 += 2 * kGbThreads * kGbPairs) {
-        int off[kGbPairs];
-        float4 a[kGbPairs], v[kGbPairs];
-#pragma unroll
-        for (int u = 0; u < kGbPairs; ++u) {
-            const int e = e0 + 2 * (threadIdx.x + u * kGbThreads);
-            const int py = e / pK, rem = e - py * pK;      // rem = px * K + k, even
-            off[u] = e < ne ? py * g.n * K + rem : -1;
-            a[u] = e < ne ? *reinterpret_cast<const float4*>(alpha + ((size_t)jy * g.n + jx) * K + off[u])
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
-            v[u] = make_float4(a[u].x * dj, a[u].y * dj, a[u].z * dj, a[u].w * dj);
-        }
-        for (int c0 = 0; c0 < nq; c0 += kGbChunk) {
-            const int cn = min(kGbChunk, nq - c0);
-            __syncthreads();
-            for (int t = threadIdx.x; t < cn; t += kGbThreads) {
-                const int q = c0 + t;
-                int i;
-                float wq;
-                if (q < knn) { i = nbr[(size_t)j * knn + q]; wq = w[(size_t)j * knn + q]; }
-                else { i = rsrc[rb + q - knn]; wq = rw[rb + q - knn]; }
-                s_off[t] = (g.origin(i / g.cnt) * g.n + g.origin(i % g.cnt)) * K;
-                s_w[t] = 0.5f * wq;
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int t = 0; t < cn; ++t) {
-                const float2* src = alpha + s_off[t];
-                const float wt = s_w[t];
-#pragma unroll
-                for (int u = 0; u < kGbPairs; ++u) {
-                    if (off[u] >= 0) {
-                        const float4 b = *reinterpret_cast<const float4*>(src + off[u]);
-                        v[u].x -= wt * b.x;
-                        v[u].y -= wt * b.y;
-                        v[u].z -= wt * b.z;
-                        v[u].w -= wt * b.w;
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kGbPairs; ++u) {
-            if (off[u] < 0) continue;
-            const int e = e0 + 2 * (threadIdx.x + u * kGbThreads);
-            if (QL) *reinterpret_cast<float4*>(QL + (size_t)j * ne + e) = v[u];
-            if (trace)
-                tr += (double)a[u].x * v[u].x + (double)a[u].y * v[u].y + (double)a[u].z * v[u].z +
-                      (double)a[u].w * v[u].w;
-        }
-    }
-    if (trace) {
-        tr = block_sum(tr);
-        if (threadIdx.x == 0) atomicAdd(trace, tr);
-    }
-}
-
-// Odd K: the same computation one coefficient at a time (the pair loads of
-// k_graph_blocks need K even for alignment and for pairs within a voxel).
 constexpr int kGbElems = 8;
 
-__global__ void __launch_bounds__(kGbThreads) k_graph_blocks_odd(const float2* __restrict__ alpha, PatchGeom g, int K,
+__global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __restrict__ alpha, PatchGeom g, int K,
                                                              const int* __restrict__ nbr,
                                                              const float* __restrict__ w, int knn,
                                                              const int* __restrict__ roff,
@@ -983,12 +905,8 @@ static mrf_status learned_maps(mrf_recon_s* R, cudaStream_t s) {
 }
 
 static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s) {
-    if (R->K % 2 == 0)
-        k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc,
-                                                    R->rw, R->deg, QL, trace);
-    else
-        k_graph_blocks_odd<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff,
-                                                        R->rsrc, R->rw, R->deg, QL, trace);
+    k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc,
+                                                R->rw, R->deg, QL, trace);
     MRF_LAUNCHED_AS("k_graph_blocks", s);
     return MRF_OK;
 }

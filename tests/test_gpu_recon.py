@@ -81,8 +81,14 @@ def test_init_scales_and_maps(prob, mode):
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_iterations_match_oracle(prob, mode):
+    """Coefficient images, cost, maps and lambda1 per iteration.  The graph and
+    lambda1 an iteration uses come from the previous maps; when those maps
+    differ from the oracle's at a near-tie voxel, lambda1 (a discrete function
+    of the maps through the kNN graph) and the cost's lambda1 Tr term move
+    with it, so those bounds widen in that case."""
     o = oracle_recon(prob)
     r = gpu_recon(prob, mode, a_norm=o.a, x_scale=o.gamma)
+    prev = (np_(r.maps()[3]).ravel() == o.maps[0].ravel()).mean()
     for it in range(3):
         o.iterate()
         cost = r.iterate(1, costs=True)[0]
@@ -90,14 +96,12 @@ def test_iterations_match_oracle(prob, mode):
         # the grouped adjoint adds its gather with float atomics in a run-dependent
         # order; near-tie matching amplifies that through the graph
         assert rel(a_g, a_o) < (3e-4 if mode else 1e-4) * (it + 1), it
-        assert cost == pytest.approx(o.cost[-1], rel=1e-4 * (it + 1))
+        assert cost == pytest.approx(o.cost[-1], rel=1e-4 * (it + 1) if prev == 1.0 else 5e-3)
         idx = np_(r.maps()[3]).ravel()
         agree = (idx == o.maps[0].ravel()).mean()
         assert agree > 0.99
-        # lambda1 = lambda1^0 / max(L) is a discrete function of the matched maps
-        # (through the kNN graph): a near-tie pick of one voxel can change the
-        # largest degree by up to one edge weight
         assert r.info()["lam1"] == pytest.approx(o.lam1, rel=1e-3 if agree == 1.0 else 3e-2)
+        prev = agree
 
 
 def test_literal_flags(prob):
@@ -143,7 +147,7 @@ def test_recon_rejects_bad_params(prob):
 
 
 def test_odd_rank_iteration_matches_oracle():
-    """K = 5: the graph term's odd-K path (pair loads need K even)."""
+    """An odd rank (K = 5) through the whole loop."""
     pr = problem(K=5)
     o = oracle_recon(pr)
     r = gpu_recon(pr, 1, a_norm=o.a, x_scale=o.gamma)
