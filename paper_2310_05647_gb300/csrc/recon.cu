@@ -941,8 +941,8 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
 // streams (stream-ordered, ends joined into s):
 //   s:       adjoint -> (join) X update -> forward -> |r|^2 -> (join) cost
 //   side[1]: graph term Q(X)L (needs the previous graph) ............ ^ join
-//   side[0]:                     SVT of the new iterate -> P, sum sigma
-//   side[1]:                     cost trace -> matching -> graph rebuild
+//   side[0]:                     SVT of the new iterate -> P, sum sigma -> cost trace
+//   side[1]:                     matching -> (wait for the trace) graph rebuild
 // The forward operator, the SVT and the matching all read only the new
 // iterate; the graph rebuild only the new maps; the accumulators they add
 // to are distinct slots.
@@ -981,15 +981,18 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     mark(sb);
     mark(sc);
     MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, sb));
-    MRF_CUDA(cudaEventRecord(R->ev[3], sb));
     if (cost) {
-        MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, sc));   // trace with the current graph
+        MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, sb));   // trace with the current graph
         // the cost weighs the trace with this iteration's lambda1, which the
-        // graph rebuild below replaces: keep a copy for k_cost
-        MRF_CUDA(cudaMemcpyAsync(R->scal + 4, R->scal + 2, sizeof(float), cudaMemcpyDeviceToDevice, sc));
+        // graph rebuild replaces: keep a copy for k_cost
+        MRF_CUDA(cudaMemcpyAsync(R->scal + 4, R->scal + 2, sizeof(float), cudaMemcpyDeviceToDevice, sb));
     }
+    MRF_CUDA(cudaEventRecord(R->ev[3], sb));
     if (R->prm.flags & MRF_RECON_LEARNED) MRF_PROPAGATE(learned_maps(R, sc));
     else MRF_PROPAGATE(match_maps(R, sc));
+    // the rebuild replaces the graph and lambda1 the trace reads
+    MRF_CUDA(cudaStreamWaitEvent(sc, R->ev[3], 0));
+    mark(sc);
     MRF_PROPAGATE(build_graph(R, sc));
     MRF_CUDA(cudaEventRecord(R->ev[4], sc));
     MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, s));

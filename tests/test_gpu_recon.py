@@ -37,9 +37,9 @@ def prob():
     return problem()
 
 
-def gpu_recon(pr, mode=0, extra_flags=0, **kw):
+def gpu_recon(pr, mode=0, extra_flags=0, plan=None, **kw):
     m = mrf()
-    plan = m.nufft_plan(pr["n"], pr["n"], f32(pr["k"]))
+    plan = plan if plan is not None else m.nufft_plan(pr["n"], pr["n"], f32(pr["k"]))
     dc = pr["D"] @ pr["phi"]
     n2 = np.sum(np.abs(pr["D"]) ** 2, axis=1)
     params = m.ReconParams(patch=8, stride=4, knn=4, flags=(8 if mode else 0) | extra_flags, **kw)
@@ -160,12 +160,21 @@ def test_odd_rank_iteration_matches_oracle():
 def test_serial_and_concurrent_iterations_agree(prob, mode):
     """MRF_RECON_SERIAL runs the same steps on one stream; the default runs
     the forward operator, the SVT and matching + graph rebuild concurrently.
-    Two runs agree up to the order of the grouped gather's atomic additions,
-    amplified through near-tie matching as in the oracle parity test."""
+    Both objects share one plan (so one tuned gather) and run one after the
+    other; they agree up to the order of the gather's atomic additions, and
+    more loosely after a near-tie voxel is matched differently (lambda1 and
+    the cost follow the maps through the kNN graph)."""
+    m = mrf()
     o = oracle_recon(prob)
-    rs = gpu_recon(prob, mode, a_norm=o.a, x_scale=o.gamma)
-    rc = gpu_recon(prob, mode, extra_flags=32, a_norm=o.a, x_scale=o.gamma)
-    cs = rs.iterate(3, costs=True)
-    cc = rc.iterate(3, costs=True)
-    assert rel(np_(rc.alpha()), np_(rs.alpha())) < 1e-3
-    np.testing.assert_allclose(cc, cs, rtol=1e-4)
+    plan = m.nufft_plan(prob["n"], prob["n"], f32(prob["k"]))
+    rs = gpu_recon(prob, mode, plan=plan, a_norm=o.a, x_scale=o.gamma)
+    rc = gpu_recon(prob, mode, extra_flags=32, plan=plan, a_norm=o.a, x_scale=o.gamma)
+    same = True
+    for it in range(3):
+        cs = rs.iterate(1, costs=True)[0]
+        cc = rc.iterate(1, costs=True)[0]
+        assert cc == pytest.approx(cs, rel=1e-5 if same else 5e-3), it
+        ia, ib = np_(rs.maps()[3]), np_(rc.maps()[3])
+        assert (ia == ib).mean() > 0.99
+        same = same and bool((ia == ib).all())
+    assert rel(np_(rc.alpha()), np_(rs.alpha())) < (1e-5 if same else 1e-3)
