@@ -141,6 +141,58 @@ __global__ void __launch_bounds__(256) k_knn_part(const int* __restrict__ F, int
     }
 }
 
+// The partitions' sorted lists of one query merged by one warp: every lane
+// holds up to kMergePer of the parts x knn candidates, and each of the knn
+// rounds takes the warp-wide (distance, index) minimum and retires it.
+constexpr int kMergePer = 8;   // parts * knn <= 8 * 32
+
+__global__ void k_knn_merge_warp(const int* __restrict__ pnbr, const unsigned* __restrict__ pd2, int parts,
+                                 int np, int knn, int* __restrict__ nbr, unsigned* __restrict__ d2out) {
+    const int q = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (q >= np) return;                      // whole warps leave together
+    unsigned cd[kMergePer];
+    int cj[kMergePer];
+    const int total = parts * knn;
+#pragma unroll
+    for (int u = 0; u < kMergePer; ++u) {
+        const int c = lane + 32 * u;
+        if (c < total) {
+            const int p = c / knn, r = c - p * knn;
+            const size_t o = ((size_t)p * np + q) * knn + r;
+            cd[u] = pd2[o];
+            cj[u] = pnbr[o];
+        } else {
+            cd[u] = 0xffffffffu;
+            cj[u] = 0x7fffffff;
+        }
+    }
+    for (int r = 0; r < knn; ++r) {
+        unsigned bd = 0xffffffffu;
+        int bj = 0x7fffffff, bu = -1;
+#pragma unroll
+        for (int u = 0; u < kMergePer; ++u)
+            if (less_dj(cd[u], cj[u], bd, bj)) { bd = cd[u]; bj = cj[u]; bu = u; }
+        unsigned wd = bd;
+        int wj = bj;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned d2 = __shfl_xor_sync(0xffffffffu, wd, o);
+            const int j2 = __shfl_xor_sync(0xffffffffu, wj, o);
+            if (less_dj(d2, j2, wd, wj)) { wd = d2; wj = j2; }
+        }
+        // the lane holding the winner retires it (indices are distinct)
+        if (bu >= 0 && bj == wj && bd == wd) {
+#pragma unroll
+            for (int u = 0; u < kMergePer; ++u)
+                if (u == bu) { cd[u] = 0xffffffffu; cj[u] = 0x7fffffff; }
+        }
+        if (lane == 0) {
+            nbr[(size_t)q * knn + r] = wj;
+            d2out[(size_t)q * knn + r] = wd;
+        }
+    }
+}
+
 __global__ void k_knn_merge(const int* __restrict__ pnbr, const unsigned* __restrict__ pd2, int parts, int np,
                             int knn, int* __restrict__ nbr, unsigned* __restrict__ d2out) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -519,7 +571,11 @@ mrf_status knn_run(KnnWorkspace& ws, const int* F, int np, int fd, int ld, int k
         }
         MRF_LAUNCHED_AS("k_knn_part", s);
     }
-    k_knn_merge<<<(np + 127) / 128, 128, 0, s>>>(ws.pnbr, ws.pd2, parts, np, knn, nbr, d2);
+    if (parts * knn <= 32 * kMergePer)
+        k_knn_merge_warp<<<(unsigned)(((size_t)np * 32 + 255) / 256), 256, 0, s>>>(ws.pnbr, ws.pd2, parts, np, knn,
+                                                                                   nbr, d2);
+    else
+        k_knn_merge<<<(np + 127) / 128, 128, 0, s>>>(ws.pnbr, ws.pd2, parts, np, knn, nbr, d2);
     MRF_LAUNCHED_AS("k_knn_merge", s);
     return MRF_OK;
 }

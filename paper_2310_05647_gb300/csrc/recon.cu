@@ -266,7 +266,8 @@ __global__ void k_fill_reverse(const int* __restrict__ nbr, const float* __restr
 __global__ void __launch_bounds__(256) k_degree(const float* __restrict__ w, int np, int knn,
                                                 const int* __restrict__ roff, const int* __restrict__ rsrc_in,
                                                 const float* __restrict__ rw_in, int* __restrict__ rsrc,
-                                                float* __restrict__ rw, float* __restrict__ deg) {
+                                                float* __restrict__ rw, float* __restrict__ deg,
+                                                unsigned* __restrict__ deg_max) {
     extern __shared__ unsigned bits[];              // [nw] bitmap, then [nw] prefix counts
     const int nw = (np + 31) >> 5;
     unsigned* pre = bits + nw;
@@ -309,7 +310,11 @@ __global__ void __launch_bounds__(256) k_degree(const float* __restrict__ w, int
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) d += rw[i];
     if (threadIdx.x < knn) d += w[(size_t)j * knn + threadIdx.x];
     d = block_sum(d);
-    if (threadIdx.x == 0) deg[j] = (float)(0.5 * d);
+    if (threadIdx.x == 0) {
+        const float dj = (float)(0.5 * d);
+        deg[j] = dj;
+        atomicMax(deg_max, __float_as_uint(dj));   // degrees are >= 0: their bits order like the values
+    }
 }
 
 // lambda1 = lambda1^0 / max(L) (or times max(L) as printed)
@@ -814,14 +819,14 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
     k_fill_reverse<<<(ne + 255) / 256, 256, 0, s>>>(R->nbr, R->w, ne, knn, R->roff, R->rpos, R->rsrc_tmp,
                                                    R->rw_tmp);
     MRF_LAUNCHED_AS("k_fill_reverse", s);
+    MRF_CUDA(cudaMemsetAsync(R->scal + 1, 0, sizeof(float), s));     // max(L), raised by k_degree
     {
         const size_t smd = sizeof(unsigned) * 2 * (size_t)((np + 31) / 32);
         MRF_CUDA(cudaFuncSetAttribute(k_degree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
-        k_degree<<<np, 256, smd, s>>>(R->w, np, knn, R->roff, R->rsrc_tmp, R->rw_tmp, R->rsrc, R->rw, R->deg);
+        k_degree<<<np, 256, smd, s>>>(R->w, np, knn, R->roff, R->rsrc_tmp, R->rw_tmp, R->rsrc, R->rw, R->deg,
+                                      reinterpret_cast<unsigned*>(R->scal + 1));
     }
     MRF_LAUNCHED_AS("k_degree", s);
-    k_max<<<1, 1024, 0, s>>>(R->deg, np, R->scal + 1);
-    MRF_LAUNCHED_AS("k_max", s);
     k_lambda<<<1, 1, 0, s>>>(R->scal + 1, R->prm.lam1_0, (R->prm.flags & MRF_RECON_LITERAL_LAMBDA1) ? 1 : 0,
                              R->scal + 2);
     MRF_LAUNCHED_AS("k_lambda", s);
