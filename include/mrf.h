@@ -194,6 +194,16 @@ mrf_status mrf_match_noalloc(const mrf_c64* x, int n, int len, const mrf_c64* di
 mrf_status mrf_patch_knn(const int* F, int np, int fd, int ld, int knn, int* nbr, unsigned* d2,
                          mrf_stream stream);
 
+/* sigma^2 of the patch-graph weights w_ij = exp(-d2_ij / sigma^2) of Eq. 7,
+ * a constant the paper does not set: the median of the non-zero entries of
+ * d2 (the mean of the two middle ones for an even count), divided by 4096^2
+ * so that it is in units of (T / Tmax)^2 like the distances of the 12-bit
+ * patch vectors of mrf_patch_knn; 1 when no entry is non-zero (or ne == 0).
+ * d2: dev uint32 [ne], any values; sigma2: dev float [1], the fp64 result
+ * rounded once to float.  Asynchronous on the stream; no scratch.  ne < 0 or
+ * a null pointer: MRF_EINVAL. */
+mrf_status mrf_graph_sigma2(const unsigned* d2, int ne, float* sigma2, mrf_stream stream);
+
 /* ------------------------------------------------------------------------
  * Learned matcher.  The paper's related work (Section I) cites replacing
  * dictionary matching by a fully connected network that maps a fingerprint

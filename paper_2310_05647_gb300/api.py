@@ -176,6 +176,16 @@ def patch_knn(F, knn, fd=None):
     return nbr, d2
 
 
+def graph_sigma2(d2):
+    """sigma^2 [1] float32 on the device: the median of the non-zero entries of
+    the squared patch distances d2 (int32 holding uint32 bits) / 4096^2, 1 if
+    none (the weight scale of the patch graph, Eq. 7)."""
+    _check(d2, "d2", torch.int32)
+    out = torch.empty((1,), dtype=torch.float32, device=d2.device)
+    _lib.call("mrf_graph_sigma2", _ptr(d2), d2.numel(), _ptr(out), _stream())
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Algorithm 1
 # ---------------------------------------------------------------------------

@@ -146,76 +146,194 @@ __global__ void k_features(const float* __restrict__ t1t2, PatchGeom g, double t
     f[1] = (int)rint((double)t1t2[2 * v + 1] / t2max * kQScale);
 }
 
-// sigma^2 = median of the non-zero kNN squared distances (1 if none), by a
-// 4 x 8-bit radix select on the exact integer distances; reported in units of
-// (T / Tmax)^2 (integer / 4096^2).  One block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_median_nonzero(const unsigned* __restrict__ v, int n,
-                                                         float* __restrict__ sigma2) {
-    __shared__ unsigned hist[256];
-    __shared__ unsigned s_prefix, s_rank;
-    __shared__ int s_nz;
-    if (threadIdx.x == 0) s_nz = 0;
+// sigma^2 = median of the non-zero kNN squared distances (1 if none) on the
+// exact integer distances, reported in units of (T / Tmax)^2 (integer /
+// 4096^2).  One block; three sweeps over the distances at most:
+//  1. a histogram on a monotone log-scale key (the position of the leading
+//     bit and the 6 bits after it: 32 x 64 bins), which also counts them;
+//     the bin holding the lower middle rank is found by a block scan;
+//  2. that bin's elements are compacted into shared memory (when they fit)
+//     and the smallest element of any higher bin is taken;
+//  3. the rank inside the bin by an 8-bit radix select over the bits the
+//     bin leaves open, on the compacted list (else on the distances again).
+// The upper middle rank is the same value when enough elements equal it,
+// else the smallest element above it.
+constexpr int kMedianThreads = 1024;
+constexpr int kMedianBins = 2048;
+constexpr int kMedianList = 4096;
+
+__device__ __forceinline__ unsigned median_bin(unsigned b) {       // b > 0
+    const int e = 31 - __clz(b);
+    const unsigned sub = e >= 6 ? (b >> (e - 6)) & 63u : (b << (6 - e)) & 63u;
+    return (unsigned)e * 64u + sub;
+}
+
+__global__ void __launch_bounds__(kMedianThreads) k_median_nonzero(const unsigned* __restrict__ v, int n,
+                                                                   float* __restrict__ sigma2) {
+    __shared__ unsigned hist[kMedianBins];
+    __shared__ unsigned list[kMedianList];
+    __shared__ unsigned s_warp[32];
+    __shared__ unsigned s_bin, s_rank, s_eq, s_prefix, s_cnt, s_above, s_total;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool vec = (reinterpret_cast<uintptr_t>(v) & 15u) == 0;
+    const int n4 = vec ? n / 4 : 0;
+    const uint4* v4 = reinterpret_cast<const uint4*>(v);
+    for (int i = tid; i < kMedianBins; i += kMedianThreads) hist[i] = 0u;
+    if (tid == 0) { s_cnt = 0u; s_above = 0xffffffffu; }
     __syncthreads();
-    int nz = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) nz += v[i] > 0u;
-    atomicAdd(&s_nz, nz);
+    // sweep 1
+    auto bin_add = [&](unsigned b) { if (b) atomicAdd(&hist[median_bin(b)], 1u); };
+#pragma unroll 4
+    for (int i = tid; i < n4; i += kMedianThreads) {
+        const uint4 q = v4[i];
+        bin_add(q.x); bin_add(q.y); bin_add(q.z); bin_add(q.w);
+    }
+    for (int i = 4 * n4 + tid; i < n; i += kMedianThreads) bin_add(v[i]);
     __syncthreads();
-    const int total = s_nz;
-    if (total == 0) {
-        if (threadIdx.x == 0) *sigma2 = 1.0f;
+    // block scan: thread t owns bins 2t and 2t + 1
+    const unsigned h0 = hist[2 * tid], h1 = hist[2 * tid + 1], own = h0 + h1;
+    unsigned incl = own;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned w = s_warp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;                              // inclusive over warps
+        if (lane == 31) s_total = w;
+    }
+    __syncthreads();
+    const unsigned total = s_total;
+    if (total == 0u) {
+        if (tid == 0) *sigma2 = 1.0f;
         return;
     }
-    // the lower middle rank by a 4 x 8-bit radix select; the upper middle
-    // rank (total / 2) is the same value when enough elements equal it, else
-    // the smallest non-zero element above it (one more pass)
-    const unsigned rank = (unsigned)(total - 1) / 2;
-    unsigned prefix = 0, mask = 0;
-    if (threadIdx.x == 0) s_rank = rank;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    const unsigned rank = (total - 1u) / 2u;
+    incl += wid ? s_warp[wid - 1] : 0u;
+    if (incl - own <= rank && rank < incl) {          // exactly one thread
+        const unsigned before = incl - own;
+        const bool first = rank < before + h0;
+        const unsigned k = 2u * tid + (first ? 0u : 1u);
+        s_bin = k;
+        s_rank = rank - (first ? before : before + h0);
+        s_eq = first ? h0 : h1;
+    }
+    __syncthreads();
+    const unsigned k = s_bin, cnt = s_eq;
+    const int e = (int)(k >> 6);
+    const unsigned lead = 64u + (k & 63u);
+    const unsigned base = e >= 6 ? lead << (e - 6) : lead >> (6 - e);
+    const bool compact = cnt <= (unsigned)kMedianList;
+    // sweep 2
+    auto keep = [&](unsigned b, bool in) {
+        if (compact) {
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            unsigned at = 0;
+            if (lane == 0 && m) at = atomicAdd(&s_cnt, (unsigned)__popc(m));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            const unsigned slot = at + __popc(m & ((1u << lane) - 1u));
+            if (in && slot < (unsigned)kMedianList) list[slot] = b;
+        }
+    };
+    unsigned above = 0xffffffffu;
+    for (int i0 = 0; i0 < n4; i0 += kMedianThreads) {        // warp-uniform trip count
+        const int i = i0 + tid;
+        const uint4 q = i < n4 ? v4[i] : make_uint4(0u, 0u, 0u, 0u);
+        const unsigned qs[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned b = qs[j];
+            const unsigned bn = b ? median_bin(b) : 0u;
+            if (b && bn > k) above = min(above, b);
+            keep(b, b && bn == k);
+        }
+    }
+    for (int i0 = 4 * n4; i0 < n; i0 += kMedianThreads) {
+        const int i = i0 + tid;
+        const unsigned b = i < n ? v[i] : 0u;
+        const unsigned bn = b ? median_bin(b) : 0u;
+        if (b && bn > k) above = min(above, b);
+        keep(b, b && bn == k);
+    }
+    for (int o = 16; o > 0; o >>= 1) above = min(above, __shfl_xor_sync(0xffffffffu, above, o));
+    if (lane == 0) atomicMin(&s_above, above);
+    if (tid == 0) s_prefix = base;
+    __syncthreads();
+    // sweep 3: the open low bits of the bin, 8 at a time from the top
+    auto in_bin = [&](unsigned b) { return b != 0u && median_bin(b) == k; };
+    const int m_list = compact ? (int)cnt : 0;
+    int bits = e > 6 ? e - 6 : 0;
+    unsigned prefix = base, mask = bits ? ~0u << bits : ~0u;
+    while (bits > 0) {
+        const int width = bits < 8 ? bits : 8;
+        const int shift = bits - width;
+        const unsigned dmask = (1u << width) - 1u;
+        if (tid < 256) hist[tid] = 0u;
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const unsigned b = v[i];
-            if (b == 0u) continue;
-            if ((b & mask) == prefix) atomicAdd(&hist[(b >> shift) & 255u], 1u);
+        auto add = [&](unsigned b) { if ((b & mask) == prefix) atomicAdd(&hist[(b >> shift) & dmask], 1u); };
+        if (compact) {
+            for (int i = tid; i < m_list; i += kMedianThreads) add(list[i]);
+        } else {
+            for (int i = tid; i < n; i += kMedianThreads) {
+                const unsigned b = v[i];
+                if (in_bin(b)) add(b);
+            }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned r = s_rank, c = 0;
-            int bucket = 0;
-            for (; bucket < 255; ++bucket) {
-                if (c + hist[bucket] > r) break;
-                c += hist[bucket];
+        if (wid == 0) {
+            const unsigned r = s_rank;
+            unsigned own8[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { own8[j] = hist[8 * lane + j]; sum += own8[j]; }
+            unsigned inc = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
             }
-            s_rank = r - c;
-            s_prefix = prefix | ((unsigned)bucket << shift);
+            const unsigned hit = __ballot_sync(0xffffffffu, inc > r);
+            if (lane == __ffs(hit) - 1) {                // the digits count every element left
+                unsigned c = inc - sum;
+                int d = 0;
+                for (; d < 7; ++d) {
+                    if (c + own8[d] > r) break;
+                    c += own8[d];
+                }
+                s_rank = r - c;
+                s_eq = own8[d];
+                s_prefix = prefix | ((unsigned)(8 * lane + d) << shift);
+            }
         }
         __syncthreads();
         prefix = s_prefix;
-        mask |= 255u << shift;
+        mask |= dmask << shift;
+        bits = shift;
     }
-    const unsigned lo = prefix;                     // value of rank (total - 1) / 2
-    // elements <= lo and the smallest element above lo (non-zero elements only)
-    __shared__ int s_le;
-    __shared__ unsigned s_above;
-    if (threadIdx.x == 0) { s_le = 0; s_above = 0xffffffffu; }
-    __syncthreads();
-    int le = 0;
-    unsigned above = 0xffffffffu;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const unsigned b = v[i];
-        if (b == 0u) continue;
-        if (b <= lo) ++le;
-        else above = min(above, b);
+    const unsigned lo = s_prefix;                    // value of rank (total - 1) / 2
+    // elements <= lo: the ones below it (rank - s_rank) and its copies (s_eq)
+    const unsigned le = rank - s_rank + s_eq;
+    unsigned hi = lo;
+    if (le <= total / 2u) {
+        unsigned up = 0xffffffffu;                   // smallest element of the bin above lo
+        if (compact) {
+            for (int i = tid; i < m_list; i += kMedianThreads) if (list[i] > lo) up = min(up, list[i]);
+        } else {
+            for (int i = tid; i < n; i += kMedianThreads) {
+                const unsigned b = v[i];
+                if (in_bin(b) && b > lo) up = min(up, b);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) up = min(up, __shfl_xor_sync(0xffffffffu, up, o));
+        if (lane == 0) atomicMin(&s_above, up);
+        __syncthreads();
+        hi = s_above;
     }
-    atomicAdd(&s_le, le);
-    atomicMin(&s_above, above);
-    __syncthreads();
-    unsigned vals[2];
-    vals[0] = lo;
-    vals[1] = s_le > total / 2 ? lo : s_above;
-    if (threadIdx.x == 0)
-        *sigma2 = (float)(0.5 * ((double)vals[0] + (double)vals[1]) / (kQScale * kQScale));
+    if (tid == 0) *sigma2 = (float)(0.5 * ((double)lo + (double)hi) / (kQScale * kQScale));
 }
 
 // w = exp(-d2 / sigma^2) on the kNN edges; in-degree counts of the reverse graph
@@ -808,7 +926,7 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
     MRF_LAUNCHED_AS("k_features", s);
     MRF_PROPAGATE(knn_run(R->knn, R->F, np, FD, (FD + 3) / 4 * 4, knn, R->nbr, R->d2, s));
     const int ne = np * knn;
-    k_median_nonzero<<<1, 1024, 0, s>>>(R->d2, ne, R->scal + 0);
+    k_median_nonzero<<<1, kMedianThreads, 0, s>>>(R->d2, ne, R->scal + 0);
     MRF_LAUNCHED_AS("k_median_nonzero", s);
     MRF_CUDA(cudaMemsetAsync(R->rcnt, 0, sizeof(int) * np, s));
     MRF_CUDA(cudaMemsetAsync(R->rpos, 0, sizeof(int) * np, s));
@@ -1157,6 +1275,14 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
 }  // namespace mrf
 
 using namespace mrf;
+
+extern "C" mrf_status mrf_graph_sigma2(const unsigned* d2, int ne, float* sigma2, mrf_stream stream) {
+    MRF_REQUIRE(ne >= 0 && sigma2 && (ne == 0 || d2), "mrf_graph_sigma2: ne < 0 or a null pointer");
+    cudaStream_t s = as_stream(stream);
+    k_median_nonzero<<<1, kMedianThreads, 0, s>>>(d2, ne, sigma2);
+    MRF_CUDA(cudaGetLastError());
+    return MRF_OK;
+}
 
 extern "C" mrf_status mrf_recon_create(mrf_recon* out, mrf_plan plan, const mrf_recon_params* prm,
                                        const mrf_c64* phi, int K, const mrf_c64* dict_c, const float* atom_norm2,

@@ -80,3 +80,65 @@ def test_knn_rejects_out_of_range_and_too_few():
     Fd, fd = _padded(np.zeros((10, 8), np.int64))
     with pytest.raises(m.MRFError):
         m.patch_knn(Fd, 10, fd=fd)
+
+
+def _sigma2_case(vals):
+    """GPU sigma^2 of the uint32 distances vals against the oracle's median,
+    bit-exact: the median of integers / 4096^2 is exact in fp64, and both
+    sides round it once to float32.  The cases cover odd and even counts,
+    middle values tied or not, a median bin larger than the kernel's
+    shared-memory list (then read from global memory), and inputs with no
+    non-zero entry."""
+    v = np.asarray(vals, np.uint64).astype(np.uint32)
+    d = torch.tensor(v.view(np.int32), device=dev())
+    got = np_(mrf().graph_sigma2(d))[0]
+    want = np.float32(ograph.sigma2(v.astype(np.float64) / float(ograph.QSCALE ** 2)))
+    assert got == want, (v.size, got, want)
+
+
+_SIGMA2_CASES = ["empty", "zeros", "one", "odd", "even_split", "even_tied", "all_equal", "low_bits",
+                 "few_distinct", "top_bit", "large", "wide_bin", "tied_bin", "small_values"]
+
+
+@pytest.mark.parametrize("case", _SIGMA2_CASES)
+def test_graph_sigma2_matches_oracle_median(case):
+    rng = np.random.default_rng(_SIGMA2_CASES.index(case))
+    if case == "empty":
+        vals = []
+    elif case == "zeros":
+        vals = np.zeros(1000)
+    elif case == "one":
+        vals = np.zeros(777); vals[500] = 123456
+    elif case == "odd":
+        vals = rng.integers(1, 2**31, 4001)
+    elif case == "even_split":                       # the two middle values differ
+        vals = np.concatenate([rng.integers(1, 1000, 3000), rng.integers(5000, 9000, 3000), np.zeros(17)])
+        rng.shuffle(vals)
+    elif case == "even_tied":                        # the two middle values are equal
+        vals = np.concatenate([np.full(2000, 40), np.full(11, 41), np.full(1989, 7), np.zeros(50)])
+        rng.shuffle(vals)
+    elif case == "all_equal":
+        vals = np.concatenate([np.full(3000, 98765), np.zeros(3)])
+    elif case == "low_bits":                          # values that differ in the lowest bits only
+        vals = 1_000_000 + rng.integers(0, 5, 10001)
+    elif case == "few_distinct":                      # the tie structure of piecewise-constant maps
+        vals = rng.choice(np.array([0, 4096, 8192, 16384 * 9, 2**24]), 39690, p=[0.3, 0.3, 0.2, 0.15, 0.05])
+    elif case == "top_bit":                           # the full 32-bit range
+        vals = rng.integers(2**31 - 10, 2**32, 5000)
+    elif case == "large":
+        vals = np.where(rng.random(200003) < 0.1, 0, rng.integers(1, 2**28, 200003))
+    elif case == "wide_bin":                          # 10^4 distinct values in one log-scale bin
+        vals = 2**20 + rng.integers(0, 2**14, 10000)
+    elif case == "tied_bin":                          # more copies of the median than the list holds
+        vals = np.concatenate([np.full(9000, 12345), rng.integers(1, 12345, 4000), rng.integers(12346, 10**6, 4000)])
+    else:                                             # values below 128 (one value per bin)
+        vals = rng.integers(0, 128, 3001)
+    _sigma2_case(vals)
+
+
+def test_graph_sigma2_of_workload_distances():
+    """sigma^2 of the kNN distances of the full-size workload's patch graph
+    (63 x 63 patches of 8 x 8, k = 10) against the oracle."""
+    F = _map_features(256, 8, 4, seed=3)
+    nbr, d2 = mrf().patch_knn(_padded(F)[0], 10, fd=F.shape[1])
+    _sigma2_case(np_(d2).view(np.uint32).ravel())
