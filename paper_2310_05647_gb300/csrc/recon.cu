@@ -435,6 +435,20 @@ __global__ void __launch_bounds__(256) k_degree(const float* __restrict__ w, int
     }
 }
 
+// copies of the forward graph and lambda1 for the cost trace
+__global__ void k_graph_snapshot(const int* __restrict__ nbr, const float* __restrict__ w,
+                                 const float* __restrict__ deg, const float* __restrict__ lam1, int ne, int np,
+                                 int* __restrict__ nbr_c, float* __restrict__ w_c, float* __restrict__ deg_c,
+                                 float* __restrict__ lam1_c) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ne) {
+        nbr_c[i] = nbr[i];
+        w_c[i] = w[i];
+    }
+    if (i < np) deg_c[i] = deg[i];
+    if (i == 0) *lam1_c = *lam1;
+}
+
 // lambda1 = lambda1^0 / max(L) (or times max(L) as printed)
 __global__ void k_lambda(const float* __restrict__ lmax, float lam1_0, int literal, float* __restrict__ lam1) {
     const float m = *lmax;
@@ -443,6 +457,11 @@ __global__ void k_lambda(const float* __restrict__ lmax, float lam1_0, int liter
 
 // (Q(X) L)_j = deg_j Q_j - 1/2 sum_{i in N(j)} w_ji Q_i - 1/2 sum_{i: j in N(i)} w_ij Q_i,
 // written per patch (QL nullable) and/or accumulated into Tr(Q L Q^H).
+// With rev == 0 only the forward kNN entries are read, with weight w instead
+// of w / 2: then sum_j <Q_j, v_j> = sum_j deg_j |Q_j|^2 - sum_j sum_{i in N(j)}
+// w_ji Re <Q_j, Q_i>, which is Tr(Q L Q^H) too (W = (K + K^T) / 2 and Re <., .>
+// is symmetric, so the reverse half of W adds the same sum as the forward
+// half), at half the neighbour reads; v_j itself is then not (Q L)_j.
 // One block per patch j, each thread up to kGbElems of its p x p x K
 // coefficients (consecutive threads read consecutive coefficients of a
 // neighbour's patch rows).  The neighbour list (forward kNN entries, then
@@ -461,7 +480,7 @@ __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __res
                                                              const int* __restrict__ roff,
                                                              const int* __restrict__ rsrc,
                                                              const float* __restrict__ rw,
-                                                             const float* __restrict__ deg,
+                                                             const float* __restrict__ deg, int rev,
                                                              float2* __restrict__ QL, double* __restrict__ trace) {
     __shared__ int s_off[kGbChunk];
     __shared__ float s_w[kGbChunk];
@@ -470,8 +489,9 @@ __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __res
     const int ne = g.p * pK;
     const int jy = g.origin(j / g.cnt), jx = g.origin(j % g.cnt);
     const float dj = deg[j];
-    const int rb = roff[j], re = roff[j + 1];
-    const int nq = knn + (re - rb);
+    const int rb = rev ? roff[j] : 0, re = rev ? roff[j + 1] : 0;
+    const int nq = knn + (rev ? re - rb : 0);
+    const float wscale = rev ? 0.5f : 1.0f;
     double tr = 0.0;
     for (int e0 = 0; e0 < ne; e0 += kGbThreads * kGbElems) {
         int off[kGbElems];
@@ -494,7 +514,7 @@ __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __res
                 if (q < knn) { i = nbr[(size_t)j * knn + q]; wq = w[(size_t)j * knn + q]; }
                 else { i = rsrc[rb + q - knn]; wq = rw[rb + q - knn]; }
                 s_off[t] = (g.origin(i / g.cnt) * g.n + g.origin(i % g.cnt)) * K;
-                s_w[t] = 0.5f * wq;
+                s_w[t] = wscale * wq;
             }
             __syncthreads();
 #pragma unroll 4
@@ -837,7 +857,11 @@ struct mrf_recon_s {
     float *w = nullptr, *rw = nullptr, *deg = nullptr;
     int *rcnt = nullptr, *roff = nullptr, *rpos = nullptr, *rsrc = nullptr, *rsrc_tmp = nullptr;
     float* rw_tmp = nullptr;
-    float* scal = nullptr;      // [0] sigma2, [1] lmax, [2] lam1, [3] scratch
+    float* scal = nullptr;      // [0] sigma2, [1] lmax, [2] lam1, [3] scratch, [4] lam1 of the cost
+    // the forward graph (nbr, w, deg) as the iteration began, read by the
+    // cost trace while the rebuild replaces the live copy (concurrent mode)
+    int* nbr_c = nullptr;
+    float *w_c = nullptr, *deg_c = nullptr;
     double* acc = nullptr;      // [0] ||r||^2, [1] trace, [2] nuclear, [3..4] dot
     double* cost = nullptr;     // [cap] cost history
     int cost_cap = 0, iters_done = 0;
@@ -1027,10 +1051,14 @@ static mrf_status learned_maps(mrf_recon_s* R, cudaStream_t s) {
     return MRF_OK;
 }
 
-static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s) {
-    k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, R->nbr, R->w, R->prm.knn, R->roff, R->rsrc,
-                                                R->rw, R->deg, QL, trace);
-    MRF_LAUNCHED_AS("k_graph_blocks", s);
+// Q(X) L into QL, or (QL null) Tr(Q L Q^H) added to *trace from the forward
+// kNN entries alone, of the live graph or (snap) of the copy taken when the
+// iteration began
+static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s, bool snap = false) {
+    k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, snap ? R->nbr_c : R->nbr,
+                                                snap ? R->w_c : R->w, R->prm.knn, R->roff, R->rsrc, R->rw,
+                                                snap ? R->deg_c : R->deg, QL ? 1 : 0, QL, trace);
+    MRF_LAUNCHED_AS(QL ? "k_graph_blocks" : "k_graph_blocks(trace)", s);
     return MRF_OK;
 }
 
@@ -1063,12 +1091,13 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
 // One iteration of the loop body, with its independent steps on three
 // streams (stream-ordered, ends joined into s):
 //   s:       adjoint -> (join) X update -> forward -> |r|^2 -> (join) cost
-//   side[1]: graph term Q(X)L (needs the previous graph) ............ ^ join
+//   side[1]: graph copy, graph term Q(X)L (the previous graph) ...... ^ join
 //   side[0]:                     SVT of the new iterate -> P, sum sigma -> cost trace
-//   side[1]:                     matching -> (wait for the trace) graph rebuild
+//   side[1]:                     matching -> graph rebuild
 // The forward operator, the SVT and the matching all read only the new
-// iterate; the graph rebuild only the new maps; the accumulators they add
-// to are distinct slots.
+// iterate; the graph rebuild only the new maps; the cost trace reads the copy
+// of the graph taken at the start, so the rebuild need not wait for it; the
+// accumulators they add to are distinct slots.
 static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     const bool cost = !(R->prm.flags & MRF_RECON_NO_COST);
     if (R->prm.flags & MRF_RECON_SERIAL) {
@@ -1087,6 +1116,12 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     MRF_CUDA(cudaEventRecord(R->ev[0], s));
     MRF_CUDA(cudaStreamWaitEvent(sc, R->ev[0], 0));
     mark(sc);
+    if (cost) {
+        const int ne = R->np * R->prm.knn;
+        k_graph_snapshot<<<(unsigned)((ne + 255) / 256), 256, 0, sc>>>(R->nbr, R->w, R->deg, R->scal + 2, ne, R->np,
+                                                                    R->nbr_c, R->w_c, R->deg_c, R->scal + 4);
+        MRF_LAUNCHED_AS("k_graph_snapshot", sc);
+    }
     MRF_PROPAGATE(graph_pass(R, R->QL, nullptr, sc));
     MRF_CUDA(cudaEventRecord(R->ev[1], sc));
     MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, s));
@@ -1104,18 +1139,10 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     mark(sb);
     mark(sc);
     MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, sb));
-    if (cost) {
-        MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, sb));   // trace with the current graph
-        // the cost weighs the trace with this iteration's lambda1, which the
-        // graph rebuild replaces: keep a copy for k_cost
-        MRF_CUDA(cudaMemcpyAsync(R->scal + 4, R->scal + 2, sizeof(float), cudaMemcpyDeviceToDevice, sb));
-    }
+    if (cost) MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, sb, true));   // trace with this iteration's graph
     MRF_CUDA(cudaEventRecord(R->ev[3], sb));
     if (R->prm.flags & MRF_RECON_LEARNED) MRF_PROPAGATE(learned_maps(R, sc));
     else MRF_PROPAGATE(match_maps(R, sc));
-    // the rebuild replaces the graph and lambda1 the trace reads
-    MRF_CUDA(cudaStreamWaitEvent(sc, R->ev[3], 0));
-    mark(sc);
     MRF_PROPAGATE(build_graph(R, sc));
     MRF_CUDA(cudaEventRecord(R->ev[4], sc));
     MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, s));
@@ -1170,6 +1197,9 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(dalloc(R, &R->rsrc_tmp, (size_t)np * knn));
     MRF_PROPAGATE(dalloc(R, &R->rw_tmp, (size_t)np * knn));
     MRF_PROPAGATE(dalloc(R, &R->deg, np));
+    MRF_PROPAGATE(dalloc(R, &R->nbr_c, (size_t)np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->w_c, (size_t)np * knn));
+    MRF_PROPAGATE(dalloc(R, &R->deg_c, np));
     MRF_PROPAGATE(dalloc(R, &R->rcnt, np));
     MRF_PROPAGATE(dalloc(R, &R->rpos, np));
     MRF_PROPAGATE(dalloc(R, &R->roff, np + 1));
