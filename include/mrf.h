@@ -158,6 +158,22 @@ mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64* dict,
                      const float* atom_norm2, const float* lut, int m, int precision,
                      int* idx, float* pd, float* t1t2, mrf_stream stream);
 
+/* mrf_match for repeated matching of the same n rows (an iterative
+ * reconstruction matches every iterate): cand (dev int32 [n][8]) carries
+ * each row's tensor-core candidates from one call to the next.  On entry
+ * the first TOPK entries of row i (TOPK = 4 for MRF_MATCH_BF16X3, 8 for
+ * MRF_MATCH_BF16) name seed atoms: the smallest FP32 score among them, less
+ * a margin above the tensor-core score error (2^-10 ||x_i||^2 split, 2^-4
+ * BF16), starts the row's candidate list, so the sweep inserts fewer atoms.
+ * Any seeds give the same candidates and winners as mrf_match; seeds that
+ * are not TOPK distinct indices in [0, m) (e.g. -1) leave the row unseeded.
+ * On return those entries hold the row's candidates; the others are left
+ * as they were.  precision: MRF_MATCH_BF16 or MRF_MATCH_BF16X3 (else
+ * MRF_EINVAL); other arguments as in mrf_match. */
+mrf_status mrf_match_seeded(const mrf_c64* x, int n, int len, const mrf_c64* dict, const float* atom_norm2,
+                            const float* lut, int m, int precision, int* cand, int* idx, float* pd,
+                            float* t1t2, mrf_stream stream);
+
 /* Same result as mrf_match with MRF_MATCH_FP32, for callers that cannot
  * allocate device memory when they match (the paper has no counterpart: this
  * is a deployment variant).  A reconstruction service that reserves the

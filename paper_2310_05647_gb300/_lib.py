@@ -38,6 +38,7 @@ SIGNATURES = {
     "mrf_epg_fisp": (i32, [vp, i32, vp, vp, i32, f32, f32, i32, vp, vp]),
     "mrf_dict_subspace": (i32, [vp, i32, i32, i32, vp, vp, vp, vp]),
     "mrf_match": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp, vp]),
+    "mrf_match_seeded": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp]),
     "mrf_match_noalloc": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp, vp]),
     "mrf_nufft_gather_tuning": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
     "mrf_patch_knn": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),

@@ -164,6 +164,28 @@ def match(x, D, lut, atom_norm2=None, precision=MATCH_FP32):
     return idx, pd, t1t2
 
 
+def match_seeded(x, D, lut, cand, atom_norm2=None, precision=MATCH_BF16X3):
+    """match() for repeated matching of the same rows: cand [n, 8] int32 on the
+    device holds each row's seed atoms on entry (-1: none) and its tensor-core
+    candidates on return; the winners are those of match() for any seeds."""
+    _check(x, "x", torch.complex64)
+    _check(D, "D", torch.complex64)
+    n, L = x.shape
+    m = D.shape[0]
+    if D.shape[1] != L:
+        raise ValueError("x and D lengths differ")
+    _check(lut, "lut", torch.float32, (m, 2))
+    _check(cand, "cand", torch.int32, (n, 8))
+    if atom_norm2 is not None:
+        _check(atom_norm2, "atom_norm2", torch.float32, (m,))
+    idx = torch.empty((n,), dtype=torch.int32, device=x.device)
+    pd = torch.empty((n,), dtype=torch.float32, device=x.device)
+    t1t2 = torch.empty((n, 2), dtype=torch.float32, device=x.device)
+    _lib.call("mrf_match_seeded", _ptr(x), n, L, _ptr(D), _ptr(atom_norm2), _ptr(lut), m, int(precision),
+              _ptr(cand), _ptr(idx), _ptr(pd), _ptr(t1t2), _stream())
+    return idx, pd, t1t2
+
+
 def patch_knn(F, knn, fd=None):
     """(nbr [np, knn] int32, d2 [np, knn] int32 holding uint32 bits) of the
     integer patch vectors F [np, ld] (entries past fd zero, ld % 4 == 0)."""

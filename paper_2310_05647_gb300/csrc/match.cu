@@ -200,9 +200,9 @@ mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* no
 
 mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
                      int precision, const float* lut, int* idx, float* pd, float* t1t2, float pd_scale,
-                     cudaStream_t s) {
+                     cudaStream_t s, int* cand_io) {
     if (tc_form(precision)) {
-        MRF_PROPAGATE(match_tc_candidates(ws, x, n, len, dict, m, tc_form(precision), s));
+        MRF_PROPAGATE(match_tc_candidates(ws, x, n, len, dict, m, tc_form(precision), s, cand_io));
         MRF_PROPAGATE(match_rerank(ws, x, n, len, dict, s));
     } else {
         k_match_fp32<<<(n + BM - 1) / BM, 256, 0, s>>>(x, n, len, dict, ws.wscore, m, ws.best_idx, ws.best_ip);
@@ -223,9 +223,9 @@ mrf_status match_finish(MatchWorkspace& ws, int n, const float* lut, int* idx, f
 
 using namespace mrf;
 
-extern "C" mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64* dict, const float* atom_norm2,
-                                const float* lut, int m, int precision, int* idx, float* pd, float* t1t2,
-                                mrf_stream stream) {
+static mrf_status match_call(const mrf_c64* x, int n, int len, const mrf_c64* dict, const float* atom_norm2,
+                             const float* lut, int m, int precision, int* cand, int* idx, float* pd, float* t1t2,
+                             mrf_stream stream) {
     MRF_REQUIRE(x && dict && lut, "mrf_match: NULL x, dict or lut");
     MRF_REQUIRE(n >= 0 && len >= 1 && len <= 2048, "mrf_match: bad n or len (%d, %d)", n, len);
     MRF_REQUIRE(m >= 1 && m <= (1 << 24), "mrf_match: bad m (%d)", m);
@@ -249,7 +249,7 @@ extern "C" mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64*
     mrf_status st = match_prepare(ws, reinterpret_cast<const float2*>(dict), atom_norm2, m, len, literal, s);
     if (st == MRF_OK)
         st = match_run(ws, reinterpret_cast<const float2*>(x), n, len, reinterpret_cast<const float2*>(dict), m,
-                       prec, lut, idx, pd, t1t2, 1.0f, s);
+                       prec, lut, idx, pd, t1t2, 1.0f, s, cand);
     if (st == MRF_OK && tcb) {
         // a bounded device wait that gave up is reported, not hidden
         int h = 0;
@@ -262,7 +262,22 @@ extern "C" mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64*
     ws.detach();
     MRF_CUDA(cudaFreeAsync(base, s));
     return st;
-    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64* dict, const float* atom_norm2,
+                                const float* lut, int m, int precision, int* idx, float* pd, float* t1t2,
+                                mrf_stream stream) {
+    return match_call(x, n, len, dict, atom_norm2, lut, m, precision, nullptr, idx, pd, t1t2, stream);
+}
+
+extern "C" mrf_status mrf_match_seeded(const mrf_c64* x, int n, int len, const mrf_c64* dict,
+                                       const float* atom_norm2, const float* lut, int m, int precision, int* cand,
+                                       int* idx, float* pd, float* t1t2, mrf_stream stream) {
+    const int prec = precision & 0xff;
+    MRF_REQUIRE(prec == MRF_MATCH_BF16 || prec == MRF_MATCH_BF16X3,
+                "mrf_match_seeded: precision must be MRF_MATCH_BF16 or MRF_MATCH_BF16X3 (got %d)", prec);
+    MRF_REQUIRE(cand || n == 0, "mrf_match_seeded: NULL cand");
+    return match_call(x, n, len, dict, atom_norm2, lut, m, precision, cand, idx, pd, t1t2, stream);
 }
 
 namespace mrf {

@@ -10,7 +10,7 @@ constexpr int kTopK = 8;   // candidates kept by the BF16 scorer for the FP32 re
 struct MatchWorkspace {
     int* best_idx = nullptr;   // [n] winning atom
     float2* best_ip = nullptr; // [n] <d_k, x> of the winner
-    int* cand = nullptr;       // [n][kTopK] BF16 candidates
+    int* cand = nullptr;       // [n][kTopK] tensor-core candidates (seeds of the next call)
     float* norm2 = nullptr;    // [m] ||d_m||^2
     float* wscore = nullptr;   // [m] score weight
     int cap_n = 0, cap_m = 0;
@@ -31,10 +31,13 @@ struct MatchWorkspace {
 // norm2/score weights of the atoms (norm2_in nullable: computed from dict)
 mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* norm2_in, int m, int len,
                          int literal, cudaStream_t s);
-// winners for n fingerprints; outputs nullable; pd multiplied by pd_scale
+// winners for n fingerprints; outputs nullable; pd multiplied by pd_scale.
+// cand_io (nullable, [n][kTopK], BF16 forms only): each row's seed atoms on
+// entry, its tensor-core candidates on return (the winners do not depend on
+// the seeds)
 mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
                      int precision, const float* lut, int* idx, float* pd, float* t1t2, float pd_scale,
-                     cudaStream_t s);
+                     cudaStream_t s, int* cand_io = nullptr);
 // bytes of the tensor-core dictionary operand for m atoms of length len
 size_t tc_operand_bytes(int m, int len, int prec);
 // operand form of a tensor-core precision: 1 BF16, 3 split BF16, 8 FP8 e4m3 (0: FP32 path)
@@ -66,7 +69,7 @@ mrf_status match_finish(MatchWorkspace& ws, int n, const float* lut, int* idx, f
                         float pd_scale, cudaStream_t s);
 // tensor-core candidate search and FP32 re-rank (match_tc.cu)
 mrf_status match_tc_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
-                               int prec, cudaStream_t s);
+                               int prec, cudaStream_t s, int* cand_io = nullptr);
 mrf_status match_rerank(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict,
                         cudaStream_t s);
 

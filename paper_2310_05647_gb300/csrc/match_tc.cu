@@ -137,26 +137,69 @@ __device__ __forceinline__ bool better_cand(float s, int i, float bs, int bi) {
     return s > bs || (s == bs && i < bi);
 }
 
-// Warp-specialised sweep over tiles of kTcAtoms atoms.  Warp 8 (producer):
-// streams each tile's B operand into a 4-stage shared ring with one bulk copy
-// (mbarrier transaction count) and issues the tile's MMAs into one of two TMEM
-// accumulator buffers.  Warps 0-7 (consumers, two per TMEM lane quarter, one
-// column half each): wait for a buffer, copy it to registers, hand it back to
-// the producer, then score.  Every wait is bounded; a wait that gives up sets
-// the error word and the block stops.
+// Starting threshold of a fingerprint's candidate list from TOPK seed atoms
+// (in a loop: the previous call's candidates of the same row): the smallest
+// FP32 score among them, less margin ||x||^2.  Any TOPK distinct atoms score
+// at most the TOPK-th best, and the tensor-core score of an atom differs from
+// its FP32 score by less than the margin (split BF16: |error| <~ 2^-12.6
+// ||x||^2 from the operand splitting and the FP32 accumulation, margin
+// 2^-10; BF16: <~ 2^-5.5, margin 2^-4), so every atom of the final top TOPK
+// scores above the threshold and the list comes out exactly as from an empty
+// start; only fewer insertions happen on the way.  -1 (no seeding) for seeds
+// that are not TOPK distinct atoms, or an all-zero fingerprint.
+template <int TOPK>
+__device__ float seed_threshold(const float2* __restrict__ xr, int len, const int* sr,
+                                const float2* __restrict__ dict, const float* __restrict__ wscore, int m,
+                                float margin) {
+    int a[TOPK];
+#pragma unroll
+    for (int q = 0; q < TOPK; ++q) {
+        a[q] = sr[q];
+        if (a[q] < 0 || a[q] >= m) return -1.f;
+    }
+#pragma unroll
+    for (int q = 1; q < TOPK; ++q)
+#pragma unroll
+        for (int r = 0; r < q; ++r)
+            if (a[q] == a[r]) return -1.f;
+    float x2 = 0.f;
+    for (int k = 0; k < len; ++k) x2 += cabs2(xr[k]);
+    if (!(x2 > 1e-30f)) return -1.f;
+    float lo = 3.4e38f;
+#pragma unroll
+    for (int q = 0; q < TOPK; ++q) {
+        const float2* dr = dict + (size_t)a[q] * len;
+        float2 sq = make_float2(0.f, 0.f);
+        for (int k = 0; k < len; ++k) sq = cadd(sq, cconjmul(dr[k], xr[k]));
+        lo = fminf(lo, cabs2(sq) * wscore[a[q]]);
+    }
+    return lo - margin * x2;
+}
+
+// Warp-specialised sweep over tiles of kTcAtoms atoms.  Warp 8 (loader):
+// streams each tile's B operand into a kTcStages-deep shared ring with one
+// bulk copy per tile (mbarrier transaction count), as far ahead as the ring
+// allows.  Warp 9 (MMA): issues each tile's MMAs into one of two TMEM
+// accumulator buffers as soon as its operand has landed and the buffer is
+// free.  Warps 0-7 (consumers, two per TMEM lane quarter, one column half
+// each): wait for a buffer, copy all of it to registers, hand it back, then
+// score.  Every wait is bounded; a wait that gives up sets the error word and
+// the block stops once the copies and MMAs it issued have finished.
 constexpr int kTcStages = 4;
 constexpr int kTcConsumers = 8;
+constexpr int kTcBlock = kTcThreads + 64;     // consumers, loader, MMA warp
 
 // PREC: 1 = BF16, 3 = split BF16 (three copies along the reduction axis),
 // 8 = FP8 e4m3.
 template <int LP, int PREC, int TOPK>
-__global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __restrict__ x, int n, int len,
+__global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restrict__ x, int n, int len,
                                                               const unsigned char* __restrict__ Bg, int ntiles,
                                                               const float* __restrict__ wscore, int m,
                                                               const float2* __restrict__ dict,
                                                               int* __restrict__ best_idx,
                                                               float2* __restrict__ best_ip, int* __restrict__ err,
-                                                              const TcSlice* __restrict__ slices, int nslices) {
+                                                              const TcSlice* __restrict__ slices, int nslices,
+                                                              const int* seed, int* cand_out) {
     constexpr bool F8 = PREC == 8;
     constexpr int SPLIT = PREC == 3 ? 3 : 1;
     constexpr int EB = F8 ? 1 : 2;                   // operand bytes
@@ -169,7 +212,7 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
     unsigned char* sB = smraw + A_BYTES;             // [kTcStages][B_BYTES]
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_bfull[kTcStages], s_bempty[kTcStages], s_afull[2], s_aempty[2];
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_loaded, s_mmas;
     __shared__ float s_ms[kTcRows][TOPK];
     __shared__ int s_mi[kTcRows][TOPK];
     __shared__ float s_rs[kTcRows];                  // FP8: row scale 448 / max |x|
@@ -190,6 +233,8 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
         dict = slices[si].dict;
         n0 = ((int)blockIdx.x - slices[si].block0) * kTcRows;
         if (n0 >= n) return;    // a launch sized for more rows than the slice holds (n written on the device)
+        seed = nullptr;
+        cand_out = nullptr;
     }
 
     if (warp == 0) {
@@ -199,6 +244,8 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
     }
     if (tid == 0) {
         s_fail = 0;
+        s_loaded = 0;
+        s_mmas = 0;
         for (int q = 0; q < kTcStages; ++q) {
             mbar_init(smem_u32(&s_bfull[q]), 1);
             mbar_init(smem_u32(&s_bempty[q]), 1);
@@ -255,20 +302,32 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
     for (int q = 0; q < TOPK; ++q) { cs[q] = -1.f; ci[q] = 0x7fffffff; }
 
     if (warp == kTcConsumers) {
-        // ------------------------------ producer ------------------------------
+        // ------------------------------- loader -------------------------------
+        if (lane == 0) {
+            int loaded = 0;
+            for (int tile = 0; tile < ntiles && !*(volatile int*)&s_fail; ++tile) {
+                const int st = tile % kTcStages;
+                // the stage is free once the MMAs of tile - kTcStages have read it
+                if (tile >= kTcStages &&
+                    !wait_parity(smem_u32(&s_bempty[st]), (tile / kTcStages - 1) & 1)) {
+                    s_fail = 1;
+                    break;
+                }
+                const uint32_t bar = smem_u32(&s_bfull[st]);
+                mbar_expect_tx(bar, B_BYTES);
+                bulk_g2s(smem_u32(sB + st * B_BYTES), Bg + (size_t)tile * B_BYTES, B_BYTES, bar);
+                loaded = tile + 1;
+            }
+            s_loaded = loaded;
+        }
+        __syncwarp();
+    } else if (warp == kTcConsumers + 1) {
+        // --------------------------------- MMA --------------------------------
         if (lane == 0) {
             // kind::f16 BF16 x BF16, or kind::f8f6f4 E4M3 x E4M3 (format code 0)
             const uint32_t idesc = F8 ? mma_idesc_f16(kTcRows, NCOL) : mma_idesc(kTcRows, NCOL);
-            int loaded = 0, mmas = 0;   // tiles whose copy / whose MMAs were issued
-            auto load = [&](int tile) {
-                const int st = tile % kTcStages;
-                const uint32_t bar = smem_u32(&s_bfull[st]);
-                mbar_expect_tx(bar, B_BYTES);
-                loaded = tile + 1;
-                bulk_g2s(smem_u32(sB + st * B_BYTES), Bg + (size_t)tile * B_BYTES, B_BYTES, bar);
-            };
-            for (int t = 0; t < kTcStages && t < ntiles; ++t) load(t);
-            for (int tile = 0; tile < ntiles && !s_fail; ++tile) {
+            int mmas = 0;
+            for (int tile = 0; tile < ntiles && !*(volatile int*)&s_fail; ++tile) {
                 const int st = tile % kTcStages, buf = tile & 1;
                 if (!wait_parity(smem_u32(&s_bfull[st]), (tile / kTcStages) & 1)) { s_fail = 1; break; }
                 if (tile >= 2 && !wait_parity(smem_u32(&s_aempty[buf]), ((tile >> 1) - 1) & 1)) {
@@ -298,28 +357,28 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
                 mmas = tile + 1;
                 mma_commit(smem_u32(&s_afull[buf]));
                 mma_commit(smem_u32(&s_bempty[st]));
-                // refill the stage of the previous tile once its MMA has read it
-                const int prev = tile - 1;
-                if (prev >= 0 && prev + kTcStages < ntiles) {
-                    const int ps = prev % kTcStages;
-                    if (!wait_parity(smem_u32(&s_bempty[ps]), (prev / kTcStages) & 1)) { s_fail = 1; break; }
-                    load(prev + kTcStages);
-                }
             }
-            // every issued MMA and copy must finish before the block reuses shared
-            // memory or releases TMEM, also when a wait gave up (bounded again)
+            // every issued MMA must finish before the block releases TMEM or
+            // its shared memory, also when a wait gave up (bounded again)
             if (mmas > 0) {
                 const int last = mmas - 1;
                 if (!wait_parity(smem_u32(&s_bempty[last % kTcStages]), (last / kTcStages) & 1)) s_fail = 1;
             }
-            if (s_fail)
-                for (int t = mmas; t < loaded; ++t)
-                    wait_parity(smem_u32(&s_bfull[t % kTcStages]), (t / kTcStages) & 1);
+            s_mmas = mmas;
         }
         __syncwarp();
     } else {
         // ------------------------------ consumers -----------------------------
         const int lq = warp & 3, half = warp >> 2;
+        if (!F8 && seed) {
+            constexpr float kMargin = PREC == 3 ? 0x1p-10f : 0x1p-4f;
+            const int row = n0 + lq * 32 + lane;
+            const float thr = row < n ? seed_threshold<TOPK>(x + (size_t)row * len, len, seed + (size_t)row * kTopK,
+                                                             dict, wscore, m, kMargin)
+                                      : -1.f;
+#pragma unroll
+            for (int q = 0; q < TOPK; ++q) cs[q] = thr;
+        }
         for (int tile = 0; tile < ntiles; ++tile) {
             const int buf = tile & 1;
             if (!wait_parity(smem_u32(&s_afull[buf]), (tile >> 1) & 1)) { s_fail = 1; break; }
@@ -330,35 +389,29 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
             // greater score" ranks a newcomer below equal earlier atoms: the
             // list stays the top TOPK by (score, then lowest index).  The list
             // settles slowly (a newcomer enters with probability ~TOPK / atoms
-            // seen), so the insertion runs only when some lane of the warp
-            // needs it.  The accumulator is read in four groups of 8 atoms (a
-            // small loop body for the instruction cache); the buffer goes back
-            // to the producer after the last group.
+            // seen, and a seeded threshold starts it near its final level), so
+            // a group of 8 atoms is tested against the threshold with one
+            // maximum and one vote, and the insertion runs only when some lane
+            // of the warp needs it.  The whole accumulator half (4 groups of 8
+            // atoms) is copied to registers first, so the buffer goes back to
+            // the MMA warp before the scoring.
             const int a0 = tile * kTcAtoms + half * (kTcAtoms / 2);
-#pragma unroll 1
-            for (int grp = 0; grp < 4; ++grp) {
-                uint32_t v[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15])
-                    : "r"(taddr + 16u * (uint32_t)grp));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                // v[0..7]: Re of the group's 8 atoms, v[8..15]: their Im; two
-                // scores per packed instruction pair, one vote per two atoms
+            auto score = [&](const uint32_t (&v)[16], int ab) {
+                // v[0..7]: Re of the group's 8 atoms, v[8..15]: their Im
+                float2 sc[4];
 #pragma unroll
-                for (int u = 0; u < 8; u += 2) {
-                    const float2 sc = abs2_pair(make_float2(__uint_as_float(v[u]), __uint_as_float(v[u + 1])),
-                                                make_float2(__uint_as_float(v[8 + u]), __uint_as_float(v[9 + u])));
-                    const bool in0 = sc.x > cs[TOPK - 1];
-                    const bool in1 = sc.y > cs[TOPK - 1];
-                    if (__any_sync(0xffffffffu, in0 || in1)) {
+                for (int u = 0; u < 4; ++u)
+                    sc[u] = abs2_pair(make_float2(__uint_as_float(v[2 * u]), __uint_as_float(v[2 * u + 1])),
+                                      make_float2(__uint_as_float(v[8 + 2 * u]), __uint_as_float(v[9 + 2 * u])));
+                const float mx = fmaxf(fmaxf(fmaxf(sc[0].x, sc[0].y), fmaxf(sc[1].x, sc[1].y)),
+                                       fmaxf(fmaxf(sc[2].x, sc[2].y), fmaxf(sc[3].x, sc[3].y)));
+                if (__any_sync(0xffffffffu, mx > cs[TOPK - 1])) {
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const float s1 = h ? sc.y : sc.x;
-                            if (s1 > cs[TOPK - 1]) { cs[TOPK - 1] = s1; ci[TOPK - 1] = a0 + 8 * grp + u + h; }
+                    for (int h = 0; h < 8; ++h) {
+                        const float s1 = (h & 1) ? sc[h >> 1].y : sc[h >> 1].x;
+                        if (s1 > cs[TOPK - 1]) {
+                            cs[TOPK - 1] = s1;
+                            ci[TOPK - 1] = ab + h;
 #pragma unroll
                             for (int r = TOPK - 1; r > 0; --r) {
                                 if (cs[r] > cs[r - 1]) {
@@ -369,15 +422,32 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
                         }
                     }
                 }
-            }
+            };
+            uint32_t va[16], vb[16], vc[16], vd[16];
+            tmem_ld16(va, taddr);
+            tmem_ld16(vb, taddr + 16u);
+            tmem_ld16(vc, taddr + 32u);
+            tmem_ld16(vd, taddr + 48u);
+            tmem_wait16(va, cs[TOPK - 1]);                  // waits for all four copies
+            tmem_wait16(vb, cs[TOPK - 1]);
+            tmem_wait16(vc, cs[TOPK - 1]);
+            tmem_wait16(vd, cs[TOPK - 1]);
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&s_aempty[buf]));
-            if (s_fail) break;
+            score(va, a0);
+            score(vb, a0 + 8);
+            score(vc, a0 + 16);
+            score(vd, a0 + 24);
+            if (*(volatile int*)&s_fail) break;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    // copies that landed for no MMA (a wait gave up): let them finish before
+    // the block's shared memory goes (bounded)
+    if (warp == kTcConsumers && lane == 0)
+        for (int t = s_mmas; t < s_loaded; ++t) wait_parity(smem_u32(&s_bfull[t % kTcStages]), (t / kTcStages) & 1);
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * NCOL));
     }
@@ -414,6 +484,9 @@ __global__ void __launch_bounds__(kTcThreads + 32) k_match_tc(const float2* __re
     // FP32 re-rank of the candidates from the original data
     const int row = n0 + lrow;
     if (row >= n) return;
+    if (cand_out)
+#pragma unroll
+        for (int q = 0; q < TOPK; ++q) cand_out[(size_t)row * kTopK + q] = ci[q];
     const float2* xr = x + (size_t)row * len;
     float bs = -1.f;
     int bi = 0x7fffffff;
@@ -444,11 +517,12 @@ size_t tc_operand_bytes(int m, int len, int prec) {
 }
 
 static mrf_status tc_launch(MatchWorkspace& ws, const float2* x, int n, int blocks, const TcSlice* slices,
-                            int nslices, int len, const float2* dict, int m, int prec, cudaStream_t s);
+                            int nslices, int len, const float2* dict, int m, int prec, cudaStream_t s,
+                            int* cand_io = nullptr);
 
 mrf_status match_tc_candidates(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
-                               int prec, cudaStream_t s) {
-    return tc_launch(ws, x, n, (n + kTcRows - 1) / kTcRows, nullptr, 0, len, dict, m, prec, s);
+                               int prec, cudaStream_t s, int* cand_io) {
+    return tc_launch(ws, x, n, (n + kTcRows - 1) / kTcRows, nullptr, 0, len, dict, m, prec, s, cand_io);
 }
 
 mrf_status match_tc_batch(MatchWorkspace& ws, const TcSlice* d_slices, int nslices, int total_blocks, int len,
@@ -497,8 +571,10 @@ mrf_status tc_prepare_operand(MatchWorkspace& ws, const float2* dict, int m, int
 }
 
 static mrf_status tc_launch(MatchWorkspace& ws, const float2* x, int n, int blocks, const TcSlice* slices,
-                            int nslices, int len, const float2* dict, int m, int prec, cudaStream_t s) {
+                            int nslices, int len, const float2* dict, int m, int prec, cudaStream_t s,
+                            int* cand_io) {
     if (!slices) MRF_PROPAGATE(tc_prepare_operand(ws, dict, m, len, prec, s));
+    int* cand = (!slices && prec != 8) ? cand_io : nullptr;     // seeds in, candidates out
     const int Lp = padded_len(len, prec);
     const int ntiles = (m + kTcAtoms - 1) / kTcAtoms;
     if (blocks == 0) return MRF_OK;
@@ -509,10 +585,11 @@ static mrf_status tc_launch(MatchWorkspace& ws, const float2* x, int n, int bloc
         const size_t sm = (size_t)kTcRows * LPV * EBV + (size_t)kTcStages * 2 * kTcAtoms * LPV * EBV;            \
         MRF_CUDA(cudaFuncSetAttribute(k_match_tc<LPV, PR, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                       (int)sm));                                                                 \
-        k_match_tc<LPV, PR, TK><<<blocks, kTcThreads + 32, sm, s>>>(x, n, len,                                   \
+        k_match_tc<LPV, PR, TK><<<blocks, kTcBlock, sm, s>>>(x, n, len,                                   \
                                                                reinterpret_cast<const unsigned char*>(ws.tc_b),  \
                                                                ntiles, ws.wscore, m, dict, ws.best_idx,          \
-                                                               ws.best_ip, ws.tc_err, slices, nslices);          \
+                                                               ws.best_ip, ws.tc_err, slices, nslices, cand,     \
+                                                               cand);                                            \
     } while (0)
     if (prec == 1) {
         if (Lp == 16) MRF_TC_LAUNCH(16, 1);

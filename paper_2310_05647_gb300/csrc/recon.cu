@@ -977,7 +977,7 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
 
 static mrf_status match_maps(mrf_recon_s* R, cudaStream_t s) {
     return match_run(R->mws, R->alpha, R->N, R->K, R->dict_c, R->m, R->prm.match_precision, R->lut, R->idx,
-                     R->pd, R->t1t2, 1.0f, s);
+                     R->pd, R->t1t2, 1.0f, s, R->mws.cand);
 }
 
 // Learned matcher: decode the network outputs into maps; a fingerprint
@@ -1210,6 +1210,9 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     R->cost_cap = 1024;
     MRF_PROPAGATE(dalloc(R, &R->cost, R->cost_cap));
     MRF_PROPAGATE(R->mws.reserve(N, R->m));
+    // the loop's matching calls score the same N rows every time: each call
+    // starts from the previous call's candidates (-1 at first: no seed)
+    MRF_CUDA(cudaMemsetAsync(R->mws.cand, 0xff, sizeof(int) * (size_t)N * kTopK, s));
     MRF_PROPAGATE(ensure_subspace_workspace(p, K));
     MRF_PROPAGATE(match_prepare(R->mws, R->dict_c, R->atom_norm2, R->m, K, 0, s));
     if (R->prm.flags & MRF_RECON_LEARNED) {
