@@ -148,7 +148,8 @@ enum {
 /* Phi_D of Eq. 5 for n fingerprints of length len:
  *   k_i   = argmax_m |<d_m, x_i>| / ||d_m||     (||d_m||^2 with the LITERAL flag)
  *   eta_i = LUT[k_i],  rho_i = max(Re<d_k, x_i> / ||d_k||^2, 0)
- * <a, b> = sum conj(a) b; ties go to the lowest index (an all-zero x gives
+ * <a, b> = sum conj(a) b; ties go to the lowest index (an all-zero x, or
+ * one whose best score is not finite -- NaN or infinite entries -- gives
  * index 0, PD 0).  x: dev [n][len]; dict: dev [m][len]; atom_norm2: dev [m]
  * ||d_m||^2 or NULL to use the rows of dict (pass the full-length norms when
  * dict holds subspace-compressed atoms d_m Phi); lut: dev float [m][2]

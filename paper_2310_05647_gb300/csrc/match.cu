@@ -97,7 +97,12 @@ __global__ void __launch_bounds__(256) k_match_fp32(const float2* __restrict__ x
             if (better(s2, i2, bsc[i], bid[i])) { bsc[i] = s2; bid[i] = i2; bip[i] = make_float2(px, py); }
         }
         const int v = v0 + ty + 16 * i;
-        if (tx == 0 && v < n) { best_idx[v] = bid[i]; best_ip[v] = bip[i]; }
+        // no finite best score (NaN or infinite entries): index 0, PD 0, like an all-zero x
+        const bool found = bid[i] < m && isfinite(bsc[i]);
+        if (tx == 0 && v < n) {
+            best_idx[v] = found ? bid[i] : 0;
+            best_ip[v] = found ? bip[i] : make_float2(0.f, 0.f);
+        }
     }
 }
 

@@ -164,7 +164,7 @@ __device__ float seed_threshold(const float2* __restrict__ xr, int len, const in
             if (a[q] == a[r]) return -1.f;
     float x2 = 0.f;
     for (int k = 0; k < len; ++k) x2 += cabs2(xr[k]);
-    if (!(x2 > 1e-30f)) return -1.f;
+    if (!(x2 > 1e-30f && x2 < 1e30f)) return -1.f;          // zero, tiny, huge or not finite
     float lo = 3.4e38f;
 #pragma unroll
     for (int q = 0; q < TOPK; ++q) {
@@ -501,8 +501,10 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restri
         const float sc = cabs2(s) * wscore[a];
         if (better_cand(sc, a, bs, bi)) { bs = sc; bi = a; bip = s; }
     }
-    best_idx[row] = bi;
-    best_ip[row] = bip;
+    // no finite best score (NaN or infinite entries): index 0, PD 0, like an all-zero x
+    const bool found = bi < m && isfinite(bs);
+    best_idx[row] = found ? bi : 0;
+    best_ip[row] = found ? bip : make_float2(0.f, 0.f);
 }
 
 // reduction length: 2 len real coefficients (times 3 for the split form),

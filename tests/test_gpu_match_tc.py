@@ -11,10 +11,11 @@ top-8 re-rank) against the FP64 oracle, on subspace-compressed atoms.
   within 1% of the best) and agree with FP32 for most fingerprints."""
 import numpy as np
 import pytest
+import torch
 
 import synth
 from oracle import dictionary, epg, match as omatch
-from gpu_util import as_f32_inputs, c64, f32, mrf, np_, rand_c
+from gpu_util import as_f32_inputs, c64, dev, f32, mrf, np_, rand_c
 
 pytestmark = pytest.mark.gpu
 BF16, BF16X3, FP8 = 1, 2, 3
@@ -128,3 +129,31 @@ def test_tc_rejects_long_fingerprints():
     D = c64(np.ones((4, 65)))
     with pytest.raises(m.MRFError):
         m.match(c64(np.ones((3, 65))), D, f32(np.ones((4, 2))), precision=FP8)
+
+
+@pytest.mark.parametrize("prec", [0, BF16, BF16X3, FP8])
+def test_non_finite_fingerprints_give_index_zero(compressed, prec):
+    """Rows with NaN or infinite entries score nothing; they come out as
+    index 0 with PD 0 (like an all-zero row), and the finite rows beside them
+    are unaffected."""
+    m = mrf()
+    Dc, n2, lut = compressed
+    rng = np.random.default_rng(20 + prec)
+    n = 300
+    X = (Dc[rng.integers(0, len(Dc), n)] * rng.uniform(0.5, 2.0, (n, 1))).astype(np.complex64)
+    bad = [3, 130, 299]
+    X[3, 2] = np.nan
+    X[130, 0] = np.inf
+    X[299, :] = complex(np.nan, np.nan)
+    args = (c64(Dc), f32(lut))
+    idx, pd, t1t2 = m.match(c64(X), *args, atom_norm2=f32(n2), precision=prec)
+    gi, gp = np_(idx), np_(pd)
+    assert np.all(gi[bad] == 0) and np.all(gp[bad] == 0)
+    good = np.setdiff1d(np.arange(n), bad)
+    ref = m.match(c64(X[good]), *args, atom_norm2=f32(n2), precision=prec)
+    np.testing.assert_array_equal(gi[good], np_(ref[0]))
+    if prec in (BF16, BF16X3):
+        cand = torch.full((n, 8), -1, dtype=torch.int32, device=dev())
+        for _ in range(2):                        # unseeded, then seeded from its own candidates
+            si, sp, _ = m.match_seeded(c64(X), *args, cand, atom_norm2=f32(n2), precision=prec)
+            assert torch.equal(si, idx) and torch.equal(sp, pd)
