@@ -256,7 +256,20 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restri
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    // A tile.  Each thread loads a batch of 8 complex coefficients (the loads
+    // in flight together) before it converts and stores them: a loop with one
+    // dependent load per element waits out the memory latency per element.
+    const int ncoef = kTcRows * len;                 // complex coefficients of the tile
+    auto load_batch = [&](int b0, float2 (&xv)[8]) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = b0 + u * (int)blockDim.x;
+            const int row = i / len, kc = i - row * len;
+            xv[u] = (i < ncoef && n0 + row < n) ? x[(size_t)(n0 + row) * len + kc] : make_float2(0.f, 0.f);
+        }
+    };
     if (F8) {
+        // FP8: rows scaled by 448 / max |x| (zero rows past n, zero padding past 2 len)
         for (int row = tid; row < kTcRows; row += blockDim.x) {
             float mx = 0.f;
             if (n0 + row < n)
@@ -267,28 +280,48 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restri
             s_rs[row] = mx > 0.f ? kE4m3Max / mx : 0.f;
         }
         __syncthreads();
-        for (int e = tid; e < kTcRows * LP; e += blockDim.x) {
-            const int row = e / LP, k = e - row * LP;
-            float v = 0.f;
-            if (n0 + row < n && k < 2 * len) {
-                const float2 xv = x[(size_t)(n0 + row) * len + (k >> 1)];
-                v = ((k & 1) ? xv.y : xv.x) * s_rs[row];
+        for (int e = tid; e < kTcRows * (LP - 2 * len); e += blockDim.x) {
+            const int w = LP - 2 * len, row = e / w;
+            sA[core_off8(row, 2 * len + (e - row * w), KC)] = 0;
+        }
+        for (int b0 = tid; b0 < ncoef; b0 += 8 * (int)blockDim.x) {
+            float2 xv[8];
+            load_batch(b0, xv);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = b0 + u * (int)blockDim.x;
+                if (i >= ncoef) break;
+                const int row = i / len, kc = i - row * len;
+                sA[core_off8(row, 2 * kc, KC)] = to_e4m3(xv[u].x * s_rs[row]);
+                sA[core_off8(row, 2 * kc + 1, KC)] = to_e4m3(xv[u].y * s_rs[row]);
             }
-            sA[core_off8(row, k, KC)] = to_e4m3(v);
         }
-    }
-    // A tile: fingerprint rows in BF16 (zero rows past n, zero padding past the
-    // SPLIT copies of the 2 len coefficients)
-    for (int e = tid; !F8 && e < kTcRows * LP; e += blockDim.x) {
-        const int row = e / LP, kk = e - row * LP;
-        const int part = kk / (2 * len), k = kk - part * 2 * len;
-        float v = 0.f;
-        if (n0 + row < n && part < SPLIT) {
-            const float2 xv = x[(size_t)(n0 + row) * len + (k >> 1)];
-            v = (k & 1) ? xv.y : xv.x;
+    } else {
+        // BF16: the SPLIT copies of the 2 len coefficients (zero rows past n,
+        // zero padding past them)
+        const int used = SPLIT * 2 * len;
+        for (int e = tid; e < kTcRows * (LP - used); e += blockDim.x) {
+            const int w = LP - used, row = e / w;
+            *reinterpret_cast<__nv_bfloat16*>(sA + core_off(row, used + (e - row * w), KC)) = __float2bfloat16_rn(0.f);
         }
-        *reinterpret_cast<__nv_bfloat16*>(sA + core_off(row, kk, KC)) =
-            part < SPLIT ? split_part(v, part, true, SPLIT) : __float2bfloat16_rn(0.f);
+        for (int b0 = tid; b0 < ncoef; b0 += 8 * (int)blockDim.x) {
+            float2 xv[8];
+            load_batch(b0, xv);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = b0 + u * (int)blockDim.x;
+                if (i >= ncoef) break;
+                const int row = i / len, kc = i - row * len;
+#pragma unroll
+                for (int part = 0; part < SPLIT; ++part) {
+                    // (Re, Im) are neighbours in one 16-byte chunk: one 4-byte store
+                    __nv_bfloat162 pr;
+                    pr.x = split_part(xv[u].x, part, true, SPLIT);
+                    pr.y = split_part(xv[u].y, part, true, SPLIT);
+                    *reinterpret_cast<__nv_bfloat162*>(sA + core_off(row, part * 2 * len + 2 * kc, KC)) = pr;
+                }
+            }
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
