@@ -137,6 +137,35 @@ __device__ __forceinline__ bool better_cand(float s, int i, float bs, int bi) {
     return s > bs || (s == bs && i < bi);
 }
 
+// FP32 inner products s_q = <d_{a_q}, x> = sum_k conj(d_{a_q,k}) x_k of C atoms
+// with one fingerprint row, summed in k order (atoms with a_q outside [0, m)
+// give 0).  The row and the atoms are read U coefficients at a time with all
+// of a chunk's loads issued before its arithmetic, so a row costs ~len / U
+// memory round trips instead of C len.
+template <int C>
+__device__ __forceinline__ void atom_products(const float2* __restrict__ xr, int len, const int (&a)[C],
+                                              const float2* __restrict__ dict, int m, float2 (&s)[C]) {
+    constexpr int U = C <= 4 ? 4 : 2;
+#pragma unroll
+    for (int q = 0; q < C; ++q) s[q] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < len; k0 += U) {
+        float2 xv[U], dv[C][U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = k0 + u < len ? xr[k0 + u] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < C; ++q)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                dv[q][u] = (a[q] >= 0 && a[q] < m && k0 + u < len) ? dict[(size_t)a[q] * len + k0 + u]
+                                                                    : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < C; ++q)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (k0 + u < len) s[q] = cadd(s[q], cconjmul(dv[q][u], xv[u]));
+    }
+}
+
 // Starting threshold of a fingerprint's candidate list from TOPK seed atoms
 // (in a loop: the previous call's candidates of the same row): the smallest
 // FP32 score among them, less margin ||x||^2.  Any TOPK distinct atoms score
@@ -162,17 +191,14 @@ __device__ float seed_threshold(const float2* __restrict__ xr, int len, const in
 #pragma unroll
         for (int r = 0; r < q; ++r)
             if (a[q] == a[r]) return -1.f;
+    float2 sq[TOPK];
+    atom_products<TOPK>(xr, len, a, dict, m, sq);
     float x2 = 0.f;
-    for (int k = 0; k < len; ++k) x2 += cabs2(xr[k]);
+    for (int k = 0; k < len; ++k) x2 += cabs2(xr[k]);       // (the row is in L1 by now)
     if (!(x2 > 1e-30f && x2 < 1e30f)) return -1.f;          // zero, tiny, huge or not finite
     float lo = 3.4e38f;
 #pragma unroll
-    for (int q = 0; q < TOPK; ++q) {
-        const float2* dr = dict + (size_t)a[q] * len;
-        float2 sq = make_float2(0.f, 0.f);
-        for (int k = 0; k < len; ++k) sq = cadd(sq, cconjmul(dr[k], xr[k]));
-        lo = fminf(lo, cabs2(sq) * wscore[a[q]]);
-    }
+    for (int q = 0; q < TOPK; ++q) lo = fminf(lo, cabs2(sq[q]) * wscore[a[q]]);
     return lo - margin * x2;
 }
 
@@ -520,7 +546,8 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restri
     if (cand_out)
 #pragma unroll
         for (int q = 0; q < TOPK; ++q) cand_out[(size_t)row * kTopK + q] = ci[q];
-    const float2* xr = x + (size_t)row * len;
+    float2 sp[TOPK];
+    atom_products<TOPK>(x + (size_t)row * len, len, ci, dict, m, sp);
     float bs = -1.f;
     int bi = 0x7fffffff;
     float2 bip = make_float2(0.f, 0.f);
@@ -528,11 +555,8 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restri
     for (int q = 0; q < TOPK; ++q) {
         const int a = ci[q];
         if (a >= m) continue;
-        const float2* dr = dict + (size_t)a * len;
-        float2 s = make_float2(0.f, 0.f);
-        for (int k = 0; k < len; ++k) s = cadd(s, cconjmul(dr[k], xr[k]));
-        const float sc = cabs2(s) * wscore[a];
-        if (better_cand(sc, a, bs, bi)) { bs = sc; bi = a; bip = s; }
+        const float sc = cabs2(sp[q]) * wscore[a];
+        if (better_cand(sc, a, bs, bi)) { bs = sc; bi = a; bip = sp[q]; }
     }
     // no finite best score (NaN or infinite entries): index 0, PD 0, like an all-zero x
     const bool found = bi < m && isfinite(bs);
