@@ -210,7 +210,10 @@ __device__ float seed_threshold(const float2* __restrict__ xr, int len, const in
 // free.  Warps 0-7 (consumers, two per TMEM lane quarter, one column half
 // each): wait for a buffer, copy all of it to registers, hand it back, then
 // score.  Every wait is bounded; a wait that gives up sets the error word and
-// the block stops once the copies and MMAs it issued have finished.
+// the block stops once the copies and MMAs it issued have finished.  (The
+// loader and MMA loops do not poll the shared error word: a shared-memory read
+// per tile costs them several hundred cycles; a role whose partner stopped
+// gives up at its own next wait.)
 constexpr int kTcStages = 4;
 constexpr int kTcConsumers = 8;
 constexpr int kTcBlock = kTcThreads + 64;     // consumers, loader, MMA warp
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restri
         // ------------------------------- loader -------------------------------
         if (lane == 0) {
             int loaded = 0;
-            for (int tile = 0; tile < ntiles && !*(volatile int*)&s_fail; ++tile) {
+            for (int tile = 0; tile < ntiles; ++tile) {
                 const int st = tile % kTcStages;
                 // the stage is free once the MMAs of tile - kTcStages have read it
                 if (tile >= kTcStages &&
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restri
             // kind::f16 BF16 x BF16, or kind::f8f6f4 E4M3 x E4M3 (format code 0)
             const uint32_t idesc = F8 ? mma_idesc_f16(kTcRows, NCOL) : mma_idesc(kTcRows, NCOL);
             int mmas = 0;
-            for (int tile = 0; tile < ntiles && !*(volatile int*)&s_fail; ++tile) {
+            for (int tile = 0; tile < ntiles; ++tile) {
                 const int st = tile % kTcStages, buf = tile & 1;
                 if (!wait_parity(smem_u32(&s_bfull[st]), (tile / kTcStages) & 1)) { s_fail = 1; break; }
                 if (tile >= 2 && !wait_parity(smem_u32(&s_aempty[buf]), ((tile >> 1) - 1) & 1)) {
