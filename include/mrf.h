@@ -330,6 +330,15 @@ mrf_status mrf_recon_maps(mrf_recon r, float* t1, float* t2, float* pd, int* idx
                           mrf_stream stream);
 /* Copy of the coefficient images alpha (dev [ny][nx][K]). */
 mrf_status mrf_recon_alpha(mrf_recon r, mrf_c64* alpha, mrf_stream stream);
+/* Work counters of the SVT step (Eq. 18) since mrf_recon_create: sweeps and
+ * rotations = the one-sided Jacobi sweeps and column-pair rotations executed,
+ * summed over patches (two patches share a warp, and a warp sweeps until
+ * both are done); patch_svts = patches x SVT launches.  For measurement: the
+ * SVD is iterative, so its work depends on the data.  Synchronises the
+ * stream.  NULL argument: MRF_EINVAL. */
+mrf_status mrf_recon_svt_stats(mrf_recon R, double* sweeps, double* rotations, double* patch_svts,
+                               mrf_stream stream);
+
 /* Scalars of the current state (host outputs, each nullable; synchronises). */
 mrf_status mrf_recon_info(mrf_recon r, double* a_norm, double* x_scale, double* lam1,
                           double* sigma2, mrf_stream stream);

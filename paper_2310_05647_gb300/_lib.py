@@ -64,6 +64,7 @@ SIGNATURES = {
     "mrf_recon_maps": (i32, [vp, vp, vp, vp, vp, vp]),
     "mrf_recon_alpha": (i32, [vp, vp, vp]),
     "mrf_recon_info": (i32, [vp, f64p, f64p, f64p, f64p, vp]),
+    "mrf_recon_svt_stats": (i32, [vp, f64p, f64p, f64p, vp]),
     "mrf_recon_destroy": (i32, [vp]),
     "mrf_launch_count": (C.c_longlong, []),
     "mrf_profile_enable": (i32, [i32]),

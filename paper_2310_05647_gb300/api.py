@@ -414,6 +414,14 @@ class Recon:
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         _lib.call("mrf_recon_restore", self.handle, buf.ctypes.data, buf.size, _stream())
 
+    def svt_stats(self):
+        """(sweeps, rotations, patch_svts): Jacobi sweeps and column-pair rotations
+        the SVT step executed since create, summed over patches, and patches x
+        SVT launches."""
+        vals = [C.c_double() for _ in range(3)]
+        _lib.call("mrf_recon_svt_stats", self.handle, *[C.byref(v) for v in vals], _stream())
+        return tuple(v.value for v in vals)
+
     def info(self):
         vals = [C.c_double() for _ in range(4)]
         _lib.call("mrf_recon_info", self.handle, *[C.byref(v) for v in vals], _stream())

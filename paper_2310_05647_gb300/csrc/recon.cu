@@ -570,7 +570,7 @@ __device__ __forceinline__ float lane_sum(float v) {
 template <int R, int KP, int LANES>
 __global__ void __launch_bounds__(128, LANES == 16 ? (R * KP <= 32 ? 3 : 2) : ((R <= 2 && KP <= 10) ? 4 : 1))
     k_svt(const float2* __restrict__ alpha, PatchGeom g, int K, float tau, float2* __restrict__ P,
-          double* __restrict__ nuc, float2* __restrict__ Vio, int warm) {
+          double* __restrict__ nuc, float2* __restrict__ Vio, int warm, unsigned long long* __restrict__ stats) {
     const int lane = threadIdx.x & 31;
     const int sl = lane & (LANES - 1), base = lane & ~(LANES - 1);
     const int j = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / LANES) + lane / LANES;
@@ -633,7 +633,9 @@ __global__ void __launch_bounds__(128, LANES == 16 ? (R * KP <= 32 ? 3 : 2) : ((
     constexpr float kJacobiTol = 2e-6f;
     constexpr float kJacobiQuad = 3e-4f;
     constexpr int NP = KP / 2;
+    int nsweep = 0, nrot = 0;     // executed sweeps and rotations of this patch (for stats)
     for (int sweep = 0; sweep < 30; ++sweep) {
+        ++nsweep;
         float n2[KP];
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
@@ -681,6 +683,7 @@ __global__ void __launch_bounds__(128, LANES == 16 ? (R * KP <= 32 ? 3 : 2) : ((
                 const float g2 = gr[i] * gr[i] + gi[i] * gi[i];
                 if (g2 > 1e-36f && g2 > kJacobiTol * kJacobiTol * al * be) {
                     rotated = true;
+                    ++nrot;
                     large |= g2 > kJacobiQuad * kJacobiQuad * al * be;
                     const float ig = rsqrtf(g2), gabs = g2 * ig;
                     // t: the root of t^2 + 2 zeta t - 1 = 0 of smaller magnitude,
@@ -733,6 +736,10 @@ __global__ void __launch_bounds__(128, LANES == 16 ? (R * KP <= 32 ? 3 : 2) : ((
         f[k] = sg > tau ? (sg - tau) / sg : 0.f;
     }
     if (nuc && active && sl == 0) atomicAdd(nuc, (double)nsum);
+    if (stats && active && sl == 0) {
+        atomicAdd(&stats[0], (unsigned long long)nsweep);
+        atomicAdd(&stats[1], (unsigned long long)nrot);
+    }
     if (Vp && sl < KP) {
 #pragma unroll
         for (int k = 0; k < KP; ++k) Vp[sl * KP + k] = v[k];
@@ -867,6 +874,8 @@ struct mrf_recon_s {
     int cost_cap = 0, iters_done = 0;
     float2* svt_v = nullptr;    // [np][svt_kp][svt_kp] right singular vectors of the last SVT
     int svt_kp = 0, svt_warm = 0;
+    unsigned long long* svt_stats = nullptr;   // executed Jacobi sweeps and rotations, summed over patches
+    double svt_patch_launches = 0.0;           // patches x SVT launches since create
     // learned matcher (MRF_RECON_LEARNED)
     float t1min = 0.f, t2min = 0.f;
     float *mlp_x = nullptr, *mlp_norm = nullptr, *mlp_y = nullptr;
@@ -909,7 +918,8 @@ static mrf_status svt(mrf_recon_s* R, const float2* alpha, float2* P, double* nu
     const bool half = rows <= 64 && KP <= 12;
     const int per_block = half ? 8 : 4;
     const unsigned blocks = (unsigned)((R->np + per_block - 1) / per_block);
-#define MRF_SVT(RR, KK, LL) k_svt<RR, KK, LL><<<blocks, 128, 0, s>>>(alpha, R->g, K, tau, P, nuc, R->svt_v, warm)
+#define MRF_SVT(RR, KK, LL) \
+    k_svt<RR, KK, LL><<<blocks, 128, 0, s>>>(alpha, R->g, K, tau, P, nuc, R->svt_v, warm, R->svt_stats)
     if (half && rows <= 32) {
         switch (KP) {
             case 4: MRF_SVT(2, 4, 16); break;
@@ -938,6 +948,7 @@ static mrf_status svt(mrf_recon_s* R, const float2* alpha, float2* P, double* nu
 #undef MRF_SVT
     MRF_LAUNCHED_AS("k_svt", s);
     R->svt_warm = 1;
+    R->svt_patch_launches += R->np;
     return MRF_OK;
 }
 
@@ -1207,6 +1218,8 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(dalloc(R, &R->acc, 8));
     R->svt_kp = K <= 4 ? 4 : K <= 8 ? 8 : K == 10 ? 10 : K <= 12 ? 12 : 16;
     MRF_PROPAGATE(dalloc(R, &R->svt_v, (size_t)np * R->svt_kp * R->svt_kp));
+    MRF_PROPAGATE(dalloc(R, &R->svt_stats, 2));
+    MRF_CUDA(cudaMemsetAsync(R->svt_stats, 0, 2 * sizeof(unsigned long long), s));
     R->cost_cap = 1024;
     MRF_PROPAGATE(dalloc(R, &R->cost, R->cost_cap));
     MRF_PROPAGATE(R->mws.reserve(N, R->m));
@@ -1404,6 +1417,19 @@ extern "C" mrf_status mrf_recon_alpha(mrf_recon R, mrf_c64* alpha, mrf_stream st
     MRF_REQUIRE(R && alpha, "mrf_recon_alpha: NULL argument");
     MRF_CUDA(cudaMemcpyAsync(alpha, R->alpha, sizeof(float2) * (size_t)R->N * R->K, cudaMemcpyDeviceToDevice,
                              as_stream(stream)));
+    return MRF_OK;
+}
+
+extern "C" mrf_status mrf_recon_svt_stats(mrf_recon R, double* sweeps, double* rotations, double* patch_svts,
+                                          mrf_stream stream) {
+    MRF_REQUIRE(R && sweeps && rotations && patch_svts, "mrf_recon_svt_stats: NULL argument");
+    cudaStream_t s = as_stream(stream);
+    unsigned long long h[2] = {0, 0};
+    MRF_CUDA(cudaMemcpyAsync(h, R->svt_stats, sizeof h, cudaMemcpyDeviceToHost, s));
+    MRF_CUDA(cudaStreamSynchronize(s));
+    *sweeps = (double)h[0];
+    *rotations = (double)h[1];
+    *patch_svts = R->svt_patch_launches;
     return MRF_OK;
 }
 

@@ -178,3 +178,18 @@ def test_serial_and_concurrent_iterations_agree(prob, mode):
         assert (ia == ib).mean() > 0.99
         same = same and bool((ia == ib).all())
     assert rel(np_(rc.alpha()), np_(rs.alpha())) < (1e-5 if same else 1e-3)
+
+
+def test_svt_work_counters():
+    """The SVT step's sweep and rotation counters: every patch of every SVT
+    launch runs at least one sweep and at most the kernel's 30, and the patch
+    count matches the launches."""
+    pr = problem()
+    rec = gpu_recon(pr, 0)
+    s0, r0, p0 = rec.svt_stats()
+    rec.iterate(3)
+    s1, r1, p1 = rec.svt_stats()
+    npatch = (p1 - p0) / 3
+    assert npatch == ((pr["n"] - 8) // 4 + 1) ** 2           # 8 x 8 patches at stride 4
+    assert npatch <= s1 - s0 <= 30 * npatch * 3
+    assert r1 - r0 >= 0
