@@ -287,12 +287,25 @@ __global__ void __launch_bounds__(kKnThreads + 32) k_knn_tc(const int* __restric
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    // A tile: centred query vectors (zero past fd and past np)
-    for (int e = tid; e < kKnRows * LP; e += blockDim.x) {
-        const int row = e / LP, k = e - row * LP;
-        const int q = q0 + row;
-        const int v = (q < np && k < fd) ? F[(size_t)q * ld + k] - kKnCentre : 0;
-        *reinterpret_cast<__half*>(sA + core_off(row, k, KC)) = __int2half_rn(v);
+    // A tile: centred query vectors (zero past fd and past np); each thread
+    // loads 8 entries before it converts and stores them, so the loads are in
+    // flight together instead of one dependent load per entry
+    for (int b0 = tid; b0 < kKnRows * LP; b0 += 8 * (int)blockDim.x) {
+        int vv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = b0 + u * (int)blockDim.x;
+            const int row = e / LP, k = e - row * LP;
+            const int q = q0 + row;
+            vv[u] = (e < kKnRows * LP && q < np && k < fd) ? F[(size_t)q * ld + k] - kKnCentre : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = b0 + u * (int)blockDim.x;
+            if (e >= kKnRows * LP) break;
+            const int row = e / LP, k = e - row * LP;
+            *reinterpret_cast<__half*>(sA + core_off(row, k, KC)) = __int2half_rn(vv[u]);
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -318,7 +331,10 @@ __global__ void __launch_bounds__(kKnThreads + 32) k_knn_tc(const int* __restric
                 bulk_g2s(smem_u32(sB + st * B_BYTES), Bg + (size_t)(t0 + tile) * (B_BYTES / 2), B_BYTES, bar);
             };
             for (int t = 0; t < kKnStages && t < ntiles; ++t) load(t);
-            for (int tile = 0; tile < ntiles && !s_fail; ++tile) {
+            // (no read of the shared error word per tile: it costs the producer
+            // several hundred cycles; a role whose partner stopped gives up at
+            // its own next bounded wait)
+            for (int tile = 0; tile < ntiles; ++tile) {
                 const int st = tile % kKnStages, buf = tile & 1;
                 if (!wait_parity(smem_u32(&s_bfull[st]), (tile / kKnStages) & 1)) { s_fail = 1; break; }
                 if (tile >= 2 && !wait_parity(smem_u32(&s_aempty[buf]), ((tile >> 1) - 1) & 1)) {
