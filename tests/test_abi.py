@@ -61,6 +61,25 @@ def test_host_validation_without_gpu(lib):
     assert lib.mrf_match(dummy, 0, 10, dummy, None, dummy, 5, 0, None, None, None, None) == 0   # empty: no-op
 
 
+def test_host_validation_of_seeded_matching_sigma2_and_svt_counters(lib):
+    dummy = C.c_void_p(16)
+    d = [C.c_double() for _ in range(3)]
+    # seeded matching: only the BF16 forms, and a candidate buffer unless n == 0
+    assert lib.mrf_match_seeded(dummy, 4, 10, dummy, None, dummy, 5, 0, dummy, None, None, None, None) == 1
+    assert "precision" in _err(lib)
+    assert lib.mrf_match_seeded(dummy, 4, 10, dummy, None, dummy, 5, 3, dummy, None, None, None, None) == 1
+    assert lib.mrf_match_seeded(dummy, 4, 10, dummy, None, dummy, 5, 2, None, None, None, None, None) == 1
+    assert "cand" in _err(lib)
+    assert lib.mrf_match_seeded(dummy, 0, 10, dummy, None, dummy, 5, 2, None, None, None, None, None) == 0
+    # sigma^2: negative counts and null pointers
+    assert lib.mrf_graph_sigma2(dummy, -1, dummy, None) == 1
+    assert lib.mrf_graph_sigma2(None, 5, dummy, None) == 1
+    assert lib.mrf_graph_sigma2(dummy, 5, None, None) == 1
+    # SVT work counters of no reconstruction
+    assert lib.mrf_recon_svt_stats(None, *[C.byref(v) for v in d], None) == 1
+    assert lib.mrf_recon_svt_stats(dummy, None, C.byref(d[1]), C.byref(d[2]), None) == 1
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_2310_05647_gb300 import _lib
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))

@@ -77,6 +77,24 @@ def test_trace_form_equals_pairwise_form():
     assert graph.trace_term(X, L, pg) == pytest.approx(0.5 * pair, rel=1e-12)
 
 
+def test_trace_from_forward_knn_lists_alone():
+    """With W = (K + K^T)/2 of a kNN graph, Tr(Q L Q^H) = sum_j deg_j |Q_j|^2 -
+    sum_j sum_{i in N(j)} w_ji Re <Q_j, Q_i>: the reverse half of W adds the
+    same sum as the forward half (the form the device's cost trace uses)."""
+    rng = np.random.default_rng(9)
+    pg = patches.PatchGrid(20, 20, 4, 2)
+    X = rng.standard_normal((20, 20, 3)) + 1j * rng.standard_normal((20, 20, 3))
+    F = rng.integers(0, 50, (pg.count, 6))
+    nbr, d2 = graph.knn(F, 5)
+    w = np.exp(-d2 / graph.sigma2(d2.astype(np.float64)))
+    L = graph.laplacian(graph.adjacency(nbr, d2, graph.sigma2(d2.astype(np.float64))))
+    deg = np.diag(L)
+    Q = pg.extract(X).reshape(pg.count, -1)
+    fwd = sum(deg[j] * np.vdot(Q[j], Q[j]).real for j in range(pg.count)) - sum(
+        w[j, q] * np.vdot(Q[j], Q[nbr[j, q]]).real for j in range(pg.count) for q in range(nbr.shape[1]))
+    assert graph.trace_term(X, L, pg) == pytest.approx(fwd, rel=1e-12)
+
+
 def test_graph_term_is_gradient_of_trace():
     # d/de Tr(Q(X+eE) L Q(X+eE)^H) at e=0 equals 2 Re <E, Q^*(Q(X) L)>
     rng = np.random.default_rng(4)
