@@ -756,9 +756,9 @@ def run_ours(args, dist):
         if "chosen" in res:
             a, b = res["chosen"]["maps"], res["learned"]["maps"]
             mask = inp["truth"][3]
-            lv["nrmse_vs_exhaustive_judge"] = {nm: float(np.sqrt(np.sum((b[i][mask] - a[i][mask]) ** 2) /
-                                                                 np.sum(a[i][mask] ** 2)))
-                                               for i, nm in enumerate(("t1", "t2", "pd"))}
+            lv["nrmse_vs_exhaustive"] = {nm: float(np.sqrt(np.sum((b[i][mask] - a[i][mask]) ** 2) /
+                                                           np.sum(a[i][mask] ** 2)))
+                                         for i, nm in enumerate(("t1", "t2", "pd"))}
     if "plain" in res and "chosen" in res:
         import numpy as np
         a, b = res["plain"]["maps"], res["chosen"]["maps"]
