@@ -67,12 +67,21 @@ __device__ double block_sum(double v) {
     return v;
 }
 
+// *acc += sum |x_i|^2 (x 16-byte aligned).  A grid of kNorm2Blocks blocks
+// reads x two values per 16-byte load; each thread sums its ~n / (blocks x
+// 256) terms in FP32, the threads and blocks add in FP64 (one atomic per
+// block: thousands of FP64 atomics on one word cost more than the read).
+constexpr int kNorm2Blocks = 4 * 152;
 __global__ void k_norm2_acc(const float2* __restrict__ x, size_t n, double* __restrict__ acc) {
-    double s = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        s += (double)cabs2(x[i]);
-    s = block_sum(s);
-    if (threadIdx.x == 0) atomicAdd(acc, s);
+    float s = 0.f;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n / 2; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 q = x4[i];
+        s += q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) s += cabs2(x[n - 1]);
+    const double d = block_sum((double)s);
+    if (threadIdx.x == 0) atomicAdd(acc, d);
 }
 
 // re/im of sum conj(a) b
@@ -1090,7 +1099,7 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
     MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, s));
     if (cost) {
         const size_t nr = (size_t)R->plan->T * R->plan->ns;
-        k_norm2_acc<<<nblk(nr), 256, 0, s>>>(R->r, nr, R->acc + 0);
+        k_norm2_acc<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->acc + 0);
         MRF_LAUNCHED_AS("k_norm2_acc", s);
         MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, s));
         k_cost<<<1, 1, 0, s>>>(R->acc, R->scal + 2, R->prm.lam2, R->cost + (it % R->cost_cap));
@@ -1159,7 +1168,7 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, s));
     if (cost) {
         const size_t nr = (size_t)R->plan->T * R->plan->ns;
-        k_norm2_acc<<<nblk(nr), 256, 0, s>>>(R->r, nr, R->acc + 0);
+        k_norm2_acc<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->acc + 0);
         MRF_LAUNCHED_AS("k_norm2_acc", s);
     }
     MRF_CUDA(cudaStreamWaitEvent(s, R->ev[3], 0));
