@@ -301,9 +301,13 @@ __global__ void k_gather_grid(const float2* __restrict__ R, int K, const int* __
     for (int i = b; i < e; ++i) {
         const int p = pt[i];
         if (p != cur) {
-            for (int k = 0; k < K; ++k) {
-                atomicAdd(&grid[(size_t)k * GG2 + cur].x, acc[k].x);
-                atomicAdd(&grid[(size_t)k * GG2 + cur].y, acc[k].y);
+            // (loops over K unrolled to the 16-entry bound: acc stays in registers)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if (k < K) {
+                    atomicAdd(&grid[(size_t)k * GG2 + cur].x, acc[k].x);
+                    atomicAdd(&grid[(size_t)k * GG2 + cur].y, acc[k].y);
+                }
                 acc[k] = make_float2(0.f, 0.f);
             }
             cur = p;
@@ -314,9 +318,12 @@ __global__ void k_gather_grid(const float2* __restrict__ R, int K, const int* __
         for (int k = 0; k < 16; ++k)
             if (k < K) acc[k] = cadd(acc[k], cscale(r[k], wi));
     }
-    for (int k = 0; k < K; ++k) {
-        atomicAdd(&grid[(size_t)k * GG2 + cur].x, acc[k].x);
-        atomicAdd(&grid[(size_t)k * GG2 + cur].y, acc[k].y);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k < K) {
+            atomicAdd(&grid[(size_t)k * GG2 + cur].x, acc[k].x);
+            atomicAdd(&grid[(size_t)k * GG2 + cur].y, acc[k].y);
+        }
     }
 }
 
@@ -357,8 +364,11 @@ __global__ void __launch_bounds__(512) k_gather_warp(const float2* __restrict__ 
         }
     }
     const int pn = __shfl_down_sync(0xffffffffu, p, 1);
-    if (valid && (lane == 31 || pn != p))
-        for (int k = 0; k < K; ++k) atomicAdd(&grid[(size_t)k * GG2 + p], c[k]);
+    if (valid && (lane == 31 || pn != p)) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)             // (unrolled: c stays in registers)
+            if (k < K) atomicAdd(&grid[(size_t)k * GG2 + p], c[k]);
+    }
 }
 
 // Inverse FFT of a strip's columns of grid image f, image rows kept.
@@ -516,19 +526,30 @@ __global__ void k_interp_groups(const float2* __restrict__ spec, int K, const in
 }
 
 // y[t][j] = scale * sum_k conj(phi[t][k]) Y[g(t)][j][k] - b[t][j]
+// One thread per (group, sample): the group's K values stay in registers and
+// every frame of the group is written from them, so Y is read once rather
+// than once per frame.
 __global__ void k_combine_fwd(const float2* __restrict__ Y, const float2* __restrict__ phi, int K,
-                              const int* __restrict__ group_of, int T, int ns, float scale,
-                              const float2* __restrict__ bsub, float2* __restrict__ y) {
+                              const int* __restrict__ gf_off, const int* __restrict__ gf, int ngroups, int ns,
+                              float scale, const float2* __restrict__ bsub, float2* __restrict__ y) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= (size_t)T * ns) return;
-    const int t = (int)(i / ns), j = (int)(i - (size_t)t * ns);
-    const float2* yv = Y + ((size_t)group_of[t] * ns + j) * K;
-    const float2* p = phi + (size_t)t * K;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int k = 0; k < K; ++k) acc = cadd(acc, cmulc(yv[k], p[k]));
-    acc = cscale(acc, scale);
-    if (bsub) acc = csub(acc, bsub[i]);
-    y[i] = acc;
+    if (i >= (size_t)ngroups * ns) return;
+    const int g = (int)(i / ns), j = (int)(i - (size_t)g * ns);
+    float2 yv[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) yv[k] = k < K ? Y[i * K + k] : make_float2(0.f, 0.f);
+    for (int q = gf_off[g]; q < gf_off[g + 1]; ++q) {
+        const int t = gf[q];
+        const float2* p = phi + (size_t)t * K;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < K) acc = cadd(acc, cmulc(yv[k], p[k]));
+        acc = cscale(acc, scale);
+        const size_t o = (size_t)t * ns + j;
+        if (bsub) acc = csub(acc, bsub[o]);
+        y[o] = acc;
+    }
 }
 
 // R[g][j][k] = sum_{t in g} phi[t][k] r[t][j]
@@ -541,15 +562,28 @@ __global__ void k_combine_adj(const float2* __restrict__ r, const float2* __rest
     float2 acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
-    for (int q = gf_off[g]; q < gf_off[g + 1]; ++q) {
-        const int t = gf[q];
-        const float2 v = r[(size_t)t * ns + j];
-        const float2* p = phi + (size_t)t * K;
+    // four frames' samples loaded before they are added (in frame order)
+    const int q1 = gf_off[g + 1];
+    for (int q0 = gf_off[g]; q0 < q1; q0 += 4) {
+        float2 v[4];
+        int tt[4];
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < K) acc[k] = cadd(acc[k], cmul(v, p[k]));
+        for (int u = 0; u < 4; ++u) {
+            tt[u] = q0 + u < q1 ? gf[q0 + u] : 0;
+            v[u] = q0 + u < q1 ? r[(size_t)tt[u] * ns + j] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (q0 + u >= q1) break;
+            const float2* p = phi + (size_t)tt[u] * K;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < K) acc[k] = cadd(acc[k], cmul(v[u], p[k]));
+        }
     }
-    for (int k = 0; k < K; ++k) R[i * K + k] = acc[k];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)                 // (unrolled: acc stays in registers)
+        if (k < K) R[i * K + k] = acc[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -1045,9 +1079,9 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
         }));
         MRF_LAUNCHED_AS("k_interp_groups", s);
     }
-    const size_t n = (size_t)p->T * p->ns;
-    k_combine_fwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->sub_Y, phi, K, p->group_of, p->T, p->ns, scale,
-                                                               b, y);
+    const size_t n = (size_t)p->ngroups * p->ns;
+    k_combine_fwd<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(p->sub_Y, phi, K, p->gf_off, p->gf, p->ngroups,
+                                                               p->ns, scale, b, y);
     MRF_LAUNCHED_AS("k_combine_fwd", s);
     return MRF_OK;
 }
