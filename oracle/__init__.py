@@ -22,7 +22,8 @@ Modules
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against
 closed forms, library routines on special cases, brute force or independent
-simulation, except ``recon.msllr`` end to end, whose final maps have no
-published value to compare against (the paper's data are unavailable):
-parity unpinned for the whole-loop output; each of its steps is pinned.
+simulation.  ``recon.MSLLR`` end to end has no published maps to compare
+against (the paper's data are unavailable); it is pinned by its steps and by
+one special case with a known answer: noiseless, fully sampled data of
+tissues that are dictionary atoms must give back the true maps.
 """

@@ -85,3 +85,35 @@ def test_stop_rule_fires():
     r = recon.MSLLR(prob["b"], prob["k"], prob["grid"], prob["phi"], prob["D"], prob["lut"], P).init()
     assert r.iterate() is True
     assert r.iterate() is False
+
+
+def test_noiseless_fully_sampled_loop_recovers_the_true_maps():
+    """A special case of Algorithm 1 with a known answer: every tissue value is
+    a dictionary atom (times a PD), every frame samples the full Cartesian
+    k-space, the data are noiseless, and the regularisation weights are small.
+    Then matching must find the true atom of every voxel at the start and keep
+    it through the iterations, and the PD must stay close to the truth (the
+    K = 6 subspace and the regularisers perturb it by a few per cent)."""
+    n, T, K = 16, 24, 6
+    t1m, t2m, pdm, mask, label = synth.phantom(n, seed=0)
+    fa, tr = synth.fisp_train(T, seed=2)
+    lut = synth.keep_t1_ge_t2(synth.log_grid(250, 3000, 10), synth.log_grid(25, 350, 8))
+    D = dictionary.simulate(lut, fa, tr)
+    phi = dictionary.subspace(D, K)
+    rng = np.random.default_rng(0)
+    pick = {r: int(rng.integers(0, len(lut))) for r in np.unique(label)}
+    idx_true = np.vectorize(pick.get)(label)
+    X = pdm.ravel()[:, None] * D[idx_true.ravel()] * mask.ravel()[:, None]
+    ax = np.arange(-n // 2, n // 2) * 2 * np.pi / n
+    ky, kx = np.meshgrid(ax, ax, indexing="ij")
+    k = np.broadcast_to(np.stack([kx.ravel(), ky.ravel()], -1), (T, n * n, 2)).copy()
+    grid = nufft.KBGrid(n, n, 2, 4)
+    b = nufft.kb_forward(X.reshape(n, n, T).transpose(2, 0, 1), k, grid)
+    P = recon.Params(patch=8, stride=4, knn=4, lam1_0=0.01, lam2=0.01, beta=0.2)
+    r = recon.MSLLR(b, k, grid, phi, D, lut, P).init()
+    assert np.all(r.maps[0][mask] == idx_true[mask])
+    idx, t1, t2, pd = r.run(5)
+    assert np.all(idx[mask] == idx_true[mask])
+    np.testing.assert_array_equal(t1[mask], lut[idx_true[mask], 0])
+    np.testing.assert_array_equal(t2[mask], lut[idx_true[mask], 1])
+    assert np.max(np.abs(pd[mask] - pdm[mask]) / pdm[mask]) < 0.05
