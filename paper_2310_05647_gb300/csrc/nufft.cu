@@ -526,30 +526,19 @@ __global__ void k_interp_groups(const float2* __restrict__ spec, int K, const in
 }
 
 // y[t][j] = scale * sum_k conj(phi[t][k]) Y[g(t)][j][k] - b[t][j]
-// One thread per (group, sample): the group's K values stay in registers and
-// every frame of the group is written from them, so Y is read once rather
-// than once per frame.
 __global__ void k_combine_fwd(const float2* __restrict__ Y, const float2* __restrict__ phi, int K,
-                              const int* __restrict__ gf_off, const int* __restrict__ gf, int ngroups, int ns,
-                              float scale, const float2* __restrict__ bsub, float2* __restrict__ y) {
+                              const int* __restrict__ group_of, int T, int ns, float scale,
+                              const float2* __restrict__ bsub, float2* __restrict__ y) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= (size_t)ngroups * ns) return;
-    const int g = (int)(i / ns), j = (int)(i - (size_t)g * ns);
-    float2 yv[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) yv[k] = k < K ? Y[i * K + k] : make_float2(0.f, 0.f);
-    for (int q = gf_off[g]; q < gf_off[g + 1]; ++q) {
-        const int t = gf[q];
-        const float2* p = phi + (size_t)t * K;
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < K) acc = cadd(acc, cmulc(yv[k], p[k]));
-        acc = cscale(acc, scale);
-        const size_t o = (size_t)t * ns + j;
-        if (bsub) acc = csub(acc, bsub[o]);
-        y[o] = acc;
-    }
+    if (i >= (size_t)T * ns) return;
+    const int t = (int)(i / ns), j = (int)(i - (size_t)t * ns);
+    const float2* yv = Y + ((size_t)group_of[t] * ns + j) * K;
+    const float2* p = phi + (size_t)t * K;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) acc = cadd(acc, cmulc(yv[k], p[k]));
+    acc = cscale(acc, scale);
+    if (bsub) acc = csub(acc, bsub[i]);
+    y[i] = acc;
 }
 
 // R[g][j][k] = sum_{t in g} phi[t][k] r[t][j]
@@ -1079,9 +1068,9 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
         }));
         MRF_LAUNCHED_AS("k_interp_groups", s);
     }
-    const size_t n = (size_t)p->ngroups * p->ns;
-    k_combine_fwd<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(p->sub_Y, phi, K, p->gf_off, p->gf, p->ngroups,
-                                                               p->ns, scale, b, y);
+    const size_t n = (size_t)p->T * p->ns;
+    k_combine_fwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p->sub_Y, phi, K, p->group_of, p->T, p->ns, scale,
+                                                               b, y);
     MRF_LAUNCHED_AS("k_combine_fwd", s);
     return MRF_OK;
 }

@@ -745,9 +745,20 @@ __global__ void __launch_bounds__(128, LANES == 16 ? (R * KP <= 32 ? 3 : 2) : ((
         f[k] = sg > tau ? (sg - tau) / sg : 0.f;
     }
     if (nuc && active && sl == 0) atomicAdd(nuc, (double)nsum);
-    if (stats && active && sl == 0) {
-        atomicAdd(&stats[0], (unsigned long long)nsweep);
-        atomicAdd(&stats[1], (unsigned long long)nrot);
+    if (stats) {
+        // block totals first: one atomic pair per block instead of per patch
+        __shared__ unsigned s_sweeps, s_rots;
+        if (threadIdx.x == 0) { s_sweeps = 0u; s_rots = 0u; }
+        __syncthreads();
+        if (active && sl == 0) {
+            atomicAdd(&s_sweeps, (unsigned)nsweep);
+            atomicAdd(&s_rots, (unsigned)nrot);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicAdd(&stats[0], (unsigned long long)s_sweeps);
+            atomicAdd(&stats[1], (unsigned long long)s_rots);
+        }
     }
     if (Vp && sl < KP) {
 #pragma unroll
