@@ -50,6 +50,23 @@ def test_knn_ties_take_lower_index():
     assert graph.sigma2(np.zeros((3, 2))) == 1.0
 
 
+def test_sigma2_is_the_median_of_the_nonzero_distances_brute_force():
+    """sigma^2 against a pure-Python median (sorted list; the mean of the two
+    middle values for an even count) of the non-zero entries, on small integer
+    sets with zeros, ties, odd and even counts."""
+    rng = np.random.default_rng(11)
+    for trial in range(200):
+        d = rng.integers(0, 6, int(rng.integers(1, 15))).astype(float)
+        nz = sorted(v for v in d.tolist() if v > 0)
+        if not nz:
+            want = 1.0
+        elif len(nz) % 2:
+            want = nz[len(nz) // 2]
+        else:
+            want = 0.5 * (nz[len(nz) // 2 - 1] + nz[len(nz) // 2])
+        assert graph.sigma2(d) == want, (trial, d)
+
+
 def test_laplacian_properties():
     rng = np.random.default_rng(2)
     F = rng.standard_normal((40, 4))
