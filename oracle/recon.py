@@ -134,12 +134,20 @@ class MSLLR:
         llr_ = float(llr.nuclear_norms(self.pg.extract(X)).sum())
         return data + self.lam1 * ms + self.p.lam2 * llr_
 
+    def gradient(self, X):
+        """The bracket of Eq. 12: A^*(A X - b) + lambda1 Q^*(Q(X) L), with L and
+        lambda1 of the current pass."""
+        r = self.A(X) - self.bs
+        return self.AH(r) + self.lam1 * graph.graph_term(X, self.L, self.pg)
+
+    def z_step(self, X):
+        """Eq. 12: Z = P_S(X - mu [gradient])."""
+        return self.PS(X - self.p.mu * self.gradient(X))
+
     def iterate(self):
         """One pass of the loop body; returns False when the stopping rule fires."""
         p, X = self.p, self.X
-        r = self.A(X) - self.bs
-        grad = self.AH(r) + self.lam1 * graph.graph_term(X, self.L, self.pg)
-        Z = self.PS(X - p.mu * grad)
+        Z = self.z_step(X)
         P = llr.svt_patches(self.pg.extract(X), 1.0 / p.beta)
         self.X = llr.x_update(Z, self.pg.adjoint(P), self.cnt, p.mu, p.lam2, p.beta,
                               literal=p.literal_xupdate)

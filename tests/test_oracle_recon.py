@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import dictionary, nufft, recon
+from oracle import dictionary, graph, nufft, recon
 
 
 def tiny_problem(n=16, T=24, ns=96, K=4, seed=0, snr_db=30.0):
@@ -117,3 +117,69 @@ def test_noiseless_fully_sampled_loop_recovers_the_true_maps():
     np.testing.assert_array_equal(t1[mask], lut[idx_true[mask], 0])
     np.testing.assert_array_equal(t2[mask], lut[idx_true[mask], 1])
     assert np.max(np.abs(pd[mask] - pdm[mask]) / pdm[mask]) < 0.05
+
+
+def _smooth(r, X):
+    """The smooth part of the objective whose gradient the bracket of Eq. 12
+    is: 1/2 ||A X - b||^2 + (lambda1 / 2) Tr(Q(X) L Q(X)^H).  For a real
+    symmetric L the gradient 2 df/d(conj X) of the trace is 2 Q^*(Q(X) L), so
+    Eq. 12's lambda1 Q^*(Q(X) L) belongs to the trace weighted lambda1 / 2."""
+    res = r.A(X) - r.bs
+    return 0.5 * float(np.sum(np.abs(res) ** 2)) + 0.5 * r.lam1 * graph.trace_term(X, r.L, r.pg)
+
+
+def _directional(f, X, E):
+    """Central difference of f along E.  f is quadratic, so the difference is
+    exact up to rounding for any step; h is taken at the scale of X."""
+    h = np.linalg.norm(X) / np.linalg.norm(E)
+    return (f(X + h * E) - f(X - h * E)) / (2 * h)
+
+
+@pytest.mark.parametrize("lam1", [None, 0.0, 3.0])
+def test_eq12_gradient_is_the_gradient_of_the_smooth_part(prob, lam1):
+    """Re <gradient(X), E> equals the directional derivative of the smooth part
+    along E for random directions, with lambda1 as the loop sets it, zero
+    (data term alone) and large (graph term dominant), so a wrong sign or
+    weight of either term fails."""
+    P = recon.Params(patch=8, stride=4, knn=4)
+    r = recon.MSLLR(prob["b"], prob["k"], prob["grid"], prob["phi"], prob["D"], prob["lut"], P).init()
+    if lam1 is not None:
+        r.lam1 = lam1
+    rng = np.random.default_rng(5)
+    X = r.X + 0.3 * np.abs(r.X).max() * (rng.standard_normal(r.X.shape) + 1j * rng.standard_normal(r.X.shape))
+    g = r.gradient(X)
+    f = lambda Y: _smooth(r, Y)
+    for _ in range(3):
+        E = rng.standard_normal(X.shape) + 1j * rng.standard_normal(X.shape)
+        d = _directional(f, X, E)
+        assert float(np.real(np.vdot(g, E))) == pytest.approx(d, rel=1e-8)
+    if lam1 == 3.0:
+        # the graph part carries a real share of the derivative here
+        ft = lambda Y: 0.5 * r.lam1 * graph.trace_term(Y, r.L, r.pg)
+        assert abs(_directional(ft, X, E)) > 1e-2 * abs(_directional(f, X, E))
+
+
+@pytest.mark.parametrize("mu", [1.0, 0.37])
+def test_eq12_z_step_is_the_projected_gradient_step(prob, mu):
+    """Z = P_S(X - mu grad): Z lies on S, and for directions E on S the step
+    (X - Z) / mu has Re <(X - Z)/mu, E> equal to the smooth part's directional
+    derivative along E (the iterate X is on S, so only the projected gradient
+    is seen there); a wrong mu, sign or lambda1 weight fails."""
+    P = recon.Params(patch=8, stride=4, knn=4, mu=mu)
+    r = recon.MSLLR(prob["b"], prob["k"], prob["grid"], prob["phi"], prob["D"], prob["lut"], P).init()
+    r.lam1 = 2.0
+    X = r.X
+    Z = r.z_step(X)
+    np.testing.assert_allclose(r.PS(Z), Z, atol=1e-10 * np.abs(Z).max())
+    step = (X - Z) / mu
+    f = lambda Y: _smooth(r, Y)
+    rng = np.random.default_rng(9)
+    for _ in range(3):
+        E = r.PS(rng.standard_normal(X.shape) + 1j * rng.standard_normal(X.shape))
+        assert float(np.real(np.vdot(step, E))) == pytest.approx(_directional(f, X, E), rel=1e-8)
+    # iterate() takes this step: with lambda2 = 0 the X update returns Z itself
+    P0 = recon.Params(patch=8, stride=4, knn=4, mu=mu, lam2=0.0)
+    r0 = recon.MSLLR(prob["b"], prob["k"], prob["grid"], prob["phi"], prob["D"], prob["lut"], P0).init()
+    Z0 = r0.z_step(r0.X)
+    r0.iterate()
+    np.testing.assert_allclose(r0.X, Z0, rtol=0, atol=1e-12 * np.abs(Z0).max())
