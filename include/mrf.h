@@ -184,9 +184,10 @@ mrf_status mrf_match_seeded(const mrf_c64* x, int n, int len, const mrf_c64* dic
  * fixed device array inside the library, sized for at most 262144
  * fingerprints (n) and 65536 atoms (m), about 3.6 MB that every GPU which
  * loads the library holds until the process exits; larger n or m return
- * MRF_EINVAL with a message.  The first call on a device looks up the
- * array's device address with that device current, so make that first call
- * before any stream capture.  All calls share the one array: calls whose
+ * MRF_EINVAL with a message.  Every call looks up the array's device address
+ * on the current device (no allocation; a context reset cannot leave a stale
+ * address behind); the first lookup on a device loads the library's module
+ * there, so make that first call before any stream capture.  All calls share the one array: calls whose
  * work overlaps on the GPU (different streams, or different host threads)
  * race and must be serialised by the caller.  Every scratch word a call reads
  * is written by the same call first, so no clearing is needed between calls.

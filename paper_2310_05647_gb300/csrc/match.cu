@@ -8,7 +8,6 @@
 // fingerprint, the running best (score, index, inner product) over all atom
 // tiles; no fingerprint x atom score is ever written to memory.  The BF16
 // tensor-core form lives in match_tc.cu.
-#include <mutex>
 
 #include "common.h"
 #include "match.h"
@@ -309,29 +308,21 @@ constexpr size_t kNoAllocBytes = round_up(sizeof(int) * kNoAllocMaxN) + round_up
 
 static __device__ __align__(256) unsigned char g_match_scratch[kNoAllocBytes];
 
-// Device address of g_match_scratch, looked up once per device (with that
-// device current) on the first call made there.
+// Device address of g_match_scratch on the current device, looked up on every
+// call: the lookup allocates nothing, and a cached address would go stale if
+// the device's primary context were destroyed (cudaDeviceReset) and the module
+// loaded again at another address.  The first lookup on a device loads the
+// library's module there, so that first call should come before any stream
+// capture.
 static char* scratch_for_current_device(mrf_status* st) {
-    static std::mutex mu;
-    static char* addr[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-        set_error("mrf_match_noalloc: no usable current device");
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_match_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("mrf_match_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
         *st = MRF_ECUDA;
         return nullptr;
     }
-    std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_match_scratch);
-        if (e != cudaSuccess) {
-            set_error("mrf_match_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            *st = MRF_ECUDA;
-            return nullptr;
-        }
-        addr[dev] = static_cast<char*>(p);
-    }
-    return addr[dev];
+    return static_cast<char*>(p);
 }
 
 }  // namespace mrf
