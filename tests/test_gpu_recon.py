@@ -37,17 +37,17 @@ def prob():
     return problem()
 
 
-def gpu_recon(pr, mode=0, extra_flags=0, plan=None, **kw):
+def gpu_recon(pr, mode=0, extra_flags=0, plan=None, patch=8, stride=4, knn=4, **kw):
     m = mrf()
     plan = plan if plan is not None else m.nufft_plan(pr["n"], pr["n"], f32(pr["k"]))
     dc = pr["D"] @ pr["phi"]
     n2 = np.sum(np.abs(pr["D"]) ** 2, axis=1)
-    params = m.ReconParams(patch=8, stride=4, knn=4, flags=(8 if mode else 0) | extra_flags, **kw)
+    params = m.ReconParams(patch=patch, stride=stride, knn=knn, flags=(8 if mode else 0) | extra_flags, **kw)
     return m.Recon(plan, params, c64(pr["phi"]), c64(dc), f32(n2), f32(pr["lut"]), c64(pr["b"]))
 
 
-def oracle_recon(pr, **kw):
-    P = orecon.Params(patch=8, stride=4, knn=4, **kw)
+def oracle_recon(pr, patch=8, stride=4, knn=4, **kw):
+    P = orecon.Params(patch=patch, stride=stride, knn=knn, **kw)
     return orecon.MSLLR(pr["b"], pr["k"], pr["grid"], pr["phi"], pr["D"], pr["lut"], P).init()
 
 
@@ -193,3 +193,63 @@ def test_svt_work_counters():
     assert npatch == ((pr["n"] - 8) // 4 + 1) ** 2           # 8 x 8 patches at stride 4
     assert npatch <= s1 - s0 <= 30 * npatch * 3
     assert r1 - r0 >= 0
+
+
+def _follow_oracle(pr, mode, iters, tol, prec=0, patch=8, stride=4, knn=4):
+    """Run the GPU loop beside the oracle's Algorithm 1 from the same start
+    (the oracle's scales a and gamma) and compare after the initialisation
+    and after every iteration: coefficient images within tol (x the
+    iteration), cost, lambda1 and maps as in test_iterations_match_oracle;
+    a voxel whose index differs must be a near-tie on the oracle's iterate."""
+    o = oracle_recon(pr, patch=patch, stride=stride, knn=knn)
+    r = gpu_recon(pr, mode, patch=patch, stride=stride, knn=knn, match_precision=prec, a_norm=o.a,
+                  x_scale=o.gamma)
+    assert rel(np_(r.alpha()), alpha_of(o)) < tol
+    T = pr["D"].shape[1]
+    prev = (np_(r.maps()[3]).ravel() == o.maps[0].ravel()).mean()
+    for it in range(iters):
+        o.iterate()
+        cost = r.iterate(1, costs=True)[0]
+        assert rel(np_(r.alpha()), alpha_of(o)) < tol * (it + 1), it
+        assert cost == pytest.approx(o.cost[-1], rel=1e-4 * (it + 1) if prev == 1.0 else 5e-3), it
+        gi = np_(r.maps()[3]).ravel()
+        oi = o.maps[0].ravel()
+        agree = (gi == oi).mean()
+        assert agree > 0.99, it
+        diff = np.nonzero(gi != oi)[0]
+        if diff.size:
+            sc = omatch.scores(o.X.reshape(-1, T)[diff], pr["D"])
+            rows = np.arange(diff.size)
+            assert np.all(sc[rows, gi[diff]] >= sc[rows, oi[diff]] * (1 - 1e-3)), it
+        assert r.info()["lam1"] == pytest.approx(o.lam1, rel=1e-3 if agree == 1.0 else 3e-2), it
+        prev = agree
+    return r, o
+
+
+@pytest.fixture(scope="module")
+def prob10():
+    return problem(K=10)
+
+
+def test_benched_configuration_follows_oracle(prob10):
+    """The loop as bench.py times its chosen variant: grouped operator,
+    split-BF16 tensor-core matching seeded from the previous call, K = 10
+    (so the SVT runs k_svt<4,10,16>, a 9-round circle schedule per sweep),
+    10 nearest patches; 4 iterations against the oracle."""
+    _follow_oracle(prob10, mode=1, iters=4, tol=3e-4, prec=2, knn=10)
+
+
+def test_plain_configuration_at_rank_10_follows_oracle(prob10):
+    """The plain variant's loop (frame-by-frame operator, FP32 matching) at
+    K = 10 and 10 nearest patches."""
+    _follow_oracle(prob10, mode=0, iters=4, tol=1e-4, prec=0, knn=10)
+
+
+# (patch, stride, K) -> the SVT instantiation the loop selects:
+#   p^2 <= 32 rows, KP <= 12: k_svt<2,KP,16>; p^2 <= 64, KP <= 12: k_svt<4,KP,16>;
+#   p^2 <= 64, KP = 16: k_svt<2,16,32>; p^2 > 64: k_svt<4,KP,32>
+@pytest.mark.parametrize("patch,stride,K", [(5, 2, 10), (11, 5, 10), (8, 4, 16), (11, 5, 16), (4, 2, 12)],
+                         ids=["svt_2_10_16", "svt_4_10_32", "svt_2_16_32", "svt_4_16_32", "svt_2_12_16"])
+def test_svt_instantiations_follow_oracle(patch, stride, K):
+    pr = problem(K=K)
+    _follow_oracle(pr, mode=0, iters=2, tol=1e-4, prec=0, patch=patch, stride=stride, knn=10)
