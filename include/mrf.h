@@ -159,6 +159,20 @@ mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64* dict,
                      const float* atom_norm2, const float* lut, int m, int precision,
                      int* idx, float* pd, float* t1t2, mrf_stream stream);
 
+/* The plain reconstruction: X = A^H y frame by frame (the adjoint of Eq. 1,
+ * the X^0 = A^* b of Algorithm 1 without the subspace projection), then
+ * dictionary matching (Eq. 5) of every voxel's full fingerprint
+ * X[:, iy, ix] of length T against dict.  y: dev [T][ns] of the plan;
+ * dict: dev [m][T]; atom_norm2, lut, precision and the outputs idx / pd /
+ * t1t2 ([ny*nx], row-major voxels) as in mrf_match with n = ny*nx and
+ * len = T.  x_rows (nullable): dev [ny*nx][T], receives the fingerprints.
+ * Scratch (the [T][ny][nx] adjoint output, and the rows when x_rows is NULL)
+ * is allocated and freed on the stream.  Needs T <= 2048. */
+mrf_status mrf_gridding_match(mrf_plan plan, const mrf_c64* y, const mrf_c64* dict,
+                              const float* atom_norm2, const float* lut, int m, int precision,
+                              int* idx, float* pd, float* t1t2, mrf_c64* x_rows,
+                              mrf_stream stream);
+
 /* mrf_match for repeated matching of the same n rows (an iterative
  * reconstruction matches every iterate): cand (dev int32 [n][8]) carries
  * each row's tensor-core candidates from one call to the next.  On entry
@@ -344,6 +358,21 @@ mrf_status mrf_recon_svt_stats(mrf_recon R, double* sweeps, double* rotations, d
 mrf_status mrf_recon_info(mrf_recon r, double* a_norm, double* x_scale, double* lam1,
                           double* sigma2, mrf_stream stream);
 mrf_status mrf_recon_destroy(mrf_recon r);
+/* One whole reconstruction (Algorithm 1) from host k-space to host maps:
+ * copies b_host (host [T][ns] of the plan; pinned memory lets the copy run
+ * asynchronously, pageable memory is staged by the runtime) to the device,
+ * runs mrf_recon_create and n_iters iterations, and copies the T1, T2 and PD
+ * maps (host float [ny*nx] each, nullable) back, with the same arguments and
+ * errors as those calls; cost_out (host double [n_iters], nullable) receives
+ * the cost per iteration.  The plan, phi, dict_c, atom_norm2 and lut stay
+ * device-resident (set up once per sequence and dictionary).  Device scratch
+ * for b and the maps is allocated and freed on the stream; the call
+ * synchronises the stream before it returns. */
+mrf_status mrf_recon_run_host(mrf_plan plan, const mrf_recon_params* params, const mrf_c64* phi,
+                              int K, const mrf_c64* dict_c, const float* atom_norm2,
+                              const float* lut, int m, const mrf_c64* b_host, int n_iters,
+                              float* t1_host, float* t2_host, float* pd_host, double* cost_out,
+                              mrf_stream stream);
 /* Checkpoint / resume.  A checkpoint is a host byte buffer holding the loop
  * state the next iteration reads (coefficient images, residual, SVT output
  * and right singular vectors, maps, cost history, iteration count) and the

@@ -15,9 +15,9 @@ import torch
 from . import _lib
 from ._lib import MRFError
 
-__all__ = ["MRFError", "NufftPlan", "Recon", "ReconParams", "dict_subspace", "epg_fisp", "match",
+__all__ = ["MRFError", "NufftPlan", "Recon", "ReconParams", "dict_subspace", "epg_fisp", "gridding_match", "match",
            "nufft_adjoint", "nufft_adjoint_subspace", "nufft_forward", "nufft_forward_subspace",
-           "nufft_plan"]
+           "nufft_plan", "recon_run_host"]
 
 MATCH_FP32, MATCH_BF16, MATCH_BF16X3, MATCH_FP8, MATCH_LITERAL_NORM2 = 0, 1, 2, 3, 0x100
 RECON_LITERAL_XUPDATE, RECON_LITERAL_LAMBDA1, RECON_NO_COST, RECON_GROUPED, RECON_LEARNED, RECON_SERIAL = (
@@ -162,6 +162,29 @@ def match(x, D, lut, atom_norm2=None, precision=MATCH_FP32):
     _lib.call("mrf_match", _ptr(x), n, L, _ptr(D), _ptr(atom_norm2), _ptr(lut), m, int(precision), _ptr(idx),
               _ptr(pd), _ptr(t1t2), _stream())
     return idx, pd, t1t2
+
+
+def gridding_match(plan, y, D, lut, atom_norm2=None, precision=MATCH_FP32, keep_rows=False):
+    """The plain reconstruction: X = A^H y frame by frame, then matching of every
+    voxel's T-frame fingerprint against D [m, T].  Returns (idx, pd, t1t2) as
+    match() for the ny*nx voxels, plus the fingerprint rows [ny*nx, T] when
+    keep_rows."""
+    _check(y, "y", torch.complex64, (plan.T, plan.ns))
+    _check(D, "D", torch.complex64)
+    m, T = D.shape
+    if T != plan.T:
+        raise ValueError("D must have one column per frame")
+    _check(lut, "lut", torch.float32, (m, 2))
+    if atom_norm2 is not None:
+        _check(atom_norm2, "atom_norm2", torch.float32, (m,))
+    n = plan.nx * plan.ny
+    idx = torch.empty((n,), dtype=torch.int32, device=y.device)
+    pd = torch.empty((n,), dtype=torch.float32, device=y.device)
+    t1t2 = torch.empty((n, 2), dtype=torch.float32, device=y.device)
+    rows = torch.empty((n, T), dtype=torch.complex64, device=y.device) if keep_rows else None
+    _lib.call("mrf_gridding_match", plan.handle, _ptr(y), _ptr(D), _ptr(atom_norm2), _ptr(lut), m, int(precision),
+              _ptr(idx), _ptr(pd), _ptr(t1t2), _ptr(rows), _stream())
+    return (idx, pd, t1t2, rows) if keep_rows else (idx, pd, t1t2)
 
 
 def match_seeded(x, D, lut, cand, atom_norm2=None, precision=MATCH_BF16X3):
@@ -435,6 +458,30 @@ class Recon:
             except Exception:
                 pass
             self.handle = None
+
+
+def recon_run_host(plan, params, phi, dict_c, atom_norm2, lut, b_host, iters, costs=False):
+    """One reconstruction from host k-space to host maps through
+    mrf_recon_run_host: b_host is a CPU complex64 tensor [T, ns] (pinned for an
+    asynchronous copy); returns CPU float32 maps (t1, t2, pd) [ny, nx] (and the
+    per-iteration costs)."""
+    K = phi.shape[1]
+    m = dict_c.shape[0]
+    _check(phi, "phi", torch.complex64, (plan.T, K))
+    _check(dict_c, "dict_c", torch.complex64, (m, K))
+    _check(atom_norm2, "atom_norm2", torch.float32, (m,))
+    _check(lut, "lut", torch.float32, (m, 2))
+    if not isinstance(b_host, torch.Tensor) or b_host.is_cuda or b_host.dtype != torch.complex64 \
+            or not b_host.is_contiguous() or tuple(b_host.shape) != (plan.T, plan.ns):
+        raise ValueError(f"b_host must be a contiguous CPU complex64 tensor of shape {(plan.T, plan.ns)}")
+    pin = b_host.is_pinned()
+    maps = [torch.empty((plan.ny, plan.nx), dtype=torch.float32, pin_memory=pin) for _ in range(3)]
+    cost = (C.c_double * max(iters, 1))() if costs else None
+    prm = params.as_c()
+    _lib.call("mrf_recon_run_host", plan.handle, C.byref(prm), _ptr(phi), K, _ptr(dict_c), _ptr(atom_norm2),
+              _ptr(lut), m, _ptr(b_host), int(iters), _ptr(maps[0]), _ptr(maps[1]), _ptr(maps[2]), cost,
+              _stream())
+    return (tuple(maps), list(cost)[:iters]) if costs else tuple(maps)
 
 
 class Batch:

@@ -58,6 +58,10 @@ def test_host_validation_without_gpu(lib):
     assert lib.mrf_epg_fisp(dummy, 3, dummy, dummy, 0, C.c_float(2.94), C.c_float(20.0), 1, dummy, None) == 1
     assert lib.mrf_epg_fisp(dummy, 3, dummy, dummy, 5000, C.c_float(2.94), C.c_float(20.0), 1, dummy, None) == 1
     assert lib.mrf_nufft_forward(None, dummy, dummy, None) == 1
+    assert lib.mrf_gridding_match(None, dummy, dummy, None, dummy, 5, 0, None, None, None, None, None) == 1
+    assert lib.mrf_gridding_match(dummy, dummy, dummy, None, dummy, 0, 0, None, None, None, None, None) == 1
+    assert lib.mrf_recon_run_host(None, None, dummy, 10, dummy, dummy, dummy, 5, dummy, 1, None, None, None,
+                                  None, None) == 1
     assert lib.mrf_match(dummy, 0, 10, dummy, None, dummy, 5, 0, None, None, None, None) == 0   # empty: no-op
 
 
