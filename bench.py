@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the batched-serving measurement")
     ap.add_argument("--workload", default=WORKLOAD, choices=["mrf256_t1000", "mrf256_t100"],
                     help="mrf256_t100: the same image with 100 frames, for small profiling captures")
+    ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)   # child process of the cpu_baseline leg
+    ap.add_argument("--no-oracle-parity", action="store_true",
+                    help="skip the oracle comparison on the reduced copy of the problem and the 64^2 x 100 line")
     return ap.parse_args()
 
 
@@ -386,9 +389,9 @@ def profile_serial(variant, inp, iters=10, warmup=3):
     sv1 = rec.svt_stats()
     # executed Jacobi work per patch and SVT launch over the profiled iterations
     dp = sv1[2] - sv0[2]
-    inp["svt_work"] = {"sweeps_per_patch": (sv1[0] - sv0[0]) / dp, "rotations_per_patch": (sv1[1] - sv0[1]) / dp}
+    work = {"sweeps_per_patch": (sv1[0] - sv0[0]) / dp, "rotations_per_patch": (sv1[1] - sv0[1]) / dp}
     del rec
-    return prof, ms / iters, iters
+    return prof, ms / iters, iters, work
 
 
 def merge_clocks(timed, sustained, sustained_ms):
@@ -519,28 +522,24 @@ def serving(seed=0, slices=16, iters=10, rounds=10):
 
 
 def e2e_chosen(inp, iters, reps=2):
-    """End to end through the public API: pinned host k-space in, host maps out."""
-    import torch
-
+    """End to end through the C ABI's host-buffer call (mrf_recon_run_host):
+    pinned host k-space in, initialisation (A^H b, matching, graph) and
+    `iters` iterations, T1/T2/PD maps back in host memory; the copies run
+    inside the call."""
     import paper_2310_05647_gb300 as mrf
 
     w = inp["w"]
     b_host = inp["b"].cpu().pin_memory()
+    p = params_for("chosen", w)
     times = []
     for r in range(reps + 1):
-        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        b = b_host.to("cuda", non_blocking=True)
-        rec = mrf.Recon(inp["plan"], params_for("chosen", w), inp["phi"], inp["comp"], inp["n2"], inp["lut"], b)
-        rec.iterate(iters)
-        maps = [t.to("cpu") for t in rec.maps()]
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        del rec
+        maps = mrf.recon_run_host(inp["plan"], p, inp["phi"], inp["comp"], inp["n2"], inp["lut"], b_host, iters)
+        dt = time.perf_counter() - t0          # the call synchronises its stream
         if r > 0:
             times.append(dt)
     h2d = b_host.numel() * 8
-    d2h = 4 * w.n * w.n * 4
+    d2h = sum(m.numel() * 4 for m in maps)
     return statistics.mean(times), h2d, d2h
 
 
@@ -617,11 +616,272 @@ def oracle_iteration_seconds(scale=1.0):
     return total, parts, sample
 
 
+# ---------------------------------------------------------------------------
+# the FP64 oracle on problems it finishes in seconds (cpu_baseline leg)
+# ---------------------------------------------------------------------------
+# A reduced copy of the 256^2 x 1000 problem (same dictionary grid, sequence
+# recipe, interleaf pattern, rank, patches, neighbours and iteration count;
+# 64^2 voxels and 100 frames) on which the oracle's Algorithm 1 runs to the
+# end, so the GPU variants' maps can be compared with the oracle's.
+SMALL = dict(n=64, frames=100, ns=256, interleaves=48)
+
+
+def _f32(a):
+    import numpy as np
+    a = np.asarray(a)
+    return a.astype(np.complex64).astype(np.complex128) if np.iscomplexobj(a) else \
+        a.astype(np.float32).astype(np.float64)
+
+
+def _save(path, **arrs):
+    import numpy as np
+    np.savez(path + ".tmp.npz", **arrs)
+    os.replace(path + ".tmp.npz", path)
+
+
+def oracle_leg(out_dir, iters):
+    """Child process: build the inputs of the reduced problem and of the 64^2 x
+    100 plain workload with the oracle (saved for the GPU side), then time the
+    oracle on both: A^H gridding + exhaustive matching, and Algorithm 1's
+    initialisation + `iters` iterations.  Run with one BLAS thread: the
+    oracle's many small SVDs are ~20x slower with a multi-threaded BLAS."""
+    import numpy as np
+
+    import synth
+    from oracle import dictionary, epg, match as omatch, nufft as onufft, recon as orecon
+
+    big = synth.WORKLOADS["mrf256_t1000"]
+    n, T, ns, il = SMALL["n"], SMALL["frames"], SMALL["ns"], SMALL["interleaves"]
+    t1, t2, pd, mask, _ = synth.phantom(n, seed=big.phantom_seed)
+    fa, tr = synth.fisp_train(T, seed=big.tr_seed)
+    lut = synth.workload_grid(big)
+    D = epg.fisp(lut[:, 0], lut[:, 1], fa, tr)
+    X = pd.reshape(-1, 1) * epg.fisp(np.maximum(t1.ravel(), 1.0), np.maximum(t2.ravel(), 1.0), fa, tr)
+    X *= mask.reshape(-1, 1)
+    k = synth.spiral_trajectory(n, T, ns, il)
+    grid = onufft.KBGrid(n, n, big.os, big.kb_width)
+    b = onufft.kb_forward(X.reshape(n, n, T).transpose(2, 0, 1), k, grid)
+    b = b + np.sqrt(np.mean(np.abs(b) ** 2) * 10 ** (-big.snr_db / 10)) * synth.complex_normal(b.shape, seed=1)
+    phi = dictionary.subspace(D, big.rank)
+    k, b, phi, D, lut, fa, tr = (_f32(a) for a in (k, b, phi, D, lut, fa, tr))
+    _save(os.path.join(out_dir, "loop_inputs.npz"), k=k, b=b, phi=phi, D=D, lut=lut, fa=fa, tr=tr, t1=t1, t2=t2,
+          pd=pd, mask=mask)
+    # 64^2 x 100 plain workload: A^H gridding then exhaustive full-length matching
+    c1 = synth.WORKLOADS["mrf64_t100"]
+    ct1, ct2, cpd, cmask, _ = synth.phantom(c1.n, seed=c1.phantom_seed)
+    cfa, ctr = synth.fisp_train(c1.frames, seed=c1.tr_seed)
+    clut = synth.workload_grid(c1)
+    cD = epg.fisp(clut[:, 0], clut[:, 1], cfa, ctr)
+    cX = cpd.reshape(-1, 1) * epg.fisp(np.maximum(ct1.ravel(), 1.0), np.maximum(ct2.ravel(), 1.0), cfa, ctr)
+    cX *= cmask.reshape(-1, 1)
+    ck = synth.spiral_trajectory(c1.n, c1.frames, c1.ns, c1.interleaves)
+    cgrid = onufft.KBGrid(c1.n, c1.n, c1.os, c1.kb_width)
+    cb = onufft.kb_forward(cX.reshape(c1.n, c1.n, c1.frames).transpose(2, 0, 1), ck, cgrid)
+    cb = cb + np.sqrt(np.mean(np.abs(cb) ** 2) * 10 ** (-c1.snr_db / 10)) * synth.complex_normal(cb.shape, seed=1)
+    ck, cb, cD, clut = (_f32(a) for a in (ck, cb, cD, clut))
+    _save(os.path.join(out_dir, "c1_inputs.npz"), k=ck, b=cb, D=cD, lut=clut, t1=ct1, t2=ct2, pd=cpd, mask=cmask)
+    reps, t0 = 3, time.perf_counter()
+    for _ in range(reps):
+        xa = onufft.kb_adjoint(cb, ck, cgrid)
+        ci, c_t1, c_t2, c_pd = omatch.match(xa.reshape(c1.frames, -1).T, cD, clut)
+    c1_s = (time.perf_counter() - t0) / reps
+    _save(os.path.join(out_dir, "c1_oracle.npz"), idx=ci, t1=c_t1, t2=c_t2, pd=c_pd, seconds=c1_s)
+    # Algorithm 1 on the reduced problem
+    t0 = time.perf_counter()
+    o = orecon.MSLLR(b, k, grid, phi, D, lut, orecon.Params(patch=big.patch, stride=big.stride,
+                                                            knn=big.knn)).init()
+    init_s = time.perf_counter() - t0
+    its = []
+    for _ in range(iters):
+        t0 = time.perf_counter()
+        o.iterate()
+        its.append(time.perf_counter() - t0)
+    idx, ot1, ot2, opd = o.maps
+    _save(os.path.join(out_dir, "loop_oracle.npz"), idx=idx, t1=ot1, t2=ot2, pd=opd / o.gamma, a=o.a, gamma=o.gamma,
+          init_s=init_s, its=np.array(its), cost=np.array(o.cost))
+
+
+def start_oracle_leg(out_dir, iters):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    log = open(os.path.join(out_dir, "oracle_leg.log"), "w")
+    return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-leg", out_dir,
+                             "--steps", str(iters)], env=env, stdout=log, stderr=subprocess.STDOUT)
+
+
+def _wait_file(path, proc, timeout=900.0):
+    t0 = time.time()
+    while not os.path.exists(path):
+        if proc.poll() is not None and not os.path.exists(path):
+            raise RuntimeError(f"oracle leg exited ({proc.returncode}) before writing {os.path.basename(path)}")
+        if time.time() - t0 > timeout:
+            raise RuntimeError(f"oracle leg: no {os.path.basename(path)} after {timeout:.0f} s")
+        time.sleep(0.2)
+    import numpy as np
+    return dict(np.load(path))
+
+
+def _nrmse(ref, est, mask):
+    import numpy as np
+    r, e = np.asarray(ref, np.float64)[mask], np.asarray(est, np.float64)[mask]
+    den = np.sum(r ** 2)
+    return float(np.sqrt(np.sum((e - r) ** 2) / den)) if den > 0 else 0.0
+
+
+def small_problem_parity(out_dir, proc, variants, iters):
+    """Each GPU variant on the reduced problem, from the oracle's inputs, for
+    `iters` iterations; T1/T2/PD NRMSE of its maps against the oracle's."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2310_05647_gb300 as mrf
+
+    inp = _wait_file(os.path.join(out_dir, "loop_inputs.npz"), proc)
+    big = synth.WORKLOADS["mrf256_t1000"]
+    dev = torch.device("cuda")
+    c64 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.complex64, device=dev)
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    n = SMALL["n"]
+    plan = mrf.nufft_plan(n, n, f32(inp["k"]), os=big.os, kb_width=big.kb_width)
+    phi, D = inp["phi"], inp["D"]
+    n2 = np.sum(np.abs(D) ** 2, axis=1)
+    args = (c64(phi), c64(D @ phi), f32(n2), f32(inp["lut"]), c64(inp["b"]))
+    mlp = None
+    if "learned" in variants:
+        draws = synth.mlp_training_draws(1_000_000, big.rank, seed=3100, t1_range=big.t1_range,
+                                         t2_range=big.t2_range)
+        ranges = (big.t1_range[0], big.t1_range[1], big.t2_range[0], big.t2_range[1],
+                  float(1.0 / np.median(np.sqrt(n2))))
+        mlp, _ = mrf.train_matcher(synth.mlp_init_params(4100), draws, f32(inp["fa"]), f32(inp["tr"]), args[0],
+                                   ranges, epochs=3, batch=1024)
+    gpu = {}
+    for v in variants:
+        rec = mrf.Recon(plan, params_for(v, big, mlp), *args)
+        rec.iterate(iters)
+        gpu[v] = [t.cpu().numpy() for t in rec.maps()]
+        del rec
+    orc = _wait_file(os.path.join(out_dir, "loop_oracle.npz"), proc)
+    mask = inp["mask"].astype(bool)
+    out = {"what": f"reduced copy of the problem ({n}^2 voxels, {SMALL['frames']} frames, {SMALL['ns']} samples "
+                   f"per frame from {SMALL['interleaves']} interleaves, the {len(D)}-atom grid, K = {big.rank}, "
+                   f"{big.patch}x{big.patch} patches at stride {big.stride}, {big.knn} neighbours): each variant's "
+                   f"maps after {iters} iterations against the FP64 oracle's Algorithm 1 after {iters} iterations "
+                   f"(each side estimates its own scales a and gamma), over the object mask",
+           "oracle_nrmse_vs_truth": {nm: _nrmse(inp[nm], orc[nm], mask) for nm in ("t1", "t2", "pd")}}
+    for v, (t1, t2, pd, idx) in gpu.items():
+        e = {"t1": _nrmse(orc["t1"], t1, mask), "t2": _nrmse(orc["t2"], t2, mask),
+             "pd": _nrmse(orc["pd"], pd, mask)}
+        if v != "learned":
+            e["index_agreement"] = float((idx.ravel() == orc["idx"].ravel()).mean())
+        e["nrmse_vs_truth"] = {nm: _nrmse(inp[nm], x, mask) for nm, x in (("t1", t1), ("t2", t2), ("pd", pd))}
+        out[v] = e
+    return out, orc
+
+
+def c1_line(out_dir, proc, reps=20):
+    """The 64^2 x 100 plain workload: A^H gridding of the 100 frames then
+    exhaustive FP32 matching of the full 100-frame fingerprints
+    (mrf_gridding_match), GPU timed with CUDA events, against the oracle."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2310_05647_gb300 as mrf
+
+    inp = _wait_file(os.path.join(out_dir, "c1_inputs.npz"), proc)
+    c1 = synth.WORKLOADS["mrf64_t100"]
+    dev = torch.device("cuda")
+    plan = mrf.nufft_plan(c1.n, c1.n, torch.tensor(inp["k"], dtype=torch.float32, device=dev), os=c1.os,
+                          kb_width=c1.kb_width)
+    b = torch.tensor(inp["b"], dtype=torch.complex64, device=dev)
+    D = torch.tensor(inp["D"], dtype=torch.complex64, device=dev)
+    lut = torch.tensor(inp["lut"], dtype=torch.float32, device=dev)
+    res = mrf.gridding_match(plan, b, D, lut)
+    torch.cuda.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = mrf.gridding_match(plan, b, D, lut)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    idx, pd, t1t2 = (t.cpu().numpy() for t in res)
+    orc = _wait_file(os.path.join(out_dir, "c1_oracle.npz"), proc)
+    mask = inp["mask"].astype(bool)
+    shp = (c1.n, c1.n)
+    g = {"t1": t1t2[:, 0].reshape(shp), "t2": t1t2[:, 1].reshape(shp), "pd": pd.reshape(shp)}
+    orc = {k: (v.reshape(shp) if np.ndim(v) == 1 else v) for k, v in orc.items()}
+    return {"workload": "mrf64_t100", "what": "A^H gridding of 100 frames (64^2, 512 golden-angle spiral samples "
+                                              "per frame) then exhaustive FP32 matching of the 100-frame "
+                                              "fingerprints against 1500 EPG atoms (mrf_gridding_match)",
+            "gpu_ms": statistics.median(ms), "oracle_ms": 1e3 * float(orc["seconds"]),
+            "speedup_vs_oracle": 1e3 * float(orc["seconds"]) / statistics.median(ms),
+            "l2": "flushed before every timed call",
+            "index_agreement_vs_oracle": float((idx == orc["idx"].ravel()).mean()),
+            "nrmse_vs_oracle": {nm: _nrmse(orc[nm], g[nm], mask) for nm in ("t1", "t2", "pd")},
+            "nrmse_vs_truth": {nm: _nrmse(inp[nm], g[nm], mask) for nm in ("t1", "t2", "pd")}}
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+def roof_entry(kname, kms, inp, peaks, hbm_peak, peak_src):
+    """Roofline record of one kernel from its mean launch duration (ms) and its
+    algorithmic work per launch."""
+    work = algorithmic_work(kname, inp)
+    if work and work[0] == "hbm":
+        ach = work[1] / (kms * 1e-3) / 1e9
+        return {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "peak_source": peak_src, "traffic": None,
+                "algorithmic_bytes_per_launch": work[1], "ms_per_launch": kms}
+    if work and work[0] == "tensor":
+        peak = peaks.get("bf16_tflops_sustained", 1716.1)
+        ach = work[1] / (kms * 1e-3) / 1e12
+        return {"kernel": kname, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": "of measured (bf16 sustained)",
+                "issued_flops_per_launch": work[1] * 3 if kname == "k_match_tc" else work[1],
+                "traffic": MEASURED_TRAFFIC.get(kname, (None,))[0],
+                "traffic_source": MEASURED_TRAFFIC.get(kname, (None, None))[1],
+                "algorithmic_flops_per_launch": work[1], "ms_per_launch": kms}
+    if work and work[0] == "alu":
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = work[1] / (kms * 1e-3) / 1e12
+        roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock",
+                "traffic": MEASURED_TRAFFIC.get(kname, (None,))[0],
+                "traffic_source": MEASURED_TRAFFIC.get(kname, (None, None))[1],
+                "ms_per_launch": kms}
+        if kname == "k_svt":
+            roof["executed_flops_per_launch"] = work[1]
+            roof["svt_work"] = inp.get("svt_work")
+            roof["flops_note"] = ("the SVD is iterative: executed flops from the kernel's own sweep and "
+                                  "rotation counters, not a fixed algorithmic count")
+            hb = svt_hbm_bytes(inp)
+            roof["algorithmic_hbm_bytes_per_launch"] = hb
+            roof["hbm_frac"] = hb / (kms * 1e-3) / 1e9 / hbm_peak
+        else:
+            roof["algorithmic_flops_per_launch"] = work[1]
+        return roof
+    return {"kernel": kname, "bound": None, "ms_per_launch": kms, "note": "no algorithmic-work model for this kernel"}
+
+
+def svt_hbm_bytes(inp):
+    """HBM bytes of one SVT launch: every patch's p^2 x K coefficients read and
+    its P written (c64), and its K x K right singular vectors read and written."""
+    w = inp["w"]
+    cnt = (w.n - w.patch) // w.stride + 1 + (1 if (w.n - w.patch) % w.stride else 0)
+    return cnt * cnt * (2 * w.patch ** 2 * w.rank * 8 + 2 * w.rank * w.rank * 8)
+
+
+ROOF_KERNELS = {"chosen": ["k_match_tc", "k_svt", "k_knn_tc", "k_graph_blocks"],
+                "plain": ["k_rows_fwd_expand", "k_cols_interp", "k_spread_cols", "k_rows_adj_reduce", "k_match_fp32"]}
 
 
 def run_reference(args, dist):
@@ -659,6 +919,11 @@ def run_ours(args, dist):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    leg, leg_dir = None, None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline and not args.no_oracle_parity:
+        # the oracle runs beside the GPU work (one host thread); its results are read at the end
+        leg_dir = tempfile.mkdtemp(prefix="mrf_oracle_")
+        leg = start_oracle_leg(leg_dir, synth_iters())
     inp = make_inputs(seed=dist.rank)
     w = inp["w"]
     variants = [v for v in args.variants.split(",") if v]
@@ -668,54 +933,20 @@ def run_ours(args, dist):
     res = {}
     for v in variants:
         res[v] = time_variant(v, inp, args.steps, args.warmup, dist)
-        if v != "plain":                       # plain runs serialised anyway
-            res[v]["serial"] = profile_serial(v, inp)
+        res[v]["serial"] = profile_serial(v, inp, iters=10 if v != "plain" else 3)
     main = "chosen" if "chosen" in res else variants[0]
     r = res[main]
     ms_step = dist.max(r["ms"]) / args.steps
     value = dist.world * 1000.0 / ms_step
     # dominant kernel of the main variant, from its serialised profile
     if "serial" in r:
-        prof, serial_ms, serial_iters = r["serial"]
+        prof, serial_ms, serial_iters, inp["svt_work"] = r["serial"]
     else:
         prof, serial_ms, serial_iters = r["profile"], r["ms"] / args.steps, args.steps
     kname = max(prof, key=lambda k: prof[k][0]) if prof else None
     roof = None
     if kname:
-        kms = prof[kname][0] / max(prof[kname][1], 1)
-        work = algorithmic_work(kname, inp)
-        if work and work[0] == "hbm":
-            ach = work[1] / (kms * 1e-3) / 1e9
-            roof = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": ach / hbm_peak, "peak_source": peak_src, "traffic": None,
-                    "algorithmic_bytes_per_launch": work[1], "ms_per_launch": kms}
-        elif work and work[0] == "tensor":
-            peak = peaks.get("bf16_tflops_sustained", 1716.1)
-            ach = work[1] / (kms * 1e-3) / 1e12
-            roof = {"kernel": kname, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "peak_source": "of measured (bf16 sustained)",
-                    "issued_flops_per_launch": work[1] * 3 if kname == "k_match_tc" else work[1],
-                    "traffic": MEASURED_TRAFFIC.get(kname, (None,))[0],
-                    "traffic_source": MEASURED_TRAFFIC.get(kname, (None, None))[1],
-                    "algorithmic_flops_per_launch": work[1], "ms_per_launch": kms}
-        elif work and work[0] == "alu":
-            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            ach = work[1] / (kms * 1e-3) / 1e12
-            roof = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock",
-                    "traffic": MEASURED_TRAFFIC.get(kname, (None,))[0],
-                    "traffic_source": MEASURED_TRAFFIC.get(kname, (None, None))[1],
-                    "ms_per_launch": kms}
-            if kname == "k_svt":
-                roof["executed_flops_per_launch"] = work[1]
-                roof["svt_work"] = inp.get("svt_work")
-                roof["flops_note"] = ("the SVD is iterative: executed flops from the kernel's own sweep and "
-                                      "rotation counters, not a fixed algorithmic count")
-            else:
-                roof["algorithmic_flops_per_launch"] = work[1]
-        else:
-            roof = {"kernel": kname, "bound": None, "ms_per_launch": kms,
-                    "note": "no algorithmic-work model for this kernel"}
+        roof = roof_entry(kname, prof[kname][0] / max(prof[kname][1], 1), inp, peaks, hbm_peak, peak_src)
     if roof is not None:
         cp = r["profile"]
         roof["timing"] = ("kernel duration from a serialised pass of the same loop (CUDA events on the launching "
@@ -779,20 +1010,63 @@ def run_ours(args, dist):
         sec = dist.max(sec)
         line["e2e"] = {"value": dist.world * w.iters / sec, "unit": "iters/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h,
-                       "what": f"host k-space -> device, init (A^H b, matching, graph), {w.iters} iterations, "
-                               f"maps -> host"}
+                       "what": f"one mrf_recon_run_host call per step: pinned host k-space -> device, init "
+                               f"(A^H b, matching, graph), {w.iters} iterations, T1/T2/PD maps -> host"}
+    for v, names in ROOF_KERNELS.items():
+        if v not in res:
+            continue
+        pv, iv = (res[v]["serial"][0], res[v]["serial"][2]) if "serial" in res[v] else (res[v]["profile"], args.steps)
+        ents = [roof_entry(k, pv[k][0] / max(pv[k][1], 1), inp, peaks, hbm_peak, peak_src) for k in names if k in pv]
+        line.setdefault("roofline_kernels", {})[v] = [
+            {kk: e[kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac", "ms_per_launch",
+                                  "algorithmic_bytes_per_launch", "algorithmic_flops_per_launch",
+                                  "executed_flops_per_launch", "hbm_frac") if kk in e} for e in ents]
+    orc = None
+    if leg is not None:
+        # failures here are reported in the line, which is still printed
+        try:
+            line["nrmse_vs_oracle"], orc = small_problem_parity(leg_dir, leg, variants, synth_iters())
+        except Exception as exc:
+            line["nrmse_vs_oracle"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        try:
+            line["c1"] = c1_line(leg_dir, leg)
+        except Exception as exc:
+            line["c1"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        try:
+            leg.wait(timeout=900)
+        except subprocess.TimeoutExpired:
+            leg.kill()
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         sec, parts, sample = oracle_iteration_seconds(scale=1.0)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "iters/s", "cores": cores(), "kind": "oracle",
-                                "sample": sample, "seconds_by_step": parts}
+                                "sample": sample, "seconds_by_step": parts, "extrapolated": True,
+                                "method": "each step of one full-size iteration timed on a bounded sample (frames, "
+                                          "voxels, patches, graph rows) and scaled to the full workload; not a "
+                                          "timed full iteration"}
+        if orc is not None:
+            its = [float(x) for x in orc["its"]]
+            line["cpu_baseline"]["measured_reduced_problem"] = {
+                "what": "the oracle's Algorithm 1 timed in full on the reduced copy of the problem (64^2 voxels, "
+                        "100 frames, same dictionary grid, rank, patches and neighbours)",
+                "seconds_per_iteration": statistics.mean(its), "iters_per_s": 1.0 / statistics.mean(its),
+                "init_seconds": float(orc["init_s"]), "iterations": len(its), "cores": 1,
+                "blas_threads": 1}
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def synth_iters():
+    import synth
+    return synth.WORKLOADS["mrf256_t1000"].iters
 
 
 def main():
     global WORKLOAD
     args = parse()
     WORKLOAD = args.workload
+    if args.oracle_leg:
+        oracle_leg(args.oracle_leg, args.steps)
+        return
     dist = Dist()
     try:
         if args.impl == "reference":
