@@ -555,236 +555,11 @@ __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __res
 }
 
 // --------------------------------------------------------------------------
-// SVT (Eq. 18): one warp per patch, one-sided (Hestenes) Jacobi on the
-// p^2 x K coefficient block; P = B diag(max(sigma - tau, 0) / sigma) V^H with
-// B = A V the orthogonalised columns.  R rows per lane, KP >= K columns (the
-// extra columns are zero and stay zero).
+// SVT (Eq. 18): k_svt in svt.cuh (Gram matrix + two-sided Jacobi per patch)
 // --------------------------------------------------------------------------
-// Vio (nullable) holds each patch's right singular vectors [np][KP][KP]: with
-// warm != 0 the sweep starts from A V_prev (the previous iterate's basis, so
-// the columns are nearly orthogonal and few sweeps are needed); the final V
-// is stored back.  The SVD computed is the same either way.
-// sum over the LANES lanes of one patch (a whole warp, or one half of it)
-template <int LANES>
-__device__ __forceinline__ float lane_sum(float v) {
-#pragma unroll
-    for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// LANES = 32: one patch per warp; LANES = 16: two patches per warp (each half
-// a patch, R rows per lane), which halves the shuffle trees and the rotation
-// arithmetic per patch.  A half-warp past the last patch works on zeros, and
-// the sweep loop ends only when neither half needs another sweep.
-template <int R, int KP, int LANES>
-__global__ void __launch_bounds__(128, LANES == 16 ? (R * KP <= 32 ? 3 : 2) : ((R <= 2 && KP <= 10) ? 4 : 1))
-    k_svt(const float2* __restrict__ alpha, PatchGeom g, int K, float tau, float2* __restrict__ P,
-          double* __restrict__ nuc, float2* __restrict__ Vio, int warm, unsigned long long* __restrict__ stats) {
-    const int lane = threadIdx.x & 31;
-    const int sl = lane & (LANES - 1), base = lane & ~(LANES - 1);
-    const int j = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / LANES) + lane / LANES;
-    const bool active = j < g.count();
-    const int pp = g.p * g.p;
-    const int jy = active ? g.origin(j / g.cnt) : 0, jx = active ? g.origin(j % g.cnt) : 0;
-    float2 a[R][KP];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int row = sl + LANES * r;
-        const bool ok = active && row < pp;
-        const int py = ok ? row / g.p : 0, px = ok ? row - py * g.p : 0;
-        const float2* src = alpha + ((size_t)(jy + py) * g.n + jx + px) * K;
-#pragma unroll
-        for (int k = 0; k < KP; ++k) a[r][k] = (ok && k < K) ? src[k] : make_float2(0.f, 0.f);
-    }
-    float2 v[KP];
-#pragma unroll
-    for (int k = 0; k < KP; ++k) v[k] = make_float2(sl == k ? 1.f : 0.f, 0.f);
-    float2* Vp = (Vio && active) ? Vio + (size_t)j * KP * KP : nullptr;
-    if (Vio && warm) {
-        // v = row `sl` of V_prev; a <- a V_prev (row i of V_prev from lane base + i)
-        if (Vp && sl < KP) {
-#pragma unroll
-            for (int k = 0; k < KP; ++k) v[k] = Vp[sl * KP + k];
-        }
-        float2 na[R][KP];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int k = 0; k < KP; ++k) na[r][k] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < KP; ++i) {
-#pragma unroll
-            for (int k = 0; k < KP; ++k) {
-                float2 vik;
-                vik.x = __shfl_sync(0xffffffffu, v[k].x, base + i);
-                vik.y = __shfl_sync(0xffffffffu, v[k].y, base + i);
-#pragma unroll
-                for (int r = 0; r < R; ++r) na[r][k] = cadd(na[r][k], cmul(a[r][i], vik));
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int k = 0; k < KP; ++k) a[r][k] = na[r][k];
-    }
-    // Parallel cyclic order (circle schedule): a sweep is KP - 1 rounds of
-    // KP / 2 disjoint column pairs that together pair every two columns once;
-    // rotations of disjoint pairs commute, so a round reduces its pairs' inner
-    // products together (one shuffle tree for all of them) and then rotates.  A pair is rotated while its normalised
-    // off-diagonal |gamma| / (|a_p| |a_q|) exceeds kJacobiTol (a few times the
-    // FP32 rounding of a p^2-term inner product: below it a rotation only
-    // moves rounding noise); a sweep without rotations ends the loop, and so
-    // does a sweep whose rotations were all below kJacobiQuad (cyclic Jacobi
-    // converges quadratically: what such a sweep leaves is of order
-    // kJacobiQuad^2 < kJacobiTol).  Column norms are recomputed exactly at each
-    // sweep and updated in closed form after each rotation
-    // (|a_p|^2 -= t |gamma|, |a_q|^2 += t |gamma|).
-    constexpr float kJacobiTol = 2e-6f;
-    constexpr float kJacobiQuad = 3e-4f;
-    constexpr int NP = KP / 2;
-    int nsweep = 0, nrot = 0;     // executed sweeps and rotations of this patch (for stats)
-    for (int sweep = 0; sweep < 30; ++sweep) {
-        ++nsweep;
-        float n2[KP];
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            n2[k] = 0.f;
-#pragma unroll
-            for (int r = 0; r < R; ++r) n2[k] += cabs2(a[r][k]);
-        }
-#pragma unroll
-        for (int o = LANES / 2; o > 0; o >>= 1)
-#pragma unroll
-            for (int k = 0; k < KP; ++k) n2[k] += __shfl_xor_sync(0xffffffffu, n2[k], o);
-        bool rotated = false, large = false;
-        // Round rd pairs the register positions (i, KP - 1 - i); between rounds
-        // the columns at positions 1 .. KP - 1 shift down by one (position 0
-        // stays), which is the circle schedule with the data moved instead of
-        // the indices: the loop body is one round (small enough for the
-        // instruction cache) and after KP - 1 rounds every column is back in
-        // its position.
-#pragma unroll 1
-        for (int rd = 0; rd < KP - 1; ++rd) {
-            float gr[NP], gi[NP];
-#pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                const int p = i, q = KP - 1 - i;
-                gr[i] = 0.f;
-                gi[i] = 0.f;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const float2 t = cconjmul(a[r][p], a[r][q]);
-                    gr[i] += t.x;
-                    gi[i] += t.y;
-                }
-            }
-#pragma unroll
-            for (int o = LANES / 2; o > 0; o >>= 1)
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    gr[i] += __shfl_xor_sync(0xffffffffu, gr[i], o);
-                    gi[i] += __shfl_xor_sync(0xffffffffu, gi[i], o);
-                }
-#pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                const int p = i, q = KP - 1 - i;
-                const float al = n2[p], be = n2[q];
-                const float g2 = gr[i] * gr[i] + gi[i] * gi[i];
-                if (g2 > 1e-36f && g2 > kJacobiTol * kJacobiTol * al * be) {
-                    rotated = true;
-                    ++nrot;
-                    large |= g2 > kJacobiQuad * kJacobiQuad * al * be;
-                    const float ig = rsqrtf(g2), gabs = g2 * ig;
-                    // t: the root of t^2 + 2 zeta t - 1 = 0 of smaller magnitude,
-                    // zeta = (|a_q|^2 - |a_p|^2) / (2 |gamma|)
-                    const float d = be - al;
-                    const float t = __fdividef(2.f * gabs, d + copysignf(sqrtf(d * d + 4.f * g2), d));
-                    const float c = rsqrtf(1.f + t * t), sn = c * t;
-                    const float2 ph = make_float2(gr[i] * ig, -gi[i] * ig);   // conj(gamma) / |gamma|
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float2 ap = a[r][p], aq = cmul(a[r][q], ph);
-                        a[r][p] = csub(cscale(ap, c), cscale(aq, sn));
-                        a[r][q] = cadd(cscale(ap, sn), cscale(aq, c));
-                    }
-                    const float2 vp = v[p], vq = cmul(v[q], ph);
-                    v[p] = csub(cscale(vp, c), cscale(vq, sn));
-                    v[q] = cadd(cscale(vp, sn), cscale(vq, c));
-                    n2[p] = al - t * gabs;
-                    n2[q] = be + t * gabs;
-                }
-            }
-            // shift positions 1 .. KP - 1 down by one
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float2 first = a[r][1];
-#pragma unroll
-                for (int k = 1; k < KP - 1; ++k) a[r][k] = a[r][k + 1];
-                a[r][KP - 1] = first;
-            }
-            {
-                const float2 first = v[1];
-                const float nf = n2[1];
-#pragma unroll
-                for (int k = 1; k < KP - 1; ++k) { v[k] = v[k + 1]; n2[k] = n2[k + 1]; }
-                v[KP - 1] = first;
-                n2[KP - 1] = nf;
-            }
-        }
-        if (!__any_sync(0xffffffffu, rotated && large)) break;
-    }
-    float f[KP];
-    float nsum = 0.f;
-#pragma unroll
-    for (int k = 0; k < KP; ++k) {
-        float s2 = 0.f;
-#pragma unroll
-        for (int r = 0; r < R; ++r) s2 += cabs2(a[r][k]);
-        const float sg = sqrtf(lane_sum<LANES>(s2));
-        nsum += sg;
-        f[k] = sg > tau ? (sg - tau) / sg : 0.f;
-    }
-    if (nuc && active && sl == 0) atomicAdd(nuc, (double)nsum);
-    if (stats) {
-        // block totals first: one atomic pair per block instead of per patch
-        __shared__ unsigned s_sweeps, s_rots;
-        if (threadIdx.x == 0) { s_sweeps = 0u; s_rots = 0u; }
-        __syncthreads();
-        if (active && sl == 0) {
-            atomicAdd(&s_sweeps, (unsigned)nsweep);
-            atomicAdd(&s_rots, (unsigned)nrot);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            atomicAdd(&stats[0], (unsigned long long)s_sweeps);
-            atomicAdd(&stats[1], (unsigned long long)s_rots);
-        }
-    }
-    if (Vp && sl < KP) {
-#pragma unroll
-        for (int k = 0; k < KP; ++k) Vp[sl * KP + k] = v[k];
-    }
-    if (!P) return;
-    // P[row][k] = sum_j B[row][j] f_j conj(V[k][j]); row k of V lives in lane base + k
-    for (int k = 0; k < K; ++k) {
-        float2 vk[KP];
-#pragma unroll
-        for (int jj = 0; jj < KP; ++jj) {
-            vk[jj].x = __shfl_sync(0xffffffffu, v[jj].x, base + k);
-            vk[jj].y = __shfl_sync(0xffffffffu, v[jj].y, base + k);
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int row = sl + LANES * r;
-            if (active && row < pp) {
-                float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int jj = 0; jj < KP; ++jj) acc = cadd(acc, cscale(cmulc(a[r][jj], vk[jj]), f[jj]));
-                P[((size_t)j * pp + row) * K + k] = acc;
-            }
-        }
-    }
-}
+}  // namespace mrf
+#include "svt.cuh"
+namespace mrf {
 
 // --------------------------------------------------------------------------
 // Z step + X step (Eq. 12 and 19), gathered per voxel:
@@ -927,6 +702,13 @@ static void free_recon(mrf_recon_s* R) {
     delete R;
 }
 
+// dynamic shared memory above the default 48 KB needs an opt-in per kernel
+template <typename Kern>
+static mrf_status svt_smem(Kern k, size_t bytes) {
+    if (bytes > 48 * 1024) MRF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return MRF_OK;
+}
+
 static mrf_status svt(mrf_recon_s* R, const float2* alpha, float2* P, double* nuc, cudaStream_t s) {
     const int K = R->K;
     const int rows = R->pp;
@@ -938,8 +720,12 @@ static mrf_status svt(mrf_recon_s* R, const float2* alpha, float2* P, double* nu
     const bool half = rows <= 64 && KP <= 12;
     const int per_block = half ? 8 : 4;
     const unsigned blocks = (unsigned)((R->np + per_block - 1) / per_block);
-#define MRF_SVT(RR, KK, LL) \
-    k_svt<RR, KK, LL><<<blocks, 128, 0, s>>>(alpha, R->g, K, tau, P, nuc, R->svt_v, warm, R->svt_stats)
+#define MRF_SVT(RR, KK, LL)                                                                                   \
+    do {                                                                                                       \
+        const size_t sm = (size_t)(128 / LL) * svt_patch_f2(KK) * sizeof(float2);                              \
+        MRF_PROPAGATE(svt_smem(k_svt<RR, KK, LL>, sm));                                                        \
+        k_svt<RR, KK, LL><<<blocks, 128, sm, s>>>(alpha, R->g, K, tau, P, nuc, R->svt_v, warm, R->svt_stats); \
+    } while (0)
     if (half && rows <= 32) {
         switch (KP) {
             case 4: MRF_SVT(2, 4, 16); break;

@@ -19,15 +19,18 @@ def test_tensor_matcher_flops():
 
 
 def test_svt_executed_flops():
-    work = {"sweeps_per_patch": 5.409, "rotations_per_patch": 164.89}
+    """Gram matrix + two-sided Jacobi on the K x K matrix: fixed work per patch
+    (Gram 8 pp NG, V transforms 24 KP^3, column norms 8 pp KP^2, M 8 KP^2 K,
+    P 8 pp KP K) plus per-sweep and per-rotation work, for KP = K = 10, 8 x 8
+    patches, 3969 patches."""
+    work = {"sweeps_per_patch": 3.0, "rotations_per_patch": 40.0}
     inp = dict(_inp(), svt_work=work)
     kind, flops = bench.algorithmic_work("k_svt", inp)
     assert kind == "alu"
-    pp, KP, K, npatch = 64, 10, 10, 63 * 63
-    per_sweep = 4 * pp * KP + 8 * pp * (KP // 2) * (KP - 1)
-    per_rot = 18 * (pp + KP)
-    fixed = 8 * pp * KP * KP + 4 * pp * KP + 10 * pp * K * KP
-    assert flops == pytest.approx(npatch * (5.409 * per_sweep + 164.89 * per_rot + fixed), rel=1e-12)
-    assert flops == pytest.approx(1.887e9, rel=2e-3)
+    fixed = 8 * 64 * 55 + 24 * 1000 + 8 * 64 * 100 + 8 * 100 * 10 + 8 * 64 * 100      # 162560
+    per_sweep = 9 * (56 * 10 + 14 * 10 * 5)                                            # 11340
+    assert fixed == 162560 and per_sweep == 11340
+    assert flops == pytest.approx(3969 * (3.0 * per_sweep + 40.0 * 30 + fixed), rel=1e-12)
+    assert flops == pytest.approx(0.785e9, rel=2e-3)
     # without counters there is no SVT model
     assert bench.algorithmic_work("k_svt", _inp()) is None
