@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=["mrf256_t1000", "mrf256_t100"],
                     help="mrf256_t100: the same image with 100 frames, for small profiling captures")
     ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)   # child process of the cpu_baseline leg
+    ap.add_argument("--only-full-length-matching", type=int, default=0, metavar="N",
+                    help="run only the full-length matching measurement with N fingerprints (profiling captures)")
     ap.add_argument("--no-oracle-parity", action="store_true",
                     help="skip the oracle comparison on the reduced copy of the problem and the 64^2 x 100 line")
     return ap.parse_args()
@@ -441,6 +443,65 @@ def precision_variants(inp, alpha, reps=5):
     return out
 
 
+def full_length_matching(peaks, reps=3, n=65536):
+    """Matching of full 1000-frame fingerprints (Eq. 5 without the subspace):
+    65536 noisy fingerprints built from the 256^2 workload's 5441 EPG atoms,
+    split-BF16 streamed tensor-core matcher against the FP32 SIMT matcher.
+    Algorithmic work: the complex GEMM, 8 N M T flops (the split form issues
+    3x that on the tensor cores)."""
+    import torch
+
+    import synth
+    import paper_2310_05647_gb300 as mrf
+    from paper_2310_05647_gb300.api import MATCH_BF16X3, MATCH_FP32
+
+    w = synth.WORKLOADS[WORKLOAD]
+    dev = torch.device("cuda")
+    fa, tr = synth.fisp_train(1000, seed=w.tr_seed)
+    f32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    lut = f32(synth.workload_grid(w))
+    D = mrf.epg_fisp(lut, f32(fa), f32(tr))
+    n2 = (D.abs() ** 2).sum(1).float().contiguous()
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    M, T = D.shape[0], D.shape[1]
+    pick = torch.randint(0, M, (n,), generator=g, device=dev)
+    noise = torch.complex(torch.randn(n, T, generator=g, device=dev), torch.randn(n, T, generator=g, device=dev))
+    X = (D[pick] * 0.8 + 0.02 * D.abs().mean() * noise).contiguous()
+    del noise
+    flops = 8.0 * n * M * T
+    peak = peaks.get("bf16_tflops_sustained", 1716.1)
+    out = {"what": f"{n} fingerprints x {M} atoms x {T} frames (full-length Eq. 5), one mrf_match call",
+           "algorithmic_flops": flops}
+    res = {}
+    for name, prec, r in (("bf16x3", MATCH_BF16X3, reps), ("fp32", MATCH_FP32, 1)):
+        res[name] = mrf.match(X, D, lut, atom_norm2=n2, precision=prec)
+        torch.cuda.synchronize()
+        mrf.profile_enable(True)
+        mrf.profile_mark()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(r):
+            res[name] = mrf.match(X, D, lut, atom_norm2=n2, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        prof = mrf.profile_read()
+        mrf.profile_enable(False)
+        ms = e0.elapsed_time(e1) / r
+        ent = {"ms_per_call": ms, "tflops_algorithmic": flops / ms / 1e9,
+               "kernels_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items()}}
+        if name == "bf16x3" and "k_match_tc_long" in prof:
+            kms = prof["k_match_tc_long"][0] / max(prof["k_match_tc_long"][1], 1)
+            ent["roofline"] = {"kernel": "k_match_tc_long", "bound": "tensor", "achieved": flops / kms / 1e9,
+                               "peak": peak, "unit": "TFLOP/s", "frac": flops / kms / 1e9 / peak,
+                               "issued_frac": 3 * flops / kms / 1e9 / peak,
+                               "peak_source": "of measured (bf16 sustained)", "ms_per_launch": kms}
+        out[name] = ent
+    out["index_agreement_bf16x3_vs_fp32"] = float((res["bf16x3"][0] == res["fp32"][0]).float().mean())
+    del X, D
+    return out
+
+
 def serving(seed=0, slices=16, iters=10, rounds=10):
     """Batched serving: `slices` slices of uneven size (grid 128^2 or 256^2, T in
     {500, 750, 1000}, 1-3 spiral arms per frame, seeded draws) sharing one atom
@@ -468,7 +529,7 @@ def serving(seed=0, slices=16, iters=10, rounds=10):
     del D
     cfg, recons, keep = [], [], []
     for i in range(slices):
-        n = int(rng.choice([128, 256]))
+        n = int(rng.choice([128, 192, 256]))
         T = int(rng.choice([500, 750, 1000]))
         per = int(rng.integers(1, 4))
         cfg.append({"n": n, "frames": T, "arms_per_frame": per})
@@ -513,8 +574,8 @@ def serving(seed=0, slices=16, iters=10, rounds=10):
     maps_ok = all(bool(torch.isfinite(r.maps()[0]).all()) for r in recons)
     del batch
     tot = sum(lat)
-    return {"what": f"{slices} slices, {iters} iterations per request; grids from {{128^2, 256^2}} (192^2 needs a "
-                    f"non-power-of-two FFT, not built), T from {{500, 750, 1000}}, 1-3 arms of {w.ns} samples per "
+    return {"what": f"{slices} slices, {iters} iterations per request; grids from {{128^2, 192^2, 256^2}}, "
+                    f"T from {{500, 750, 1000}}, 1-3 arms of {w.ns} samples per "
                     f"frame, shared {len(lut)}-atom grid, split-BF16 matching, no cost terms",
             "slices": cfg,
             "throughput_slice_iters_per_s": slices * iters * rounds / tot,
@@ -550,7 +611,10 @@ def e2e_chosen(inp, iters, reps=2):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample of one iteration, extrapolated)
 # ---------------------------------------------------------------------------
-def oracle_iteration_seconds(scale=1.0):
+ORACLE_SAMPLE_SCALE = 0.25     # one sample size for the reference arm and the cpu_baseline leg
+
+
+def oracle_iteration_seconds(scale=ORACLE_SAMPLE_SCALE):
     """Seconds the FP64 oracle needs for one Algorithm 1 iteration at 256^2 x 1000,
     extrapolated from timed samples of each step (frames, voxels, patches and
     graph rows), with `scale` shrinking every sample."""
@@ -813,6 +877,17 @@ def c1_line(out_dir, proc, reps=20):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     idx, pd, t1t2 = (t.cpu().numpy() for t in res)
+    tc = mrf.gridding_match(plan, b, D, lut, precision=2)
+    ms_tc = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tc = mrf.gridding_match(plan, b, D, lut, precision=2)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_tc.append(e0.elapsed_time(e1))
+    tc_idx = tc[0].cpu().numpy()
     orc = _wait_file(os.path.join(out_dir, "c1_oracle.npz"), proc)
     mask = inp["mask"].astype(bool)
     shp = (c1.n, c1.n)
@@ -822,6 +897,8 @@ def c1_line(out_dir, proc, reps=20):
                                               "per frame) then exhaustive FP32 matching of the 100-frame "
                                               "fingerprints against 1500 EPG atoms (mrf_gridding_match)",
             "gpu_ms": statistics.median(ms), "oracle_ms": 1e3 * float(orc["seconds"]),
+            "gpu_ms_split_bf16_tensor": statistics.median(ms_tc),
+            "index_agreement_split_bf16_vs_oracle": float((tc_idx == orc["idx"].ravel()).mean()),
             "speedup_vs_oracle": 1e3 * float(orc["seconds"]) / statistics.median(ms),
             "l2": "flushed before every timed call",
             "index_agreement_vs_oracle": float((idx == orc["idx"].ravel()).mean()),
@@ -902,19 +979,27 @@ ROOF_KERNELS = {"chosen": ["k_match_tc", "k_svt", "k_knn_tc", "k_graph_blocks"],
 def run_reference(args, dist):
     if dist.rank != 0:
         return
-    times = []
+    times, walls = [], []
     sample = ""
     for i in range(args.warmup + args.steps):
-        s, _, sample = oracle_iteration_seconds(scale=0.25)
+        t0 = time.perf_counter()
+        s, _, sample = oracle_iteration_seconds()
+        wall = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(s)
+            walls.append(wall)
     sec = statistics.mean(times)
     val = 1.0 / sec
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "implementation": "FP64 CPU oracle (NumPy), literal full-frame form"},
-            "cpu_baseline": {"kind": "oracle", "value": val, "unit": "iters/s", "cores": cores(), "sample": sample},
+            "cpu_baseline": {"kind": "oracle", "value": val, "unit": "iters/s", "cores": cores(), "sample": sample,
+                             "extrapolated": True,
+                             "method": "each step times every stage of one full-size iteration on a bounded sample "
+                                       "and scales it to the full workload; ms_per_step is that extrapolated "
+                                       "iteration time, not the wall time of the step",
+                             "sample_wall_seconds_per_step": statistics.mean(walls)},
             "e2e": {"value": val, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -932,6 +1017,10 @@ def run_ours(args, dist):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
+    if args.only_full_length_matching:
+        print(json.dumps({"full_length_matching": full_length_matching(peaks, reps=1,
+                                                                       n=args.only_full_length_matching)}))
+        return
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     leg, leg_dir = None, None
@@ -1018,6 +1107,8 @@ def run_ours(args, dist):
                     "ms per mrf_match call, index agreement and map NRMSE vs FP32 exhaustive matching"
                     % (inp["atoms"], w.rank),
             **precision_variants(inp, res["chosen"]["alpha"])}
+    if dist.world == 1:
+        line["full_length_matching"] = full_length_matching(peaks)
     if not args.no_serving and dist.world == 1:
         line["serving"] = serving(seed=dist.rank)
     if not args.no_e2e:
@@ -1052,7 +1143,7 @@ def run_ours(args, dist):
         except subprocess.TimeoutExpired:
             leg.kill()
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        sec, parts, sample = oracle_iteration_seconds(scale=1.0)
+        sec, parts, sample = oracle_iteration_seconds()
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "iters/s", "cores": cores(), "kind": "oracle",
                                 "sample": sample, "seconds_by_step": parts, "extrapolated": True,
                                 "method": "each step of one full-size iteration timed on a bounded sample (frames, "

@@ -137,11 +137,11 @@ mrf_status mrf_dict_subspace(const mrf_c64* dict, int m, int T, int K, mrf_c64* 
 
 enum {
     MRF_MATCH_FP32 = 0,        /* exhaustive FP32 inner products (plain form) */
-    MRF_MATCH_BF16 = 1,        /* BF16 tensor-core scores, FP32 top-8 re-rank (2 len <= 128) */
+    MRF_MATCH_BF16 = 1,        /* BF16 tensor-core scores, FP32 top-8 re-rank */
     MRF_MATCH_BF16X3 = 2,      /* split BF16 (hi/lo, three products in one GEMM), FP32 top-4
-                                  re-rank: tensor-core speed at ~2^-16 score error (6 len <= 128) */
+                                  re-rank: tensor-core speed at ~2^-16 score error */
     MRF_MATCH_FP8 = 3,         /* FP8 e4m3 tensor-core scores (atoms scaled to unit norm x 448,
-                                  fingerprints by 448 / max |x|), FP32 top-8 re-rank (2 len <= 128) */
+                                  fingerprints by 448 / max |x|), FP32 top-8 re-rank (len <= 64) */
     MRF_MATCH_LITERAL_NORM2 = 0x100 /* flag: argmax of |<d,x>|/||d||^2 as printed in Eq. 5 */
 };
 
@@ -154,7 +154,14 @@ enum {
  * ||d_m||^2 or NULL to use the rows of dict (pass the full-length norms when
  * dict holds subspace-compressed atoms d_m Phi); lut: dev float [m][2]
  * (T1, T2).  Outputs (each nullable): idx dev int [n], pd dev float [n],
- * t1t2 dev float [n][2].  1 <= len <= 2048, 1 <= m <= 2^24. */
+ * t1t2 dev float [n][2].  1 <= len <= 2048, 1 <= m <= 2^24.  The BF16 forms
+ * keep the fingerprint tile resident in shared memory while the padded
+ * reduction (2 len reals, three copies for the split form) fits 128 elements
+ * (len <= 64 BF16, len <= 21 split BF16), and stream both operands along the
+ * reduction axis beyond that (full-length fingerprints, e.g. 1000 frames);
+ * the results follow the same rules either way.  Scratch is allocated and
+ * freed on the stream; a tensor-core call synchronises the stream to report
+ * a device wait that gave up (MRF_ETIMEOUT). */
 mrf_status mrf_match(const mrf_c64* x, int n, int len, const mrf_c64* dict,
                      const float* atom_norm2, const float* lut, int m, int precision,
                      int* idx, float* pd, float* t1t2, mrf_stream stream);
@@ -184,7 +191,8 @@ mrf_status mrf_gridding_match(mrf_plan plan, const mrf_c64* y, const mrf_c64* di
  * are not TOPK distinct indices in [0, m) (e.g. -1) leave the row unseeded.
  * On return those entries hold the row's candidates; the others are left
  * as they were.  precision: MRF_MATCH_BF16 or MRF_MATCH_BF16X3 (else
- * MRF_EINVAL); other arguments as in mrf_match. */
+ * MRF_EINVAL), with the fingerprint tile resident (len <= 64 BF16, <= 21
+ * split BF16; longer: MRF_EINVAL); other arguments as in mrf_match. */
 mrf_status mrf_match_seeded(const mrf_c64* x, int n, int len, const mrf_c64* dict, const float* atom_norm2,
                             const float* lut, int m, int precision, int* cand, int* idx, float* pd,
                             float* t1t2, mrf_stream stream);

@@ -1,12 +1,12 @@
 // Batched shared-memory Stockham FFT used by the NUFFT kernels.
 //
-// One transform of power-of-two length N lives in shared memory at
-// s[i * stride], i < N, and is processed by N/8 threads.  Each pass of radix R
-// (8 while the remaining factor allows, then 4 or 2) reads R strided inputs
-// per butterfly, applies the twiddles, runs an R-point DFT in registers and
+// One transform of length N (a power of two, or 3 times one) lives in shared
+// memory at a fixed stride.  Each pass of radix R (3 for the factor 3, 8 while
+// the remaining factor allows, then 4 or 2) reads R strided inputs per
+// butterfly, applies the twiddles, runs an R-point DFT in registers and
 // writes to the self-sorting (Stockham) positions, so the result comes out in
 // natural order with no bit reversal.  Every thread of the block calls each
-// pass (idle ones with active = false) because passes end in __syncthreads().
+// pass because passes end in __syncthreads().
 //
 // Forward: X[m] = sum_n x[n] exp(-2 pi i m n / N); inverse (INV): the same
 // sum with exp(+2 pi i m n / N), unnormalised.
@@ -79,67 +79,25 @@ __device__ __forceinline__ void dft8(float2* v) {
     v[7] = csub(e3, o3);
 }
 
+// X0 = a + b + c, X1,2 = a - (b + c)/2 -/+ i (sqrt(3)/2)(b - c) (forward;
+// the sign of the i term flips for the inverse)
+template <bool INV>
+__device__ __forceinline__ void dft3(float2* v) {
+    const float h = 0.86602540378443865f;       // sqrt(3) / 2
+    const float2 a = v[0], t1 = cadd(v[1], v[2]);
+    const float2 t2 = csub(a, cscale(t1, 0.5f));
+    const float2 t3 = rot90<INV>(cscale(csub(v[1], v[2]), h));
+    v[0] = cadd(a, t1);
+    v[1] = cadd(t2, t3);
+    v[2] = csub(t2, t3);
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft_r(float2* v) {
     if constexpr (R == 8) dft8<INV>(v);
     else if constexpr (R == 4) dft4<INV>(v);
+    else if constexpr (R == 3) dft3<INV>(v);
     else dft2<INV>(v);
-}
-
-// One Stockham pass of radix R over a length-N transform.  Ns = product of the
-// radices of the passes already done.
-template <int N, int R, bool INV>
-__device__ __forceinline__ void stockham_pass(float2* s, int stride, int Ns, int tid, bool active,
-                                              const float2* tw) {
-    constexpr int NB = N / R;       // butterflies
-    constexpr int TPF = N / 8;      // threads per transform
-    constexpr int PER = NB / TPF;   // butterflies per thread (8 / R)
-    float2 v[PER][R];
-    if (active) {
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int j = tid + q * TPF;
-            const int jm = j & (Ns - 1);
-            const int step = N / (Ns * R);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float2 x = s[(j + r * NB) * stride];
-                if (r > 0) x = twiddle<INV>(x, tw[r * jm * step]);
-                v[q][r] = x;
-            }
-            dft_r<R, INV>(v[q]);
-        }
-    }
-    __syncthreads();
-    if (active) {
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int j = tid + q * TPF;
-            const int jm = j & (Ns - 1);
-            const int d = (j - jm) * R + jm;
-#pragma unroll
-            for (int r = 0; r < R; ++r) s[(d + r * Ns) * stride] = v[q][r];
-        }
-    }
-    __syncthreads();
-}
-
-__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
-
-// Full in-place transform; ends with the data in natural order and synced.
-template <int N, bool INV>
-__device__ __forceinline__ void fft_smem(float2* s, int stride, int tid, bool active, const float2* tw) {
-    constexpr int L = ilog2(N);
-    constexpr int N8 = L / 3;
-    constexpr int REM = L % 3;
-    int Ns = 1;
-#pragma unroll
-    for (int p = 0; p < N8; ++p) {
-        stockham_pass<N, 8, INV>(s, stride, Ns, tid, active, tw);
-        Ns *= 8;
-    }
-    if constexpr (REM == 2) stockham_pass<N, 4, INV>(s, stride, Ns, tid, active, tw);
-    if constexpr (REM == 1) stockham_pass<N, 2, INV>(s, stride, Ns, tid, active, tw);
 }
 
 }  // namespace mrf
@@ -155,7 +113,9 @@ namespace mrf {
 // bstride = 1) or rows padded to an odd stride (estride = 1, bstride = N + 1)
 // every shared-memory access of a warp is bank-conflict free.
 // ---------------------------------------------------------------------------
-template <int N, int R, int NWK, bool INV>
+// One pass of radix R after sub-transforms of length Ns (POW2: Ns a power of
+// two, so j mod Ns is a mask).
+template <int N, int R, int NWK, bool INV, bool POW2>
 __device__ __forceinline__ void batch_pass(float2* t, int es, int Ns, int wk, const float2* tw) {
     constexpr int NB = N / R;
     constexpr int PER = (NB + NWK - 1) / NWK;
@@ -164,7 +124,7 @@ __device__ __forceinline__ void batch_pass(float2* t, int es, int Ns, int wk, co
     for (int q = 0; q < PER; ++q) {
         const int j = wk + q * NWK;
         if (j < NB) {
-            const int jm = j & (Ns - 1);
+            const int jm = POW2 ? (j & (Ns - 1)) : (j % Ns);
             const int step = N / (Ns * R);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -180,7 +140,7 @@ __device__ __forceinline__ void batch_pass(float2* t, int es, int Ns, int wk, co
     for (int q = 0; q < PER; ++q) {
         const int j = wk + q * NWK;
         if (j < NB) {
-            const int jm = j & (Ns - 1);
+            const int jm = POW2 ? (j & (Ns - 1)) : (j % Ns);
             const int d = (j - jm) * R + jm;
 #pragma unroll
             for (int r = 0; r < R; ++r) t[(d + r * Ns) * es] = v[q][r];
@@ -189,23 +149,33 @@ __device__ __forceinline__ void batch_pass(float2* t, int es, int Ns, int wk, co
     __syncthreads();
 }
 
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+// Lengths N = 2^a, or 3 x 2^a (a radix-3 pass first, then the power of two).
 template <int N, int B, int NT, bool INV>
 __device__ __forceinline__ void fft_batch(float2* s, int estride, int bstride, const float2* tw) {
     static_assert(NT % B == 0, "block size must be a multiple of the batch");
+    constexpr bool POW2 = (N & (N - 1)) == 0;
+    static_assert(POW2 || (N % 3 == 0 && ((N / 3) & (N / 3 - 1)) == 0), "N = 2^a or 3 x 2^a");
     constexpr int NWK = NT / B;
-    constexpr int L = ilog2(N);
+    constexpr int M = POW2 ? N : N / 3;       // the power-of-two part
+    constexpr int L = ilog2(M);
     constexpr int N8 = L / 3;
     constexpr int REM = L % 3;
     float2* t = s + (threadIdx.x % B) * bstride;
     const int wk = threadIdx.x / B;
     int Ns = 1;
+    if constexpr (!POW2) {
+        batch_pass<N, 3, NWK, INV, false>(t, estride, Ns, wk, tw);
+        Ns = 3;
+    }
 #pragma unroll
     for (int p = 0; p < N8; ++p) {
-        batch_pass<N, 8, NWK, INV>(t, estride, Ns, wk, tw);
+        batch_pass<N, 8, NWK, INV, POW2>(t, estride, Ns, wk, tw);
         Ns *= 8;
     }
-    if constexpr (REM == 2) batch_pass<N, 4, NWK, INV>(t, estride, Ns, wk, tw);
-    if constexpr (REM == 1) batch_pass<N, 2, NWK, INV>(t, estride, Ns, wk, tw);
+    if constexpr (REM == 2) batch_pass<N, 4, NWK, INV, POW2>(t, estride, Ns, wk, tw);
+    if constexpr (REM == 1) batch_pass<N, 2, NWK, INV, POW2>(t, estride, Ns, wk, tw);
 }
 
 }  // namespace mrf

@@ -205,7 +205,9 @@ mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* no
 mrf_status match_run(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m,
                      int precision, const float* lut, int* idx, float* pd, float* t1t2, float pd_scale,
                      cudaStream_t s, int* cand_io) {
-    if (tc_form(precision)) {
+    if (tc_form(precision) && tc_long(len, tc_form(precision))) {
+        MRF_PROPAGATE(match_tc_long(ws, x, n, len, dict, m, tc_form(precision), s));
+    } else if (tc_form(precision)) {
         MRF_PROPAGATE(match_tc_candidates(ws, x, n, len, dict, m, tc_form(precision), s, cand_io));
         MRF_PROPAGATE(match_rerank(ws, x, n, len, dict, s));
     } else {
@@ -243,7 +245,13 @@ static mrf_status match_call(const mrf_c64* x, int n, int len, const mrf_c64* di
     cudaStream_t s = as_stream(stream);
     // stream-ordered scratch: released on the stream after the kernels
     MatchWorkspace ws;
-    const size_t tcb = prec == MRF_MATCH_FP32 ? 0 : tc_operand_bytes(m, len, tc_form(prec));
+    MRF_REQUIRE(!(prec == MRF_MATCH_FP8 && tc_long(len, 8)),
+                "mrf_match: FP8 matching supports lengths up to 64 (got %d)", len);
+    MRF_REQUIRE(!(cand && tc_long(len, tc_form(prec))),
+                "mrf_match_seeded: lengths beyond the resident tile are not seeded (got %d)", len);
+    const size_t tcb = prec == MRF_MATCH_FP32 ? 0
+                       : tc_long(len, tc_form(prec)) ? tc_long_scratch_bytes(n, m, len, tc_form(prec))
+                                                     : tc_operand_bytes(m, len, tc_form(prec));
     const size_t bytes = sizeof(int) * (size_t)n + sizeof(float2) * (size_t)n + sizeof(int) * (size_t)n * kTopK +
                          2 * sizeof(float) * (size_t)m + tcb + 8 * 256;
     char* base = nullptr;

@@ -72,5 +72,11 @@ mrf_status match_tc_candidates(MatchWorkspace& ws, const float2* x, int n, int l
                                int prec, cudaStream_t s, int* cand_io = nullptr);
 mrf_status match_rerank(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict,
                         cudaStream_t s);
+// full-length fingerprints (a padded reduction beyond the resident tile of
+// k_match_tc): the streamed tensor-core matcher of match_tc_long.cu
+bool tc_long(int len, int prec);
+size_t tc_long_scratch_bytes(int n, int m, int len, int prec);
+mrf_status match_tc_long(MatchWorkspace& ws, const float2* x, int n, int len, const float2* dict, int m, int prec,
+                         cudaStream_t s);
 
 }  // namespace mrf

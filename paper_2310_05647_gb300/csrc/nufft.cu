@@ -7,12 +7,13 @@
 //                      inverse FFT along x + crop + deapod  (k_rows_adj)
 //
 // The oversampled grid G x G of a frame is never written to HBM: the column
-// kernels own a 32-column strip of the frame in shared memory ([G][32], one
-// column per lane of a warp), transform it there and interpolate (or spread)
-// the samples binned to that strip.  A forward strip owns 32 - (W - 1)
-// columns and carries W - 1 halo columns so each sample's W x W nodes are in
-// the tile; an adjoint strip owns all 32 columns and a sample that straddles
-// two strips is spread by both.  Only the half-oversampled intermediate
+// kernels own a 16-column strip of the frame in shared memory ([G][16], 64 KB
+// at G = 512, so three blocks share an SM and one block's loads overlap
+// another's transforms), transform it there and interpolate (or spread) the
+// samples binned to that strip.  A forward strip owns 16 - (W - 1) columns
+// and carries W - 1 halo columns so each sample's W x W nodes are in the
+// tile; an adjoint strip owns all 16 columns and a sample that straddles two
+// strips is spread by both.  Only the half-oversampled intermediate
 // H1 [T][ny][G] (rows transformed along x) goes through memory.  Row kernels
 // transform 16 rows per block in a [16][G + 1] tile (odd row stride, one row
 // per lane).  Samples are binned on the host when the plan is built; frames
@@ -33,8 +34,8 @@
 
 namespace mrf {
 
-constexpr int kTile = 32;        // columns per strip tile (one per lane)
-constexpr int kColThreads = 512; // threads of the strip kernels
+constexpr int kTile = 16;        // columns per strip tile (64 KB at G = 512: three blocks per SM)
+constexpr int kColThreads = 256; // threads of the strip kernels
 constexpr int kRowB = 16;        // rows (or frames) per row-kernel block
 constexpr int kRowThreads = 256; // threads of the row kernels
 
@@ -58,6 +59,17 @@ __device__ __forceinline__ void unpack(const int4 r, int& j, int& mx0, int& my0,
 // centred coordinate held at grid index g
 template <int G>
 __device__ __forceinline__ int centred(int g) { return g < G / 2 ? g : g - G; }
+
+// v mod G in [0, G) (grids of 2^a or 3 x 2^a points)
+template <int G>
+__device__ __forceinline__ int wrapg(int v) {
+    if constexpr ((G & (G - 1)) == 0) {
+        return v & (G - 1);
+    } else {
+        const int r = v % G;
+        return r < 0 ? r + G : r;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Forward stage 1: rows.  SRC 0: frames x[t][iy][ix]; SRC 1: coefficient image
@@ -148,7 +160,7 @@ __device__ __forceinline__ void load_strip(float2* tile, const float2* __restric
         const int gy = idx / kTile, c = idx & (kTile - 1);
         const int iy = centred<G>(gy) + ny / 2;
         float2 v = make_float2(0.f, 0.f);
-        if (iy >= 0 && iy < ny) v = h1f[(size_t)iy * G + ((c0 + c) & (G - 1))];
+        if (iy >= 0 && iy < ny) v = h1f[(size_t)iy * G + (wrapg<G>(c0 + c))];
         tile[idx] = v;
     }
     __syncthreads();
@@ -189,7 +201,7 @@ __global__ void __launch_bounds__(kColThreads) k_cols_interp(const float2* __res
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int b = 0; b < W; ++b) {
-            const float2* tr = tile + ((my0 + b) & (G - 1)) * kTile + lc;
+            const float2* tr = tile + (wrapg<G>(my0 + b)) * kTile + lc;
             float2 rs = make_float2(0.f, 0.f);
 #pragma unroll
             for (int a = 0; a < W; ++a) rs = cadd(rs, cscale(tr[a], wx[a]));
@@ -256,11 +268,11 @@ __global__ void __launch_bounds__(kColThreads) k_spread_cols(const float2* __res
             kb_weights<W>(fy, beta, wy);
 #pragma unroll
             for (int a = 0; a < W; ++a) {
-                const int lc = ((mx0 + a) & (G - 1)) - c0;
+                const int lc = (wrapg<G>(mx0 + a)) - c0;
                 if (lc < 0 || lc >= kTile) continue;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
-                    float2* p = tile + ((my0 + b) & (G - 1)) * kTile + lc;
+                    float2* p = tile + (wrapg<G>(my0 + b)) * kTile + lc;
                     const float w = wx[a] * wy[b];
                     atomicAdd(&p->x, w * v.x);
                     atomicAdd(&p->y, w * v.y);
@@ -273,7 +285,7 @@ __global__ void __launch_bounds__(kColThreads) k_spread_cols(const float2* __res
     float2* dst = h1 + (size_t)f * ny * G;
     for (int idx = threadIdx.x; idx < ny * kTile; idx += kColThreads) {
         const int iy = idx / kTile, c = idx & (kTile - 1);
-        const int gy = (iy - ny / 2) & (G - 1);
+        const int gy = wrapg<G>(iy - ny / 2);
         dst[(size_t)iy * G + c0 + c] = tile[gy * kTile + c];
     }
 }
@@ -391,7 +403,7 @@ __global__ void __launch_bounds__(kColThreads) k_cols_inv(const float2* __restri
     float2* dst = h1 + (size_t)f * ny * G;
     for (int idx = threadIdx.x; idx < ny * kTile; idx += kColThreads) {
         const int iy = idx / kTile, c = idx & (kTile - 1);
-        const int gy = (iy - ny / 2) & (G - 1);
+        const int gy = wrapg<G>(iy - ny / 2);
         dst[(size_t)iy * G + c0 + c] = tile[gy * kTile + c];
     }
 }
@@ -422,7 +434,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_adj(const float2* __restri
         const int r = idx / nx, ix = idx - r * nx;
         const int iy = iy0 + r;
         if (iy >= ny) continue;
-        const float2 v = cscale(rows[r * LD + ((ix - nx / 2) & (G - 1))], inv_dx[ix] * inv_dy[iy] * scale);
+        const float2 v = cscale(rows[r * LD + (wrapg<G>(ix - nx / 2))], inv_dx[ix] * inv_dy[iy] * scale);
         if (DST == 0) x[((size_t)t * ny + iy) * nx + ix] = v;
         else x[((size_t)iy * nx + ix) * K + t] = v;
     }
@@ -432,7 +444,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_adj(const float2* __restri
 // frames t of part p of (A^H y)_t[iy][ix] phi[t][k].  Block = one image row,
 // 16 frames per inner step.
 template <int G>
-__global__ void __launch_bounds__(kRowThreads) k_rows_adj_reduce(const float2* __restrict__ h1,
+__global__ void __launch_bounds__(kRowThreads, 2) k_rows_adj_reduce(const float2* __restrict__ h1,
                                                                  const float2* __restrict__ phi, int K, int T,
                                                                  int frames_per_part,
                                                                  float2* __restrict__ partial,
@@ -470,7 +482,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_adj_reduce(const float2* _
             const int pidx = threadIdx.x + q * kRowThreads;
             if (pidx < nx * K) {
                 const int ix = pidx / K, k = pidx - ix * K;
-                const int gx = (ix - nx / 2) & (G - 1);
+                const int gx = wrapg<G>(ix - nx / 2);
                 float2 s = make_float2(0.f, 0.f);
                 for (int f = 0; f < nf; ++f) s = cadd(s, cmul(rows[f * LD + gx], ph[f * K + k]));
                 acc[q] = cadd(acc[q], cscale(s, inv_dx[ix] * sy));
@@ -509,13 +521,13 @@ __global__ void k_interp_groups(const float2* __restrict__ spec, int K, const in
     kb_weights<W>(fy, beta, wy);
     int col[W];
 #pragma unroll
-    for (int a = 0; a < W; ++a) col[a] = (mx0 + a) & (G - 1);
+    for (int a = 0; a < W; ++a) col[a] = wrapg<G>(mx0 + a);
     for (int k = 0; k < K; ++k) {
         const float2* s = spec + (size_t)k * G * G;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int b = 0; b < W; ++b) {
-            const float2* r = s + (size_t)((my0 + b) & (G - 1)) * G;
+            const float2* r = s + (size_t)(wrapg<G>(my0 + b)) * G;
             float2 rs = make_float2(0.f, 0.f);
 #pragma unroll
             for (int a = 0; a < W; ++a) rs = cadd(rs, cscale(r[col[a]], wx[a]));
@@ -597,13 +609,14 @@ static mrf_status set_smem(Kern kernel, size_t bytes) {
     return MRF_OK;
 }
 
-static bool supported_grid(int g) { return g == 64 || g == 128 || g == 256 || g == 512; }
+static bool supported_grid(int g) { return g == 64 || g == 128 || g == 256 || g == 384 || g == 512; }
 
 #define MRF_DISPATCH_G(G_, ...)                                                          \
     switch (G_) {                                                                        \
         case 64: { constexpr int GG = 64; __VA_ARGS__; break; }                          \
         case 128: { constexpr int GG = 128; __VA_ARGS__; break; }                        \
         case 256: { constexpr int GG = 256; __VA_ARGS__; break; }                        \
+        case 384: { constexpr int GG = 384; __VA_ARGS__; break; }                        \
         case 512: { constexpr int GG = 512; __VA_ARGS__; break; }                        \
         default: MRF_REQUIRE(false, "unsupported grid size %d", G_);                     \
     }
@@ -865,7 +878,7 @@ extern "C" mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int T, int n
     MRF_REQUIRE(nx > 0 && ny > 0 && nx % 2 == 0 && ny % 2 == 0, "mrf_nufft_plan: nx, ny must be even and > 0");
     MRF_REQUIRE(nx == ny, "mrf_nufft_plan: square images only (nx %d, ny %d)", nx, ny);
     MRF_REQUIRE(supported_grid(os * nx) && supported_grid(os * ny),
-                "mrf_nufft_plan: os*nx and os*ny must be in {64,128,256,512} (got %d, %d)", os * nx, os * ny);
+                "mrf_nufft_plan: os*nx and os*ny must be in {64,128,256,384,512} (got %d, %d)", os * nx, os * ny);
     MRF_REQUIRE(T >= 1 && ns >= 1 && ns < (1 << 24), "mrf_nufft_plan: bad nframes/ns (%d, %d)", T, ns);
     cudaStream_t s = as_stream(stream);
     auto* p = new mrf_plan_s();

@@ -5,9 +5,9 @@
 struct mrf_plan_s {
     int nx = 0, ny = 0, T = 0, ns = 0, os = 2, W = 4;
     int gx = 0, gy = 0;           // oversampled grid
-    int sf = 29;                  // grid columns owned by a forward strip (32 - (W - 1))
+    int sf = 13;                  // grid columns owned by a forward strip (strip width - (W - 1))
     int nstrips_f = 0;            // forward strips: ceil(gx / sf)
-    int nstrips_a = 0;            // adjoint strips: gx / 32
+    int nstrips_a = 0;            // adjoint strips: gx / strip width
     int ngroups = 0;              // distinct per-frame trajectories
     float beta = 0.f;             // Kaiser-Bessel shape
     double beta_d = 0.0;

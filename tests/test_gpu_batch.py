@@ -142,3 +142,39 @@ def test_gather_autotuner_choice_and_result():
     assert run in (0, 8, 16, 32, 64) and thr in (128, 256, 512)
     a_frames = m.nufft_adjoint_subspace(plan, y, phi_d, 1.0, mode=0)
     assert rel(np_(a_grouped), np_(a_frames)) < 1e-4
+
+
+def test_batched_slice_follows_oracle():
+    """One slice of a batch (32^2, 24 frames) against the FP64 oracle's
+    Algorithm 1 over three batched iterations, beside a 192^2 slice (the
+    384-point grid of the mixed-radix FFT) on the same atom grid and sequence;
+    the small slice uses the oracle's scales, so both start from the same
+    point and its coefficient images must stay within the grouped form's
+    per-iteration bound."""
+    from test_gpu_recon import alpha_of, gpu_recon, oracle_recon, problem
+    m = mrf()
+    pr = problem()
+    o = oracle_recon(pr)
+    small = gpu_recon(pr, 1, extra_flags=4, a_norm=o.a, x_scale=o.gamma, match_precision=2)
+    # the large slice: a 192^2 phantom through the same sequence and atoms
+    import synth as sy
+    n = 192
+    T = pr["D"].shape[1]
+    t1, t2, pd, mask, _ = sy.phantom(n, seed=5)
+    lut = f32(pr["lut"])
+    fa, tr = sy.fisp_train(T, seed=2)
+    pairs = np.stack([np.maximum(t1.ravel(), 1.0), np.maximum(t2.ravel(), 1.0)], -1)
+    S = m.epg_fisp(f32(pairs), f32(fa), f32(tr))
+    X = (S * c64((pd * mask).ravel())[:, None]).T.contiguous().view(T, n, n)
+    plan = m.nufft_plan(n, n, f32(sy.spiral_trajectory(n, T, 768, 6).astype(np.float32)))
+    b = m.nufft_forward(plan, X)
+    big = m.Recon(plan, m.ReconParams(patch=8, stride=4, knn=4, flags=8 | 4, match_precision=2),
+                  c64(pr["phi"]), c64(pr["D"] @ pr["phi"]), f32(np.sum(np.abs(pr["D"]) ** 2, 1)), lut, b)
+    batch = m.Batch([small, big])
+    for it in range(3):
+        o.iterate()
+        batch.iterate(1)
+        assert rel(np_(small.alpha()), alpha_of(o)) < 3e-4 * (it + 1), it
+        agree = (np_(small.maps()[3]).ravel() == o.maps[0].ravel()).mean()
+        assert agree > 0.99, it
+    assert np.all(np.isfinite(np_(big.maps()[0])))

@@ -120,17 +120,21 @@ def test_tc_ragged_atoms_and_lengths(prec):
         assert _near_tie_ok(X, D, n2, gi, oi, rtol=rtol) >= 0.995, (n, mm, L)
 
 
-def test_tc_rejects_long_fingerprints():
+def test_long_fingerprint_limits():
+    """Beyond the resident tile the BF16 forms switch to the streamed matcher
+    (tests/test_gpu_match_long.py); FP8 stops at 64 entries and seeded
+    matching at the resident tile, both with MRF_EINVAL."""
     m = mrf()
-    D = c64(np.ones((4, 70)))
-    with pytest.raises(m.MRFError):
-        m.match(c64(np.ones((3, 70))), D, f32(np.ones((4, 2))), precision=BF16)
-    D = c64(np.ones((4, 30)))
-    with pytest.raises(m.MRFError):
-        m.match(c64(np.ones((3, 30))), D, f32(np.ones((4, 2))), precision=BF16X3)
     D = c64(np.ones((4, 65)))
     with pytest.raises(m.MRFError):
         m.match(c64(np.ones((3, 65))), D, f32(np.ones((4, 2))), precision=FP8)
+    D = c64(np.ones((4, 30)))
+    cand = torch.full((3, 8), -1, dtype=torch.int32, device=dev())
+    with pytest.raises(m.MRFError):
+        m.match_seeded(c64(np.ones((3, 30))), D, f32(np.ones((4, 2))), cand, precision=BF16X3)
+    # 70 and 30 entries now run on the streamed kernel
+    idx, _, _ = m.match(c64(np.ones((3, 70))), c64(np.ones((4, 70))), f32(np.ones((4, 2))), precision=BF16)
+    assert np.all(np_(idx) == 0)
 
 
 @pytest.mark.parametrize("prec", [0, BF16, BF16X3, FP8])

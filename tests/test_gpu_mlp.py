@@ -174,3 +174,55 @@ def test_learned_matcher_in_the_loop():
         assert np.all(np.isfinite(maps["learned"][i]))
     idx = maps["learned"][3]
     assert np.all((idx == -1) | ((idx >= 0) & (idx < len(lut))))
+
+
+def test_learned_matcher_gain_over_exhaustive_matching():
+    """What the trained network gains over the method without it, measured in
+    the loop at K = 10 on a 128^2 image matched against the 5441-atom grid of
+    the 256^2 workload: per iteration, the device time of the matching step
+    (features, network inference on the tensor cores, decoding and the
+    exhaustive fallback) against the seeded split-BF16 exhaustive matcher,
+    from the library's per-kernel CUDA events with the steps serialised;
+    the learned maps stay within the error of the exhaustive loop's maps
+    that the in-loop test allows."""
+    m = mrf()
+    w = synth.WORKLOADS["mrf256_t100"]
+    fa, tr = synth.fisp_train(100, seed=w.tr_seed)
+    lut = synth.workload_grid(w)
+    D = m.epg_fisp(f32(lut), f32(fa), f32(tr))
+    phi, comp, n2 = m.dict_subspace(D, 10)
+    pd_scale = float(1.0 / np.median(np.sqrt(np_(n2))))
+    ranges = (w.t1_range[0], w.t1_range[1], w.t2_range[0], w.t2_range[1], pd_scale)
+    net, _ = m.train_matcher(synth.mlp_init_params(21), synth.mlp_training_draws(300_000, 10, seed=22,
+                                                                                  t1_range=w.t1_range,
+                                                                                  t2_range=w.t2_range),
+                             f32(fa), f32(tr), phi, ranges, epochs=3, batch=1024)
+    n = 128
+    t1, t2, pd, mask, _ = synth.phantom(n, seed=0)
+    pairs = np.stack([np.maximum(t1.ravel(), 1.0), np.maximum(t2.ravel(), 1.0)], -1)
+    S = m.epg_fisp(f32(pairs), f32(fa), f32(tr))
+    X = (S * c64((pd * mask).ravel())[:, None]).T.contiguous().view(100, n, n)
+    k = f32(synth.spiral_trajectory(n, 100, 1024, 24).astype(np.float32))
+    b = m.nufft_forward(m.nufft_plan(n, n, k), X)
+    match_kernels = {"exhaustive": ("k_match_tc", "k_match_finish"),
+                     "learned": ("k_mlp_features", "k_mlp_infer_tc", "k_learned_decode", "k_fallback_gather",
+                                 "k_fallback_scatter", "k_match_tc", "k_match_finish")}
+    ms, maps = {}, {}
+    for name, flags, mlp in (("exhaustive", 8 | 32, None), ("learned", 8 | 16 | 32, net)):
+        p = m.ReconParams(patch=8, stride=4, knn=10, flags=flags, match_precision=2, mlp=mlp)
+        r = m.Recon(m.nufft_plan(n, n, k), p, phi, comp, n2, f32(lut), b)
+        r.iterate(2)
+        torch.cuda.synchronize()
+        m.profile_enable(True)
+        m.profile_mark()
+        r.iterate(5)
+        torch.cuda.synchronize()
+        prof = m.profile_read()
+        m.profile_enable(False)
+        ms[name] = sum(prof[kn][0] for kn in match_kernels[name] if kn in prof) / 5
+        maps[name] = [np_(v) for v in r.maps()]
+    assert ms["learned"] < 0.8 * ms["exhaustive"], ms
+    mk = mask.astype(bool)
+    for i in (0, 1):
+        e = np.linalg.norm((maps["learned"][i] - maps["exhaustive"][i])[mk]) / np.linalg.norm(maps["exhaustive"][i][mk])
+        assert e < 0.25, (i, e)

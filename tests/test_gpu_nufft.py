@@ -32,10 +32,16 @@ def _case(n, T, ns, interleaves, width=4, seed=0):
     (64, 9, 512, 0, 4),       # G = 128, golden-angle spiral
     (128, 4, 1024, 2, 4),     # G = 256
     (256, 3, 2048, 48, 4),    # G = 512, the 256^2 spiral arm of 2048 samples
+    (192, 4, 1536, 3, 4),     # G = 384 = 3 x 128: the mixed-radix FFT (192^2 serving slices)
+    (48, 5, 400, -1, 6),      # G = 96 = 3 x 32 is not a supported grid: checked below
 ])
 def test_forward_adjoint_match_oracle(n, T, ns, il, w):
     m = mrf()
     k, x, y, grid = _case(n, T, ns, il, w)
+    if 2 * n == 96:
+        with pytest.raises(m.MRFError):
+            m.nufft_plan(n, n, f32(k), kb_width=w)
+        return
     plan = m.nufft_plan(n, n, f32(k), kb_width=w)
     yg = np_(m.nufft_forward(plan, c64(x)))
     assert rel(yg, onufft.kb_forward(x, k, grid)) < TOL
@@ -107,3 +113,25 @@ def test_bad_arguments_raise():
         m.nufft_plan(48, 48, k)                                # grid 96 unsupported
     with pytest.raises(m.MRFError):
         m.nufft_plan(32, 32, f32(np.full((2, 4, 2), 4.0)))     # outside [-pi, pi]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_subspace_forms_on_the_384_grid(mode):
+    """Both operator forms on a 192^2 image (G = 384, mixed radix 3 x 2^7)
+    against the oracle applied to the expanded frames."""
+    m = mrf()
+    n, T, ns, K = 192, 12, 1536, 4
+    rng = np.random.default_rng(3)
+    k = synth.spiral_trajectory(n, T, ns, 4)
+    phi, _ = np.linalg.qr(rand_c(rng, T, K))
+    alpha = rand_c(rng, n, n, K)
+    y = rand_c(rng, T, ns)
+    k, phi, alpha, y = as_f32_inputs(k, phi, alpha, y)
+    grid = onufft.KBGrid(n, n, 2, 4)
+    plan = m.nufft_plan(n, n, f32(k))
+    yg = np_(m.nufft_forward_subspace(plan, c64(alpha), c64(phi), 1.0, mode=mode))
+    frames = np.einsum("yxk,tk->tyx", alpha, phi.conj())
+    assert rel(yg, onufft.kb_forward(frames, k, grid)) < TOL
+    ag = np_(m.nufft_adjoint_subspace(plan, c64(y), c64(phi), 1.0, mode=mode))
+    ao = np.einsum("tyx,tk->yxk", onufft.kb_adjoint(y, k, grid), phi)
+    assert rel(ag, ao) < TOL
