@@ -453,7 +453,7 @@ def full_length_matching(peaks, reps=3, n=65536):
 
     import synth
     import paper_2310_05647_gb300 as mrf
-    from paper_2310_05647_gb300.api import MATCH_BF16X3, MATCH_FP32
+    from paper_2310_05647_gb300.api import MATCH_BF16, MATCH_BF16X3, MATCH_FP32
 
     w = synth.WORKLOADS[WORKLOAD]
     dev = torch.device("cuda")
@@ -474,7 +474,7 @@ def full_length_matching(peaks, reps=3, n=65536):
     out = {"what": f"{n} fingerprints x {M} atoms x {T} frames (full-length Eq. 5), one mrf_match call",
            "algorithmic_flops": flops}
     res = {}
-    for name, prec, r in (("bf16x3", MATCH_BF16X3, reps), ("fp32", MATCH_FP32, 1)):
+    for name, prec, r in (("bf16x3", MATCH_BF16X3, reps), ("bf16", MATCH_BF16, reps), ("fp32", MATCH_FP32, 1)):
         res[name] = mrf.match(X, D, lut, atom_norm2=n2, precision=prec)
         torch.cuda.synchronize()
         mrf.profile_enable(True)
@@ -490,14 +490,15 @@ def full_length_matching(peaks, reps=3, n=65536):
         ms = e0.elapsed_time(e1) / r
         ent = {"ms_per_call": ms, "tflops_algorithmic": flops / ms / 1e9,
                "kernels_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items()}}
-        if name == "bf16x3" and "k_match_tc_long" in prof:
+        if name != "fp32" and "k_match_tc_long" in prof:
             kms = prof["k_match_tc_long"][0] / max(prof["k_match_tc_long"][1], 1)
             ent["roofline"] = {"kernel": "k_match_tc_long", "bound": "tensor", "achieved": flops / kms / 1e9,
                                "peak": peak, "unit": "TFLOP/s", "frac": flops / kms / 1e9 / peak,
-                               "issued_frac": 3 * flops / kms / 1e9 / peak,
+                               "issued_frac": (3 if name == "bf16x3" else 1) * flops / kms / 1e9 / peak,
                                "peak_source": "of measured (bf16 sustained)", "ms_per_launch": kms}
         out[name] = ent
-    out["index_agreement_bf16x3_vs_fp32"] = float((res["bf16x3"][0] == res["fp32"][0]).float().mean())
+    for name in ("bf16x3", "bf16"):
+        out[f"index_agreement_{name}_vs_fp32"] = float((res[name][0] == res["fp32"][0]).float().mean())
     del X, D
     return out
 

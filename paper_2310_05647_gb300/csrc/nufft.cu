@@ -60,6 +60,27 @@ __device__ __forceinline__ void unpack(const int4 r, int& j, int& mx0, int& my0,
 template <int G>
 __device__ __forceinline__ int centred(int g) { return g < G / 2 ? g : g - G; }
 
+// Block-wide global -> shared staging: element i in [0, n) is produced by
+// ld(i) (a global load, or zero) and stored by st(i, v); each thread issues
+// U loads before its U stores, so U loads per thread are in flight at once
+// instead of one load-to-store round trip per element.
+template <int U, typename Ld, typename St>
+__device__ __forceinline__ void stage_block(int n, Ld ld, St st) {
+    for (int b = threadIdx.x; b < n; b += U * (int)blockDim.x) {
+        float2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = b + u * (int)blockDim.x;
+            v[u] = i < n ? ld(i) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = b + u * (int)blockDim.x;
+            if (i < n) st(i, v[u]);
+        }
+    }
+}
+
 // v mod G in [0, G) (grids of 2^a or 3 x 2^a points)
 template <int G>
 __device__ __forceinline__ int wrapg(int v) {
@@ -87,17 +108,20 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd(const float2* __restri
     const int t = blockIdx.y;
     const int iy0 = blockIdx.x * kRowB;
     fft_twiddles<G>(tw);
-    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
-        const int r = idx / G, g = idx - r * G;
-        const int iy = iy0 + r;
-        const int ix = centred<G>(g) + nx / 2;
-        float2 v = make_float2(0.f, 0.f);
-        if (iy < ny && ix >= 0 && ix < nx) {
-            v = SRC == 0 ? x[((size_t)t * ny + iy) * nx + ix] : x[((size_t)iy * nx + ix) * K + t];
-            v = cscale(v, inv_dx[ix] * inv_dy[iy]);
-        }
-        rows[r * LD + g] = v;
-    }
+    stage_block<8>(
+        kRowB * G,
+        [&](int idx) {
+            const int r = idx / G, g = idx - r * G;
+            const int iy = iy0 + r;
+            const int ix = centred<G>(g) + nx / 2;
+            float2 v = make_float2(0.f, 0.f);
+            if (iy < ny && ix >= 0 && ix < nx) {
+                v = SRC == 0 ? x[((size_t)t * ny + iy) * nx + ix] : x[((size_t)iy * nx + ix) * K + t];
+                v = cscale(v, inv_dx[ix] * inv_dy[iy]);
+            }
+            return v;
+        },
+        [&](int idx, float2 v) { rows[(idx / G) * LD + idx % G] = v; });
     __syncthreads();
     fft_batch<G, kRowB, kRowThreads, false>(rows, 1, LD, tw);
     for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
@@ -156,13 +180,14 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd_expand(const float2* _
 // the shared tile [G][kTile]; rows outside the image's support are zero.
 template <int G>
 __device__ __forceinline__ void load_strip(float2* tile, const float2* __restrict__ h1f, int c0, int ny) {
-    for (int idx = threadIdx.x; idx < G * kTile; idx += blockDim.x) {
-        const int gy = idx / kTile, c = idx & (kTile - 1);
-        const int iy = centred<G>(gy) + ny / 2;
-        float2 v = make_float2(0.f, 0.f);
-        if (iy >= 0 && iy < ny) v = h1f[(size_t)iy * G + (wrapg<G>(c0 + c))];
-        tile[idx] = v;
-    }
+    stage_block<4>(
+        G * kTile,
+        [&](int idx) {
+            const int gy = idx / kTile, c = idx & (kTile - 1);
+            const int iy = centred<G>(gy) + ny / 2;
+            return (iy >= 0 && iy < ny) ? h1f[(size_t)iy * G + wrapg<G>(c0 + c)] : make_float2(0.f, 0.f);
+        },
+        [&](int idx, float2 v) { tile[idx] = v; });
     __syncthreads();
 }
 
@@ -172,7 +197,7 @@ __device__ __forceinline__ void load_strip(float2* tile, const float2* __restric
 // columns.  y = scale * interp - b  (b nullable).
 // ---------------------------------------------------------------------------
 template <int G, int W>
-__global__ void __launch_bounds__(kColThreads) k_cols_interp(const float2* __restrict__ h1,
+__global__ void __launch_bounds__(kColThreads, 3) k_cols_interp(const float2* __restrict__ h1,
                                                              float2* __restrict__ y,
                                                              const float2* __restrict__ bsub, float scale,
                                                              const int4* __restrict__ rec,
@@ -216,7 +241,7 @@ __global__ void __launch_bounds__(kColThreads) k_cols_interp(const float2* __res
 
 // Column FFTs of whole images, spectrum written out (grouped subspace form).
 template <int G>
-__global__ void __launch_bounds__(kColThreads) k_cols_store(const float2* __restrict__ h1,
+__global__ void __launch_bounds__(kColThreads, 3) k_cols_store(const float2* __restrict__ h1,
                                                             float2* __restrict__ spec, int ny) {
     extern __shared__ float2 sm[];
     float2* tw = sm;
@@ -240,7 +265,7 @@ __global__ void __launch_bounds__(kColThreads) k_cols_store(const float2* __rest
 // R[g][j][k] of every group (blockIdx.y = k).
 // ---------------------------------------------------------------------------
 template <int G, int W, int SRC>
-__global__ void __launch_bounds__(kColThreads) k_spread_cols(const float2* __restrict__ y, int K,
+__global__ void __launch_bounds__(kColThreads, 3) k_spread_cols(const float2* __restrict__ y, int K,
                                                              float2* __restrict__ h1,
                                                              const int4* __restrict__ rec,
                                                              const int* __restrict__ off,
@@ -385,7 +410,7 @@ __global__ void __launch_bounds__(512) k_gather_warp(const float2* __restrict__ 
 
 // Inverse FFT of a strip's columns of grid image f, image rows kept.
 template <int G>
-__global__ void __launch_bounds__(kColThreads) k_cols_inv(const float2* __restrict__ grid,
+__global__ void __launch_bounds__(kColThreads, 3) k_cols_inv(const float2* __restrict__ grid,
                                                           float2* __restrict__ h1, int ny) {
     extern __shared__ float2 sm[];
     float2* tw = sm;
@@ -394,10 +419,9 @@ __global__ void __launch_bounds__(kColThreads) k_cols_inv(const float2* __restri
     const int c0 = strip * kTile;
     fft_twiddles<G>(tw);
     const float2* src = grid + (size_t)f * G * G;
-    for (int idx = threadIdx.x; idx < G * kTile; idx += kColThreads) {
-        const int gy = idx / kTile, c = idx & (kTile - 1);
-        tile[idx] = src[(size_t)gy * G + c0 + c];
-    }
+    stage_block<4>(
+        G * kTile, [&](int idx) { return src[(size_t)(idx / kTile) * G + c0 + (idx & (kTile - 1))]; },
+        [&](int idx, float2 v) { tile[idx] = v; });
     __syncthreads();
     fft_batch<G, kTile, kColThreads, true>(tile, kTile, 1, tw);
     float2* dst = h1 + (size_t)f * ny * G;
@@ -423,11 +447,13 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_adj(const float2* __restri
     const int t = blockIdx.y;
     const int iy0 = blockIdx.x * kRowB;
     fft_twiddles<G>(tw);
-    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
-        const int r = idx / G, g = idx - r * G;
-        const int iy = iy0 + r;
-        rows[r * LD + g] = iy < ny ? h1[((size_t)t * ny + iy) * G + g] : make_float2(0.f, 0.f);
-    }
+    stage_block<8>(
+        kRowB * G,
+        [&](int idx) {
+            const int iy = iy0 + idx / G;
+            return iy < ny ? h1[((size_t)t * ny + iy) * G + idx % G] : make_float2(0.f, 0.f);
+        },
+        [&](int idx, float2 v) { rows[(idx / G) * LD + idx % G] = v; });
     __syncthreads();
     fft_batch<G, kRowB, kRowThreads, true>(rows, 1, LD, tw);
     for (int idx = threadIdx.x; idx < kRowB * nx; idx += kRowThreads) {
@@ -466,10 +492,13 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_rows_adj_reduce(const float2
     for (int q = 0; q < MAXQ; ++q) acc[q] = make_float2(0.f, 0.f);
     const float sy = inv_dy[iy];
     for (int t0 = tb; t0 < te; t0 += kRowB) {
-        for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
-            const int r = idx / G, g = idx - r * G;
-            rows[r * LD + g] = t0 + r < te ? h1[((size_t)(t0 + r) * ny + iy) * G + g] : make_float2(0.f, 0.f);
-        }
+        stage_block<8>(
+            kRowB * G,
+            [&](int idx) {
+                const int r = idx / G;
+                return t0 + r < te ? h1[((size_t)(t0 + r) * ny + iy) * G + idx % G] : make_float2(0.f, 0.f);
+            },
+            [&](int idx, float2 v) { rows[(idx / G) * LD + idx % G] = v; });
         for (int i = threadIdx.x; i < kRowB * K; i += kRowThreads) {
             const int tt = t0 + i / K;
             ph[i] = tt < te ? phi[(size_t)tt * K + (i % K)] : make_float2(0.f, 0.f);
