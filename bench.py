@@ -571,7 +571,7 @@ def serving(seed=0, slices=16, iters=10, rounds=10):
         t0 = time.perf_counter()
         batch.iterate(iters)              # synchronises
         lat.append(time.perf_counter() - t0)
-    tuning = [r.plan.gather_tuning() for r in recons]
+    tuning = [r.plan.tuning() for r in recons]
     maps_ok = all(bool(torch.isfinite(r.maps()[0]).all()) for r in recons)
     del batch
     tot = sum(lat)
@@ -584,7 +584,7 @@ def serving(seed=0, slices=16, iters=10, rounds=10):
                            "rounds": rounds},
             "unbatched_slice_iters_per_s": slices * iters / seq_s,
             "kernels_per_batched_iteration": per_iter_kernels,
-            "gather_tuning_run_threads": tuning, "maps_finite": maps_ok}
+            "autotuned": [dict(n=c["n"], **t) for c, t in zip(cfg, tuning)], "maps_finite": maps_ok}
 
 
 def e2e_chosen(inp, iters, reps=2):

@@ -77,6 +77,13 @@ mrf_status mrf_nufft_destroy(mrf_plan plan);
  * kernel (entries reduced per thread, threads per block), timed on this
  * plan's own table on its first grouped adjoint; 0, 0 before that call. */
 mrf_status mrf_nufft_gather_tuning(mrf_plan plan, int* run, int* threads);
+/* Everything the plan's autotuners chose for the grouped operator (0 until
+ * the first grouped transform ran): the adjoint gather's entries per thread
+ * and block size (as mrf_nufft_gather_tuning) and the strip width (16, 32
+ * or 64 columns, 64 only where its shared tile fits) of the column FFTs of
+ * the K coefficient spectra, picked by timing each candidate on the plan's
+ * grid.  Each output nullable. */
+mrf_status mrf_nufft_tuning(mrf_plan plan, int* gather_run, int* gather_threads, int* strip_width);
 
 /* y = A x over all frames.  x: dev [nframes][ny][nx] mrf_c64;
  * y: dev [nframes][ns] mrf_c64 (overwritten). */

@@ -68,6 +68,13 @@ class NufftPlan:
         _lib.call("mrf_nufft_gather_tuning", self.handle, C.byref(run), C.byref(thr))
         return run.value, thr.value
 
+    def tuning(self):
+        """The grouped operator's tuned choices: {"gather_run", "gather_threads",
+        "strip_width"} (0 before the first grouped transform)."""
+        v = [C.c_int(0) for _ in range(3)]
+        _lib.call("mrf_nufft_tuning", self.handle, *[C.byref(x) for x in v])
+        return dict(zip(("gather_run", "gather_threads", "strip_width"), (x.value for x in v)))
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:

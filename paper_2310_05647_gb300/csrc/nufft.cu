@@ -176,14 +176,14 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd_expand(const float2* _
     }
 }
 
-// Load a strip (kTile columns starting at c0, wrapping) of one image's H1 into
-// the shared tile [G][kTile]; rows outside the image's support are zero.
-template <int G>
+// Load a strip (TILE columns starting at c0, wrapping) of one image's H1 into
+// the shared tile [G][TILE]; rows outside the image's support are zero.
+template <int G, int TILE = kTile>
 __device__ __forceinline__ void load_strip(float2* tile, const float2* __restrict__ h1f, int c0, int ny) {
     stage_block<4>(
-        G * kTile,
+        G * TILE,
         [&](int idx) {
-            const int gy = idx / kTile, c = idx & (kTile - 1);
+            const int gy = idx / TILE, c = idx & (TILE - 1);
             const int iy = centred<G>(gy) + ny / 2;
             return (iy >= 0 && iy < ny) ? h1f[(size_t)iy * G + wrapg<G>(c0 + c)] : make_float2(0.f, 0.f);
         },
@@ -240,20 +240,23 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols_interp(const float2* __
 }
 
 // Column FFTs of whole images, spectrum written out (grouped subspace form).
-template <int G>
-__global__ void __launch_bounds__(kColThreads, 3) k_cols_store(const float2* __restrict__ h1,
-                                                            float2* __restrict__ spec, int ny) {
+// Strips of TILE columns (16 workers per column: TILE * 16 threads); the
+// width is chosen per plan by tune_cols.
+template <int G, int TILE>
+__global__ void __launch_bounds__(TILE * 16) k_cols_store(const float2* __restrict__ h1,
+                                                         float2* __restrict__ spec, int ny) {
+    constexpr int NT = TILE * 16;
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* tile = sm + G;
     const int strip = blockIdx.x, f = blockIdx.y;
-    const int c0 = strip * kTile;
+    const int c0 = strip * TILE;
     fft_twiddles<G>(tw);
-    load_strip<G>(tile, h1 + (size_t)f * ny * G, c0, ny);
-    fft_batch<G, kTile, kColThreads, false>(tile, kTile, 1, tw);
+    load_strip<G, TILE>(tile, h1 + (size_t)f * ny * G, c0, ny);
+    fft_batch<G, TILE, NT, false>(tile, TILE, 1, tw);
     float2* dst = spec + (size_t)f * G * G;
-    for (int idx = threadIdx.x; idx < G * kTile; idx += kColThreads) {
-        const int gy = idx / kTile, c = idx & (kTile - 1);
+    for (int idx = threadIdx.x; idx < G * TILE; idx += NT) {
+        const int gy = idx / TILE, c = idx & (TILE - 1);
         dst[(size_t)gy * G + c0 + c] = tile[idx];
     }
 }
@@ -408,27 +411,29 @@ __global__ void __launch_bounds__(512) k_gather_warp(const float2* __restrict__ 
     }
 }
 
-// Inverse FFT of a strip's columns of grid image f, image rows kept.
-template <int G>
-__global__ void __launch_bounds__(kColThreads, 3) k_cols_inv(const float2* __restrict__ grid,
-                                                          float2* __restrict__ h1, int ny) {
+// Inverse FFT of a strip's columns of grid image f, image rows kept (strips
+// of TILE columns, TILE * 16 threads, as k_cols_store).
+template <int G, int TILE>
+__global__ void __launch_bounds__(TILE * 16) k_cols_inv(const float2* __restrict__ grid,
+                                                       float2* __restrict__ h1, int ny) {
+    constexpr int NT = TILE * 16;
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* tile = sm + G;
     const int strip = blockIdx.x, f = blockIdx.y;
-    const int c0 = strip * kTile;
+    const int c0 = strip * TILE;
     fft_twiddles<G>(tw);
     const float2* src = grid + (size_t)f * G * G;
     stage_block<4>(
-        G * kTile, [&](int idx) { return src[(size_t)(idx / kTile) * G + c0 + (idx & (kTile - 1))]; },
+        G * TILE, [&](int idx) { return src[(size_t)(idx / TILE) * G + c0 + (idx & (TILE - 1))]; },
         [&](int idx, float2 v) { tile[idx] = v; });
     __syncthreads();
-    fft_batch<G, kTile, kColThreads, true>(tile, kTile, 1, tw);
+    fft_batch<G, TILE, NT, true>(tile, TILE, 1, tw);
     float2* dst = h1 + (size_t)f * ny * G;
-    for (int idx = threadIdx.x; idx < ny * kTile; idx += kColThreads) {
-        const int iy = idx / kTile, c = idx & (kTile - 1);
+    for (int idx = threadIdx.x; idx < ny * TILE; idx += NT) {
+        const int iy = idx / TILE, c = idx & (TILE - 1);
         const int gy = wrapg<G>(iy - ny / 2);
-        dst[(size_t)iy * G + c0 + c] = tile[gy * kTile + c];
+        dst[(size_t)iy * G + c0 + c] = tile[gy * TILE + c];
     }
 }
 
@@ -836,6 +841,79 @@ static mrf_status launch_gather(const mrf_plan_s* p, int run, int threads, int K
 // Runs once per plan and K, on the first grouped adjoint (which already
 // synchronises to build the table); the candidates add into sub_spec, which
 // the caller clears afterwards.
+// Grouped column FFTs with a strip width chosen per plan: the K coefficient
+// spectra are transformed column strip by column strip; wider strips mean
+// fewer, larger blocks (more threads per block, fewer blocks per SM).
+static size_t col_smem(int G, int tile) { return (size_t)(G + G * tile) * sizeof(float2); }
+constexpr size_t kMaxDynSmem = 227 * 1024;
+
+template <int GG, int TT>
+static mrf_status cols_pass(mrf_plan_s* p, int K, bool inverse, cudaStream_t s) {
+    const size_t sm = col_smem(GG, TT);
+    const dim3 grid((unsigned)(p->gx / TT), (unsigned)K);
+    if (inverse) {
+        MRF_PROPAGATE(set_smem(k_cols_inv<GG, TT>, sm));
+        k_cols_inv<GG, TT><<<grid, TT * 16, sm, s>>>(p->sub_spec, p->sub_h1, p->ny);
+        MRF_LAUNCHED_AS("k_cols_inv", s);
+    } else {
+        MRF_PROPAGATE(set_smem(k_cols_store<GG, TT>, sm));
+        k_cols_store<GG, TT><<<grid, TT * 16, sm, s>>>(p->sub_h1, p->sub_spec, p->ny);
+        MRF_LAUNCHED_AS("k_cols_store", s);
+    }
+    return MRF_OK;
+}
+
+static mrf_status launch_cols(mrf_plan_s* p, int K, int tile, bool inverse, cudaStream_t s) {
+    MRF_REQUIRE(col_smem(p->gy, tile) <= kMaxDynSmem, "strip width %d does not fit grid %d", tile, p->gy);
+    MRF_DISPATCH_G(p->gy, {
+        if (tile == 16) return cols_pass<GG, 16>(p, K, inverse, s);
+        if (tile == 32) return cols_pass<GG, 32>(p, K, inverse, s);
+        if constexpr (GG <= 384) return cols_pass<GG, 64>(p, K, inverse, s);
+    });
+    set_error("unsupported strip width %d", tile);
+    return MRF_EINVAL;
+}
+
+// Strip width of the grouped column FFTs for this plan: each candidate's
+// forward and inverse passes timed over three repetitions (after a warm-up)
+// on the plan's own buffers, before the operator writes them.
+static mrf_status tune_cols(mrf_plan_s* p, int K, cudaStream_t s) {
+    if (p->col_tuned_K == K) return MRF_OK;
+    static const int tiles[] = {16, 32, 64};
+    cudaEvent_t e0, e1;
+    MRF_CUDA(cudaEventCreate(&e0));
+    MRF_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bt = 16;
+    mrf_status st = MRF_OK;
+    for (int t : tiles) {
+        if (col_smem(p->gy, t) > kMaxDynSmem) continue;
+        st = launch_cols(p, K, t, false, s);
+        if (st == MRF_OK) st = launch_cols(p, K, t, true, s);
+        if (st == MRF_OK && cudaEventRecord(e0, s) != cudaSuccess) st = MRF_ECUDA;
+        for (int rep = 0; st == MRF_OK && rep < 3; ++rep) {
+            st = launch_cols(p, K, t, false, s);
+            if (st == MRF_OK) st = launch_cols(p, K, t, true, s);
+        }
+        float ms = 0.f;
+        if (st != MRF_OK || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            if (st == MRF_OK) {
+                set_error("strip-width autotuner: timing failed");
+                st = MRF_ECUDA;
+            }
+            break;
+        }
+        if (ms < best) { best = ms; bt = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MRF_OK) return st;
+    p->col_tile = bt;
+    p->col_tuned_K = K;
+    return MRF_OK;
+}
+
 static mrf_status tune_gather(mrf_plan_s* p, int K, cudaStream_t s) {
     if (p->gat_tuned_K == K) return MRF_OK;
     static const int runs[] = {0, 8, 16, 32, 64};
@@ -1044,6 +1122,14 @@ fail:
     return e == cudaErrorMemoryAllocation ? MRF_ENOMEM : MRF_ECUDA;
 }
 
+extern "C" mrf_status mrf_nufft_tuning(mrf_plan p, int* gather_run, int* gather_threads, int* strip_width) {
+    MRF_REQUIRE(p != nullptr, "mrf_nufft_tuning: NULL plan");
+    if (gather_run) *gather_run = p->gat_tuned_K ? p->gat_run : 0;
+    if (gather_threads) *gather_threads = p->gat_tuned_K ? p->gat_threads : 0;
+    if (strip_width) *strip_width = p->col_tuned_K ? p->col_tile : 0;
+    return MRF_OK;
+}
+
 extern "C" mrf_status mrf_nufft_gather_tuning(mrf_plan p, int* run, int* threads) {
     MRF_REQUIRE(p && run && threads, "mrf_nufft_gather_tuning: NULL argument");
     *run = p->gat_tuned_K ? p->gat_run : 0;
@@ -1091,17 +1177,9 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
         return launch_cols_interp(p, p->h1, y, b, scale, s);
     }
     MRF_PROPAGATE(ensure_subspace_workspace(p, K));
+    MRF_PROPAGATE(tune_cols(p, K, s));                 // before the buffers hold this call's data
     MRF_PROPAGATE(launch_rows_fwd(p, alpha, 1, K, K, p->sub_h1, s));
-    {
-        const int G = p->gy;
-        dim3 grid(p->nstrips_a, K);
-        const size_t sm = tile_smem(G);
-        MRF_DISPATCH_G(G, {
-            MRF_PROPAGATE(set_smem(k_cols_store<GG>, sm));
-            k_cols_store<GG><<<grid, kColThreads, sm, s>>>(p->sub_h1, p->sub_spec, p->ny);
-        });
-        MRF_LAUNCHED_AS("k_cols_store", s);
-    }
+    MRF_PROPAGATE(launch_cols(p, K, p->col_tile, false, s));
     {
         const int total = p->ngroups * p->ns;
         MRF_DISPATCH_G(p->gx, MRF_DISPATCH_W(p->W, {
@@ -1141,6 +1219,7 @@ mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, i
         MRF_LAUNCHED_AS("k_sum_parts", s);
         return MRF_OK;
     }
+    MRF_PROPAGATE(tune_cols(p, K, s));                 // before the buffers hold this call's data
     {
         const size_t n = (size_t)p->ngroups * p->ns;
         k_combine_adj<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(y, phi, K, p->gf_off, p->gf, p->ngroups, p->ns,
@@ -1153,13 +1232,7 @@ mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, i
         const int G = p->gy;
         MRF_CUDA(cudaMemsetAsync(p->sub_spec, 0, sizeof(float2) * (size_t)K * G * G, s));
         MRF_PROPAGATE(launch_gather(p, p->gat_run, p->gat_threads, K, s));
-        dim3 grid(p->nstrips_a, K);
-        const size_t sm = tile_smem(G);
-        MRF_DISPATCH_G(G, {
-            MRF_PROPAGATE(set_smem(k_cols_inv<GG>, sm));
-            k_cols_inv<GG><<<grid, kColThreads, sm, s>>>(p->sub_spec, p->sub_h1, p->ny);
-        });
-        MRF_LAUNCHED_AS("k_cols_inv", s);
+        MRF_PROPAGATE(launch_cols(p, K, p->col_tile, true, s));
     }
     MRF_PROPAGATE(launch_rows_adj(p, p->sub_h1, alpha_out, 1, K, K, scale, s));
     return MRF_OK;

@@ -30,6 +30,8 @@ struct mrf_plan_s {
     int gat_run = 32;             // tuned entries per thread of k_gather_grid
     int gat_threads = 128;        // tuned block size of k_gather_grid
     int gat_tuned_K = 0;          // K the tuning was done for (0: not tuned)
+    int col_tile = 16;            // tuned strip width of the grouped column FFTs (16, 32 or 64)
+    int col_tuned_K = 0;          // K the strip width was tuned for (0: not tuned)
     int* gf_off = nullptr;        // [ngroups + 1] frames of each group (CSR)
     int* gf = nullptr;            // [T]
     float2* h1 = nullptr;         // [T][ny][gx] rows transformed along x

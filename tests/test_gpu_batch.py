@@ -127,12 +127,17 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     assert idx.shape == (300,) and idx.min() >= 0 and idx.max() < 40
 
 
-def test_gather_autotuner_choice_and_result():
+@pytest.mark.parametrize("n", [64, 192, 256])
+def test_gather_autotuner_choice_and_result(n):
+    """The grouped operator's autotuners (adjoint gather: entries per thread
+    and block size; column FFTs: strip width) pick from their candidates on
+    each grid, and the grouped adjoint and forward with the tuned choices give
+    the frame form's result."""
     m = mrf()
-    n = 64
     k = synth.spiral_trajectory(n, T, NS, IL).astype(np.float32)
     plan = m.nufft_plan(n, n, f32(k))
     assert plan.gather_tuning() == (0, 0)
+    assert plan.tuning()["strip_width"] == 0
     rng = np.random.default_rng(1)
     phi, _ = np.linalg.qr(rand_c(rng, T, K))
     phi_d = c64(phi)
@@ -140,8 +145,15 @@ def test_gather_autotuner_choice_and_result():
     a_grouped = m.nufft_adjoint_subspace(plan, y, phi_d, 1.0, mode=1)
     run, thr = plan.gather_tuning()
     assert run in (0, 8, 16, 32, 64) and thr in (128, 256, 512)
+    tune = plan.tuning()
+    assert (tune["gather_run"], tune["gather_threads"]) == (run, thr)
+    assert tune["strip_width"] in ((16, 32, 64) if 2 * n <= 384 else (16, 32))
     a_frames = m.nufft_adjoint_subspace(plan, y, phi_d, 1.0, mode=0)
     assert rel(np_(a_grouped), np_(a_frames)) < 1e-4
+    alpha = c64(rand_c(rng, n, n, K))
+    y1 = m.nufft_forward_subspace(plan, alpha, phi_d, 1.0, mode=1)
+    y0 = m.nufft_forward_subspace(plan, alpha, phi_d, 1.0, mode=0)
+    assert rel(np_(y1), np_(y0)) < 1e-4
 
 
 def test_batched_slice_follows_oracle():
