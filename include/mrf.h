@@ -283,9 +283,12 @@ mrf_status mrf_mlp_train_step(mrf_mlp net, const float* x, const float* t, int B
                               mrf_stream stream);
 /* y: dev [n][3] network outputs for x: dev [n][20]. */
 mrf_status mrf_mlp_infer(mrf_mlp net, const float* x, int n, float* y, mrf_stream stream);
-/* Inference engine: tensor_cores = 1 (default) runs tcgen05 BF16 products
- * with every layer's input rounded to BF16; 0 runs the SIMT kernel with FP32
- * activations. */
+/* Engine: tensor_cores = 1 (default) runs inference as tcgen05 BF16 products
+ * with every layer's input rounded to BF16, and the training products
+ * (mrf_mlp_grad, mrf_mlp_train_step) as tcgen05 split-BF16 products (hi and
+ * lo parts of the FP32 operands, FP32 accumulation: FP32-accurate to ~2^-16);
+ * 0 runs SIMT kernels with FP32 activations for both.  A device wait of the
+ * tensor-core kernels that gives up is reported by mrf_mlp_check. */
 mrf_status mrf_mlp_set_engine(mrf_mlp net, int tensor_cores);
 /* MRF_ETIMEOUT if a bounded device wait of the tensor-core inference gave up
  * (synchronises `stream`). */

@@ -4,12 +4,13 @@
 // per unit input norm, standing in for dictionary matching (Eq. 5) in the
 // loop; the paper's related work (Section I) cites this replacement.
 //
-// Everything is hand-written SIMT code: training-set synthesis from EPG
-// signals, forward and backward passes (a strided tiled GEMM for the three
-// products of every layer, plus bias/GELU, loss, GELU-derivative and bias-sum
-// kernels), Adam, and a fused inference kernel.  Weights are used in BF16
-// (a copy of the FP32 master weights refreshed by every Adam step), biases
-// and all activations and accumulations are FP32.
+// Everything is hand-written: training-set synthesis from EPG signals,
+// forward and backward passes (the three products of every layer on the
+// tensor cores -- split BF16 operands, FP32 accumulation, gemm_tc.cuh -- or a
+// strided SIMT GEMM, plus bias/GELU, loss, GELU-derivative and bias-sum
+// kernels), Adam, and inference (tcgen05, or a fused SIMT kernel).  Weights
+// are used in BF16 (a copy of the FP32 master weights refreshed by every Adam
+// step), biases and all activations and accumulations are FP32.
 //
 // Parameter layout (packed, host and device): per layer W [out][in]
 // row-major, then b [out].  Loss 1 / (2B) sum (y - t)^2.
@@ -20,6 +21,7 @@
 #include <vector>
 
 #include "common.h"
+#include "gemm_tc.cuh"
 #include "mlp.h"
 #include "tc5.cuh"
 
@@ -100,9 +102,28 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const TA* __r
         }
 }
 
+template <typename TA, typename TB, int NT>
+static mrf_status gemm_tc_launch(int M, int N, int K, const TA* A, int sam, int sak, const TB* B, int sbk, int sbn,
+                                 float* C, int ldc, bool accumulate, int* err, cudaStream_t s) {
+    constexpr bool split_b = !std::is_same<TB, __nv_bfloat16>::value;
+    const size_t sm = (size_t)2 * kGtM * kGtK * 2 + (size_t)(split_b ? 2 : 1) * NT * kGtK * 2;
+    MRF_CUDA(cudaFuncSetAttribute(k_gemm_tc<TA, TB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const dim3 grid((unsigned)((N + NT - 1) / NT), (unsigned)((M + kGtM - 1) / kGtM));
+    k_gemm_tc<TA, TB, NT><<<grid, 128, sm, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, accumulate ? 1 : 0, err);
+    MRF_LAUNCHED_AS("k_mlp_gemm_tc", s);
+    return MRF_OK;
+}
+
+// tc: the tensor-core kernel (split BF16, FP32-accurate products; a device
+// wait that gives up raises *err), else the SIMT kernel
 template <typename TA, typename TB>
 static mrf_status gemm(int M, int N, int K, const TA* A, int sam, int sak, const TB* B, int sbk, int sbn, float* C,
-                       int ldc, bool accumulate, cudaStream_t s) {
+                       int ldc, bool accumulate, cudaStream_t s, bool tc = false, int* err = nullptr) {
+    if (tc) {
+        if (N <= 16) return gemm_tc_launch<TA, TB, 16>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, accumulate, err, s);
+        if (N <= 32) return gemm_tc_launch<TA, TB, 32>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, accumulate, err, s);
+        return gemm_tc_launch<TA, TB, 128>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, accumulate, err, s);
+    }
     dim3 grid((N + 63) / 64, (M + 63) / 64);
     k_gemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, accumulate ? 1 : 0);
     MRF_LAUNCHED_AS("k_mlp_gemm", s);
@@ -526,7 +547,7 @@ struct mrf_mlp_s {
     long long step = 0;
     bool wt_fresh = false;
     unsigned char* wtc = nullptr;   // tensor-core weight operands, layer by layer
-    bool tensor_cores = true;       // inference on tcgen05 (false: the SIMT kernel)
+    bool tensor_cores = true;       // inference and training products on tcgen05 (false: SIMT kernels)
     int* err = nullptr;             // set when a bounded device wait gave up
     float decode[5] = {};
 };
@@ -610,7 +631,8 @@ static mrf_status forward_backward(mrf_mlp_s* N, const float* x, const float* t,
     for (int l = 0; l < kLayers; ++l) {
         const int in = kSizes[l], out = kSizes[l + 1];
         // Z = H W^T: B(k, n) = W[n][k]
-        MRF_PROPAGATE(gemm(B, out, in, h, in, 1, N->wb + N->L.w[l], 1, in, N->z[l], out, false, s));
+        MRF_PROPAGATE(gemm(B, out, in, h, in, 1, N->wb + N->L.w[l], 1, in, N->z[l], out, false, s, N->tensor_cores,
+                           N->err));
         k_bias_act<<<nblk((size_t)B * out), 256, 0, s>>>(N->z[l], N->w + N->L.b[l], B, out, l < kLayers - 1,
                                                           N->a[l]);
         MRF_LAUNCHED_AS("k_mlp_bias_act", s);
@@ -623,13 +645,15 @@ static mrf_status forward_backward(mrf_mlp_s* N, const float* x, const float* t,
         const int in = kSizes[l], out = kSizes[l + 1];
         const float* hin = l > 0 ? N->a[l - 1] : x;
         // dW = dZ^T H: A(m, k) = dZ[k][m], B(k, n) = H[k][n]
-        MRF_PROPAGATE(gemm(out, in, B, dz, 1, out, hin, in, 1, N->g + N->L.w[l], in, false, s));
+        MRF_PROPAGATE(gemm(out, in, B, dz, 1, out, hin, in, 1, N->g + N->L.w[l], in, false, s, N->tensor_cores,
+                           N->err));
         k_bias_grad<<<(out + 255) / 256, 256, 0, s>>>(dz, B, out, N->g + N->L.b[l]);
         MRF_LAUNCHED_AS("k_mlp_bias_grad", s);
         if (l > 0) {
             float* dh = dz == N->d0 ? N->d1 : N->d0;
             // dH = dZ W: B(k, n) = W[k][n]
-            MRF_PROPAGATE(gemm(B, in, out, dz, out, 1, N->wb + N->L.w[l], in, 1, dh, in, false, s));
+            MRF_PROPAGATE(gemm(B, in, out, dz, out, 1, N->wb + N->L.w[l], in, 1, dh, in, false, s, N->tensor_cores,
+                               N->err));
             k_gelu_bwd<<<nblk((size_t)B * in), 256, 0, s>>>(dh, N->z[l - 1], (size_t)B * in, dh);
             MRF_LAUNCHED_AS("k_mlp_gelu_bwd", s);
             dz = dh;

@@ -93,6 +93,30 @@ def test_training_set_matches_oracle():
     assert rel(np_(y), yo) < 1e-5
 
 
+def test_tensor_core_and_simt_training_products_agree():
+    """The training products run on tcgen05 (split BF16, FP32 accumulation)
+    by default; the SIMT engine computes the same gradient to the split
+    form's ~2^-16, on a batch whose 1000 rows are not a multiple of the
+    128-row tile, and both match the oracle's backward pass."""
+    net = _net(3, batch=1000)
+    rng = np.random.default_rng(4)
+    B = 1000
+    x = rng.standard_normal((B, 20)).astype(np.float32)
+    t = rng.standard_normal((B, 3)).astype(np.float32)
+    g_tc, l_tc = net.grad(f32(x), f32(t))
+    g_tc = np_(g_tc).astype(np.float64)
+    net.check()
+    net.set_engine(tensor_cores=False)
+    g_si, l_si = net.grad(f32(x), f32(t))
+    g_si = np_(g_si).astype(np.float64)
+    net.set_engine(tensor_cores=True)
+    assert rel(g_tc, g_si) < 2e-5
+    assert float(np_(l_tc)[0]) == pytest.approx(float(np_(l_si)[0]), rel=1e-5)
+    theta = _used_params(net)
+    y, cache = omlp.forward(theta, x.astype(np.float64))
+    assert rel(g_tc, omlp.backward(theta, cache, y, t.astype(np.float64))) < 1e-4
+
+
 def test_inference_matches_oracle_forward():
     """SIMT engine: FP32 activations.  Tensor-core engine: each layer's input
     rounded to BF16 (the oracle rounds the same way, from its FP64 values, so
