@@ -156,17 +156,27 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd_expand(const float2* _
     }
     __syncthreads();
     const float sy = inv_dy[iy];
-    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
-        const int r = idx / G, g = idx - r * G;
+    // a thread per grid column: the pixel's K coefficients in registers, the
+    // 16 frames' basis rows read as shared-memory broadcasts
+    for (int g = threadIdx.x; g < G; g += kRowThreads) {
         const int ix = centred<G>(g) + nx / 2;
-        float2 v = make_float2(0.f, 0.f);
-        if (ix >= 0 && ix < nx && t0 + r < T) {
-            const float2* a = arow + ix * K;
-            const float2* p = ph + r * K;
-            for (int k = 0; k < K; ++k) v = cadd(v, cmulc(a[k], p[k]));
-            v = cscale(v, inv_dx[ix] * sy);
+        if (ix < 0 || ix >= nx) {
+#pragma unroll
+            for (int r = 0; r < kRowB; ++r) rows[r * LD + g] = make_float2(0.f, 0.f);
+            continue;
         }
-        rows[r * LD + g] = v;
+        float2 a[16];                                   // K <= 16 (unrolled: stays in registers)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[k] = k < K ? arow[ix * K + k] : make_float2(0.f, 0.f);
+        const float sc = inv_dx[ix] * sy;
+#pragma unroll 4
+        for (int r = 0; r < kRowB; ++r) {
+            float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < K) v = cadd(v, cmulc(a[k], ph[r * K + k]));
+            rows[r * LD + g] = t0 + r < T ? cscale(v, sc) : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     fft_batch<G, kRowB, kRowThreads, false>(rows, 1, LD, tw);
@@ -483,7 +493,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_rows_adj_reduce(const float2
                                                                  const float* __restrict__ inv_dy, int nx,
                                                                  int ny) {
     constexpr int LD = G + 1;
-    constexpr int MAXQ = 16;               // (nx * K) / kRowThreads <= 16 (nx <= 256, K <= 16)
+    constexpr int MAXK = 16;               // a thread per image column ix (nx <= 256), all K <= 16 coefficients
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* rows = sm + G;                 // [kRowB][G + 1]
@@ -492,9 +502,11 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_rows_adj_reduce(const float2
     const int tb = part * frames_per_part;
     const int te = min(T, tb + frames_per_part);
     fft_twiddles<G>(tw);
-    float2 acc[MAXQ];
+    float2 acc[MAXK];
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < MAXK; ++q) acc[q] = make_float2(0.f, 0.f);
+    const int ix = threadIdx.x;
+    const int gx = wrapg<G>(ix - nx / 2);
     const float sy = inv_dy[iy];
     for (int t0 = tb; t0 < te; t0 += kRowB) {
         stage_block<8>(
@@ -511,23 +523,23 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_rows_adj_reduce(const float2
         __syncthreads();
         fft_batch<G, kRowB, kRowThreads, true>(rows, 1, LD, tw);
         const int nf = min(kRowB, te - t0);
+        if (ix < nx) {
+            // one load of the pixel's value per frame serves all K products;
+            // the frame's basis row is a shared-memory broadcast
+            for (int f = 0; f < nf; ++f) {
+                const float2 rv = rows[f * LD + gx];
 #pragma unroll
-        for (int q = 0; q < MAXQ; ++q) {
-            const int pidx = threadIdx.x + q * kRowThreads;
-            if (pidx < nx * K) {
-                const int ix = pidx / K, k = pidx - ix * K;
-                const int gx = wrapg<G>(ix - nx / 2);
-                float2 s = make_float2(0.f, 0.f);
-                for (int f = 0; f < nf; ++f) s = cadd(s, cmul(rows[f * LD + gx], ph[f * K + k]));
-                acc[q] = cadd(acc[q], cscale(s, inv_dx[ix] * sy));
+                for (int k = 0; k < MAXK; ++k)
+                    if (k < K) acc[k] = cadd(acc[k], cmul(rv, ph[f * K + k]));
             }
         }
         __syncthreads();
     }
+    if (ix < nx) {
+        const float sc = inv_dx[ix] * sy;
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-        const int pidx = threadIdx.x + q * kRowThreads;
-        if (pidx < nx * K) partial[((size_t)part * ny + iy) * nx * K + pidx] = acc[q];
+        for (int k = 0; k < MAXK; ++k)
+            if (k < K) partial[(((size_t)part * ny + iy) * nx + ix) * K + k] = cscale(acc[k], sc);
     }
 }
 
