@@ -17,6 +17,7 @@
 // and the singular values of Q_i(X) (p^2 x T) equal those of Q_i(alpha)
 // (p^2 x K) because Phi has orthonormal columns.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <cmath>
 #include <vector>
@@ -386,58 +387,60 @@ __global__ void k_fill_reverse(const int* __restrict__ nbr, const float* __restr
 }
 
 // Order each reverse list by source index (a fixed summation order) and
-// compute the degrees of W = (K + K^T)/2.  One block per target patch: the
+// compute the degrees of W = (K + K^T)/2.  One warp per target patch: the
 // sources of a list are distinct, so each one's rank is the number of set
-// bits below it in a bitmap of the list (prefix popcounts), which sorts the
-// list in O(np / 32 + length) per target regardless of hub sizes.
-__global__ void __launch_bounds__(256) k_degree(const float* __restrict__ w, int np, int knn,
-                                                const int* __restrict__ roff, const int* __restrict__ rsrc_in,
-                                                const float* __restrict__ rw_in, int* __restrict__ rsrc,
-                                                float* __restrict__ rw, float* __restrict__ deg,
-                                                unsigned* __restrict__ deg_max) {
-    extern __shared__ unsigned bits[];              // [nw] bitmap, then [nw] prefix counts
+// bits below it in the warp's bitmap of the list (prefix popcounts over the
+// np / 32 words, a lane per contiguous chunk), which sorts the list in
+// O(np / 32 + length) whatever the hub sizes; the degree sums the sorted
+// reverse weights and the forward weights in a fixed order.
+constexpr int kDegWarps = 8;
+__global__ void __launch_bounds__(kDegWarps * 32) k_degree(const float* __restrict__ w, int np, int knn,
+                                                           const int* __restrict__ roff,
+                                                           const int* __restrict__ rsrc_in,
+                                                           const float* __restrict__ rw_in, int* __restrict__ rsrc,
+                                                           float* __restrict__ rw, float* __restrict__ deg,
+                                                           unsigned* __restrict__ deg_max) {
+    extern __shared__ unsigned smd[];                     // per warp: [nw] bitmap, then [nw] prefix counts
     const int nw = (np + 31) >> 5;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * kDegWarps + wib;
+    if (j >= np) return;                                  // whole warps
+    unsigned* bits = smd + (size_t)wib * 2 * nw;
     unsigned* pre = bits + nw;
-    const int j = blockIdx.x;
-    const int b = roff[j], e = roff[j + 1];
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) bits[i] = 0u;
-    __syncthreads();
-    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-        const int src = rsrc_in[i];
+    const int b = roff[j], n = roff[j + 1] - b;
+    for (int i = lane; i < nw; i += 32) bits[i] = 0u;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        const int src = rsrc_in[b + i];
         atomicOr(&bits[src >> 5], 1u << (src & 31));
     }
-    __syncthreads();
-    // exclusive prefix of the popcounts (block-wide, chunked per thread)
-    __shared__ unsigned part[256];
-    const int per = (nw + blockDim.x - 1) / blockDim.x;
-    const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
+    __syncwarp();
+    const int per = (nw + 31) >> 5;
+    const int w0 = min(nw, lane * per), w1 = min(nw, w0 + per);
     unsigned acc = 0;
     for (int i = w0; i < w1; ++i) acc += __popc(bits[i]);
-    part[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        const unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    unsigned incl = acc;                                  // inclusive scan over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
     }
-    unsigned run = part[threadIdx.x] - acc;
+    unsigned run = incl - acc;
     for (int i = w0; i < w1; ++i) { pre[i] = run; run += __popc(bits[i]); }
-    __syncthreads();
-    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-        const int src = rsrc_in[i];
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        const int src = rsrc_in[b + i];
         const unsigned word = bits[src >> 5] & ((1u << (src & 31)) - 1u);
         const int at = b + (int)(pre[src >> 5] + __popc(word));
         rsrc[at] = src;
-        rw[at] = rw_in[i];
+        rw[at] = rw_in[b + i];
     }
-    __syncthreads();
-    // fixed-order sum: strided partial sums, then a fixed reduction tree
+    __syncwarp();                                         // the sorted list, read back by the warp
     double d = 0.0;
-    for (int i = b + threadIdx.x; i < e; i += blockDim.x) d += rw[i];
-    if (threadIdx.x < knn) d += w[(size_t)j * knn + threadIdx.x];
-    d = block_sum(d);
-    if (threadIdx.x == 0) {
+    for (int i = lane; i < n; i += 32) d += rw[b + i];
+    for (int q = lane; q < knn; q += 32) d += w[(size_t)j * knn + q];
+    d = warp_sum(d);
+    if (lane == 0) {
         const float dj = (float)(0.5 * d);
         deg[j] = dj;
         atomicMax(deg_max, __float_as_uint(dj));   // degrees are >= 0: their bits order like the values
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __res
     }
     if (trace) {
         tr = block_sum(tr);
-        if (threadIdx.x == 0) atomicAdd(trace, tr);
+        if (threadIdx.x == 0) trace[j] = tr;        // the patch's share; k_cost sums them in order
     }
 }
 
@@ -613,10 +616,14 @@ __global__ void k_xupdate(float2* __restrict__ alpha, const float2* __restrict__
     alpha[e] = cscale(cadd(z, cscale(qp, c)), 1.f / den);
 }
 
-__global__ void k_cost(const double* __restrict__ acc, const float* __restrict__ lam1, float lam2,
-                       double* __restrict__ out) {
-    // acc: [0] ||r||^2, [1] Tr(Q L Q^H), [2] sum of nuclear norms
-    *out = 0.5 * acc[0] + (double)(*lam1) * acc[1] + (double)lam2 * acc[2];
+// acc: [0] ||r||^2, [2] sum of nuclear norms; trace: the np patches' shares
+// of Tr(Q L Q^H), summed here in a fixed order (one block)
+__global__ void k_cost(const double* __restrict__ acc, const double* __restrict__ trace, int np,
+                       const float* __restrict__ lam1, float lam2, double* __restrict__ out) {
+    double t = 0.0;
+    for (int j = threadIdx.x; j < np; j += blockDim.x) t += trace[j];
+    t = block_sum(t);
+    if (threadIdx.x == 0) *out = 0.5 * acc[0] + (double)(*lam1) * t + (double)lam2 * acc[2];
 }
 
 __global__ void k_maps(const float* __restrict__ t1t2, const float* __restrict__ pd, const int* __restrict__ idx,
@@ -664,7 +671,8 @@ struct mrf_recon_s {
     // cost trace while the rebuild replaces the live copy (concurrent mode)
     int* nbr_c = nullptr;
     float *w_c = nullptr, *deg_c = nullptr;
-    double* acc = nullptr;      // [0] ||r||^2, [1] trace, [2] nuclear, [3..4] dot
+    double* acc = nullptr;      // [0] ||r||^2, [1] (unused), [2] nuclear, [3..4] dot
+    double* trace = nullptr;    // [np] the patches' shares of Tr(Q L Q^H)
     double* cost = nullptr;     // [cap] cost history
     int cost_cap = 0, iters_done = 0;
     float2* svt_v = nullptr;    // [np][svt_kp][svt_kp] right singular vectors of the last SVT
@@ -780,10 +788,11 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
     MRF_LAUNCHED_AS("k_fill_reverse", s);
     MRF_CUDA(cudaMemsetAsync(R->scal + 1, 0, sizeof(float), s));     // max(L), raised by k_degree
     {
-        const size_t smd = sizeof(unsigned) * 2 * (size_t)((np + 31) / 32);
+        const size_t smd = sizeof(unsigned) * 2 * (size_t)((np + 31) / 32) * kDegWarps;
         MRF_CUDA(cudaFuncSetAttribute(k_degree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
-        k_degree<<<np, 256, smd, s>>>(R->w, np, knn, R->roff, R->rsrc_tmp, R->rw_tmp, R->rsrc, R->rw, R->deg,
-                                      reinterpret_cast<unsigned*>(R->scal + 1));
+        k_degree<<<(unsigned)((np + kDegWarps - 1) / kDegWarps), kDegWarps * 32, smd, s>>>(
+            R->w, np, knn, R->roff, R->rsrc_tmp, R->rw_tmp, R->rsrc, R->rw, R->deg,
+            reinterpret_cast<unsigned*>(R->scal + 1));
     }
     MRF_LAUNCHED_AS("k_degree", s);
     k_lambda<<<1, 1, 0, s>>>(R->scal + 1, R->prm.lam1_0, (R->prm.flags & MRF_RECON_LITERAL_LAMBDA1) ? 1 : 0,
@@ -868,9 +877,9 @@ static mrf_status learned_maps(mrf_recon_s* R, cudaStream_t s) {
     return MRF_OK;
 }
 
-// Q(X) L into QL, or (QL null) Tr(Q L Q^H) added to *trace from the forward
-// kNN entries alone, of the live graph or (snap) of the copy taken when the
-// iteration began
+// Q(X) L into QL, or (QL null) each patch's share of Tr(Q L Q^H) from the
+// forward kNN entries alone into trace[np], of the live graph or (snap) of
+// the copy taken when the iteration began
 static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s, bool snap = false) {
     k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, snap ? R->nbr_c : R->nbr,
                                                 snap ? R->w_c : R->w, R->prm.knn, R->roff, R->rsrc, R->rw,
@@ -898,8 +907,8 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
         const size_t nr = (size_t)R->plan->T * R->plan->ns;
         k_norm2_acc<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->acc + 0);
         MRF_LAUNCHED_AS("k_norm2_acc", s);
-        MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, s));
-        k_cost<<<1, 1, 0, s>>>(R->acc, R->scal + 2, R->prm.lam2, R->cost + (it % R->cost_cap));
+        MRF_PROPAGATE(graph_pass(R, nullptr, R->trace, s));
+        k_cost<<<1, 256, 0, s>>>(R->acc, R->trace, R->np, R->scal + 2, R->prm.lam2, R->cost + (it % R->cost_cap));
         MRF_LAUNCHED_AS("k_cost", s);
     }
     return MRF_OK;
@@ -956,7 +965,7 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     mark(sb);
     mark(sc);
     MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, sb));
-    if (cost) MRF_PROPAGATE(graph_pass(R, nullptr, R->acc + 1, sb, true));   // trace with this iteration's graph
+    if (cost) MRF_PROPAGATE(graph_pass(R, nullptr, R->trace, sb, true));     // trace with this iteration's graph
     MRF_CUDA(cudaEventRecord(R->ev[3], sb));
     if (R->prm.flags & MRF_RECON_LEARNED) MRF_PROPAGATE(learned_maps(R, sc));
     else MRF_PROPAGATE(match_maps(R, sc));
@@ -972,7 +981,7 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     MRF_CUDA(cudaStreamWaitEvent(s, R->ev[4], 0));
     mark(s);
     if (cost) {
-        k_cost<<<1, 1, 0, s>>>(R->acc, R->scal + 4, R->prm.lam2, R->cost + (it % R->cost_cap));
+        k_cost<<<1, 256, 0, s>>>(R->acc, R->trace, R->np, R->scal + 4, R->prm.lam2, R->cost + (it % R->cost_cap));
         MRF_LAUNCHED_AS("k_cost", s);
     }
     return MRF_OK;
@@ -1022,6 +1031,7 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(dalloc(R, &R->roff, np + 1));
     MRF_PROPAGATE(dalloc(R, &R->scal, 8));
     MRF_PROPAGATE(dalloc(R, &R->acc, 8));
+    MRF_PROPAGATE(dalloc(R, &R->trace, (size_t)np));
     R->svt_kp = K <= 4 ? 4 : K <= 8 ? 8 : K == 10 ? 10 : K <= 12 ? 12 : 16;
     MRF_PROPAGATE(dalloc(R, &R->svt_v, (size_t)np * R->svt_kp * R->svt_kp));
     MRF_PROPAGATE(dalloc(R, &R->svt_stats, 2));
