@@ -321,23 +321,30 @@ def time_variant(variant, inp, steps, warmup, dist):
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    mrf.profile_enable(True)
     launches0 = mrf.launch_count()
     dist.barrier()
     torch.cuda.synchronize()
     with Clocks(torch.cuda.current_device()) as clk:
         for i in range(steps):
             flush.zero_()
-            mrf.profile_mark()
             starts[i].record()
             rec.iterate(1)
             ends[i].record()
         torch.cuda.synchronize()
     dist.barrier()
     launches = mrf.launch_count() - launches0
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    # per-kernel intervals of the same concurrent loop, from an untimed pass
+    # with the profiler on (it records an event per launch, so the loop then
+    # launches its kernels one by one instead of replaying the recorded one)
+    mrf.profile_enable(True)
+    for i in range(steps):
+        flush.zero_()
+        mrf.profile_mark()
+        rec.iterate(1)
+    torch.cuda.synchronize()
     prof = mrf.profile_read()
     mrf.profile_enable(False)
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     # results after warm-up + the timed steps (read before the clock window below)
     t1, t2, pd, idx = rec.maps()
     maps = [t.cpu().numpy() for t in (t1, t2, pd)]

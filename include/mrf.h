@@ -326,10 +326,13 @@ enum {
     MRF_RECON_LEARNED = 16,         /* maps from the learned matcher (params.mlp, K = 10); fingerprints
                                        it maps outside the dictionary's T1/T2 box, or to T1 < T2, are
                                        matched exhaustively instead (needs a tensor-core precision) */
-    MRF_RECON_SERIAL = 32           /* run an iteration's steps one after another on the caller's
+    MRF_RECON_SERIAL = 32,          /* run an iteration's steps one after another on the caller's
                                        stream (default: the forward operator, the SVT and matching +
                                        graph rebuild run concurrently on internal streams, joined into
                                        the caller's stream; same results) */
+    MRF_RECON_EAGER = 64            /* launch every iteration's kernels one by one (default: from the
+                                       second iteration on, one iteration is recorded once as a CUDA
+                                       graph on the caller's stream and replayed; same results) */
 };
 
 typedef struct {
@@ -355,7 +358,11 @@ mrf_status mrf_recon_create(mrf_recon* out, mrf_plan plan, const mrf_recon_param
                             const float* atom_norm2, const float* lut, int m,
                             const mrf_c64* b, mrf_stream stream);
 /* Run n_iters iterations.  cost_out: host double [n_iters] (nullable); when
- * given (and costs are enabled) the call synchronises to return them. */
+ * given (and costs are enabled) the call synchronises to return them.
+ * Unless MRF_RECON_EAGER or MRF_RECON_SERIAL is set (or the per-kernel
+ * profiler is on), the first iteration after the first one is recorded as a
+ * CUDA graph (stream capture of the caller's stream, which must then not be
+ * capturing already) and every later iteration replays it. */
 mrf_status mrf_recon_iter(mrf_recon r, int n_iters, double* cost_out, mrf_stream stream);
 /* Current maps: t1, t2, pd (PD divided back by gamma): dev float [ny][nx];
  * idx: dev int [ny][nx].  Each nullable. */

@@ -22,6 +22,7 @@ __all__ = ["MRFError", "NufftPlan", "Recon", "ReconParams", "dict_subspace", "ep
 MATCH_FP32, MATCH_BF16, MATCH_BF16X3, MATCH_FP8, MATCH_LITERAL_NORM2 = 0, 1, 2, 3, 0x100
 RECON_LITERAL_XUPDATE, RECON_LITERAL_LAMBDA1, RECON_NO_COST, RECON_GROUPED, RECON_LEARNED, RECON_SERIAL = (
     1, 2, 4, 8, 16, 32)
+RECON_EAGER = 64
 
 
 def _stream():

@@ -55,6 +55,14 @@ Profiler& prof() {
 std::atomic<long long> g_launches{0};
 }  // namespace
 
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+void note_replayed_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool profiling_enabled() {
+    Profiler& P = prof();
+    std::lock_guard<std::mutex> lk(P.mu);
+    return P.on;
+}
+
 void note_launch(const char* name, cudaStream_t s) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     Profiler& P = prof();

@@ -18,6 +18,12 @@ void set_error(const char* fmt, ...);
 // recorded on the launching stream and the interval since the previous event
 // on that stream is charged to the kernel.
 void note_launch(const char* name, cudaStream_t s);
+// kernels launched so far (every launch site's report), and a CUDA graph
+// replay's kernels added to that count
+long long launches_so_far();
+void note_replayed_launches(long long n);
+// the per-kernel profiler is recording (launches must then go one by one)
+bool profiling_enabled();
 
 inline cudaStream_t as_stream(mrf_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -617,13 +617,20 @@ __global__ void k_xupdate(float2* __restrict__ alpha, const float2* __restrict__
 }
 
 // acc: [0] ||r||^2, [2] sum of nuclear norms; trace: the np patches' shares
-// of Tr(Q L Q^H), summed here in a fixed order (one block)
+// of Tr(Q L Q^H), summed here in a fixed order (one block).  The cost goes to
+// cost[*slot], and the slot moves on (the iteration count modulo cap, kept on
+// the device so that a recorded iteration replays unchanged).
 __global__ void k_cost(const double* __restrict__ acc, const double* __restrict__ trace, int np,
-                       const float* __restrict__ lam1, float lam2, double* __restrict__ out) {
+                       const float* __restrict__ lam1, float lam2, double* __restrict__ cost,
+                       int* __restrict__ slot, int cap) {
     double t = 0.0;
     for (int j = threadIdx.x; j < np; j += blockDim.x) t += trace[j];
     t = block_sum(t);
-    if (threadIdx.x == 0) *out = 0.5 * acc[0] + (double)(*lam1) * t + (double)lam2 * acc[2];
+    if (threadIdx.x == 0) {
+        const int q = *slot;
+        cost[q] = 0.5 * acc[0] + (double)(*lam1) * t + (double)lam2 * acc[2];
+        *slot = q + 1 == cap ? 0 : q + 1;
+    }
 }
 
 __global__ void k_maps(const float* __restrict__ t1t2, const float* __restrict__ pd, const int* __restrict__ idx,
@@ -673,6 +680,9 @@ struct mrf_recon_s {
     float *w_c = nullptr, *deg_c = nullptr;
     double* acc = nullptr;      // [0] ||r||^2, [1] (unused), [2] nuclear, [3..4] dot
     double* trace = nullptr;    // [np] the patches' shares of Tr(Q L Q^H)
+    int* cost_slot = nullptr;   // [1] where the next cost goes (iterations done modulo cost_cap)
+    cudaGraphExec_t iter_exec = nullptr;   // one recorded iteration (replayed), or none
+    long long iter_kernels = 0;            // kernels in it
     double* cost = nullptr;     // [cap] cost history
     int cost_cap = 0, iters_done = 0;
     float2* svt_v = nullptr;    // [np][svt_kp][svt_kp] right singular vectors of the last SVT
@@ -686,8 +696,8 @@ struct mrf_recon_s {
     float2* fb_x = nullptr;
     mrf::TcSlice* fb_table = nullptr;
     // concurrency inside one iteration: two side streams and their events
-    cudaStream_t side[2] = {nullptr, nullptr};
-    cudaEvent_t ev[5] = {};
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // [2]: where a recorded iteration replays
+    cudaEvent_t ev[7] = {};                               // [5], [6]: fork to and join from side[2]
     std::vector<void*> owned;
 };
 
@@ -702,6 +712,7 @@ static mrf_status dalloc(mrf_recon_s* R, T** p, size_t n) {
 
 static void free_recon(mrf_recon_s* R) {
     if (!R) return;
+    if (R->iter_exec) cudaGraphExecDestroy(R->iter_exec);
     for (cudaStream_t t : R->side)
         if (t) cudaStreamDestroy(t);
     for (cudaEvent_t e : R->ev)
@@ -908,7 +919,8 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
         k_norm2_acc<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->acc + 0);
         MRF_LAUNCHED_AS("k_norm2_acc", s);
         MRF_PROPAGATE(graph_pass(R, nullptr, R->trace, s));
-        k_cost<<<1, 256, 0, s>>>(R->acc, R->trace, R->np, R->scal + 2, R->prm.lam2, R->cost + (it % R->cost_cap));
+        k_cost<<<1, 256, 0, s>>>(R->acc, R->trace, R->np, R->scal + 2, R->prm.lam2, R->cost, R->cost_slot,
+                                 R->cost_cap);
         MRF_LAUNCHED_AS("k_cost", s);
     }
     return MRF_OK;
@@ -981,7 +993,8 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     MRF_CUDA(cudaStreamWaitEvent(s, R->ev[4], 0));
     mark(s);
     if (cost) {
-        k_cost<<<1, 256, 0, s>>>(R->acc, R->trace, R->np, R->scal + 4, R->prm.lam2, R->cost + (it % R->cost_cap));
+        k_cost<<<1, 256, 0, s>>>(R->acc, R->trace, R->np, R->scal + 4, R->prm.lam2, R->cost, R->cost_slot,
+                                 R->cost_cap);
         MRF_LAUNCHED_AS("k_cost", s);
     }
     return MRF_OK;
@@ -1032,6 +1045,8 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(dalloc(R, &R->scal, 8));
     MRF_PROPAGATE(dalloc(R, &R->acc, 8));
     MRF_PROPAGATE(dalloc(R, &R->trace, (size_t)np));
+    MRF_PROPAGATE(dalloc(R, &R->cost_slot, 1));
+    MRF_CUDA(cudaMemsetAsync(R->cost_slot, 0, sizeof(int), s));
     R->svt_kp = K <= 4 ? 4 : K <= 8 ? 8 : K == 10 ? 10 : K <= 12 ? 12 : 16;
     MRF_PROPAGATE(dalloc(R, &R->svt_v, (size_t)np * R->svt_kp * R->svt_kp));
     MRF_PROPAGATE(dalloc(R, &R->svt_stats, 2));
@@ -1176,7 +1191,10 @@ extern "C" mrf_status mrf_recon_create(mrf_recon* out, mrf_plan plan, const mrf_
         if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess) t = nullptr;
     for (cudaEvent_t& e : R->ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) e = nullptr;
-    if (!R->side[0] || !R->side[1] || !R->ev[0] || !R->ev[1] || !R->ev[2] || !R->ev[3] || !R->ev[4]) {
+    bool made = true;
+    for (cudaStream_t t : R->side) made = made && t;
+    for (cudaEvent_t e : R->ev) made = made && e;
+    if (!made) {
         free_recon(R);
         set_error("mrf_recon_create: could not create the loop's streams and events");
         return MRF_ECUDA;
@@ -1206,7 +1224,47 @@ extern "C" mrf_status mrf_recon_iter(mrf_recon R, int n_iters, double* cost_out,
     MRF_REQUIRE(n_iters >= 0 && n_iters <= R->cost_cap, "mrf_recon_iter: n_iters must be in [0, %d]", R->cost_cap);
     cudaStream_t s = as_stream(stream);
     const int first = R->iters_done;
-    for (int i = 0; i < n_iters; ++i) MRF_PROPAGATE(iteration(R, first + i, s));
+    for (int i = 0; i < n_iters; ++i) {
+        // the first iteration runs eagerly (tuners, lazily built operands, the
+        // SVT's cold start); the next one is recorded and then replayed
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        MRF_CUDA(cudaStreamIsCapturing(s, &cap));
+        const bool graph = !(R->prm.flags & (MRF_RECON_EAGER | MRF_RECON_SERIAL)) && first + i >= 1 &&
+                           R->svt_warm && !profiling_enabled() && cap == cudaStreamCaptureStatusNone;
+        if (!graph) {
+            MRF_PROPAGATE(iteration(R, first + i, s));
+            continue;
+        }
+        // recorded and replayed on an internal stream that follows the
+        // caller's (which may be a default stream, which cannot be captured)
+        cudaStream_t si = R->side[2];
+        MRF_CUDA(cudaEventRecord(R->ev[5], s));
+        MRF_CUDA(cudaStreamWaitEvent(si, R->ev[5], 0));
+        if (!R->iter_exec) {
+            const long long before = launches_so_far();
+            const double svt_before = R->svt_patch_launches;
+            MRF_CUDA(cudaStreamBeginCapture(si, cudaStreamCaptureModeRelaxed));
+            const mrf_status st = iteration(R, first + i, si);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(si, &g);
+            if (st != MRF_OK || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                if (st != MRF_OK) return st;
+                MRF_CUDA(e);
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&R->iter_exec, g, 0);
+            cudaGraphDestroy(g);
+            MRF_CUDA(ei);
+            R->iter_kernels = launches_so_far() - before;
+            note_replayed_launches(-R->iter_kernels);            // counted again at each replay
+            R->svt_patch_launches = svt_before;
+        }
+        MRF_CUDA(cudaGraphLaunch(R->iter_exec, si));
+        MRF_CUDA(cudaEventRecord(R->ev[6], si));
+        MRF_CUDA(cudaStreamWaitEvent(s, R->ev[6], 0));
+        note_replayed_launches(R->iter_kernels);
+        R->svt_patch_launches += R->np;
+    }
     R->iters_done += n_iters;
     if (cost_out && n_iters > 0) {
         if (R->prm.flags & MRF_RECON_NO_COST) {
@@ -1373,6 +1431,15 @@ extern "C" mrf_status mrf_recon_restore(mrf_recon R, const void* buf, size_t byt
     }
     R->iters_done = h.iters_done;
     R->svt_warm = h.svt_warm;
+    if (R->iter_exec) {                         // recorded before the restore: record again
+        cudaGraphExecDestroy(R->iter_exec);
+        R->iter_exec = nullptr;
+    }
+    {
+        const int slot = R->iters_done % R->cost_cap;
+        MRF_CUDA(cudaMemcpyAsync(R->cost_slot, &slot, sizeof(int), cudaMemcpyHostToDevice, s));
+        MRF_CUDA(cudaStreamSynchronize(s));
+    }
     MRF_PROPAGATE(build_graph(R, s));
     MRF_CUDA(cudaStreamSynchronize(s));
     return MRF_OK;

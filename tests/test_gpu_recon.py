@@ -180,6 +180,33 @@ def test_serial_and_concurrent_iterations_agree(prob, mode):
     assert rel(np_(rc.alpha()), np_(rs.alpha())) < (1e-5 if same else 1e-3)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_replayed_iterations_agree_with_eager_ones(prob, mode):
+    """From the second iteration on, the loop records one iteration as a CUDA
+    graph and replays it; MRF_RECON_EAGER launches every kernel one by one.
+    Both agree as the serial and concurrent forms do (up to the order of the
+    gather's atomic additions), including a call that runs several
+    iterations, and the costs come back in iteration order."""
+    m = mrf()
+    o = oracle_recon(prob)
+    plan = m.nufft_plan(prob["n"], prob["n"], f32(prob["k"]))
+    rg = gpu_recon(prob, mode, plan=plan, a_norm=o.a, x_scale=o.gamma)
+    re = gpu_recon(prob, mode, extra_flags=64, plan=plan, a_norm=o.a, x_scale=o.gamma)
+    same = True
+    for it in range(3):
+        cg = rg.iterate(1, costs=True)[0]
+        ce = re.iterate(1, costs=True)[0]
+        assert cg == pytest.approx(ce, rel=1e-5 if same else 5e-3), it
+        ig, ie = np_(rg.maps()[3]), np_(re.maps()[3])
+        assert (ig == ie).mean() > 0.99
+        same = same and bool((ig == ie).all())
+    cg = rg.iterate(3, costs=True)
+    ce = re.iterate(3, costs=True)
+    for a, b in zip(cg, ce):
+        assert a == pytest.approx(b, rel=1e-5 if same else 5e-3)
+    assert rel(np_(rg.alpha()), np_(re.alpha())) < (1e-5 if same else 1e-3)
+
+
 def test_svt_work_counters():
     """The SVT step's sweep and rotation counters: every patch of every SVT
     launch runs at least one sweep and at most the kernel's 30, and the patch
