@@ -904,7 +904,6 @@ static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStre
 static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t s) {
     const size_t NK = (size_t)R->N * R->K;
     const float inv_a = (float)(1.0 / R->a);
-    MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, s));
     MRF_PROPAGATE(graph_pass(R, R->QL, nullptr, s));
     const float c = R->prm.mu * R->prm.lam2 * R->prm.beta;
     k_xupdate<<<(unsigned)((NK + 255) / 256), 256, 0, s>>>(
@@ -912,6 +911,8 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
         (R->prm.flags & MRF_RECON_LITERAL_XUPDATE) ? 1 : 0, nullptr);
     MRF_LAUNCHED_AS("k_xupdate", s);
     MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, s));
+    // the next pass's gradient of the data term, A*(r), from this residual
+    MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, s));
     if (cost) MRF_CUDA(cudaMemsetAsync(R->acc, 0, 3 * sizeof(double), s));
     MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, s));
     if (cost) {
@@ -928,14 +929,17 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
 
 // One iteration of the loop body, with its independent steps on three
 // streams (stream-ordered, ends joined into s):
-//   s:       adjoint -> (join) X update -> forward -> |r|^2 -> (join) cost
-//   side[1]: graph copy, graph term Q(X)L (the previous graph) ...... ^ join
+//   s:       (join) X update -> forward -> |r|^2 -> next A*(r) -> (join) cost
+//   side[1]: graph copy, graph term Q(X)L (the previous graph) ^ join
 //   side[0]:                     SVT of the new iterate -> P, sum sigma -> cost trace
 //   side[1]:                     matching -> graph rebuild
 // The forward operator, the SVT and the matching all read only the new
 // iterate; the graph rebuild only the new maps; the cost trace reads the copy
 // of the graph taken at the start, so the rebuild need not wait for it; the
-// accumulators they add to are distinct slots.
+// accumulators they add to are distinct slots.  The data term's gradient
+// A*(r) for the next pass is computed as soon as this pass's residual is
+// (create and restore compute the first one), so it runs beside the matching
+// and the graph rebuild instead of beside the next graph term.
 static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     const bool cost = !(R->prm.flags & MRF_RECON_NO_COST);
     if (R->prm.flags & MRF_RECON_SERIAL) {
@@ -962,7 +966,6 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     }
     MRF_PROPAGATE(graph_pass(R, R->QL, nullptr, sc));
     MRF_CUDA(cudaEventRecord(R->ev[1], sc));
-    MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, s));
     MRF_CUDA(cudaStreamWaitEvent(s, R->ev[1], 0));
     mark(s);
     const float c = R->prm.mu * R->prm.lam2 * R->prm.beta;
@@ -989,6 +992,9 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
         k_norm2_acc<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->acc + 0);
         MRF_LAUNCHED_AS("k_norm2_acc", s);
     }
+    // the next pass's gradient of the data term, A*(r), beside the matching
+    // and graph rebuild (it needs only this residual)
+    MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, s));
     MRF_CUDA(cudaStreamWaitEvent(s, R->ev[3], 0));
     MRF_CUDA(cudaStreamWaitEvent(s, R->ev[4], 0));
     mark(s);
@@ -1144,6 +1150,7 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(match_maps(R, s));                     // maps in the scaled units
     MRF_PROPAGATE(build_graph(R, s));
     MRF_PROPAGATE(subspace_forward(p, R->alpha, R->phi, K, inv_a, R->bs, R->r, R->mode, s));
+    MRF_PROPAGATE(subspace_adjoint(p, R->r, R->phi, K, inv_a, R->grad, R->mode, s));   // the first pass's A*(r)
     MRF_PROPAGATE(svt(R, R->alpha, R->P, nullptr, s));
     MRF_CUDA(cudaStreamSynchronize(s));
     return MRF_OK;
@@ -1431,6 +1438,8 @@ extern "C" mrf_status mrf_recon_restore(mrf_recon R, const void* buf, size_t byt
     }
     R->iters_done = h.iters_done;
     R->svt_warm = h.svt_warm;
+    // the next pass's A*(r), from the restored residual
+    MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, (float)(1.0 / R->a), R->grad, R->mode, s));
     if (R->iter_exec) {                         // recorded before the restore: record again
         cudaGraphExecDestroy(R->iter_exec);
         R->iter_exec = nullptr;
