@@ -56,6 +56,45 @@ __device__ __forceinline__ void unpack(const int4 r, int& j, int& mx0, int& my0,
     fy = __int_as_float(r.w);
 }
 
+// KB weights of every strip record, computed once per plan (they depend on
+// the trajectory only): w[i][0..W) along x, w[i][W..2W) along y
+template <int W>
+__global__ void k_rec_weights(const int4* __restrict__ rec, int n, float beta, float* __restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int j, mx0, my0;
+    float fx, fy;
+    unpack(rec[i], j, mx0, my0, fx, fy);
+    float wx[W], wy[W];
+    kb_weights<W>(fx, beta, wx);
+    kb_weights<W>(fy, beta, wy);
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        w[(size_t)i * 2 * W + a] = wx[a];
+        w[(size_t)i * 2 * W + W + a] = wy[a];
+    }
+}
+
+// the stored weights of record i (2 W floats, 16-byte aligned: W = 4 or 6)
+template <int W>
+__device__ __forceinline__ void load_weights(const float* __restrict__ w, int i, float (&wx)[W], float (&wy)[W]) {
+    const float4* q = reinterpret_cast<const float4*>(w) + (size_t)i * (W / 2);
+    float v[2 * W];
+#pragma unroll
+    for (int c = 0; c < W / 2; ++c) {
+        const float4 f = q[c];
+        v[4 * c] = f.x;
+        v[4 * c + 1] = f.y;
+        v[4 * c + 2] = f.z;
+        v[4 * c + 3] = f.w;
+    }
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        wx[a] = v[a];
+        wy[a] = v[W + a];
+    }
+}
+
 // centred coordinate held at grid index g
 template <int G>
 __device__ __forceinline__ int centred(int g) { return g < G / 2 ? g : g - G; }
@@ -211,9 +250,10 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols_interp(const float2* __
                                                              float2* __restrict__ y,
                                                              const float2* __restrict__ bsub, float scale,
                                                              const int4* __restrict__ rec,
+                                                             const float* __restrict__ wts,
                                                              const int* __restrict__ off,
                                                              const int* __restrict__ group_of, int ny, int ns,
-                                                             int nstrips, float beta) {
+                                                             int nstrips) {
     constexpr int SF = kTile - (W - 1);
     extern __shared__ float2 sm[];
     float2* tw = sm;
@@ -230,8 +270,7 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols_interp(const float2* __
         float fx, fy;
         unpack(rec[i], j, mx0, my0, fx, fy);
         float wx[W], wy[W];
-        kb_weights<W>(fx, beta, wx);
-        kb_weights<W>(fy, beta, wy);
+        load_weights<W>(wts, i, wx, wy);
         const int lc = mx0 - c0;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -281,9 +320,10 @@ template <int G, int W, int SRC>
 __global__ void __launch_bounds__(kColThreads, 3) k_spread_cols(const float2* __restrict__ y, int K,
                                                              float2* __restrict__ h1,
                                                              const int4* __restrict__ rec,
+                                                             const float* __restrict__ wts,
                                                              const int* __restrict__ off,
                                                              const int* __restrict__ group_of, int ngroups,
-                                                             int ny, int ns, int nstrips, float beta) {
+                                                             int ny, int ns, int nstrips) {
     extern __shared__ float2 sm[];
     float2* tw = sm;
     float2* tile = sm + G;                 // [G][kTile]
@@ -302,8 +342,7 @@ __global__ void __launch_bounds__(kColThreads, 3) k_spread_cols(const float2* __
             unpack(rec[i], j, mx0, my0, fx, fy);
             const float2 v = SRC == 0 ? y[(size_t)f * ns + j] : y[((size_t)g * ns + j) * K + f];
             float wx[W], wy[W];
-            kb_weights<W>(fx, beta, wx);
-            kb_weights<W>(fy, beta, wy);
+            load_weights<W>(wts, i, wx, wy);
 #pragma unroll
             for (int a = 0; a < W; ++a) {
                 const int lc = (wrapg<G>(mx0 + a)) - c0;
@@ -702,8 +741,8 @@ mrf_status launch_cols_interp(const mrf_plan_s* p, const float2* h1, float2* y, 
     const size_t sm = tile_smem(G);
     MRF_DISPATCH_G(G, MRF_DISPATCH_W(p->W, {
         MRF_PROPAGATE(set_smem(k_cols_interp<GG, WW>, sm));
-        k_cols_interp<GG, WW><<<grid, kColThreads, sm, s>>>(h1, y, b, scale, p->fwd_rec, p->fwd_off,
-                                                            p->group_of, p->ny, p->ns, p->nstrips_f, p->beta);
+        k_cols_interp<GG, WW><<<grid, kColThreads, sm, s>>>(h1, y, b, scale, p->fwd_rec, p->fwd_w, p->fwd_off,
+                                                            p->group_of, p->ny, p->ns, p->nstrips_f);
     }));
     MRF_LAUNCHED_AS("k_cols_interp", s);
     return MRF_OK;
@@ -717,14 +756,14 @@ mrf_status launch_spread_cols(const mrf_plan_s* p, const float2* y, int src_mode
     MRF_DISPATCH_G(G, MRF_DISPATCH_W(p->W, {
         if (src_mode == 0) {
             MRF_PROPAGATE(set_smem(k_spread_cols<GG, WW, 0>, sm));
-            k_spread_cols<GG, WW, 0><<<grid, kColThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_off, p->group_of,
-                                                                   p->ngroups, p->ny, p->ns, p->nstrips_a,
-                                                                   p->beta);
+            k_spread_cols<GG, WW, 0><<<grid, kColThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_w, p->adj_off,
+                                                                   p->group_of, p->ngroups, p->ny, p->ns,
+                                                                   p->nstrips_a);
         } else {
             MRF_PROPAGATE(set_smem(k_spread_cols<GG, WW, 1>, sm));
-            k_spread_cols<GG, WW, 1><<<grid, kColThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_off, p->group_of,
-                                                                   p->ngroups, p->ny, p->ns, p->nstrips_a,
-                                                                   p->beta);
+            k_spread_cols<GG, WW, 1><<<grid, kColThreads, sm, s>>>(y, K, h1, p->adj_rec, p->adj_w, p->adj_off,
+                                                                   p->group_of, p->ngroups, p->ny, p->ns,
+                                                                   p->nstrips_a);
         }
     }));
     MRF_LAUNCHED_AS("k_spread_cols", s);
@@ -756,7 +795,7 @@ mrf_status launch_rows_adj(const mrf_plan_s* p, const float2* h1, float2* dst, i
 // ---------------------------------------------------------------------------
 static void free_plan(mrf_plan_s* p) {
     if (!p) return;
-    void* ptrs[] = {p->inv_dx, p->inv_dy, p->fwd_rec, p->fwd_off, p->adj_rec, p->adj_off, p->grec,
+    void* ptrs[] = {p->inv_dx, p->inv_dy, p->fwd_rec, p->fwd_off, p->adj_rec, p->adj_off, p->fwd_w, p->adj_w, p->grec,
                     p->group_of, p->gf_off, p->gf, p->h1, p->sub_h1, p->sub_spec, p->sub_Y, p->sub_R,
                     p->sub_partial, p->gat_off, p->gat_pt, p->gat_smp, p->gat_w};
     for (void* q : ptrs)
@@ -1123,6 +1162,25 @@ extern "C" mrf_status mrf_nufft_plan(mrf_plan* out, int nx, int ny, int T, int n
     ALLOC_COPY(p->gf_off, gfoff);
     ALLOC_COPY(p->gf, gf);
 #undef ALLOC_COPY
+    // the records' KB weights, once (the same expression the kernels used to
+    // evaluate per frame, so the operator's values are unchanged)
+    e = cudaMalloc(&p->fwd_w, sizeof(float) * 2 * W * std::max<size_t>(frec.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p->adj_w, sizeof(float) * 2 * W * std::max<size_t>(arec.size(), 1));
+    if (e != cudaSuccess) goto fail;
+    {
+        const int nf = (int)frec.size(), na = (int)arec.size();
+        const float bt = p->beta;
+        if (W == 4) {
+            if (nf) k_rec_weights<4><<<(nf + 255) / 256, 256>>>(p->fwd_rec, nf, bt, p->fwd_w);
+            if (na) k_rec_weights<4><<<(na + 255) / 256, 256>>>(p->adj_rec, na, bt, p->adj_w);
+        } else {
+            if (nf) k_rec_weights<6><<<(nf + 255) / 256, 256>>>(p->fwd_rec, nf, bt, p->fwd_w);
+            if (na) k_rec_weights<6><<<(na + 255) / 256, 256>>>(p->adj_rec, na, bt, p->adj_w);
+        }
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) goto fail;
+    }
     e = cudaMalloc(&p->h1, sizeof(float2) * (size_t)T * ny * p->gx);
     if (e != cudaSuccess) goto fail;
     *out = p;

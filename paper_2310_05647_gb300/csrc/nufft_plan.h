@@ -17,6 +17,8 @@ struct mrf_plan_s {
     int4* fwd_rec = nullptr;      // samples by (group, forward strip of the first x node)
     int* fwd_off = nullptr;       // [ngroups * nstrips_f + 1]
     int4* adj_rec = nullptr;      // samples by (group, every adjoint strip they touch)
+    float* fwd_w = nullptr;       // [fwd_rec entries][2 W] KB weights of each record: W along x, then W along y
+    float* adj_w = nullptr;       // [adj_rec entries][2 W] the same for the adjoint records
     int* adj_off = nullptr;       // [ngroups * nstrips_a + 1]
     int4* grec = nullptr;         // samples in (group, index) order
     int* group_of = nullptr;      // [T]
