@@ -109,6 +109,16 @@ __global__ void k_scale_copy(const float2* __restrict__ x, size_t n, float s, fl
         y[i] = cscale(x[i], s);
 }
 
+// y = x / sqrt(*n2) (a power-iteration step's normalisation, read on the
+// device; zero when the norm is not positive)
+__global__ void k_scale_by_norm(const float2* __restrict__ x, size_t n, const double* __restrict__ n2,
+                                float2* __restrict__ y) {
+    const double nw = sqrt(*n2);
+    const float s = nw > 0.0 ? (float)(1.0 / nw) : 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = cscale(x[i], s);
+}
+
 __global__ void k_fill(float2* __restrict__ x, size_t n, float2 v) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         x[i] = v;
@@ -1107,7 +1117,9 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     } else {
         k_fill<<<nblk(NK), 256, 0, s>>>(R->alpha, NK, make_float2((float)(1.0 / std::sqrt((double)NK)), 0.f));
         MRF_LAUNCHED_AS("k_fill", s);
-        double lam = 0.0;
+        // (the steps queue back to back: each normalisation reads its norm on
+        // the device; the estimate and the last norm come back once)
+        double h[4] = {0.0, 0.0, 0.0, 0.0};
         for (int it = 0; it < R->prm.power_iters; ++it) {
             MRF_PROPAGATE(subspace_forward(p, R->alpha, R->phi, K, 1.0f, nullptr, R->r, R->mode, s));
             MRF_PROPAGATE(subspace_adjoint(p, R->r, R->phi, K, 1.0f, R->grad, R->mode, s));
@@ -1116,15 +1128,16 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
             MRF_LAUNCHED_AS("k_dot_acc", s);
             k_norm2_acc<<<nblk(NK), 256, 0, s>>>(R->grad, NK, R->acc + 2);
             MRF_LAUNCHED_AS("k_norm2_acc", s);
-            double h[4];
+            k_scale_by_norm<<<nblk(NK), 256, 0, s>>>(R->grad, NK, R->acc + 2, R->alpha);
+            MRF_LAUNCHED_AS("k_scale_by_norm", s);
+        }
+        if (R->prm.power_iters > 0) {
             MRF_CUDA(cudaMemcpyAsync(h, R->acc, sizeof(h), cudaMemcpyDeviceToHost, s));
             MRF_CUDA(cudaStreamSynchronize(s));
-            lam = h[0];
-            const double nw = std::sqrt(h[2]);
-            MRF_REQUIRE(nw > 0.0, "mrf_recon_create: the operator maps the start vector to zero");
-            k_scale_copy<<<nblk(NK), 256, 0, s>>>(R->grad, NK, (float)(1.0 / nw), R->alpha);
-            MRF_LAUNCHED_AS("k_scale_copy", s);
         }
+        const double lam = h[0];
+        MRF_REQUIRE(R->prm.power_iters <= 0 || h[2] > 0.0,
+                    "mrf_recon_create: the operator maps the start vector to zero");
         MRF_REQUIRE(lam > 0.0, "mrf_recon_create: non-positive operator norm estimate");
         R->a = std::sqrt(lam);
     }
