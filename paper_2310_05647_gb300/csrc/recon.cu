@@ -930,8 +930,8 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
         k_norm2_acc<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->acc + 0);
         MRF_LAUNCHED_AS("k_norm2_acc", s);
         MRF_PROPAGATE(graph_pass(R, nullptr, R->trace, s));
-        k_cost<<<1, 256, 0, s>>>(R->acc, R->trace, R->np, R->scal + 2, R->prm.lam2, R->cost, R->cost_slot,
-                                 R->cost_cap);
+        k_cost<<<1, 1024, 0, s>>>(R->acc, R->trace, R->np, R->scal + 2, R->prm.lam2, R->cost, R->cost_slot,
+                                  R->cost_cap);
         MRF_LAUNCHED_AS("k_cost", s);
     }
     return MRF_OK;
@@ -1009,8 +1009,8 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     MRF_CUDA(cudaStreamWaitEvent(s, R->ev[4], 0));
     mark(s);
     if (cost) {
-        k_cost<<<1, 256, 0, s>>>(R->acc, R->trace, R->np, R->scal + 4, R->prm.lam2, R->cost, R->cost_slot,
-                                 R->cost_cap);
+        k_cost<<<1, 1024, 0, s>>>(R->acc, R->trace, R->np, R->scal + 4, R->prm.lam2, R->cost, R->cost_slot,
+                                  R->cost_cap);
         MRF_LAUNCHED_AS("k_cost", s);
     }
     return MRF_OK;
