@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __res
     const int rb = rev ? roff[j] : 0, re = rev ? roff[j + 1] : 0;
     const int nq = knn + (rev ? re - rb : 0);
     const float wscale = rev ? 0.5f : 1.0f;
-    double tr = 0.0;
+    float tr = 0.f;                 // this thread's share (kGbElems terms a pass), in FP32
     for (int e0 = 0; e0 < ne; e0 += kGbThreads * kGbElems) {
         int off[kGbElems];
         float2 a[kGbElems], v[kGbElems];
@@ -558,12 +558,12 @@ __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __res
             if (off[u] < 0) continue;
             const int e = e0 + threadIdx.x + u * kGbThreads;
             if (QL) QL[(size_t)j * ne + e] = v[u];
-            if (trace) tr += (double)a[u].x * v[u].x + (double)a[u].y * v[u].y;
+            if (trace) tr += a[u].x * v[u].x + a[u].y * v[u].y;
         }
     }
     if (trace) {
-        tr = block_sum(tr);
-        if (threadIdx.x == 0) trace[j] = tr;        // the patch's share; k_cost sums them in order
+        const double t = block_sum((double)tr);     // the patch's share in FP64
+        if (threadIdx.x == 0) trace[j] = t;         // k_cost sums the shares in order
     }
 }
 
