@@ -106,22 +106,30 @@ __global__ void __launch_bounds__(256) k_match_fp32(const float2* __restrict__ x
 }
 
 // per-atom weights of the score: 1/||d||^2 (argmax of |s|^2/||d||^2 is the
-// argmax of |s|/||d||) or 1/||d||^4 for the literal |s|/||d||^2.
+// argmax of |s|/||d||) or 1/||d||^4 for the literal |s|/||d||^2.  One warp
+// per atom: the lanes read consecutive entries and sum their (non-negative)
+// terms in FP32, len / 32 of them each; the 32 lane sums are combined in FP64
+// by a fixed shuffle tree (FP64 work per element is slow on this GPU).
 __global__ void k_match_weights(const float2* __restrict__ dict, const float* __restrict__ norm2_in, int m, int len,
                                 int literal, float* __restrict__ norm2, float* __restrict__ wscore) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= m) return;
+    const int a = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (a >= m) return;                                   // whole warps
     float n2;
     if (norm2_in) {
         n2 = norm2_in[a];
     } else {
-        double s = 0.0;
-        for (int k = 0; k < len; ++k) s += (double)cabs2(dict[(size_t)a * len + k]);
+        float f = 0.f;
+        for (int k = lane; k < len; k += 32) f += cabs2(dict[(size_t)a * len + k]);
+        double s = (double)f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         n2 = (float)s;
     }
-    norm2[a] = n2;
-    const float inv = n2 > 0.f ? 1.0f / n2 : 0.f;
-    wscore[a] = literal ? inv * inv : inv;
+    if (lane == 0) {
+        norm2[a] = n2;
+        const float inv = n2 > 0.f ? 1.0f / n2 : 0.f;
+        wscore[a] = literal ? inv * inv : inv;
+    }
 }
 
 __global__ void k_match_finish(const int* __restrict__ best_idx, const float2* __restrict__ best_ip, int n,
@@ -196,7 +204,8 @@ mrf_status MatchWorkspace::reserve(int n, int m) {
 
 mrf_status match_prepare(MatchWorkspace& ws, const float2* dict, const float* norm2_in, int m, int len,
                          int literal, cudaStream_t s) {
-    k_match_weights<<<(m + 255) / 256, 256, 0, s>>>(dict, norm2_in, m, len, literal, ws.norm2, ws.wscore);
+    k_match_weights<<<(unsigned)(((size_t)m * 32 + 255) / 256), 256, 0, s>>>(dict, norm2_in, m, len, literal,
+                                                                             ws.norm2, ws.wscore);
     MRF_LAUNCHED_AS("k_match_weights", s);
     ws.tc_dict = nullptr;   // the tensor-core operand carries the weights: rebuild it
     return MRF_OK;
