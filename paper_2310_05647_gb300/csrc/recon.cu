@@ -152,6 +152,17 @@ static unsigned nblk(size_t n, int t = 256) { return (unsigned)std::min<size_t>(
 // every device.
 constexpr double kQScale = 4096.0;
 
+// rint(t / tmax * 4096) as the FP64 oracle rounds it.  The FP32 quotient
+// scaled by 4096 (exact) is within 2^-13 of the exact value for ratios up to
+// 1 (2^-12 up to 2) and the FP64 one within 2^-41, so away from a half (more
+// than 2^-10) both round to the same integer; near a half, for large ratios
+// and for non-finite values the FP64 expression decides.
+__device__ __forceinline__ int quantise(float t, double tmax) {
+    const float y = __fdiv_rn(t, (float)tmax) * (float)kQScale;
+    if (fabsf(y) < 2.f * (float)kQScale && fabsf(y - floorf(y) - 0.5f) > 0x1p-10f) return (int)rintf(y);
+    return (int)rint((double)t / tmax * kQScale);
+}
+
 __global__ void k_features(const float* __restrict__ t1t2, PatchGeom g, double t1max, double t2max, int FD4,
                            int* __restrict__ F) {
     const int pp = g.p * g.p;
@@ -162,8 +173,8 @@ __global__ void k_features(const float* __restrict__ t1t2, PatchGeom g, double t
     const int y = g.origin(i / g.cnt) + py, x = g.origin(i % g.cnt) + px;
     const size_t v = (size_t)y * g.n + x;
     int* f = F + (size_t)i * FD4 + 2 * q;
-    f[0] = (int)rint((double)t1t2[2 * v] / t1max * kQScale);
-    f[1] = (int)rint((double)t1t2[2 * v + 1] / t2max * kQScale);
+    f[0] = quantise(t1t2[2 * v], t1max);
+    f[1] = quantise(t1t2[2 * v + 1], t2max);
 }
 
 // sigma^2 = median of the non-zero kNN squared distances (1 if none) on the
