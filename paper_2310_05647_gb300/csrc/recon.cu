@@ -505,7 +505,7 @@ __global__ void k_lambda(const float* __restrict__ lmax, float lam1_0, int liter
 // per warp; measured slower on this latency-bound kernel.)
 constexpr int kGbThreads = 128;
 constexpr int kGbChunk = 256;
-constexpr int kGbElems = 8;
+constexpr int kGbElems = 5;      // 8 x 8 x 10 coefficients = 5 per thread: no idle slots, 55 registers
 
 __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __restrict__ alpha, PatchGeom g, int K,
                                                              const int* __restrict__ nbr,
