@@ -178,4 +178,97 @@ __device__ __forceinline__ void fft_batch(float2* s, int estride, int bstride, c
     if constexpr (REM == 1) batch_pass<N, 2, NWK, INV, POW2>(t, estride, Ns, wk, tw);
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident four-step transform of 512-point columns (the strip
+// kernels at grid 512).  N = 512 = 16 x 32 with n = t + 16 m, k = k1 + 32 k2:
+//   X[k1 + 32 k2] = sum_t W16^(t k2) W512^(t k1) sum_m W32^(m k1) x[t + 16 m].
+// A 16-column strip takes 256 threads, thread (c = tid % 16, t = tid / 16):
+// the 32-point DFT over m of its column's elements t + 16 m in registers,
+// the W512^(t k1) twiddles, one exchange through shared memory, then the two
+// 16-point DFTs over t for k1 = 2 t, 2 t + 1 in registers.  Each element
+// crosses shared memory once (a write and a read) instead of once per
+// radix-8 pass (three, plus the twiddle reads).
+// ---------------------------------------------------------------------------
+// exp(-2 pi i j / 32)
+static __constant__ float2 c_w32[32] = {
+    {1.0f, 0.0f}, {0.98078528f, -0.195090322f}, {0.923879533f, -0.382683432f}, {0.831469612f, -0.555570233f},
+    {0.707106781f, -0.707106781f}, {0.555570233f, -0.831469612f}, {0.382683432f, -0.923879533f}, {0.195090322f, -0.98078528f},
+    {0.0f, -1.0f}, {-0.195090322f, -0.98078528f}, {-0.382683432f, -0.923879533f}, {-0.555570233f, -0.831469612f},
+    {-0.707106781f, -0.707106781f}, {-0.831469612f, -0.555570233f}, {-0.923879533f, -0.382683432f}, {-0.98078528f, -0.195090322f},
+    {-1.0f, 0.0f}, {-0.98078528f, 0.195090322f}, {-0.923879533f, 0.382683432f}, {-0.831469612f, 0.555570233f},
+    {-0.707106781f, 0.707106781f}, {-0.555570233f, 0.831469612f}, {-0.382683432f, 0.923879533f}, {-0.195090322f, 0.98078528f},
+    {0.0f, 1.0f}, {0.195090322f, 0.98078528f}, {0.382683432f, 0.923879533f}, {0.555570233f, 0.831469612f},
+    {0.707106781f, 0.707106781f}, {0.831469612f, 0.555570233f}, {0.923879533f, 0.382683432f}, {0.98078528f, 0.195090322f}};
+
+// natural-order DFT of length 32 (m = a + 4 b: DFT8 over b, twiddles
+// W32^(a kb), DFT4 over a; X[kb + 8 ka])
+template <bool INV>
+__device__ __forceinline__ void dft32(float2 (&v)[32]) {
+    float2 u[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) u[a][b] = v[a + 4 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) dft8<INV>(u[a]);
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+#pragma unroll
+        for (int kb = 1; kb < 8; ++kb) u[a][kb] = twiddle<INV>(u[a][kb], c_w32[a * kb]);
+#pragma unroll
+    for (int kb = 0; kb < 8; ++kb) {
+        float2 w[4] = {u[0][kb], u[1][kb], u[2][kb], u[3][kb]};
+        dft4<INV>(w);
+#pragma unroll
+        for (int ka = 0; ka < 4; ++ka) v[kb + 8 * ka] = w[ka];
+    }
+}
+
+// natural-order DFT of length 16 (m = a + 4 b: DFT4 over b, twiddles
+// W16^(a kb) = W32^(2 a kb), DFT4 over a; X[kb + 4 ka])
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+    float2 u[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) u[a][b] = v[a + 4 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) dft4<INV>(u[a]);
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+#pragma unroll
+        for (int kb = 1; kb < 4; ++kb) u[a][kb] = twiddle<INV>(u[a][kb], c_w32[2 * a * kb]);
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+        float2 w[4] = {u[0][kb], u[1][kb], u[2][kb], u[3][kb]};
+        dft4<INV>(w);
+#pragma unroll
+        for (int ka = 0; ka < 4; ++ka) v[kb + 4 * ka] = w[ka];
+    }
+}
+
+// The four-step transform of a 16-column strip (blockDim 256).  x: the
+// thread's inputs x[t + 16 m], m = 0..31, of column c; buf: [512][16] shared
+// scratch (free on entry; free again on return); tw: tw[k] = exp(-2 pi i k /
+// 512).  out[j][k2] = X[(2 t + j) + 32 k2] of column c.
+template <bool INV>
+__device__ __forceinline__ void col512(float2 (&x)[32], float2* buf, const float2* tw, float2 (&out)[2][16]) {
+    const int c = threadIdx.x & 15, t = threadIdx.x >> 4;
+    dft32<INV>(x);
+#pragma unroll
+    for (int k1 = 1; k1 < 32; ++k1) x[k1] = twiddle<INV>(x[k1], tw[(t * k1) & 511]);
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) buf[(k1 * 16 + t) * 16 + c] = x[k1];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int k1 = 2 * t + j;
+#pragma unroll
+        for (int tt = 0; tt < 16; ++tt) out[j][tt] = buf[(k1 * 16 + tt) * 16 + c];
+        dft16<INV>(out[j]);
+    }
+    __syncthreads();
+}
+
 }  // namespace mrf

@@ -246,7 +246,7 @@ __device__ __forceinline__ void load_strip(float2* tile, const float2* __restric
 // columns.  y = scale * interp - b  (b nullable).
 // ---------------------------------------------------------------------------
 template <int G, int W>
-__global__ void __launch_bounds__(kColThreads, 3) k_cols_interp(const float2* __restrict__ h1,
+__global__ void __launch_bounds__(kColThreads, G == 512 ? 2 : 3) k_cols_interp(const float2* __restrict__ h1,
                                                              float2* __restrict__ y,
                                                              const float2* __restrict__ bsub, float scale,
                                                              const int4* __restrict__ rec,
@@ -261,8 +261,31 @@ __global__ void __launch_bounds__(kColThreads, 3) k_cols_interp(const float2* __
     const int strip = blockIdx.x, t = blockIdx.y;
     const int c0 = strip * SF;
     fft_twiddles<G>(tw);
-    load_strip<G>(tile, h1 + (size_t)t * ny * G, c0, ny);
-    fft_batch<G, kTile, kColThreads, false>(tile, kTile, 1, tw);
+    if constexpr (G == 512) {
+        // the strip's columns straight into registers (rows t' + 16 m of
+        // column c), the four-step transform, the spectrum into the tile
+        static_assert(kTile == 16 && kColThreads == 256, "the four-step form maps 256 threads to 16 columns");
+        const int c = threadIdx.x & 15, tq = threadIdx.x >> 4;
+        const float2* h1f = h1 + (size_t)t * ny * G;
+        const int col = wrapg<G>(c0 + c);
+        float2 x[32];
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            const int iy = centred<G>(tq + 16 * m) + ny / 2;
+            x[m] = (iy >= 0 && iy < ny) ? h1f[(size_t)iy * G + col] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();                                // the twiddle table
+        float2 out[2][16];
+        col512<false>(x, tile, tw, out);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) tile[((2 * tq + j) + 32 * k2) * kTile + c] = out[j][k2];
+        __syncthreads();
+    } else {
+        load_strip<G>(tile, h1 + (size_t)t * ny * G, c0, ny);
+        fft_batch<G, kTile, kColThreads, false>(tile, kTile, 1, tw);
+    }
     const int g = group_of[t];
     const int beg = off[g * nstrips + strip], end = off[g * nstrips + strip + 1];
     for (int i = beg + threadIdx.x; i < end; i += kColThreads) {
@@ -358,6 +381,10 @@ __global__ void __launch_bounds__(kColThreads, 3) k_spread_cols(const float2* __
         }
     }
     __syncthreads();
+    // (the register-resident four-step transform of the strip kernels at grid
+    // 512 needs 128 registers here, which halves the blocks per SM; the
+    // spread phase's shared-memory atomics need them more than the transform
+    // gains: measured 1.11 against 1.04 ms per 1000 frames)
     fft_batch<G, kTile, kColThreads, true>(tile, kTile, 1, tw);
     float2* dst = h1 + (size_t)f * ny * G;
     for (int idx = threadIdx.x; idx < ny * kTile; idx += kColThreads) {
