@@ -271,4 +271,40 @@ __device__ __forceinline__ void col512(float2 (&x)[32], float2* buf, const float
     __syncthreads();
 }
 
+// The same four-step transform for 16 rows of 512 points held one row per
+// 16 threads (blockDim 256, thread (t = tid % 16, r = tid / 16)): x holds
+// x[t + 16 m] of row r.  buf: 32 x 257 shared scratch (free on entry and on
+// return; the odd stride keeps both exchange directions conflict-free); tw2:
+// tw2[k1 * 16 + t] = exp(-2 pi i t k1 / 512) (row512_twiddles).
+// out[j][k2] = X[(t + 16 j) + 32 k2] of row r.
+constexpr int kRow512Buf = 32 * 257;
+
+__device__ __forceinline__ void row512_twiddles(float2* tw2) {
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) {
+        const int k1 = i >> 4, t = i & 15;
+        float s, c;
+        sincospif(-2.0f * (float)((t * k1) & 511) / 512.0f, &s, &c);
+        tw2[i] = make_float2(c, s);
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void row512(float2 (&x)[32], float2* buf, const float2* tw2, float2 (&out)[2][16]) {
+    const int t = threadIdx.x & 15, r = threadIdx.x >> 4;
+    dft32<INV>(x);
+#pragma unroll
+    for (int k1 = 1; k1 < 32; ++k1) x[k1] = twiddle<INV>(x[k1], tw2[k1 * 16 + t]);
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) buf[k1 * 257 + r * 16 + t] = x[k1];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int k1 = t + 16 * j;
+#pragma unroll
+        for (int tt = 0; tt < 16; ++tt) out[j][tt] = buf[k1 * 257 + r * 16 + tt];
+        dft16<INV>(out[j]);
+    }
+    __syncthreads();
+}
+
 }  // namespace mrf

@@ -38,6 +38,11 @@ constexpr int kTile = 16;        // columns per strip tile (64 KB at G = 512: th
 constexpr int kColThreads = 256; // threads of the strip kernels
 constexpr int kRowB = 16;        // rows (or frames) per row-kernel block
 constexpr int kRowThreads = 256; // threads of the row kernels
+// elements of the row kernels' [kRowB][G + 1] row tile, enlarged at grid 512
+// to hold the four-step transform's exchange buffer
+__host__ __device__ constexpr int row_region(int G) {
+    return G == 512 && kRow512Buf > kRowB * (G + 1) ? kRow512Buf : kRowB * (G + 1);
+}
 
 template <int W>
 __device__ __forceinline__ void kb_weights(float f, float beta, float* w) {
@@ -181,13 +186,14 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd_expand(const float2* _
                                                                  int ny) {
     extern __shared__ float2 sm[];
     constexpr int LD = G + 1;
-    float2* tw = sm;
+    float2* tw = sm;                       // (grid 512: the four-step table, row512_twiddles)
     float2* rows = sm + G;                 // [kRowB][G + 1]
-    float2* arow = rows + kRowB * LD;      // [nx][K]
+    float2* arow = rows + row_region(G);   // [nx][K]
     float2* ph = arow + nx * K;            // [kRowB][K]
     const int iy = blockIdx.x;
     const int t0 = blockIdx.y * kRowB;
-    fft_twiddles<G>(tw);
+    if constexpr (G == 512) row512_twiddles(tw);
+    else fft_twiddles<G>(tw);
     for (int i = threadIdx.x; i < nx * K; i += kRowThreads) arow[i] = alpha[(size_t)iy * nx * K + i];
     for (int i = threadIdx.x; i < kRowB * K; i += kRowThreads) {
         const int tt = t0 + i / K;
@@ -218,10 +224,30 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd_expand(const float2* _
         }
     }
     __syncthreads();
-    fft_batch<G, kRowB, kRowThreads, false>(rows, 1, LD, tw);
-    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
-        const int r = idx / G, g = idx - r * G;
-        if (t0 + r < T) h1[((size_t)(t0 + r) * ny + iy) * G + g] = rows[r * LD + g];
+    if constexpr (G == 512) {
+        // frame row r's elements t + 16 m into registers, the four-step
+        // transform, the spectrum straight from registers to H1
+        static_assert(kRowB == 16 && kRowThreads == 256, "the four-step form maps 256 threads to 16 rows");
+        const int t = threadIdx.x & 15, r = threadIdx.x >> 4;
+        float2 x[32];
+#pragma unroll
+        for (int m = 0; m < 32; ++m) x[m] = rows[r * LD + t + 16 * m];
+        __syncthreads();                                // every row read before the exchange reuses them
+        float2 out[2][16];
+        row512<false>(x, rows, tw, out);
+        if (t0 + r < T) {
+            float2* dst = h1 + ((size_t)(t0 + r) * ny + iy) * G;
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) dst[(t + 16 * j) + 32 * k2] = out[j][k2];
+        }
+    } else {
+        fft_batch<G, kRowB, kRowThreads, false>(rows, 1, LD, tw);
+        for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
+            const int r = idx / G, g = idx - r * G;
+            if (t0 + r < T) h1[((size_t)(t0 + r) * ny + iy) * G + g] = rows[r * LD + g];
+        }
     }
 }
 
@@ -561,13 +587,14 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_rows_adj_reduce(const float2
     constexpr int LD = G + 1;
     constexpr int MAXK = 16;               // a thread per image column ix (nx <= 256), all K <= 16 coefficients
     extern __shared__ float2 sm[];
-    float2* tw = sm;
+    float2* tw = sm;                       // (grid 512: the four-step table, row512_twiddles)
     float2* rows = sm + G;                 // [kRowB][G + 1]
-    float2* ph = rows + kRowB * LD;        // [kRowB][K]
+    float2* ph = rows + row_region(G);     // [kRowB][K]
     const int iy = blockIdx.x, part = blockIdx.y;
     const int tb = part * frames_per_part;
     const int te = min(T, tb + frames_per_part);
-    fft_twiddles<G>(tw);
+    if constexpr (G == 512) row512_twiddles(tw);
+    else fft_twiddles<G>(tw);
     float2 acc[MAXK];
 #pragma unroll
     for (int q = 0; q < MAXK; ++q) acc[q] = make_float2(0.f, 0.f);
@@ -575,19 +602,47 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_rows_adj_reduce(const float2
     const int gx = wrapg<G>(ix - nx / 2);
     const float sy = inv_dy[iy];
     for (int t0 = tb; t0 < te; t0 += kRowB) {
-        stage_block<8>(
-            kRowB * G,
-            [&](int idx) {
-                const int r = idx / G;
-                return t0 + r < te ? h1[((size_t)(t0 + r) * ny + iy) * G + idx % G] : make_float2(0.f, 0.f);
-            },
-            [&](int idx, float2 v) { rows[(idx / G) * LD + idx % G] = v; });
-        for (int i = threadIdx.x; i < kRowB * K; i += kRowThreads) {
-            const int tt = t0 + i / K;
-            ph[i] = tt < te ? phi[(size_t)tt * K + (i % K)] : make_float2(0.f, 0.f);
+        if constexpr (G == 512) {
+            // frame row r's elements t + 16 m straight into registers, the
+            // four-step inverse transform, the image's columns back into the
+            // row tile for the reduction
+            static_assert(kRowB == 16 && kRowThreads == 256, "the four-step form maps 256 threads to 16 rows");
+            const int t = threadIdx.x & 15, r = threadIdx.x >> 4;
+            float2 x[32];
+            const float2* src = h1 + ((size_t)(t0 + r) * ny + iy) * G;
+#pragma unroll
+            for (int m = 0; m < 32; ++m) x[m] = t0 + r < te ? src[t + 16 * m] : make_float2(0.f, 0.f);
+            for (int i = threadIdx.x; i < kRowB * K; i += kRowThreads) {
+                const int tt = t0 + i / K;
+                ph[i] = tt < te ? phi[(size_t)tt * K + (i % K)] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();                            // the twiddle table (first pass)
+            float2 out[2][16];
+            row512<true>(x, rows, tw, out);
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) {
+                    const int g = (t + 16 * j) + 32 * k2;
+                    const int cx = centred<G>(g) + nx / 2;
+                    if (cx >= 0 && cx < nx) rows[r * LD + g] = out[j][k2];
+                }
+            __syncthreads();
+        } else {
+            stage_block<8>(
+                kRowB * G,
+                [&](int idx) {
+                    const int r = idx / G;
+                    return t0 + r < te ? h1[((size_t)(t0 + r) * ny + iy) * G + idx % G] : make_float2(0.f, 0.f);
+                },
+                [&](int idx, float2 v) { rows[(idx / G) * LD + idx % G] = v; });
+            for (int i = threadIdx.x; i < kRowB * K; i += kRowThreads) {
+                const int tt = t0 + i / K;
+                ph[i] = tt < te ? phi[(size_t)tt * K + (i % K)] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            fft_batch<G, kRowB, kRowThreads, true>(rows, 1, LD, tw);
         }
-        __syncthreads();
-        fft_batch<G, kRowB, kRowThreads, true>(rows, 1, LD, tw);
         const int nf = min(kRowB, te - t0);
         if (ix < nx) {
             // one load of the pixel's value per frame serves all K products;
@@ -1264,7 +1319,7 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
     if (mode == 0) {
         const int G = p->gx;
         dim3 grid(p->ny, (p->T + kRowB - 1) / kRowB);
-        const size_t sm = (size_t)(G + kRowB * (G + 1) + p->nx * K + kRowB * K) * sizeof(float2);
+        const size_t sm = (size_t)(G + row_region(G) + p->nx * K + kRowB * K) * sizeof(float2);
         MRF_DISPATCH_G(G, {
             MRF_PROPAGATE(set_smem(k_rows_fwd_expand<GG>, sm));
             k_rows_fwd_expand<GG><<<grid, kRowThreads, sm, s>>>(alpha, phi, K, p->T, p->h1, p->inv_dx, p->inv_dy,
@@ -1302,7 +1357,7 @@ mrf_status subspace_adjoint(mrf_plan_s* p, const float2* y, const float2* phi, i
         MRF_PROPAGATE(launch_spread_cols(p, y, 0, 0, p->T, p->h1, s));
         const int G = p->gx;
         dim3 grid(p->ny, p->parts);
-        const size_t sm = (size_t)(G + kRowB * (G + 1) + kRowB * K) * sizeof(float2);
+        const size_t sm = (size_t)(G + row_region(G) + kRowB * K) * sizeof(float2);
         MRF_DISPATCH_G(G, {
             MRF_PROPAGATE(set_smem(k_rows_adj_reduce<GG>, sm));
             k_rows_adj_reduce<GG><<<grid, kRowThreads, sm, s>>>(p->h1, phi, K, p->T, p->frames_per_part,
