@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd(const float2* __restri
 // Forward stage 1 in subspace form: frame t row iy is sum_k alpha[iy][ix][k]
 // conj(phi[t][k]).  Block = one image row x 16 frames.
 template <int G>
-__global__ void __launch_bounds__(kRowThreads) k_rows_fwd_expand(const float2* __restrict__ alpha,
+__global__ void __launch_bounds__(kRowThreads, 3) k_rows_fwd_expand(const float2* __restrict__ alpha,
                                                                  const float2* __restrict__ phi, int K, int T,
                                                                  float2* __restrict__ h1,
                                                                  const float* __restrict__ inv_dx,
@@ -188,13 +188,11 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd_expand(const float2* _
     constexpr int LD = G + 1;
     float2* tw = sm;                       // (grid 512: the four-step table, row512_twiddles)
     float2* rows = sm + G;                 // [kRowB][G + 1]
-    float2* arow = rows + row_region(G);   // [nx][K]
-    float2* ph = arow + nx * K;            // [kRowB][K]
+    float2* ph = rows + row_region(G);     // [kRowB][K]
     const int iy = blockIdx.x;
     const int t0 = blockIdx.y * kRowB;
     if constexpr (G == 512) row512_twiddles(tw);
     else fft_twiddles<G>(tw);
-    for (int i = threadIdx.x; i < nx * K; i += kRowThreads) arow[i] = alpha[(size_t)iy * nx * K + i];
     for (int i = threadIdx.x; i < kRowB * K; i += kRowThreads) {
         const int tt = t0 + i / K;
         ph[i] = tt < T ? phi[(size_t)tt * K + (i % K)] : make_float2(0.f, 0.f);
@@ -210,9 +208,11 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd_expand(const float2* _
             for (int r = 0; r < kRowB; ++r) rows[r * LD + g] = make_float2(0.f, 0.f);
             continue;
         }
+        // (read once from the coefficient image: the row's 20 KB stay in L1)
+        const float2* arow = alpha + ((size_t)iy * nx + ix) * K;
         float2 a[16];                                   // K <= 16 (unrolled: stays in registers)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) a[k] = k < K ? arow[ix * K + k] : make_float2(0.f, 0.f);
+        for (int k = 0; k < 16; ++k) a[k] = k < K ? arow[k] : make_float2(0.f, 0.f);
         const float sc = inv_dx[ix] * sy;
 #pragma unroll 4
         for (int r = 0; r < kRowB; ++r) {
@@ -1319,7 +1319,7 @@ mrf_status subspace_forward(mrf_plan_s* p, const float2* alpha, const float2* ph
     if (mode == 0) {
         const int G = p->gx;
         dim3 grid(p->ny, (p->T + kRowB - 1) / kRowB);
-        const size_t sm = (size_t)(G + row_region(G) + p->nx * K + kRowB * K) * sizeof(float2);
+        const size_t sm = (size_t)(G + row_region(G) + kRowB * K) * sizeof(float2);
         MRF_DISPATCH_G(G, {
             MRF_PROPAGATE(set_smem(k_rows_fwd_expand<GG>, sm));
             k_rows_fwd_expand<GG><<<grid, kRowThreads, sm, s>>>(alpha, phi, K, p->T, p->h1, p->inv_dx, p->inv_dy,
