@@ -350,12 +350,32 @@ __global__ void __launch_bounds__(TILE * 16) k_cols_store(const float2* __restri
     const int strip = blockIdx.x, f = blockIdx.y;
     const int c0 = strip * TILE;
     fft_twiddles<G>(tw);
-    load_strip<G, TILE>(tile, h1 + (size_t)f * ny * G, c0, ny);
-    fft_batch<G, TILE, NT, false>(tile, TILE, 1, tw);
     float2* dst = spec + (size_t)f * G * G;
-    for (int idx = threadIdx.x; idx < G * TILE; idx += NT) {
-        const int gy = idx / TILE, c = idx & (TILE - 1);
-        dst[(size_t)gy * G + c0 + c] = tile[idx];
+    if constexpr (G == 512 && TILE == 16) {
+        // register-resident four-step transform: the image's columns straight
+        // into registers, the spectrum straight out of them
+        const int c = threadIdx.x & 15, tq = threadIdx.x >> 4;
+        const float2* h1f = h1 + (size_t)f * ny * G;
+        float2 x[32];
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+            const int iy = centred<G>(tq + 16 * m) + ny / 2;
+            x[m] = (iy >= 0 && iy < ny) ? h1f[(size_t)iy * G + c0 + c] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();                                // the twiddle table
+        float2 out[2][16];
+        col512<false>(x, tile, tw, out);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) dst[(size_t)((2 * tq + j) + 32 * k2) * G + c0 + c] = out[j][k2];
+    } else {
+        load_strip<G, TILE>(tile, h1 + (size_t)f * ny * G, c0, ny);
+        fft_batch<G, TILE, NT, false>(tile, TILE, 1, tw);
+        for (int idx = threadIdx.x; idx < G * TILE; idx += NT) {
+            const int gy = idx / TILE, c = idx & (TILE - 1);
+            dst[(size_t)gy * G + c0 + c] = tile[idx];
+        }
     }
 }
 
@@ -526,16 +546,35 @@ __global__ void __launch_bounds__(TILE * 16) k_cols_inv(const float2* __restrict
     const int c0 = strip * TILE;
     fft_twiddles<G>(tw);
     const float2* src = grid + (size_t)f * G * G;
-    stage_block<4>(
-        G * TILE, [&](int idx) { return src[(size_t)(idx / TILE) * G + c0 + (idx & (TILE - 1))]; },
-        [&](int idx, float2 v) { tile[idx] = v; });
-    __syncthreads();
-    fft_batch<G, TILE, NT, true>(tile, TILE, 1, tw);
     float2* dst = h1 + (size_t)f * ny * G;
-    for (int idx = threadIdx.x; idx < ny * TILE; idx += NT) {
-        const int iy = idx / TILE, c = idx & (TILE - 1);
-        const int gy = wrapg<G>(iy - ny / 2);
-        dst[(size_t)iy * G + c0 + c] = tile[gy * TILE + c];
+    if constexpr (G == 512 && TILE == 16) {
+        // register-resident four-step inverse transform: the grid's columns
+        // straight into registers, the image rows straight out of them
+        const int c = threadIdx.x & 15, tq = threadIdx.x >> 4;
+        float2 x[32];
+#pragma unroll
+        for (int m = 0; m < 32; ++m) x[m] = src[(size_t)(tq + 16 * m) * G + c0 + c];
+        __syncthreads();                                // the twiddle table
+        float2 out[2][16];
+        col512<true>(x, tile, tw, out);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) {
+                const int iy = centred<G>((2 * tq + j) + 32 * k2) + ny / 2;
+                if (iy >= 0 && iy < ny) dst[(size_t)iy * G + c0 + c] = out[j][k2];
+            }
+    } else {
+        stage_block<4>(
+            G * TILE, [&](int idx) { return src[(size_t)(idx / TILE) * G + c0 + (idx & (TILE - 1))]; },
+            [&](int idx, float2 v) { tile[idx] = v; });
+        __syncthreads();
+        fft_batch<G, TILE, NT, true>(tile, TILE, 1, tw);
+        for (int idx = threadIdx.x; idx < ny * TILE; idx += NT) {
+            const int iy = idx / TILE, c = idx & (TILE - 1);
+            const int gy = wrapg<G>(iy - ny / 2);
+            dst[(size_t)iy * G + c0 + c] = tile[gy * TILE + c];
+        }
     }
 }
 
