@@ -151,27 +151,45 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_fwd(const float2* __restri
     constexpr int LD = G + 1;
     const int t = blockIdx.y;
     const int iy0 = blockIdx.x * kRowB;
-    fft_twiddles<G>(tw);
-    stage_block<8>(
-        kRowB * G,
-        [&](int idx) {
+    auto value = [&](int iy, int g) {
+        const int ix = centred<G>(g) + nx / 2;
+        float2 v = make_float2(0.f, 0.f);
+        if (iy < ny && ix >= 0 && ix < nx) {
+            v = SRC == 0 ? x[((size_t)t * ny + iy) * nx + ix] : x[((size_t)iy * nx + ix) * K + t];
+            v = cscale(v, inv_dx[ix] * inv_dy[iy]);
+        }
+        return v;
+    };
+    if constexpr (G == 512) {
+        // row r's elements tq + 16 m straight into registers, the four-step
+        // transform, the spectrum straight out of them
+        const int tq = threadIdx.x & 15, r = threadIdx.x >> 4, iy = iy0 + r;
+        row512_twiddles(tw);
+        float2 xr[32];
+#pragma unroll
+        for (int m = 0; m < 32; ++m) xr[m] = value(iy, tq + 16 * m);
+        __syncthreads();                                // the twiddle table
+        float2 out[2][16];
+        row512<false>(xr, rows, tw, out);
+        if (iy < ny) {
+            float2* dst = h1 + ((size_t)t * ny + iy) * G;
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) dst[(tq + 16 * j) + 32 * k2] = out[j][k2];
+        }
+    } else {
+        fft_twiddles<G>(tw);
+        stage_block<8>(
+            kRowB * G, [&](int idx) { return value(iy0 + idx / G, idx % G); },
+            [&](int idx, float2 v) { rows[(idx / G) * LD + idx % G] = v; });
+        __syncthreads();
+        fft_batch<G, kRowB, kRowThreads, false>(rows, 1, LD, tw);
+        for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
             const int r = idx / G, g = idx - r * G;
             const int iy = iy0 + r;
-            const int ix = centred<G>(g) + nx / 2;
-            float2 v = make_float2(0.f, 0.f);
-            if (iy < ny && ix >= 0 && ix < nx) {
-                v = SRC == 0 ? x[((size_t)t * ny + iy) * nx + ix] : x[((size_t)iy * nx + ix) * K + t];
-                v = cscale(v, inv_dx[ix] * inv_dy[iy]);
-            }
-            return v;
-        },
-        [&](int idx, float2 v) { rows[(idx / G) * LD + idx % G] = v; });
-    __syncthreads();
-    fft_batch<G, kRowB, kRowThreads, false>(rows, 1, LD, tw);
-    for (int idx = threadIdx.x; idx < kRowB * G; idx += kRowThreads) {
-        const int r = idx / G, g = idx - r * G;
-        const int iy = iy0 + r;
-        if (iy < ny) h1[((size_t)t * ny + iy) * G + g] = rows[r * LD + g];
+            if (iy < ny) h1[((size_t)t * ny + iy) * G + g] = rows[r * LD + g];
+        }
     }
 }
 
@@ -592,23 +610,49 @@ __global__ void __launch_bounds__(kRowThreads) k_rows_adj(const float2* __restri
     float2* rows = sm + G;
     const int t = blockIdx.y;
     const int iy0 = blockIdx.x * kRowB;
-    fft_twiddles<G>(tw);
-    stage_block<8>(
-        kRowB * G,
-        [&](int idx) {
-            const int iy = iy0 + idx / G;
-            return iy < ny ? h1[((size_t)t * ny + iy) * G + idx % G] : make_float2(0.f, 0.f);
-        },
-        [&](int idx, float2 v) { rows[(idx / G) * LD + idx % G] = v; });
-    __syncthreads();
-    fft_batch<G, kRowB, kRowThreads, true>(rows, 1, LD, tw);
-    for (int idx = threadIdx.x; idx < kRowB * nx; idx += kRowThreads) {
-        const int r = idx / nx, ix = idx - r * nx;
-        const int iy = iy0 + r;
-        if (iy >= ny) continue;
-        const float2 v = cscale(rows[r * LD + (wrapg<G>(ix - nx / 2))], inv_dx[ix] * inv_dy[iy] * scale);
-        if (DST == 0) x[((size_t)t * ny + iy) * nx + ix] = v;
-        else x[((size_t)iy * nx + ix) * K + t] = v;
+    if constexpr (G == 512) {
+        // row r's elements tq + 16 m straight into registers, the four-step
+        // inverse transform, the image's columns straight out of them
+        const int tq = threadIdx.x & 15, r = threadIdx.x >> 4, iy = iy0 + r;
+        row512_twiddles(tw);
+        float2 xr[32];
+        const float2* src = h1 + ((size_t)t * ny + iy) * G;
+#pragma unroll
+        for (int m = 0; m < 32; ++m) xr[m] = iy < ny ? src[tq + 16 * m] : make_float2(0.f, 0.f);
+        __syncthreads();                                // the twiddle table
+        float2 out[2][16];
+        row512<true>(xr, rows, tw, out);
+        if (iy < ny) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) {
+                    const int ix = centred<G>((tq + 16 * j) + 32 * k2) + nx / 2;
+                    if (ix < 0 || ix >= nx) continue;
+                    const float2 v = cscale(out[j][k2], inv_dx[ix] * inv_dy[iy] * scale);
+                    if (DST == 0) x[((size_t)t * ny + iy) * nx + ix] = v;
+                    else x[((size_t)iy * nx + ix) * K + t] = v;
+                }
+        }
+    } else {
+        fft_twiddles<G>(tw);
+        stage_block<8>(
+            kRowB * G,
+            [&](int idx) {
+                const int iy = iy0 + idx / G;
+                return iy < ny ? h1[((size_t)t * ny + iy) * G + idx % G] : make_float2(0.f, 0.f);
+            },
+            [&](int idx, float2 v) { rows[(idx / G) * LD + idx % G] = v; });
+        __syncthreads();
+        fft_batch<G, kRowB, kRowThreads, true>(rows, 1, LD, tw);
+        for (int idx = threadIdx.x; idx < kRowB * nx; idx += kRowThreads) {
+            const int r = idx / nx, ix = idx - r * nx;
+            const int iy = iy0 + r;
+            if (iy >= ny) continue;
+            const float2 v = cscale(rows[r * LD + (wrapg<G>(ix - nx / 2))], inv_dx[ix] * inv_dy[iy] * scale);
+            if (DST == 0) x[((size_t)t * ny + iy) * nx + ix] = v;
+            else x[((size_t)iy * nx + ix) * K + t] = v;
+        }
     }
 }
 
@@ -834,7 +878,7 @@ static bool supported_grid(int g) { return g == 64 || g == 128 || g == 256 || g 
         default: MRF_REQUIRE(false, "unsupported kernel width %d", W_);                  \
     }
 
-static size_t rows_smem(int G) { return (size_t)(G + kRowB * (G + 1)) * sizeof(float2); }
+static size_t rows_smem(int G) { return (size_t)(G + row_region(G)) * sizeof(float2); }
 static size_t tile_smem(int G) { return (size_t)(G + G * kTile) * sizeof(float2); }
 
 mrf_status launch_rows_fwd(const mrf_plan_s* p, const float2* src, int src_mode, int K, int nf, float2* h1,
