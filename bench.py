@@ -267,6 +267,7 @@ def algorithmic_work(kernel, inp):
         "k_cols_interp": ("hbm", T * (frame_h1 + ns * 8 + ns * 8 + ns * 8)),
         # spread + column IFFT: samples read + H1 written
         "k_spread_cols": ("hbm", T * (ns * 8 + ns * 8 + frame_h1)),
+        "k_spread_gather": ("hbm", T * (ns * 8 + ns * 8 + frame_h1)),     # the sorted-gather form, same bytes
         # row IFFT + subspace reduction: H1 read + partial coefficient images
         "k_rows_adj_reduce": ("hbm", T * frame_h1),
         "k_rows_fwd": ("hbm", T * (n * n * 8 + frame_h1)),
@@ -993,7 +994,7 @@ def svt_hbm_bytes(inp):
 
 
 ROOF_KERNELS = {"chosen": ["k_match_tc", "k_svt", "k_knn_tc", "k_graph_blocks"],
-                "plain": ["k_rows_fwd_expand", "k_cols_interp", "k_spread_cols", "k_rows_adj_reduce", "k_match_fp32"]}
+                "plain": ["k_rows_fwd_expand", "k_cols_interp", "k_spread_gather", "k_rows_adj_reduce", "k_match_fp32"]}
 
 
 def run_reference(args, dist):

@@ -458,6 +458,84 @@ __global__ void __launch_bounds__(kColThreads, 3) k_spread_cols(const float2* __
     }
 }
 
+// Frame-form adjoint stage 1 as a sorted gather: the strip's (point, sample,
+// weight) entries of its frame's interleaf group, ordered by point.  Each
+// thread reduces a run of kSpRun consecutive entries and adds a partial sum
+// to the tile only where the point changes, so the crowded k-space centre
+// costs a few shared-memory adds instead of contended atomics per tap.  Then
+// the inverse FFT of the strip's columns and the image rows, as k_spread_cols.
+constexpr int kSpRun = 8;
+
+template <int G>
+__global__ void __launch_bounds__(kColThreads, G == 512 ? 2 : 3) k_spread_gather(const float2* __restrict__ y,
+                                                               float2* __restrict__ h1,
+                                                               const int* __restrict__ loc,
+                                                               const int* __restrict__ smp,
+                                                               const float* __restrict__ w,
+                                                               const int* __restrict__ off,
+                                                               const int* __restrict__ group_of, int ny, int ns,
+                                                               int nstrips) {
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* tile = sm + G;                 // [G][kTile]
+    float* tf = reinterpret_cast<float*>(tile);
+    const int strip = blockIdx.x, f = blockIdx.y;
+    const int c0 = strip * kTile;
+    fft_twiddles<G>(tw);
+    for (int i = threadIdx.x; i < G * kTile; i += kColThreads) tile[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int g = group_of[f];
+    const int beg = off[g * nstrips + strip], end = off[g * nstrips + strip + 1];
+    const float2* yf = y + (size_t)f * ns;
+    for (int b = beg + threadIdx.x * kSpRun; b < end; b += kColThreads * kSpRun) {
+        const int e = min(b + kSpRun, end);
+        int cur = loc[b];
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i = b; i < e; ++i) {
+            const int p = loc[i];
+            if (p != cur) {
+                atomicAdd(&tf[2 * cur], acc.x);
+                atomicAdd(&tf[2 * cur + 1], acc.y);
+                acc = make_float2(0.f, 0.f);
+                cur = p;
+            }
+            const float2 v = yf[smp[i]];
+            const float wi = w[i];
+            acc.x += wi * v.x;
+            acc.y += wi * v.y;
+        }
+        atomicAdd(&tf[2 * cur], acc.x);
+        atomicAdd(&tf[2 * cur + 1], acc.y);
+    }
+    __syncthreads();
+    float2* dst = h1 + (size_t)f * ny * G;
+    if constexpr (G == 512) {
+        // the tile's columns into registers, the register-resident four-step
+        // inverse transform, the image rows straight out of registers
+        const int c = threadIdx.x & 15, tq = threadIdx.x >> 4;
+        float2 x[32];
+#pragma unroll
+        for (int m = 0; m < 32; ++m) x[m] = tile[(tq + 16 * m) * kTile + c];
+        __syncthreads();                                // every read of the tile before it is reused
+        float2 out[2][16];
+        col512<true>(x, tile, tw, out);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) {
+                const int iy = centred<G>((2 * tq + j) + 32 * k2) + ny / 2;
+                if (iy >= 0 && iy < ny) dst[(size_t)iy * G + c0 + c] = out[j][k2];
+            }
+    } else {
+        fft_batch<G, kTile, kColThreads, true>(tile, kTile, 1, tw);
+        for (int idx = threadIdx.x; idx < ny * kTile; idx += kColThreads) {
+            const int iy = idx / kTile, c = idx & (kTile - 1);
+            const int gy = wrapg<G>(iy - ny / 2);
+            dst[(size_t)iy * G + c0 + c] = tile[gy * kTile + c];
+        }
+    }
+}
+
 // Grouped adjoint stage 1 without same-address contention: the contributions
 // of every group sample to the oversampled grid are precomputed as
 // (grid point, sample, weight) entries sorted by point.  Each thread reduces
@@ -913,11 +991,90 @@ mrf_status launch_cols_interp(const mrf_plan_s* p, const float2* h1, float2* y, 
     return MRF_OK;
 }
 
-mrf_status launch_spread_cols(const mrf_plan_s* p, const float2* y, int src_mode, int K, int nf, float2* h1,
+// The frame-form spread's sorted entries (host, double-precision KB weights as
+// the grouped gather table's), built once per plan; skipped (the atomic
+// spread then runs) beyond kFspMaxEntries entries.
+constexpr size_t kFspMaxEntries = (size_t)1 << 24;
+
+static mrf_status build_frame_spread(mrf_plan_s* p, cudaStream_t s) {
+    if (p->fsp_tried) return MRF_OK;
+    p->fsp_tried = true;
+    const int NG = p->ngroups, ns = p->ns, W = p->W, SAN = p->nstrips_a, G = p->gx;
+    if ((size_t)NG * ns * W * W > kFspMaxEntries || G != p->gy) return MRF_OK;
+    const double beta = p->beta_d;
+    std::vector<int4> grec((size_t)NG * ns);
+    MRF_CUDA(cudaMemcpyAsync(grec.data(), p->grec, sizeof(int4) * grec.size(), cudaMemcpyDeviceToHost, s));
+    MRF_CUDA(cudaStreamSynchronize(s));
+    auto kb = [&](double u) {
+        const double z = 2.0 * u / W;
+        const double arg = std::max(0.0, 1.0 - z * z);
+        return std::cyl_bessel_i(0.0, beta * std::sqrt(arg));
+    };
+    struct Ent { int key, loc, smp; float w; };
+    std::vector<int> foff((size_t)NG * SAN + 1, 0);
+    std::vector<int> floc, fsmp;
+    std::vector<float> fw;
+    floc.reserve((size_t)NG * ns * W * W);
+    fsmp.reserve(floc.capacity());
+    fw.reserve(floc.capacity());
+    std::vector<Ent> ents;
+    for (int g = 0; g < NG; ++g) {
+        ents.clear();
+        for (int j = 0; j < ns; ++j) {
+            const int4 r = grec[(size_t)g * ns + j];
+            const int mxw = r.y & 0xffff, myw = (r.y >> 16) & 0xffff;
+            float fxf, fyf;
+            std::memcpy(&fxf, &r.z, 4);
+            std::memcpy(&fyf, &r.w, 4);
+            for (int a = 0; a < W; ++a) {
+                const int col = (mxw + a) % G;
+                const double wa = kb((double)fxf - a);
+                for (int b = 0; b < W; ++b) {
+                    const int row = (myw + b) % G;
+                    const int loc = row * kTile + (col % kTile);
+                    ents.push_back({(col / kTile) * (G * kTile) + loc, loc, j, (float)(wa * kb((double)fyf - b))});
+                }
+            }
+        }
+        std::stable_sort(ents.begin(), ents.end(), [](const Ent& x, const Ent& y) { return x.key < y.key; });
+        for (const Ent& e : ents) {
+            foff[(size_t)g * SAN + e.key / (G * kTile) + 1]++;
+            floc.push_back(e.loc);
+            fsmp.push_back(e.smp);
+            fw.push_back(e.w);
+        }
+    }
+    for (size_t i = 0; i + 1 < foff.size(); ++i) foff[i + 1] += foff[i];
+    MRF_CUDA(cudaMalloc(&p->fsp_loc, sizeof(int) * std::max<size_t>(floc.size(), 1)));
+    MRF_CUDA(cudaMalloc(&p->fsp_smp, sizeof(int) * std::max<size_t>(fsmp.size(), 1)));
+    MRF_CUDA(cudaMalloc(&p->fsp_w, sizeof(float) * std::max<size_t>(fw.size(), 1)));
+    MRF_CUDA(cudaMemcpy(p->fsp_loc, floc.data(), sizeof(int) * floc.size(), cudaMemcpyHostToDevice));
+    MRF_CUDA(cudaMemcpy(p->fsp_smp, fsmp.data(), sizeof(int) * fsmp.size(), cudaMemcpyHostToDevice));
+    MRF_CUDA(cudaMemcpy(p->fsp_w, fw.data(), sizeof(float) * fw.size(), cudaMemcpyHostToDevice));
+    int* off = nullptr;
+    MRF_CUDA(cudaMalloc(&off, sizeof(int) * foff.size()));
+    MRF_CUDA(cudaMemcpy(off, foff.data(), sizeof(int) * foff.size(), cudaMemcpyHostToDevice));
+    p->fsp_off = off;
+    return MRF_OK;
+}
+
+mrf_status launch_spread_cols(mrf_plan_s* p, const float2* y, int src_mode, int K, int nf, float2* h1,
                               cudaStream_t s) {
     const int G = p->gy;
     dim3 grid(p->nstrips_a, nf);
     const size_t sm = tile_smem(G);
+    if (src_mode == 0) {
+        MRF_PROPAGATE(build_frame_spread(p, s));
+        if (p->fsp_off) {
+            MRF_DISPATCH_G(G, {
+                MRF_PROPAGATE(set_smem(k_spread_gather<GG>, sm));
+                k_spread_gather<GG><<<grid, kColThreads, sm, s>>>(y, h1, p->fsp_loc, p->fsp_smp, p->fsp_w, p->fsp_off,
+                                                                 p->group_of, p->ny, p->ns, p->nstrips_a);
+            });
+            MRF_LAUNCHED_AS("k_spread_gather", s);
+            return MRF_OK;
+        }
+    }
     MRF_DISPATCH_G(G, MRF_DISPATCH_W(p->W, {
         if (src_mode == 0) {
             MRF_PROPAGATE(set_smem(k_spread_cols<GG, WW, 0>, sm));
@@ -960,7 +1117,8 @@ mrf_status launch_rows_adj(const mrf_plan_s* p, const float2* h1, float2* dst, i
 // ---------------------------------------------------------------------------
 static void free_plan(mrf_plan_s* p) {
     if (!p) return;
-    void* ptrs[] = {p->inv_dx, p->inv_dy, p->fwd_rec, p->fwd_off, p->adj_rec, p->adj_off, p->fwd_w, p->adj_w, p->grec,
+    void* ptrs[] = {p->inv_dx, p->inv_dy, p->fwd_rec, p->fwd_off, p->adj_rec, p->adj_off, p->fwd_w, p->adj_w,
+                    p->fsp_off, p->fsp_loc, p->fsp_smp, p->fsp_w, p->grec,
                     p->group_of, p->gf_off, p->gf, p->h1, p->sub_h1, p->sub_spec, p->sub_Y, p->sub_R,
                     p->sub_partial, p->gat_off, p->gat_pt, p->gat_smp, p->gat_w};
     for (void* q : ptrs)

@@ -19,6 +19,14 @@ struct mrf_plan_s {
     int4* adj_rec = nullptr;      // samples by (group, every adjoint strip they touch)
     float* fwd_w = nullptr;       // [fwd_rec entries][2 W] KB weights of each record: W along x, then W along y
     float* adj_w = nullptr;       // [adj_rec entries][2 W] the same for the adjoint records
+    // frame-form spread as a sorted gather: every (group sample, tap) entry
+    // ordered by (group, adjoint strip, point within the strip); built at the
+    // first frame-form adjoint unless too large (then the atomic spread runs)
+    int* fsp_off = nullptr;       // [ngroups * nstrips_a + 1] (also marks the table as built)
+    int* fsp_loc = nullptr;       // point within the strip: gy * strip width + column
+    int* fsp_smp = nullptr;       // sample index within the group's frame
+    float* fsp_w = nullptr;       // KB weight of the tap
+    bool fsp_tried = false;       // the build was attempted (it may have been skipped)
     int* adj_off = nullptr;       // [ngroups * nstrips_a + 1]
     int4* grec = nullptr;         // samples in (group, index) order
     int* group_of = nullptr;      // [T]
