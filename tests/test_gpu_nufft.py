@@ -34,6 +34,8 @@ def _case(n, T, ns, interleaves, width=4, seed=0):
     (256, 3, 2048, 48, 4),    # G = 512, the 256^2 spiral arm of 2048 samples
     (192, 4, 1536, 3, 4),     # G = 384 = 3 x 128: the mixed-radix FFT (192^2 serving slices)
     (48, 5, 400, -1, 6),      # G = 96 = 3 x 32 is not a supported grid: checked below
+    (32, 600, 2048, -1, 4),   # 600 distinct frames x 2048 samples x 16 taps: beyond the sorted
+                              # spread table's 2^24 entries, so the adjoint takes the atomic spread
 ])
 def test_forward_adjoint_match_oracle(n, T, ns, il, w):
     m = mrf()
