@@ -85,6 +85,21 @@ __global__ void k_norm2_acc(const float2* __restrict__ x, size_t n, double* __re
     if (threadIdx.x == 0) atomicAdd(acc, d);
 }
 
+// part[b] = block b's sum of |x_i|^2, the same split of x as k_norm2_acc
+// (kNorm2Blocks blocks); k_cost adds the parts in block order, so the sum is
+// the same on every run.
+__global__ void k_norm2_part(const float2* __restrict__ x, size_t n, double* __restrict__ part) {
+    float s = 0.f;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n / 2; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 q = x4[i];
+        s += q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) s += cabs2(x[n - 1]);
+    const double d = block_sum((double)s);
+    if (threadIdx.x == 0) part[blockIdx.x] = d;
+}
+
 // re/im of sum conj(a) b
 __global__ void k_dot_acc(const float2* __restrict__ a, const float2* __restrict__ b, size_t n,
                           double* __restrict__ acc) {
@@ -376,24 +391,59 @@ __global__ void k_edge_weights(const int* __restrict__ nbr, const unsigned* __re
     atomicAdd(&rcnt[nbr[e]], 1);
 }
 
-// exclusive scan of n counts (one block)
-__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cnt, int n, int* __restrict__ off) {
-    __shared__ int part[1024];
+// Neighbour lists of the graph term are cut into chunks of kGbSplit entries
+// (the knn forward entries, then the reverse list).  The patch's own block
+// takes the first chunk; each further chunk is an extra work item whose
+// partial sum its own block writes, and the last of the patch's blocks to
+// finish adds them to the first chunk's sum in chunk order.  The patches of a flat region tie at distance 0, and
+// ties go to the lower index, so they all name the region's lowest-index
+// patches: a few patches collect reverse lists of a thousand entries or more
+// against a mean of knn, which one block would otherwise read alone.
+constexpr int kGbSplit = 32;
+__host__ __device__ inline int gb_extra_chunks(int nq) { return nq > kGbSplit ? (nq - 1) / kGbSplit : 0; }
+// an upper bound of the extra chunks of a graph (sum of (nq - 1) / kGbSplit,
+// with sum nq = 2 np knn)
+inline int gb_max_extra(int np, int knn) { return (int)((2LL * np * knn) / kGbSplit) + 1; }
+
+// Exclusive scans of the reverse counts (off: list offsets) and of the patches'
+// extra chunks (xoff), the patch of every extra chunk (xpatch[xoff[n]]), and
+// zeroed fold counts (xcnt), in one block.
+__global__ void __launch_bounds__(1024) k_scan_graph(const int* __restrict__ cnt, int n, int knn,
+                                                     int* __restrict__ off, int* __restrict__ xoff,
+                                                     int* __restrict__ xpatch, int* __restrict__ xcnt) {
+    __shared__ int part[1024], xpart[1024];
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int b = threadIdx.x * per, e = min(n, b + per);
-    int s = 0;
-    for (int i = b; i < e; ++i) s += cnt[i];
+    int s = 0, xs = 0;
+    for (int i = b; i < e; ++i) {
+        s += cnt[i];
+        xs += gb_extra_chunks(knn + cnt[i]);
+    }
     part[threadIdx.x] = s;
+    xpart[threadIdx.x] = xs;
     __syncthreads();
     for (int o = 1; o < (int)blockDim.x; o <<= 1) {
         const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        const int xv = threadIdx.x >= (unsigned)o ? xpart[threadIdx.x - o] : 0;
         __syncthreads();
         part[threadIdx.x] += v;
+        xpart[threadIdx.x] += xv;
         __syncthreads();
     }
-    int run = part[threadIdx.x] - s;
-    for (int i = b; i < e; ++i) { off[i] = run; run += cnt[i]; }
-    if (threadIdx.x == blockDim.x - 1) off[n] = part[threadIdx.x];
+    int run = part[threadIdx.x] - s, xrun = xpart[threadIdx.x] - xs;
+    for (int i = b; i < e; ++i) {
+        off[i] = run;
+        xoff[i] = xrun;
+        xcnt[i] = 0;
+        run += cnt[i];
+        const int nx = gb_extra_chunks(knn + cnt[i]);
+        for (int c = 0; c < nx; ++c) xpatch[xrun + c] = i;
+        xrun += nx;
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        off[n] = part[threadIdx.x];
+        xoff[n] = xpart[threadIdx.x];
+    }
 }
 
 __global__ void k_fill_reverse(const int* __restrict__ nbr, const float* __restrict__ w, int ne, int knn,
@@ -502,68 +552,154 @@ __global__ void k_lambda(const float* __restrict__ lmax, float lam1_0, int liter
 // (offset of the neighbour patch's first coefficient, w / 2), so the inner
 // loop is one gather and two FMAs per coefficient and neighbour.  (Pairs of
 // coefficients per 16-byte load halve the loads but leave fewer in flight
-// per warp; measured slower on this latency-bound kernel.)
+// per warp; measured slower on this latency-bound kernel.)  With xoff set
+// (Q(X)L), a list longer than kGbSplit entries is cut: the patch's block
+// reads its first kGbSplit entries, and each further chunk gets a block of
+// its own (blocks [0, xoff[np]), ahead of the patches' blocks) that writes
+// its partial sum to xpart.  Each of these blocks then counts itself in
+// xcnt[j] (after a fence); the last of patch j's blocks adds the partials to
+// QL_j in chunk order (the same order whichever block is last) and resets
+// the count.  No block waits for another.  Grid: np blocks, plus
+// gb_max_extra(np, knn) with xoff.
 constexpr int kGbThreads = 128;
 constexpr int kGbChunk = 256;
 constexpr int kGbElems = 5;      // 8 x 8 x 10 coefficients = 5 per thread: no idle slots, 55 registers
+static_assert(kGbChunk >= kGbSplit, "a cut chunk is staged in one round");
 
-__global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __restrict__ alpha, PatchGeom g, int K,
-                                                             const int* __restrict__ nbr,
-                                                             const float* __restrict__ w, int knn,
-                                                             const int* __restrict__ roff,
-                                                             const int* __restrict__ rsrc,
-                                                             const float* __restrict__ rw,
-                                                             const float* __restrict__ deg, int rev,
-                                                             float2* __restrict__ QL, double* __restrict__ trace) {
+// v[u] -= wscale * w_q * (coefficient off[u] of neighbour patch i_q), q in
+// [q0, q1) of patch j's list (forward entries q < knn, then the reverse list
+// from rb); a block-wide call (stages the list in s_off / s_w).
+__device__ __forceinline__ void gb_gather(const float2* __restrict__ alpha, const PatchGeom& g, int K, int j,
+                                          const int* __restrict__ nbr, const float* __restrict__ w, int knn,
+                                          int rb, const int* __restrict__ rsrc, const float* __restrict__ rw,
+                                          float wscale, int q0, int q1, const int (&off)[kGbElems],
+                                          float2 (&v)[kGbElems], int* s_off, float* s_w) {
+    for (int c0 = q0; c0 < q1; c0 += kGbChunk) {
+        const int cn = min(kGbChunk, q1 - c0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cn; t += kGbThreads) {
+            const int q = c0 + t;
+            int i;
+            float wq;
+            if (q < knn) { i = nbr[(size_t)j * knn + q]; wq = w[(size_t)j * knn + q]; }
+            else { i = rsrc[rb + q - knn]; wq = rw[rb + q - knn]; }
+            s_off[t] = (g.origin(i / g.cnt) * g.n + g.origin(i % g.cnt)) * K;
+            s_w[t] = wscale * wq;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int t = 0; t < cn; ++t) {
+            const float2* src = alpha + s_off[t];
+            const float wt = s_w[t];
+#pragma unroll
+            for (int u = 0; u < kGbElems; ++u) {
+                if (off[u] >= 0) {
+                    const float2 b = src[off[u]];
+                    v[u].x -= wt * b.x;
+                    v[u].y -= wt * b.y;
+                }
+            }
+        }
+    }
+}
+
+// coefficient offsets (within a patch, relative to its first coefficient in
+// the image) of this thread's kGbElems coefficients of pass e0, -1 past ne
+__device__ __forceinline__ void gb_offsets(const PatchGeom& g, int K, int pK, int ne, int e0,
+                                           int (&off)[kGbElems]) {
+#pragma unroll
+    for (int u = 0; u < kGbElems; ++u) {
+        const int e = e0 + threadIdx.x + u * kGbThreads;
+        const int py = e / pK, rem = e - py * pK;      // rem = px * K + k
+        off[u] = e < ne ? py * g.n * K + rem : -1;
+    }
+}
+
+// Block-wide: count this block in xcnt[j] once its writes are visible; the
+// last of patch j's nx + 1 blocks folds the chunks' partial sums
+// xpart[xoff[j] ..] into QL_j, in chunk order, with L2 reads (other SMs
+// wrote them), and resets the count.
+__device__ __forceinline__ void gb_count_and_fold(int j, int ne, const int* __restrict__ xoff,
+                                                  int* __restrict__ xcnt, float2* __restrict__ xpart,
+                                                  float2* __restrict__ QL, int* s_last) {
+    __threadfence();
+    __syncthreads();
+    const int x0 = xoff[j], x1 = xoff[j + 1];
+    if (threadIdx.x == 0) *s_last = atomicAdd(&xcnt[j], 1) == x1 - x0;
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) xcnt[j] = 0;
+    for (int e = threadIdx.x; e < ne; e += kGbThreads) {
+        float2 v = __ldcg(QL + (size_t)j * ne + e);
+#pragma unroll 4
+        for (int x = x0; x < x1; ++x) v = cadd(v, __ldcg(xpart + (size_t)x * ne + e));
+        QL[(size_t)j * ne + e] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kGbThreads, 9) k_graph_blocks(const float2* __restrict__ alpha, PatchGeom g,
+                                                                int K, const int* __restrict__ nbr,
+                                                                const float* __restrict__ w, int knn,
+                                                                const int* __restrict__ roff,
+                                                                const int* __restrict__ rsrc,
+                                                                const float* __restrict__ rw,
+                                                                const float* __restrict__ deg, int rev,
+                                                                const int* __restrict__ xoff,
+                                                                const int* __restrict__ xpatch,
+                                                                float2* __restrict__ xpart, int* __restrict__ xcnt,
+                                                                float2* __restrict__ QL, double* __restrict__ trace) {
     __shared__ int s_off[kGbChunk];
     __shared__ float s_w[kGbChunk];
-    const int j = blockIdx.x;
+    __shared__ int s_last;
+    const int np = g.count();
     const int pK = g.p * K;
     const int ne = g.p * pK;
+    const bool cut = rev && xoff;
+    const int X = cut ? xoff[np] : 0;
+    if ((int)blockIdx.x < X) {
+        // extra chunk x of patch j = xpatch[x]: list entries [c kGbSplit,
+        // (c + 1) kGbSplit), c = 1 + x - xoff[j]; its partial sum
+        // -1/2 sum w Q_i goes to xpart[x][p x p x K].  These blocks come
+        // first, so the longest chains start while the patches' blocks run.
+        const int x = blockIdx.x;
+        const int j = xpatch[x];
+        const int rb = roff[j], nq = knn + roff[j + 1] - rb;
+        const int q0 = (1 + x - xoff[j]) * kGbSplit, q1 = min(nq, q0 + kGbSplit);
+        for (int e0 = 0; e0 < ne; e0 += kGbThreads * kGbElems) {
+            int off[kGbElems];
+            float2 v[kGbElems];
+            gb_offsets(g, K, pK, ne, e0, off);
+#pragma unroll
+            for (int u = 0; u < kGbElems; ++u) v[u] = make_float2(0.f, 0.f);
+            gb_gather(alpha, g, K, j, nbr, w, knn, rb, rsrc, rw, 0.5f, q0, q1, off, v, s_off, s_w);
+#pragma unroll
+            for (int u = 0; u < kGbElems; ++u)
+                if (off[u] >= 0) xpart[(size_t)x * ne + e0 + threadIdx.x + u * kGbThreads] = v[u];
+        }
+        gb_count_and_fold(j, ne, xoff, xcnt, xpart, QL, &s_last);
+        return;
+    }
+    const int j = (int)blockIdx.x - X;
+    if (j >= np) return;
     const int jy = g.origin(j / g.cnt), jx = g.origin(j % g.cnt);
     const float dj = deg[j];
     const int rb = rev ? roff[j] : 0, re = rev ? roff[j + 1] : 0;
     const int nq = knn + (rev ? re - rb : 0);
     const float wscale = rev ? 0.5f : 1.0f;
+    const bool split = cut && xoff[j + 1] > xoff[j];
+    const int q1 = split ? kGbSplit : nq;           // the list's first chunk, or all of it
     float tr = 0.f;                 // this thread's share (kGbElems terms a pass), in FP32
     for (int e0 = 0; e0 < ne; e0 += kGbThreads * kGbElems) {
         int off[kGbElems];
         float2 a[kGbElems], v[kGbElems];
+        gb_offsets(g, K, pK, ne, e0, off);
 #pragma unroll
         for (int u = 0; u < kGbElems; ++u) {
-            const int e = e0 + threadIdx.x + u * kGbThreads;
-            const int py = e / pK, rem = e - py * pK;      // rem = px * K + k
-            off[u] = e < ne ? py * g.n * K + rem : -1;
-            a[u] = e < ne ? alpha[((size_t)jy * g.n + jx) * K + off[u]] : make_float2(0.f, 0.f);
+            a[u] = off[u] >= 0 ? alpha[((size_t)jy * g.n + jx) * K + off[u]] : make_float2(0.f, 0.f);
             v[u] = cscale(a[u], dj);
         }
-        for (int c0 = 0; c0 < nq; c0 += kGbChunk) {
-            const int cn = min(kGbChunk, nq - c0);
-            __syncthreads();
-            for (int t = threadIdx.x; t < cn; t += kGbThreads) {
-                const int q = c0 + t;
-                int i;
-                float wq;
-                if (q < knn) { i = nbr[(size_t)j * knn + q]; wq = w[(size_t)j * knn + q]; }
-                else { i = rsrc[rb + q - knn]; wq = rw[rb + q - knn]; }
-                s_off[t] = (g.origin(i / g.cnt) * g.n + g.origin(i % g.cnt)) * K;
-                s_w[t] = wscale * wq;
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int t = 0; t < cn; ++t) {
-                const float2* src = alpha + s_off[t];
-                const float wt = s_w[t];
-#pragma unroll
-                for (int u = 0; u < kGbElems; ++u) {
-                    if (off[u] >= 0) {
-                        const float2 b = src[off[u]];
-                        v[u].x -= wt * b.x;
-                        v[u].y -= wt * b.y;
-                    }
-                }
-            }
-        }
+        gb_gather(alpha, g, K, j, nbr, w, knn, rb, rsrc, rw, wscale, 0, q1, off, v, s_off, s_w);
 #pragma unroll
         for (int u = 0; u < kGbElems; ++u) {
             if (off[u] < 0) continue;
@@ -572,6 +708,7 @@ __global__ void __launch_bounds__(kGbThreads) k_graph_blocks(const float2* __res
             if (trace) tr += a[u].x * v[u].x + a[u].y * v[u].y;
         }
     }
+    if (split) gb_count_and_fold(j, ne, xoff, xcnt, xpart, QL, &s_last);
     if (trace) {
         const double t = block_sum((double)tr);     // the patch's share in FP64
         if (threadIdx.x == 0) trace[j] = t;         // k_cost sums the shares in order
@@ -637,19 +774,26 @@ __global__ void k_xupdate(float2* __restrict__ alpha, const float2* __restrict__
     alpha[e] = cscale(cadd(z, cscale(qp, c)), 1.f / den);
 }
 
-// acc: [0] ||r||^2, [2] sum of nuclear norms; trace: the np patches' shares
-// of Tr(Q L Q^H), summed here in a fixed order (one block).  The cost goes to
+// The cost of Algorithm 1 from its shares, each summed in a fixed order (one
+// block), so that it is the same on every run: shares[0, np) the patches'
+// shares of Tr(Q L Q^H), shares[np, 2 np) their nuclear norms, shares[2 np,
+// 2 np + kNorm2Blocks) the blocks' parts of ||r||^2.  The cost goes to
 // cost[*slot], and the slot moves on (the iteration count modulo cap, kept on
 // the device so that a recorded iteration replays unchanged).
-__global__ void k_cost(const double* __restrict__ acc, const double* __restrict__ trace, int np,
-                       const float* __restrict__ lam1, float lam2, double* __restrict__ cost,
-                       int* __restrict__ slot, int cap) {
-    double t = 0.0;
-    for (int j = threadIdx.x; j < np; j += blockDim.x) t += trace[j];
+__global__ void k_cost(const double* __restrict__ shares, int np, const float* __restrict__ lam1, float lam2,
+                       double* __restrict__ cost, int* __restrict__ slot, int cap) {
+    double t = 0.0, nu = 0.0, r2 = 0.0;
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+        t += shares[j];
+        nu += shares[np + j];
+    }
+    for (int j = threadIdx.x; j < kNorm2Blocks; j += blockDim.x) r2 += shares[2 * np + j];
     t = block_sum(t);
+    nu = block_sum(nu);
+    r2 = block_sum(r2);
     if (threadIdx.x == 0) {
         const int q = *slot;
-        cost[q] = 0.5 * acc[0] + (double)(*lam1) * t + (double)lam2 * acc[2];
+        cost[q] = 0.5 * r2 + (double)(*lam1) * t + (double)lam2 * nu;
         *slot = q + 1 == cap ? 0 : q + 1;
     }
 }
@@ -693,14 +837,20 @@ struct mrf_recon_s {
     mrf::KnnWorkspace knn;      // kNN scratch (operand tiles, per-partition lists)
     float *w = nullptr, *rw = nullptr, *deg = nullptr;
     int *rcnt = nullptr, *roff = nullptr, *rpos = nullptr, *rsrc = nullptr, *rsrc_tmp = nullptr;
+    // the graph term's cut lists: extra-chunk offsets [np + 1], patch of each
+    // extra chunk and the chunks' partial sums [gb_max_extra][p x p x K]
+    int *xoff = nullptr, *xpatch = nullptr, *xcnt = nullptr;     // xcnt: [np] blocks done per cut patch
+    float2* xpart = nullptr;
     float* rw_tmp = nullptr;
     float* scal = nullptr;      // [0] sigma2, [1] lmax, [2] lam1, [3] scratch, [4] lam1 of the cost
     // the forward graph (nbr, w, deg) as the iteration began, read by the
     // cost trace while the rebuild replaces the live copy (concurrent mode)
     int* nbr_c = nullptr;
     float *w_c = nullptr, *deg_c = nullptr;
-    double* acc = nullptr;      // [0] ||r||^2, [1] (unused), [2] nuclear, [3..4] dot
-    double* trace = nullptr;    // [np] the patches' shares of Tr(Q L Q^H)
+    double* acc = nullptr;      // [0..1] dot, [2] norm (the power iteration for a)
+    // [np] the patches' shares of Tr(Q L Q^H), [np] their nuclear norms,
+    // [kNorm2Blocks] the blocks' parts of ||r||^2 (summed by k_cost)
+    double* trace = nullptr;
     int* cost_slot = nullptr;   // [1] where the next cost goes (iterations done modulo cost_cap)
     cudaGraphExec_t iter_exec = nullptr;   // one recorded iteration (replayed), or none
     long long iter_kernels = 0;            // kernels in it
@@ -813,8 +963,8 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
     MRF_CUDA(cudaMemsetAsync(R->rpos, 0, sizeof(int) * np, s));
     k_edge_weights<<<(ne + 255) / 256, 256, 0, s>>>(R->nbr, R->d2, ne, R->scal + 0, R->w, R->rcnt);
     MRF_LAUNCHED_AS("k_edge_weights", s);
-    k_scan<<<1, 1024, 0, s>>>(R->rcnt, np, R->roff);
-    MRF_LAUNCHED_AS("k_scan", s);
+    k_scan_graph<<<1, 1024, 0, s>>>(R->rcnt, np, knn, R->roff, R->xoff, R->xpatch, R->xcnt);
+    MRF_LAUNCHED_AS("k_scan_graph", s);
     k_fill_reverse<<<(ne + 255) / 256, 256, 0, s>>>(R->nbr, R->w, ne, knn, R->roff, R->rpos, R->rsrc_tmp,
                                                    R->rw_tmp);
     MRF_LAUNCHED_AS("k_fill_reverse", s);
@@ -913,9 +1063,13 @@ static mrf_status learned_maps(mrf_recon_s* R, cudaStream_t s) {
 // forward kNN entries alone into trace[np], of the live graph or (snap) of
 // the copy taken when the iteration began
 static mrf_status graph_pass(mrf_recon_s* R, float2* QL, double* trace, cudaStream_t s, bool snap = false) {
-    k_graph_blocks<<<R->np, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, snap ? R->nbr_c : R->nbr,
-                                                snap ? R->w_c : R->w, R->prm.knn, R->roff, R->rsrc, R->rw,
-                                                snap ? R->deg_c : R->deg, QL ? 1 : 0, QL, trace);
+    // Q(X)L reads the reverse lists, which only the live graph has, and cuts
+    // the long ones (extra chunks first in the grid)
+    const int grid = R->np + (QL ? gb_max_extra(R->np, R->prm.knn) : 0);
+    k_graph_blocks<<<grid, kGbThreads, 0, s>>>(R->alpha, R->g, R->K, snap ? R->nbr_c : R->nbr, snap ? R->w_c : R->w,
+                                               R->prm.knn, R->roff, R->rsrc, R->rw, snap ? R->deg_c : R->deg,
+                                               QL ? 1 : 0, QL ? R->xoff : nullptr, R->xpatch, R->xpart, R->xcnt, QL,
+                                               trace);
     MRF_LAUNCHED_AS(QL ? "k_graph_blocks" : "k_graph_blocks(trace)", s);
     return MRF_OK;
 }
@@ -934,15 +1088,13 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
     MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, s));
     // the next pass's gradient of the data term, A*(r), from this residual
     MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, s));
-    if (cost) MRF_CUDA(cudaMemsetAsync(R->acc, 0, 3 * sizeof(double), s));
-    MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, s));
+    MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->trace + R->np : nullptr, s));
     if (cost) {
         const size_t nr = (size_t)R->plan->T * R->plan->ns;
-        k_norm2_acc<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->acc + 0);
-        MRF_LAUNCHED_AS("k_norm2_acc", s);
+        k_norm2_part<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->trace + 2 * (size_t)R->np);
+        MRF_LAUNCHED_AS("k_norm2_part", s);
         MRF_PROPAGATE(graph_pass(R, nullptr, R->trace, s));
-        k_cost<<<1, 1024, 0, s>>>(R->acc, R->trace, R->np, R->scal + 2, R->prm.lam2, R->cost, R->cost_slot,
-                                  R->cost_cap);
+        k_cost<<<1, 1024, 0, s>>>(R->trace, R->np, R->scal + 2, R->prm.lam2, R->cost, R->cost_slot, R->cost_cap);
         MRF_LAUNCHED_AS("k_cost", s);
     }
     return MRF_OK;
@@ -957,7 +1109,7 @@ static mrf_status iteration_pre(mrf_recon_s* R, int it, bool cost, cudaStream_t 
 // The forward operator, the SVT and the matching all read only the new
 // iterate; the graph rebuild only the new maps; the cost trace reads the copy
 // of the graph taken at the start, so the rebuild need not wait for it; the
-// accumulators they add to are distinct slots.  The data term's gradient
+// shares they write are distinct ranges.  The data term's gradient
 // A*(r) for the next pass is computed as soon as this pass's residual is
 // (create and restore compute the first one), so it runs beside the matching
 // and the graph rebuild instead of beside the next graph term.
@@ -994,13 +1146,12 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
         R->alpha, R->grad, R->QL, R->P, R->g, R->K, R->prm.mu, c, R->scal + 2,
         (R->prm.flags & MRF_RECON_LITERAL_XUPDATE) ? 1 : 0, nullptr);
     MRF_LAUNCHED_AS("k_xupdate", s);
-    if (cost) MRF_CUDA(cudaMemsetAsync(R->acc, 0, 3 * sizeof(double), s));
     MRF_CUDA(cudaEventRecord(R->ev[2], s));                  // the new iterate
     MRF_CUDA(cudaStreamWaitEvent(sb, R->ev[2], 0));
     MRF_CUDA(cudaStreamWaitEvent(sc, R->ev[2], 0));
     mark(sb);
     mark(sc);
-    MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->acc + 2 : nullptr, sb));
+    MRF_PROPAGATE(svt(R, R->alpha, R->P, cost ? R->trace + R->np : nullptr, sb));
     if (cost) MRF_PROPAGATE(graph_pass(R, nullptr, R->trace, sb, true));     // trace with this iteration's graph
     MRF_CUDA(cudaEventRecord(R->ev[3], sb));
     if (R->prm.flags & MRF_RECON_LEARNED) MRF_PROPAGATE(learned_maps(R, sc));
@@ -1010,8 +1161,8 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, s));
     if (cost) {
         const size_t nr = (size_t)R->plan->T * R->plan->ns;
-        k_norm2_acc<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->acc + 0);
-        MRF_LAUNCHED_AS("k_norm2_acc", s);
+        k_norm2_part<<<kNorm2Blocks, 256, 0, s>>>(R->r, nr, R->trace + 2 * (size_t)R->np);
+        MRF_LAUNCHED_AS("k_norm2_part", s);
     }
     // the next pass's gradient of the data term, A*(r), beside the matching
     // and graph rebuild (it needs only this residual)
@@ -1020,8 +1171,7 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     MRF_CUDA(cudaStreamWaitEvent(s, R->ev[4], 0));
     mark(s);
     if (cost) {
-        k_cost<<<1, 1024, 0, s>>>(R->acc, R->trace, R->np, R->scal + 4, R->prm.lam2, R->cost, R->cost_slot,
-                                  R->cost_cap);
+        k_cost<<<1, 1024, 0, s>>>(R->trace, R->np, R->scal + 4, R->prm.lam2, R->cost, R->cost_slot, R->cost_cap);
         MRF_LAUNCHED_AS("k_cost", s);
     }
     return MRF_OK;
@@ -1069,9 +1219,16 @@ static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     MRF_PROPAGATE(dalloc(R, &R->rcnt, np));
     MRF_PROPAGATE(dalloc(R, &R->rpos, np));
     MRF_PROPAGATE(dalloc(R, &R->roff, np + 1));
+    {
+        const int xmax = mrf::gb_max_extra(np, knn);
+        MRF_PROPAGATE(dalloc(R, &R->xoff, np + 1));
+        MRF_PROPAGATE(dalloc(R, &R->xpatch, xmax));
+        MRF_PROPAGATE(dalloc(R, &R->xpart, (size_t)xmax * R->pp * K));
+        MRF_PROPAGATE(dalloc(R, &R->xcnt, np));
+    }
     MRF_PROPAGATE(dalloc(R, &R->scal, 8));
     MRF_PROPAGATE(dalloc(R, &R->acc, 8));
-    MRF_PROPAGATE(dalloc(R, &R->trace, (size_t)np));
+    MRF_PROPAGATE(dalloc(R, &R->trace, 2 * (size_t)np + kNorm2Blocks));
     MRF_PROPAGATE(dalloc(R, &R->cost_slot, 1));
     MRF_CUDA(cudaMemsetAsync(R->cost_slot, 0, sizeof(int), s));
     R->svt_kp = K <= 4 ? 4 : K <= 8 ? 8 : K == 10 ? 10 : K <= 12 ? 12 : 16;

@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(128, 4)
         nsum += sg;
         f[k] = sg > tau ? (sg - tau) / sg : 0.f;
     }
-    if (nuc && active && sl == 0) atomicAdd(nuc, (double)nsum);
+    if (nuc && active && sl == 0) nuc[j] = (double)nsum;     // the patch's share, summed in order later
     if (stats) {
         // block totals first: one atomic pair per block instead of per patch
         __shared__ unsigned s_sweeps, s_rots;

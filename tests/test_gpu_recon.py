@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import dictionary, epg, match as omatch, nufft as onufft, recon as orecon
+from oracle import dictionary, epg, graph as ograph, match as omatch, nufft as onufft, recon as orecon
 from gpu_util import as_f32_inputs, c64, f32, mrf, np_, rand_c, rel
 
 pytestmark = pytest.mark.gpu
@@ -280,3 +280,18 @@ def test_plain_configuration_at_rank_10_follows_oracle(prob10):
 def test_svt_instantiations_follow_oracle(patch, stride, K):
     pr = problem(K=K)
     _follow_oracle(pr, mode=0, iters=2, tol=1e-4, prec=0, patch=patch, stride=stride, knn=10)
+
+
+def test_cut_neighbour_lists_follow_oracle():
+    """The patches of a flat region tie at distance 0 and all name the
+    region's lowest-index patches, whose reverse lists grow far past the mean
+    of 2 knn entries.  The graph term cuts every list longer than 64 entries:
+    separate blocks sum the chunks after the first, and the patch's block
+    adds them in chunk order.  8 x 8 patches at stride 2 on a 64 x 64 image
+    (841 patches, 10 neighbours) give lists of more than 128 entries (two
+    extra chunks); the loop follows the oracle through them."""
+    pr = problem(n=64)
+    r, o = _follow_oracle(pr, mode=0, iters=2, tol=1e-4, prec=0, patch=8, stride=2, knn=10)
+    F = ograph.features(o.maps[1], o.maps[2], o.pg, o.t1max, o.t2max)
+    nbr, _ = ograph.knn(F, 10)
+    assert 10 + np.bincount(nbr.ravel(), minlength=F.shape[0]).max() > 128
