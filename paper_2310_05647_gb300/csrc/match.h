@@ -57,6 +57,8 @@ struct TcSlice {
     const unsigned char* Bg;     // tensor-core operand of the slice's dictionary
     const float* wscore;         // score weights
     const float2* dict;          // FP32 dictionary (re-rank)
+    int* cand = nullptr;         // [n][kTopK] the previous call's candidates in (seeds, -1: none), this
+                                 // call's out; null: no seeding (always null at FP8)
 };
 // build (or reuse) the tensor-core operand of dict in ws
 mrf_status tc_prepare_operand(MatchWorkspace& ws, const float2* dict, int m, int len, int prec, cudaStream_t s);

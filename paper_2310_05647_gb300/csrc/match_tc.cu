@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restri
         dict = slices[si].dict;
         n0 = ((int)blockIdx.x - slices[si].block0) * kTcRows;
         if (n0 >= n) return;    // a launch sized for more rows than the slice holds (n written on the device)
-        seed = nullptr;
-        cand_out = nullptr;
+        seed = F8 ? nullptr : slices[si].cand;
+        cand_out = F8 ? nullptr : slices[si].cand;
     }
 
     if (warp == 0) {

@@ -1177,16 +1177,6 @@ static mrf_status iteration(mrf_recon_s* R, int it, cudaStream_t s) {
     return MRF_OK;
 }
 
-static double read_double(const double* d, cudaStream_t s, mrf_status* st) {
-    double h = 0.0;
-    if (cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        *st = MRF_ECUDA;
-        set_error("device read failed: %s", cudaGetErrorString(cudaGetLastError()));
-    }
-    return h;
-}
-
 static mrf_status create(mrf_recon_s* R, const float2* b, cudaStream_t s) {
     mrf_plan_s* p = R->plan;
     const int K = R->K, N = R->N, np = R->np, knn = R->prm.knn;
@@ -1637,19 +1627,24 @@ extern "C" mrf_status mrf_recon_restore(mrf_recon R, const void* buf, size_t byt
 
 // ---------------------------------------------------------------------------
 // Batched serving: S independent slices (their own plans and sizes, one
-// shared dictionary) advanced together.  One batched iteration forks the
-// slices' pre-matching steps onto one stream each, matches every slice's
-// fingerprints in a single tensor-core launch (a slice table maps the
-// launch's blocks to slices), and forks again for the per-slice matching
-// epilogue and graph rebuild.  The first mrf_batch_iter runs one iteration
+// shared dictionary) advanced together.  One batched iteration forks each
+// slice's graph term and X update onto a stream of its own; from the new
+// iterate on, the slice's SVT and its forward operator + next gradient run on
+// two more streams, while one tensor-core launch matches every slice's
+// fingerprints (a slice table maps the launch's blocks to slices) as soon as
+// all iterates are new; each slice's matching epilogue and graph rebuild
+// follow it, and everything joins at the end.  The first mrf_batch_iter runs one iteration
 // eagerly (lazy tables, the spread autotuner, the warm SVT state) and then
 // captures the fork/join sequence into a CUDA graph that every later
 // iteration replays with one launch.
 // ---------------------------------------------------------------------------
 struct mrf_batch_s {
     std::vector<mrf_recon_s*> R;
-    std::vector<cudaStream_t> st;
-    std::vector<cudaEvent_t> ev;
+    // per slice: graph term, X update, forward, next gradient (st); SVT (sv);
+    // matching epilogue and graph rebuild (sg); the new iterate (ev), and the
+    // ends of the three streams (eva, evv, evg)
+    std::vector<cudaStream_t> st, sv, sg;
+    std::vector<cudaEvent_t> ev, eva, evv, evg;
     cudaEvent_t fork = nullptr, fork2 = nullptr;
     cudaStream_t cs = nullptr;      // the batch's own stream (the one captured; joined to the caller's)
     cudaEvent_t entry = nullptr, exit = nullptr;
@@ -1666,8 +1661,10 @@ static void free_batch(mrf_batch_s* B) {
     if (!B) return;
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
-    for (cudaStream_t t : B->st) cudaStreamDestroy(t);
-    for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
+    for (auto* v : {&B->st, &B->sv, &B->sg})
+        for (cudaStream_t t : *v) cudaStreamDestroy(t);
+    for (auto* v : {&B->ev, &B->eva, &B->evv, &B->evg})
+        for (cudaEvent_t e : *v) cudaEventDestroy(e);
     if (B->fork) cudaEventDestroy(B->fork);
     if (B->fork2) cudaEventDestroy(B->fork2);
     if (B->entry) cudaEventDestroy(B->entry);
@@ -1683,22 +1680,50 @@ static mrf_status batch_iteration(mrf_batch_s* B, cudaStream_t s) {
     const int form = tc_form(R0->prm.match_precision);
     MRF_CUDA(cudaEventRecord(B->fork, s));
     for (int i = 0; i < S; ++i) {
-        MRF_CUDA(cudaStreamWaitEvent(B->st[i], B->fork, 0));
-        MRF_PROPAGATE(iteration_pre(B->R[i], 0, false, B->st[i]));
-        MRF_CUDA(cudaEventRecord(B->ev[i], B->st[i]));
-    }
-    for (int i = 0; i < S; ++i) MRF_CUDA(cudaStreamWaitEvent(s, B->ev[i], 0));
-    if (form) MRF_PROPAGATE(match_tc_batch(R0->mws, B->d_slices, S, B->total_blocks, R0->K, R0->m, form, s));
-    MRF_CUDA(cudaEventRecord(B->fork2, s));
-    for (int i = 0; i < S; ++i) {
         mrf_recon_s* R = B->R[i];
-        MRF_CUDA(cudaStreamWaitEvent(B->st[i], B->fork2, 0));
-        if (form) MRF_PROPAGATE(match_finish(R->mws, R->N, R->lut, R->idx, R->pd, R->t1t2, 1.0f, B->st[i]));
-        else MRF_PROPAGATE(match_maps(R, B->st[i]));      // FP32: one exhaustive launch per slice
-        MRF_PROPAGATE(build_graph(R, B->st[i]));
-        MRF_CUDA(cudaEventRecord(B->ev[i], B->st[i]));
+        cudaStream_t t = B->st[i], tv = B->sv[i], tg = B->sg[i];
+        const size_t NK = (size_t)R->N * R->K;
+        const float inv_a = (float)(1.0 / R->a);
+        MRF_CUDA(cudaStreamWaitEvent(t, B->fork, 0));
+        MRF_PROPAGATE(graph_pass(R, R->QL, nullptr, t));
+        const float c = R->prm.mu * R->prm.lam2 * R->prm.beta;
+        k_xupdate<<<(unsigned)((NK + 255) / 256), 256, 0, t>>>(
+            R->alpha, R->grad, R->QL, R->P, R->g, R->K, R->prm.mu, c, R->scal + 2,
+            (R->prm.flags & MRF_RECON_LITERAL_XUPDATE) ? 1 : 0, nullptr);
+        MRF_LAUNCHED_AS("k_xupdate", t);
+        MRF_CUDA(cudaEventRecord(B->ev[i], t));             // the new iterate
+        MRF_CUDA(cudaStreamWaitEvent(tv, B->ev[i], 0));
+        MRF_PROPAGATE(svt(R, R->alpha, R->P, nullptr, tv));
+        MRF_CUDA(cudaEventRecord(B->evv[i], tv));
+        if (!form) {
+            // FP32: one exhaustive launch per slice
+            MRF_CUDA(cudaStreamWaitEvent(tg, B->ev[i], 0));
+            MRF_PROPAGATE(match_maps(R, tg));
+            MRF_PROPAGATE(build_graph(R, tg));
+            MRF_CUDA(cudaEventRecord(B->evg[i], tg));
+        }
+        MRF_PROPAGATE(subspace_forward(R->plan, R->alpha, R->phi, R->K, inv_a, R->bs, R->r, R->mode, t));
+        MRF_PROPAGATE(subspace_adjoint(R->plan, R->r, R->phi, R->K, inv_a, R->grad, R->mode, t));
+        MRF_CUDA(cudaEventRecord(B->eva[i], t));
     }
-    for (int i = 0; i < S; ++i) MRF_CUDA(cudaStreamWaitEvent(s, B->ev[i], 0));
+    if (form) {
+        for (int i = 0; i < S; ++i) MRF_CUDA(cudaStreamWaitEvent(s, B->ev[i], 0));
+        MRF_PROPAGATE(match_tc_batch(R0->mws, B->d_slices, S, B->total_blocks, R0->K, R0->m, form, s));
+        MRF_CUDA(cudaEventRecord(B->fork2, s));
+        for (int i = 0; i < S; ++i) {
+            mrf_recon_s* R = B->R[i];
+            cudaStream_t tg = B->sg[i];
+            MRF_CUDA(cudaStreamWaitEvent(tg, B->fork2, 0));
+            MRF_PROPAGATE(match_finish(R->mws, R->N, R->lut, R->idx, R->pd, R->t1t2, 1.0f, tg));
+            MRF_PROPAGATE(build_graph(R, tg));
+            MRF_CUDA(cudaEventRecord(B->evg[i], tg));
+        }
+    }
+    for (int i = 0; i < S; ++i) {
+        MRF_CUDA(cudaStreamWaitEvent(s, B->eva[i], 0));
+        MRF_CUDA(cudaStreamWaitEvent(s, B->evv[i], 0));
+        MRF_CUDA(cudaStreamWaitEvent(s, B->evg[i], 0));
+    }
     return MRF_OK;
 }
 
@@ -1754,8 +1779,11 @@ extern "C" mrf_status mrf_batch_create(mrf_batch* out, const mrf_recon* recons, 
     for (int i = 0; i < count; ++i) {
         mrf_recon_s* R = recons[i];
         B->R.push_back(R);
+        // each slice's matching is seeded from its previous call's candidates,
+        // as in the loop of a single slice
         table.push_back({R->alpha, R->N, B->total_blocks, R->mws.best_idx, R->mws.best_ip,
-                         static_cast<const unsigned char*>(R->mws.tc_b), R->mws.wscore, R->dict_c});
+                         static_cast<const unsigned char*>(R->mws.tc_b), R->mws.wscore, R->dict_c,
+                         form == 8 ? nullptr : R->mws.cand});
         B->total_blocks += (R->N + 127) / 128;
     }
     mrf_status st = MRF_OK;
@@ -1772,14 +1800,19 @@ extern "C" mrf_status mrf_batch_create(mrf_batch* out, const mrf_recon* recons, 
         if (e != cudaSuccess) fail("slice table upload", e);
     }
     for (int i = 0; st == MRF_OK && i < count; ++i) {
-        cudaStream_t t;
-        cudaEvent_t ev;
-        e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
-        if (e != cudaSuccess) { fail("cudaStreamCreateWithFlags", e); break; }
-        B->st.push_back(t);
-        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e != cudaSuccess) { fail("cudaEventCreateWithFlags", e); break; }
-        B->ev.push_back(ev);
+        for (auto* v : {&B->st, &B->sv, &B->sg}) {
+            cudaStream_t t;
+            e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
+            if (e != cudaSuccess) { fail("cudaStreamCreateWithFlags", e); break; }
+            v->push_back(t);
+        }
+        for (auto* v : {&B->ev, &B->eva, &B->evv, &B->evg}) {
+            if (st != MRF_OK) break;
+            cudaEvent_t ev;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) { fail("cudaEventCreateWithFlags", e); break; }
+            v->push_back(ev);
+        }
     }
     if (st == MRF_OK && ((e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming)) != cudaSuccess ||
                          (e = cudaEventCreateWithFlags(&B->fork2, cudaEventDisableTiming)) != cudaSuccess ||
