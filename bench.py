@@ -248,6 +248,8 @@ def nrmse(truth, maps):
 MEASURED_TRAFFIC = {
     "k_match_tc": (8819200, "ncu --set full, mrf256_t100 workload, launch shape of the full workload "
                             "(profiles/k_match_tc_mrf256_t100.md)"),
+    "k_graph_blocks": (5970176, "ncu --set full of the Q(X)L launch, mrf256_t100 workload, launch shape of the "
+                                "full workload (profiles/graph_kernels_mrf256_t100.md)"),
 }
 
 
