@@ -241,6 +241,17 @@ mrf_status mrf_match_noalloc(const mrf_c64* x, int n, int len, const mrf_c64* di
 mrf_status mrf_patch_knn(const int* F, int np, int fd, int ld, int knn, int* nbr, unsigned* d2,
                          mrf_stream stream);
 
+/* mrf_patch_knn with a seed list: seed (dev int32 [np][knn], read-only, may
+ * be nbr itself) is a previous neighbour list, in the loop the graph of the
+ * previous iteration.  For fd <= 128, where the seeds of row i are knn
+ * distinct rows j != i, the largest distance from F_i to them bounds the
+ * search for row i: no candidate farther than that can be among its knn
+ * nearest, so fewer candidates pass the tensor-core epilogue.  Other seed
+ * lists give no bound.  The result is the same as mrf_patch_knn's for any
+ * seed values; errors as in mrf_patch_knn, plus MRF_EINVAL for a NULL seed. */
+mrf_status mrf_patch_knn_seeded(const int* F, int np, int fd, int ld, int knn, const int* seed, int* nbr,
+                                unsigned* d2, mrf_stream stream);
+
 /* sigma^2 of the patch-graph weights w_ij = exp(-d2_ij / sigma^2) of Eq. 7,
  * a constant the paper does not set: the median of the non-zero entries of
  * d2 (the mean of the two middle ones for an even count), divided by 4096^2

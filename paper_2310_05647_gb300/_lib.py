@@ -46,6 +46,7 @@ SIGNATURES = {
     "mrf_nufft_gather_tuning": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
     "mrf_nufft_tuning": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
     "mrf_patch_knn": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),
+    "mrf_patch_knn_seeded": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     "mrf_graph_sigma2": (i32, [vp, i32, vp, vp]),
     "mrf_batch_create": (i32, [C.POINTER(vp), C.POINTER(vp), i32, vp]),
     "mrf_batch_iter": (i32, [vp, i32, vp]),

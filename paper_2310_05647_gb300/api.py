@@ -217,15 +217,24 @@ def match_seeded(x, D, lut, cand, atom_norm2=None, precision=MATCH_BF16X3):
     return idx, pd, t1t2
 
 
-def patch_knn(F, knn, fd=None):
+def patch_knn(F, knn, fd=None, seed=None):
     """(nbr [np, knn] int32, d2 [np, knn] int32 holding uint32 bits) of the
-    integer patch vectors F [np, ld] (entries past fd zero, ld % 4 == 0)."""
+    integer patch vectors F [np, ld] (entries past fd zero, ld % 4 == 0).
+    seed (int32 [np, knn], optional): a previous neighbour list that bounds
+    the search; the result does not depend on it."""
     _check(F, "F", torch.int32)
     npatch, ld = F.shape
     fd = ld if fd is None else int(fd)
     nbr = torch.empty((npatch, knn), dtype=torch.int32, device=F.device)
     d2 = torch.empty((npatch, knn), dtype=torch.int32, device=F.device)
-    _lib.call("mrf_patch_knn", _ptr(F), npatch, fd, ld, int(knn), _ptr(nbr), _ptr(d2), _stream())
+    if seed is None:
+        _lib.call("mrf_patch_knn", _ptr(F), npatch, fd, ld, int(knn), _ptr(nbr), _ptr(d2), _stream())
+    else:
+        _check(seed, "seed", torch.int32)
+        if tuple(seed.shape) != (npatch, knn):
+            raise ValueError(f"seed must be [{npatch}, {knn}] (got {tuple(seed.shape)})")
+        _lib.call("mrf_patch_knn_seeded", _ptr(F), npatch, fd, ld, int(knn), _ptr(seed), _ptr(nbr), _ptr(d2),
+                  _stream())
     return nbr, d2
 
 

@@ -38,7 +38,7 @@ constexpr int kKnConsumers = 8;
 constexpr int kKnThreads = 32 * kKnConsumers;
 constexpr int kKnCentre = 2048;
 constexpr int kKnMaxTcFd = 128;
-constexpr int kKnMaxParts = 8;
+constexpr int kKnMaxParts = 16;
 
 __device__ __forceinline__ bool less_dj(unsigned d, int j, unsigned d2, int j2) {
     return d < d2 || (d == d2 && j < j2);
@@ -217,9 +217,11 @@ __global__ void k_knn_merge(const int* __restrict__ pnbr, const unsigned* __rest
 
 // Candidate operand: tile t holds candidates 64 t .. 64 t + 63; B row 2 c is
 // h of candidate c, row 2 c + 1 its l (zero past fd and past np), in the
-// core-matrix layout; nrm[j] = |c_j|^2.  One warp per candidate.
+// core-matrix layout; nrm[j] = |c_j|^2; with seed, bound[j] (below).  One
+// warp per candidate.
 __global__ void k_knn_prepare(const int* __restrict__ F, int np, int fd, int ld, int LP, int ntiles,
-                              __half* __restrict__ Bg, int* __restrict__ nrm, int* __restrict__ err) {
+                              __half* __restrict__ Bg, int* __restrict__ nrm, int* __restrict__ err,
+                              const int* __restrict__ seed, int knn, unsigned* __restrict__ bound) {
     const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= ntiles * kKnTile) return;
     const int tile = j / kKnTile, c = j - tile * kKnTile;
@@ -227,11 +229,17 @@ __global__ void k_knn_prepare(const int* __restrict__ F, int np, int fd, int ld,
     __half* bt = Bg + (size_t)tile * 2 * kKnTile * LP;
     int s = 0;
     bool bad = false;
-    for (int k = lane; k < LP; k += 32) {
+    int fv[kKnMaxTcFd / 32];            // the row's entries k = lane + 32 i (LP <= 128)
+#pragma unroll
+    for (int i = 0; i < kKnMaxTcFd / 32; ++i) {
+        const int k = lane + 32 * i;
+        fv[i] = kKnCentre;
+        if (k >= LP) continue;
         int v = 0;
         if (j < np && k < fd) {
             int f = F[(size_t)j * ld + k];
             if (f < 0 || f > 2 * kKnCentre) { bad = true; f = kKnCentre; }
+            fv[i] = f;
             v = f - kKnCentre;
         }
         const int h = (v + 16) >> 5;        // floor((v + 16) / 32)
@@ -244,6 +252,47 @@ __global__ void k_knn_prepare(const int* __restrict__ F, int np, int fd, int ld,
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(err, 1);
     if (lane == 0 && j < np) nrm[j] = s;
+    if (!seed || j >= np) return;
+    // bound[j]: an upper bound of row j's knn-th smallest distance from a
+    // seed list (the previous graph): the largest exact distance from F_j to
+    // the seed rows when these are knn distinct rows other than j (any knn
+    // such rows are candidates, so the knn nearest lie within it), else
+    // UINT_MAX (no bound).  Lane t < knn holds seed t; the seeds' rows are
+    // read four at a time, their loads in flight together.  |F_jk - F_ik|
+    // <= 4096 and fd <= 128 keep the sums exact in 32 bits.
+    const int sj = lane < knn ? seed[(size_t)j * knn + lane] : -1;
+    bool ok = lane >= knn || (sj >= 0 && sj < np && sj != j);
+    for (int t = 0; t < knn; ++t) {
+        const int o = __shfl_sync(0xffffffffu, sj, t);
+        if (lane < knn && t != lane && o == sj) ok = false;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    unsigned bmax = 0u;
+    if (ok) {
+        for (int t0 = 0; t0 < knn; t0 += 4) {
+            unsigned dd[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u;
+                const int r = __shfl_sync(0xffffffffu, sj, t & 31);
+                unsigned d = 0u;
+                if (t < knn) {
+#pragma unroll
+                    for (int i = 0; i < kKnMaxTcFd / 32; ++i) {
+                        const int k = lane + 32 * i;
+                        if (k < fd) {
+                            const int df = fv[i] - F[(size_t)r * ld + k];
+                            d += (unsigned)(df * df);
+                        }
+                    }
+                }
+                dd[u] = d;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) bmax = max(bmax, __reduce_add_sync(0xffffffffu, dd[u]));
+        }
+    }
+    if (lane == 0) bound[j] = ok ? bmax : 0xffffffffu;
 }
 
 template <int KN>
@@ -251,7 +300,8 @@ __global__ void __launch_bounds__(kKnThreads + 32) k_knn_tc(const int* __restric
                                                             int LP, const __half* __restrict__ Bg,
                                                             const int* __restrict__ nrm, int per, int knn,
                                                             int* __restrict__ pnbr, unsigned* __restrict__ pd2,
-                                                            int* __restrict__ err) {
+                                                            int* __restrict__ err,
+                                                            const unsigned* __restrict__ bound) {
     const int KC = LP / 8;
     const int A_BYTES = kKnRows * LP * 2;
     const int B_BYTES = 2 * kKnTile * LP * 2;
@@ -380,6 +430,9 @@ __global__ void __launch_bounds__(kKnThreads + 32) k_knn_tc(const int* __restric
         const int lq = warp & 3, half = warp >> 2;
         const int qrow = q0 + lq * 32 + lane;
         const unsigned nq = qrow < np ? (unsigned)nrm[qrow] : 0u;
+        // candidates farther than the query's bound cannot be among its knn
+        // nearest (UINT_MAX: no bound)
+        const unsigned tq = bound && qrow < np ? bound[qrow] : 0xffffffffu;
         for (int tile = 0; tile < ntiles; ++tile) {
             const int buf = tile & 1;
             const int jb = cb + tile * kKnTile + half * (kKnTile / 2);
@@ -418,7 +471,7 @@ __global__ void __launch_bounds__(kKnThreads + 32) k_knn_tc(const int* __restric
                         const int cl = __float2int_rn(__uint_as_float(v[2 * (u + h) + 1]));
                         const unsigned nb = __shfl_sync(0xffffffffu, nbl, q);
                         d[h] = nq + nb - 2u * (unsigned)(32 * ch + cl);
-                        if (j >= ce || j == qrow) d[h] = 0xffffffffu;
+                        if (j >= ce || j == qrow || d[h] > tq) d[h] = 0xffffffffu;
                     }
                     if (__any_sync(0xffffffffu, d[0] < bd[KN - 1] || d[1] < bd[KN - 1])) {
 #pragma unroll
@@ -495,8 +548,8 @@ static int tc_kn(int knn) { return knn <= 8 ? 8 : knn <= 10 ? 10 : knn <= 16 ? 1
 KnnWorkspace::~KnnWorkspace() { release(); }
 
 void KnnWorkspace::release() {
-    cudaFree(bop); cudaFree(nrm); cudaFree(pnbr); cudaFree(pd2); cudaFree(err);
-    bop = nullptr; nrm = nullptr; pnbr = nullptr; pd2 = nullptr; err = nullptr;
+    cudaFree(bop); cudaFree(nrm); cudaFree(bound); cudaFree(pnbr); cudaFree(pd2); cudaFree(err);
+    bop = nullptr; nrm = nullptr; bound = nullptr; pnbr = nullptr; pd2 = nullptr; err = nullptr;
     bop_bytes = 0; part_entries = 0; np_cap = 0;
 }
 
@@ -523,8 +576,10 @@ mrf_status KnnWorkspace::reserve(int np, int fd, int knn) {
         }
         if (np_cap < np) {
             cudaFree(nrm);
-            nrm = nullptr; np_cap = 0;
+            cudaFree(bound);
+            nrm = nullptr; bound = nullptr; np_cap = 0;
             MRF_CUDA(cudaMalloc(&nrm, sizeof(int) * (size_t)np));
+            MRF_CUDA(cudaMalloc(&bound, sizeof(unsigned) * (size_t)np));
             np_cap = np;
         }
     }
@@ -532,7 +587,7 @@ mrf_status KnnWorkspace::reserve(int np, int fd, int knn) {
 }
 
 mrf_status knn_run(KnnWorkspace& ws, const int* F, int np, int fd, int ld, int knn, int* nbr, unsigned* d2,
-                   cudaStream_t s) {
+                   cudaStream_t s, const int* seed) {
     MRF_REQUIRE(F && nbr && d2, "patch kNN: NULL pointer");
     MRF_REQUIRE(knn >= 1 && knn <= 32, "patch kNN: knn = %d outside [1, 32]", knn);
     MRF_REQUIRE(np > knn, "patch kNN: needs more than knn = %d vectors (got %d)", knn, np);
@@ -545,7 +600,8 @@ mrf_status knn_run(KnnWorkspace& ws, const int* F, int np, int fd, int ld, int k
         const int ntiles = (np + kKnTile - 1) / kKnTile;
         const size_t thr = (size_t)ntiles * kKnTile * 32;
         k_knn_prepare<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(F, np, fd, ld, LP, ntiles,
-                                                                     static_cast<__half*>(ws.bop), ws.nrm, ws.err);
+                                                                     static_cast<__half*>(ws.bop), ws.nrm, ws.err,
+                                                                     seed, knn, ws.bound);
         MRF_LAUNCHED_AS("k_knn_prepare", s);
         // about two blocks per SM: 128 queries x one candidate partition each
         const int qb = (np + kKnRows - 1) / kKnRows;
@@ -562,7 +618,8 @@ mrf_status knn_run(KnnWorkspace& ws, const int* F, int np, int fd, int ld, int k
         MRF_CUDA(cudaFuncSetAttribute(k_knn_tc<KNV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
         k_knn_tc<KNV><<<grid, kKnThreads + 32, sm, s>>>(F, np, fd, ld, LP,                                  \
                                                         static_cast<const __half*>(ws.bop), ws.nrm, per,    \
-                                                        knn, ws.pnbr, ws.pd2, ws.err);                      \
+                                                        knn, ws.pnbr, ws.pd2, ws.err,                       \
+                                                        seed ? ws.bound : nullptr);                         \
     } while (0)
         if (kn == 8) MRF_KNN_LAUNCH(8);
         else if (kn == 10) MRF_KNN_LAUNCH(10);
@@ -600,11 +657,11 @@ mrf_status knn_run(KnnWorkspace& ws, const int* F, int np, int fd, int ld, int k
 
 using namespace mrf;
 
-extern "C" mrf_status mrf_patch_knn(const int* F, int np, int fd, int ld, int knn, int* nbr, unsigned* d2,
-                                    mrf_stream stream) {
+static mrf_status patch_knn(const int* F, int np, int fd, int ld, int knn, const int* seed, int* nbr, unsigned* d2,
+                            mrf_stream stream) {
     cudaStream_t s = as_stream(stream);
     KnnWorkspace ws;
-    MRF_PROPAGATE(knn_run(ws, F, np, fd, ld, knn, nbr, d2, s));
+    MRF_PROPAGATE(knn_run(ws, F, np, fd, ld, knn, nbr, d2, s, seed));
     int h = 0;
     MRF_CUDA(cudaMemcpyAsync(&h, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     MRF_CUDA(cudaStreamSynchronize(s));
@@ -614,4 +671,15 @@ extern "C" mrf_status mrf_patch_knn(const int* F, int np, int fd, int ld, int kn
         return MRF_ETIMEOUT;
     }
     return MRF_OK;
+}
+
+extern "C" mrf_status mrf_patch_knn(const int* F, int np, int fd, int ld, int knn, int* nbr, unsigned* d2,
+                                    mrf_stream stream) {
+    return patch_knn(F, np, fd, ld, knn, nullptr, nbr, d2, stream);
+}
+
+extern "C" mrf_status mrf_patch_knn_seeded(const int* F, int np, int fd, int ld, int knn, const int* seed, int* nbr,
+                                           unsigned* d2, mrf_stream stream) {
+    MRF_REQUIRE(seed != nullptr, "mrf_patch_knn_seeded: NULL seed");
+    return patch_knn(F, np, fd, ld, knn, seed, nbr, d2, stream);
 }

@@ -839,6 +839,7 @@ struct mrf_recon_s {
     int *rcnt = nullptr, *roff = nullptr, *rpos = nullptr, *rsrc = nullptr, *rsrc_tmp = nullptr;
     // the graph term's cut lists: extra-chunk offsets [np + 1], patch of each
     // extra chunk and the chunks' partial sums [gb_max_extra][p x p x K]
+    bool graph_built = false;   // nbr holds a graph (the previous one seeds the next kNN search)
     int *xoff = nullptr, *xpatch = nullptr, *xcnt = nullptr;     // xcnt: [np] blocks done per cut patch
     float2* xpart = nullptr;
     float* rw_tmp = nullptr;
@@ -955,7 +956,11 @@ static mrf_status build_graph(mrf_recon_s* R, cudaStream_t s) {
                                                                              (double)R->t2max,
                                                                              (FD + 3) / 4 * 4, R->F);
     MRF_LAUNCHED_AS("k_features", s);
-    MRF_PROPAGATE(knn_run(R->knn, R->F, np, FD, (FD + 3) / 4 * 4, knn, R->nbr, R->d2, s));
+    // from the second build on, the previous graph seeds the search (the
+    // result does not depend on it)
+    MRF_PROPAGATE(knn_run(R->knn, R->F, np, FD, (FD + 3) / 4 * 4, knn, R->nbr, R->d2, s,
+                          R->graph_built ? R->nbr : nullptr));
+    R->graph_built = true;
     const int ne = np * knn;
     k_median_nonzero<<<1, kMedianThreads, 0, s>>>(R->d2, ne, R->scal + 0);
     MRF_LAUNCHED_AS("k_median_nonzero", s);

@@ -65,7 +65,7 @@ def test_host_validation_without_gpu(lib):
     assert lib.mrf_match(dummy, 0, 10, dummy, None, dummy, 5, 0, None, None, None, None) == 0   # empty: no-op
 
 
-def test_host_validation_of_seeded_matching_sigma2_and_svt_counters(lib):
+def test_host_validation_of_seeded_matching_knn_sigma2_and_svt_counters(lib):
     dummy = C.c_void_p(16)
     d = [C.c_double() for _ in range(3)]
     # seeded matching: only the BF16 forms, and a candidate buffer unless n == 0
@@ -79,6 +79,9 @@ def test_host_validation_of_seeded_matching_sigma2_and_svt_counters(lib):
     assert lib.mrf_graph_sigma2(dummy, -1, dummy, None) == 1
     assert lib.mrf_graph_sigma2(None, 5, dummy, None) == 1
     assert lib.mrf_graph_sigma2(dummy, 5, None, None) == 1
+    # seeded kNN: the seed list is required
+    assert lib.mrf_patch_knn_seeded(dummy, 20, 8, 8, 4, None, dummy, dummy, None) == 1
+    assert "seed" in _err(lib)
     # SVT work counters of no reconstruction
     assert lib.mrf_recon_svt_stats(None, *[C.byref(v) for v in d], None) == 1
     assert lib.mrf_recon_svt_stats(dummy, None, C.byref(d[1]), C.byref(d[2]), None) == 1

@@ -142,3 +142,38 @@ def test_graph_sigma2_of_workload_distances():
     F = _map_features(256, 8, 4, seed=3)
     nbr, d2 = mrf().patch_knn(_padded(F)[0], 10, fd=F.shape[1])
     _sigma2_case(np_(d2).view(np.uint32).ravel())
+
+
+def _seeds(kind, F, knn, rng):
+    n = F.shape[0]
+    if kind == "exact":
+        return ograph.knn(F.astype(np.int64), knn)[0]
+    if kind == "previous_maps":                     # the loop's case: the graph of other maps
+        return ograph.knn(_map_features(128, 8, 4, seed=11).astype(np.int64), knn)[0]
+    rows = np.stack([rng.choice(np.delete(np.arange(n), i), knn, replace=False) for i in range(n)])
+    if kind == "invalid":                           # lists that give no bound, beside valid ones
+        rows[0, 3] = 0                              # the row itself
+        rows[1, 5] = rows[1, 2]                     # a repeated row
+        rows[2, 0] = -1
+        rows[3, 9] = n
+        rows[4:40] = rng.integers(0, n, (36, knn))  # arbitrary values
+    return rows
+
+
+@pytest.mark.parametrize("kind", ["exact", "previous_maps", "random", "invalid"])
+def test_seeded_knn_matches_oracle(kind):
+    """A seed list (in the loop: the previous iteration's graph) only bounds
+    each row's search by the largest distance to its knn distinct seeds; the
+    neighbours and distances stay the oracle's whatever the seeds, including
+    lists that give no bound (the row itself, a repeated row, out-of-range
+    or arbitrary values).  961 patch vectors of piecewise-constant maps
+    (many exact ties), k = 10."""
+    F = _map_features(128, 8, 4, seed=3)
+    knn = 10
+    seed = _seeds(kind, F, knn, np.random.default_rng(7))
+    Fd, fd = _padded(F)
+    sd = torch.tensor(np.ascontiguousarray(seed, np.int32), device=dev())
+    nbr, d2 = mrf().patch_knn(Fd, knn, fd=fd, seed=sd)
+    onbr, od2 = ograph.knn(F.astype(np.int64), knn)
+    np.testing.assert_array_equal(np_(d2).view(np.uint32).astype(np.int64), od2)
+    np.testing.assert_array_equal(np_(nbr).astype(np.int64), onbr)
