@@ -437,7 +437,11 @@ __global__ void __launch_bounds__(kKnThreads + 32) k_knn_tc(const int* __restric
             const int buf = tile & 1;
             const int jb = cb + tile * kKnTile + half * (kKnTile / 2);
             const unsigned nbl = jb + lane < ce ? (unsigned)__ldg(nrm + jb + lane) : 0u;
-            if (!wait_parity(smem_u32(&s_afull[buf]), (tile >> 1) & 1)) { s_fail = 1; break; }
+            // (the warp leaves together: its votes and aligned TMEM loads name every lane)
+            if (!__all_sync(0xffffffffu, wait_parity(smem_u32(&s_afull[buf]), (tile >> 1) & 1))) {
+                s_fail = 1;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t taddr = tmem + (uint32_t)(buf * NCOL) + ((uint32_t)(lq * 32) << 16) +
                                    (uint32_t)(half * (NCOL / 2));
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(kKnThreads + 32) k_knn_tc(const int* __restric
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&s_aempty[buf]));
-            if (s_fail) break;
+            if (__any_sync(0xffffffffu, s_fail)) break;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");

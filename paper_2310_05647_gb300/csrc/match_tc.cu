@@ -378,7 +378,11 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_match_tc(const float2* __restri
         }
         for (int tile = 0; tile < ntiles; ++tile) {
             const int buf = tile & 1;
-            if (!wait_parity(smem_u32(&s_afull[buf]), (tile >> 1) & 1)) { s_fail = 1; break; }
+            // (the warp leaves together: its votes and aligned TMEM loads name every lane)
+            if (!__all_sync(0xffffffffu, wait_parity(smem_u32(&s_afull[buf]), (tile >> 1) & 1))) {
+                s_fail = 1;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t taddr = tmem + (uint32_t)(buf * NCOL) + ((uint32_t)(lq * 32) << 16) +
                                    (uint32_t)(half * (NCOL / 2));

@@ -274,7 +274,11 @@ __global__ void __launch_bounds__(kLThreads, 1)
         const int lq = warp & 3, half = warp >> 2;
         for (int tile = 0; tile < nt; ++tile) {
             const int buf = tile & 1;
-            if (!wait_parity(smem_u32(&s_afull[buf]), (uint32_t)((tile >> 1) & 1))) { s_fail = 1; break; }
+            // (the warp leaves together: its votes and aligned TMEM loads name every lane)
+            if (!__all_sync(0xffffffffu, wait_parity(smem_u32(&s_afull[buf]), (uint32_t)((tile >> 1) & 1)))) {
+                s_fail = 1;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t tbase = tmem + (uint32_t)(buf * kLCols) + ((uint32_t)(lq * 32) << 16) +
                                    (uint32_t)(half * (kLCols / 2));
