@@ -147,3 +147,26 @@ def test_integer_distances_are_exact_ties():
     nbr, d2 = graph.knn(F, 3)
     np.testing.assert_array_equal(nbr[0], [3, 1, 2])
     np.testing.assert_array_equal(d2[0], [4, 9, 9])
+
+
+def test_kth_distance_is_bounded_by_any_k_other_rows():
+    """Any k distinct rows other than i are candidates for row i, so the
+    k-th smallest distance of the exact kNN is at most the largest distance
+    from row i to them: the bound with which a previous graph seeds the
+    search.  Checked against the graph of other features (a stale graph),
+    random rows and the exact lists themselves (where it is attained),
+    and brute force on the same rows."""
+    rng = np.random.default_rng(4)
+    k = 6
+    F = rng.integers(0, 40, (300, 5))
+    F[100:160] = F[100]                               # a flat block: exact ties
+    nbr, d2 = graph.knn(F, k)
+    brute = np.sort(((F[:, None, :] - F[None, :, :]) ** 2).sum(-1) + np.diag(np.full(len(F), 10**9)), axis=1)
+    np.testing.assert_array_equal(d2, brute[:, :k])
+    stale, _ = graph.knn(rng.integers(0, 40, (300, 5)), k)
+    rand = np.stack([rng.choice(np.delete(np.arange(300), i), k, replace=False) for i in range(300)])
+    for seeds in (stale, rand, nbr):
+        assert all(len(set(r)) == k and i not in r for i, r in enumerate(seeds))
+        bound = ((F[:, None, :] - F[seeds]) ** 2).sum(-1).max(axis=1)
+        assert np.all(d2[:, k - 1] <= bound)
+    np.testing.assert_array_equal(((F[:, None, :] - F[nbr]) ** 2).sum(-1).max(axis=1), d2[:, k - 1])
