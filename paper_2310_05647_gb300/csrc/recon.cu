@@ -395,10 +395,11 @@ __global__ void k_edge_weights(const int* __restrict__ nbr, const unsigned* __re
 // (the knn forward entries, then the reverse list).  The patch's own block
 // takes the first chunk; each further chunk is an extra work item whose
 // partial sum its own block writes, and the last of the patch's blocks to
-// finish adds them to the first chunk's sum in chunk order.  The patches of a flat region tie at distance 0, and
-// ties go to the lower index, so they all name the region's lowest-index
-// patches: a few patches collect reverse lists of a thousand entries or more
-// against a mean of knn, which one block would otherwise read alone.
+// finish adds them to the first chunk's sum in chunk order.  The patches of
+// a flat region tie at distance 0, and ties go to the lower index, so they
+// all name the region's lowest-index patches: a few patches collect reverse
+// lists of a thousand entries or more against a mean list length of 2 knn,
+// which one block would otherwise read alone.
 constexpr int kGbSplit = 32;
 __host__ __device__ inline int gb_extra_chunks(int nq) { return nq > kGbSplit ? (nq - 1) / kGbSplit : 0; }
 // an upper bound of the extra chunks of a graph (sum of (nq - 1) / kGbSplit,
@@ -545,10 +546,11 @@ __global__ void k_lambda(const float* __restrict__ lmax, float lam1_0, int liter
 // w_ji Re <Q_j, Q_i>, which is Tr(Q L Q^H) too (W = (K + K^T) / 2 and Re <., .>
 // is symmetric, so the reverse half of W adds the same sum as the forward
 // half), at half the neighbour reads; v_j itself is then not (Q L)_j.
-// One block per patch j, each thread up to kGbElems of its p x p x K
-// coefficients (consecutive threads read consecutive coefficients of a
-// neighbour's patch rows).  The neighbour list (forward kNN entries, then
-// the reverse list) is staged in shared memory kGbChunk entries at a time as
+// One block per patch j (plus the cut lists' chunk blocks, below), each
+// thread up to kGbElems of its p x p x K coefficients (consecutive threads
+// read consecutive coefficients of a neighbour's patch rows).  The neighbour
+// list (forward kNN entries, then the reverse list) is staged in shared
+// memory kGbChunk entries at a time as
 // (offset of the neighbour patch's first coefficient, w / 2), so the inner
 // loop is one gather and two FMAs per coefficient and neighbour.  (Pairs of
 // coefficients per 16-byte load halve the loads but leave fewer in flight
